@@ -1,0 +1,195 @@
+"""Plain FP64 CPU oracle for Probabilistic Inclusion Depth (PID).
+
+TEST INFRASTRUCTURE ONLY. The tests, the smoke check and the CPU-baseline leg of
+the benchmark call this module; the library and its Python binding never do.
+It shares no code with the CUDA path: it is a direct transcription of the
+paper's definitions, slow and obviously correct, computed in float64 from the
+same float32 inputs the GPU receives.
+
+Every function cites the passage it follows:
+  Eq. 1            epsilon-subset operator (Sec. 3.1)
+  Eq. 2            inside region of a contour, F_i(x) < q_i (Sec. 3.1)
+  Eq. 3, Eq. 4     eID inclusion fractions and their minimum (Sec. 3.1)
+  Eq. 6            mass of a probabilistic mask (Sec. 3.2)
+  Eq. 9            probabilistic inclusion operator, ratio form (Sec. 3.2)
+  Eq. 10           PID (Sec. 3.2)
+  Eq. 12, 13, 14   uniform and non-uniform (cell-measure weighted) grids (Sec. 3.4)
+  Eq. 15, Eq. 16   mean contour and PID-mean (Sec. 4.1)
+  Sec. 3.5         probabilistic mask from a scalar field and an isovalue distribution
+  Sec. 5.1         ranking: higher rank = lower depth
+
+Readings where the paper is silent (each also listed in the design notes):
+  * Zero-mass reference mask: u subset_p v = 0 (Sec. 3.2), unlike eID's 1 (Eq. 1).
+  * The sums over j in Eq. 10 / Eq. 14 include j = i and are normalised by 1/N.
+  * Isovalue distribution q ~ Normal(mu, sigma): u(x) = P(F(x) < q) =
+    Phi((mu - F(x)) / sigma) (inside = sub-level set, Eq. 2); sigma = 0 gives the
+    strict indicator 1[F < mu]; `superlevel` swaps to P(F(x) > q).
+  * Ranking ties: depth descending, then member index ascending.
+
+Parity pins: every function here is pinned by the CPU tests (closed forms,
+brute-force set counts, invariants, textbook values); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erfc as _erfc
+
+__all__ = [
+    "cell_measure",
+    "mass",
+    "inclusion",
+    "inclusion_matrix",
+    "pid",
+    "mean_contour",
+    "pid_mean",
+    "iso_soft_mask",
+    "rank_by_depth",
+    "eps_subset",
+    "eid",
+]
+
+
+def _f64(a) -> np.ndarray:
+    return np.asarray(a, dtype=np.float64)
+
+
+def cell_measure(M: int, w=None) -> np.ndarray:
+    """Cell measure w_x of Eq. 13; a uniform grid (Eq. 12) is w_x = 1."""
+    if w is None:
+        return np.ones(M, dtype=np.float64)
+    w = _f64(w).reshape(-1)
+    if w.shape[0] != M:
+        raise ValueError("weights must have one entry per cell")
+    if not np.all(w > 0):
+        raise ValueError("cell measures must be positive (Sec. 3.4, w_x > 0)")
+    return w
+
+
+def mass(U, w=None) -> np.ndarray:
+    """m(u_i) = sum_x w_x u_i(x): Eq. 6 with the cell-wise constant measure of Eq. 13."""
+    U = np.atleast_2d(_f64(U))
+    w = cell_measure(U.shape[1], w)
+    return U @ w
+
+
+def inclusion(u, v, w=None) -> float:
+    """u subset_p v = sum_x w u v / sum_x w u (Eq. 9 with Eq. 13); 0 if m(u) = 0."""
+    u = _f64(u).reshape(-1)
+    v = _f64(v).reshape(-1)
+    w = cell_measure(u.shape[0], w)
+    m = float(np.dot(w, u))
+    if m == 0.0:
+        return 0.0
+    return float(np.dot(w * u, v) / m)
+
+
+def inclusion_matrix(U, w=None) -> np.ndarray:
+    """P[i, j] = u_i subset_p u_j for every ordered pair, in the penalty form of Eq. 14:
+
+        P[i, j] = 1 - sum_x w_x u_i(x) (1 - u_j(x)) / sum_x w_x u_i(x),
+
+    with P[i, :] = 0 when m(u_i) = 0 (zero-mass convention of Sec. 3.2).
+    """
+    U = np.atleast_2d(_f64(U))
+    w = cell_measure(U.shape[1], w)
+    m = U @ w                                   # Eq. 6
+    penalty = (U * w) @ (1.0 - U).T             # sum_x w u_i (1 - u_j)
+    P = np.zeros_like(penalty)
+    nz = m > 0
+    P[nz, :] = 1.0 - penalty[nz, :] / m[nz, None]
+    return P
+
+
+def pid(U, w=None):
+    """Full PID over all N^2 ordered pairs (Eq. 10, weighted sums of Eq. 14).
+
+    IN_in(i)  = (1/N) sum_j u_i subset_p u_j
+    IN_out(i) = (1/N) sum_j u_j subset_p u_i
+    PID(i)    = min(IN_in(i), IN_out(i))
+    Returns (in_in, in_out, depth) as float64 arrays of length N.
+    """
+    P = inclusion_matrix(U, w)
+    N = P.shape[0]
+    in_in = P.sum(axis=1) / N
+    in_out = P.sum(axis=0) / N
+    return in_in, in_out, np.minimum(in_in, in_out)
+
+
+def mean_contour(U) -> np.ndarray:
+    """u_bar(x) = (1/N) sum_i u_i(x) (Eq. 15)."""
+    U = np.atleast_2d(_f64(U))
+    return U.mean(axis=0)
+
+
+def pid_mean(U, w=None):
+    """PID-mean (Eq. 16): each member against the mean contour only.
+
+    IN_in^mean(i)  = u_i subset_p u_bar
+    IN_out^mean(i) = u_bar subset_p u_i
+    Returns (in_in, in_out, depth).
+    """
+    U = np.atleast_2d(_f64(U))
+    ubar = mean_contour(U)
+    N = U.shape[0]
+    in_in = np.array([inclusion(U[i], ubar, w) for i in range(N)])
+    in_out = np.array([inclusion(ubar, U[i], w) for i in range(N)])
+    return in_in, in_out, np.minimum(in_in, in_out)
+
+
+def iso_soft_mask(F, mu: float, sigma: float, superlevel: bool = False) -> np.ndarray:
+    """Probabilistic mask from a scalar field and a Normal isovalue distribution (Sec. 3.5).
+
+    The inside of a contour is the sub-level set F(x) < q (Eq. 2). With the isovalue
+    q ~ Normal(mu, sigma) the membership probability is
+        u(x) = P(F(x) < q) = Phi((mu - F(x)) / sigma) = erfc((F(x) - mu) / (sigma sqrt 2)) / 2.
+    sigma = 0 degenerates to the strict indicator 1[F(x) < mu]. `superlevel` takes the
+    super-level set F(x) > q instead: u(x) = Phi((F(x) - mu) / sigma), or 1[F(x) > mu].
+    """
+    F = _f64(F)
+    if sigma < 0:
+        raise ValueError("sigma must be >= 0")
+    if sigma == 0.0:
+        return (F > mu).astype(np.float64) if superlevel else (F < mu).astype(np.float64)
+    z = (F - mu) / (sigma * math.sqrt(2.0))
+    if superlevel:
+        z = -z
+    return 0.5 * _erfc(z)
+
+
+def rank_by_depth(depth) -> np.ndarray:
+    """Rank 0 = deepest member; higher rank = lower depth (Sec. 5.1).
+
+    Ties are broken by the lower member index (a stable sort on descending depth).
+    Returns rank[i] for every member i (int32).
+    """
+    depth = _f64(depth).reshape(-1)
+    order = sorted(range(depth.shape[0]), key=lambda i: (-depth[i], i))
+    rank = np.empty(depth.shape[0], dtype=np.int32)
+    for r, i in enumerate(order):
+        rank[i] = r
+    return rank
+
+
+# ---------------------------------------------------------------------------
+# Epsilon Inclusion Depth on binary masks (Sec. 3.1), by set counts.
+# Used by the tests as the binary specialisation of PID (Eq. 5).
+# ---------------------------------------------------------------------------
+
+def eps_subset(A: set, B: set) -> float:
+    """A subset_eps B = 1 - |A minus B| / |A|, and 1 if |A| = 0 (Eq. 1)."""
+    if len(A) == 0:
+        return 1.0
+    return 1.0 - len(A - B) / len(A)
+
+
+def eid(sets):
+    """eID over a list of cell-index sets (Eq. 3 and Eq. 4), counting measure.
+
+    Returns (in_in, in_out, depth); the sums over j include j = i (Eq. 3).
+    """
+    N = len(sets)
+    in_in = np.array([sum(eps_subset(sets[i], sets[j]) for j in range(N)) / N for i in range(N)])
+    in_out = np.array([sum(eps_subset(sets[j], sets[i]) for j in range(N)) / N for i in range(N)])
+    return in_in, in_out, np.minimum(in_in, in_out)
