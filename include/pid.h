@@ -1,0 +1,186 @@
+/*
+ * pid.h — C ABI of the Probabilistic Inclusion Depth (PID) library for GB300 (sm_103a).
+ *
+ * The library computes, on one GPU, the data depth of every member of an ensemble of
+ * N probabilistic (soft) masks u_i : {cells} -> [0,1] defined on M grid cells with
+ * positive cell measures w_x (Sec. 3.2, Sec. 3.4 of the paper):
+ *
+ *   mass                m_i        = sum_x w_x u_i(x)                          (Eq. 6, Eq. 13)
+ *   inclusion operator  u subset_p v = sum_x w u v / sum_x w u, 0 if m(u) = 0  (Eq. 9, Eq. 13)
+ *   full PID            IN_in(i)  = (1/N) sum_j u_i subset_p u_j
+ *                       IN_out(i) = (1/N) sum_j u_j subset_p u_i
+ *                       PID(i)    = min(IN_in(i), IN_out(i))                   (Eq. 10, Eq. 14)
+ *   PID-mean            u_bar = (1/N) sum_i u_i;  IN_in = u_i subset_p u_bar,
+ *                       IN_out = u_bar subset_p u_i, depth = min              (Eq. 15, Eq. 16)
+ *
+ * and the fuzzy isocontour map of Sec. 3.5 that turns a scalar field F_i and an
+ * isovalue distribution q ~ Normal(mu, sigma) into the soft mask
+ *   u_i(x) = P(F_i(x) < q) = Phi((mu - F_i(x)) / sigma)        (inside = sub-level set, Eq. 2)
+ * (sigma = 0 gives the indicator 1[F < mu]; `superlevel` selects P(F > q) instead).
+ *
+ * Conventions shared by every call
+ *   - All array arguments are DEVICE pointers owned by the caller (for example the data
+ *     pointers of torch CUDA tensors), except where a name ends in `_host`.
+ *   - Ensemble data are row-major [N][ld] float32: member i, cell x at data[i*ld + x];
+ *     ld >= M. Cell measures w are float32 [M], or NULL for unit measure (uniform grid,
+ *     Eq. 12). Cell measures must be > 0 (Sec. 3.4).
+ *   - Outputs are float64 [N] (depths and inclusion fractions), int32 [N] (ranks:
+ *     0 = deepest; ties go to the lower member index), float64 [N*N] (row-major inclusion
+ *     matrix P[i*N + j] = u_i subset_p u_j). Any output pointer may be NULL to skip it.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL = legacy
+ *     default stream). Outputs are valid once the stream has been synchronised.
+ *   - Errors are returned, never raised with abort or a device trap. Argument errors are
+ *     detected on the host before anything is enqueued. Errors found on the device (input
+ *     out of [0,1] when validation is on, a bounded device wait that ran out) set a
+ *     device-side error word of the handle; pid_sync() reports and clears it.
+ *   - A handle owns device workspace. Calls made with one handle must not run
+ *     concurrently on different streams; use one handle per concurrent stream.
+ */
+#ifndef PID_H_
+#define PID_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pid_status {
+  PID_OK = 0,
+  PID_ERR_INVALID_ARG = 1,  /* bad size, stride, pointer or option (host-side check) */
+  PID_ERR_DOMAIN = 2,       /* validation found u outside [0,1], a NaN, or w <= 0 */
+  PID_ERR_OOM = 3,          /* workspace would exceed the handle's HBM budget, or cudaMalloc failed */
+  PID_ERR_CUDA = 4,         /* a CUDA runtime call failed (see pid_last_error) */
+  PID_ERR_TIMEOUT = 5,      /* a bounded device wait ran out; the kernel returned early */
+  PID_ERR_BUSY = 6,         /* serving: queue full or server not accepting */
+  PID_ERR_CANCELLED = 7,    /* serving: request cancelled or server stopped */
+  PID_ERR_UNSUPPORTED = 8   /* size or option outside what this build implements */
+} pid_status;
+
+/* Which depth is computed. */
+typedef enum pid_mode {
+  PID_MODE_MEAN = 0,        /* PID-mean, Eq. 16: one streaming pass, O(NM) */
+  PID_MODE_FULL = 1,        /* full PID, Eq. 10: N x N Gram G = U diag(w) U^T on tensor cores */
+  PID_MODE_FULL_LINEAR = 2  /* full PID, exactly, in O(NM) (two streaming passes, FP32) */
+} pid_mode;
+
+/* Operand precision of the tensor-core Gram (PID_MODE_FULL). Accumulation is FP32, the
+ * final normalisation FP64. PID_FP32 is accepted for FULL and selects FULL_LINEAR. */
+typedef enum pid_precision {
+  PID_FP32 = 0,
+  PID_BF16 = 1,             /* u sqrt(w) rounded to bfloat16 */
+  PID_SPLIT_BF16 = 2,       /* hi + lo bfloat16 pair; products hi*hi + hi*lo + lo*hi */
+  PID_FP8 = 3               /* E4M3 with a per-member power-of-two scale */
+} pid_precision;
+
+typedef enum pid_iso_kind {
+  PID_ISO_NORMAL = 0        /* isovalue q ~ Normal(mu, sigma), Sec. 3.5 */
+} pid_iso_kind;
+
+/* Isovalue distribution for pid_soft_masks / pid_from_fields (Sec. 3.5). */
+typedef struct pid_iso {
+  int32_t kind;             /* pid_iso_kind */
+  int32_t superlevel;       /* 0: inside = {F < q} (Eq. 2); 1: inside = {F > q} */
+  double mu;                /* mean isovalue */
+  double sigma;             /* standard deviation, >= 0 (0 = hard threshold at mu) */
+} pid_iso;
+
+typedef struct pid_options {
+  int32_t mode;             /* pid_mode */
+  int32_t precision;        /* pid_precision (PID_MODE_FULL only) */
+  int32_t validate;         /* 1: check u in [0,1] / finite fields and w > 0 on the device */
+  int32_t reserved;         /* must be 0 */
+} pid_options;
+
+typedef struct pid_handle_s* pid_handle;
+
+/* Create a handle on CUDA device `device`. `hbm_budget_bytes` caps the workspace the
+ * handle may allocate (0 = no cap). Allocation happens lazily, on the first call that
+ * needs more workspace (never while the stream is being captured). */
+pid_status pid_create(pid_handle* out, int device, size_t hbm_budget_bytes);
+/* Release the handle and its workspace. NULL is accepted. */
+pid_status pid_destroy(pid_handle h);
+/* Synchronise `stream`, then report (and clear) the handle's device error word. */
+pid_status pid_sync(pid_handle h, void* stream);
+/* Static text for a status code. */
+const char* pid_status_string(pid_status s);
+/* Detail text of the handle's most recent error (thread-unsafe; valid until the next call). */
+const char* pid_last_error(pid_handle h);
+/* Workspace bytes currently held by the handle. */
+size_t pid_workspace_bytes(pid_handle h);
+
+/*
+ * pid_soft_masks — the isovalue map alone (Sec. 3.5): U_out[i*ld_out + x] = u_i(x) for
+ * x < M. F: [N][ld] float32 scalar fields; U_out: [N][ld_out] float32, ld_out >= M.
+ * Cells x in [M, ld_out) of U_out are not written.
+ */
+pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                          const pid_iso* iso, float* U_out, int64_t ld_out, void* stream);
+
+/*
+ * pid_mean — PID-mean (Eq. 15-16) of soft masks U [N][ld] with cell measures w [M] (or NULL).
+ * Every member is compared with the mean contour u_bar; one fused pass over U.
+ */
+pid_status pid_mean(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
+                    const float* w, double* depth, double* in_in, double* in_out,
+                    int32_t* rank, void* stream);
+
+/*
+ * pid_full — full PID over all N^2 ordered pairs (Eq. 10 with the weighted sums of Eq. 14).
+ * opt->mode = PID_MODE_FULL uses the tensor-core Gram in opt->precision and can return
+ * the inclusion matrix P (N*N, row-major, P[i*N+j] = u_i subset_p u_j) and err_est[0],
+ * the largest |IN_in(Gram) - IN_in(exact FP32)| over members, where the exact value comes
+ * from the identity IN_in(i) = u_i subset_p u_bar (Eq. 17). opt->mode =
+ * PID_MODE_FULL_LINEAR computes the same depths exactly in O(NM); P and err_est are then
+ * not written. opt may be NULL (FULL_LINEAR, no validation).
+ */
+pid_status pid_full(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
+                    const float* w, const pid_options* opt, double* depth, double* in_in,
+                    double* in_out, int32_t* rank, double* P, double* err_est, void* stream);
+
+/*
+ * pid_from_fields — the isovalue map fused in front of the depth computation: u_i is
+ * computed on the fly from the scalar fields F [N][ld] and `iso`, never stored. opt
+ * selects PID-mean, full PID (Gram) or full PID (linear) exactly as for pid_mean/pid_full.
+ */
+pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                           const float* w, const pid_iso* iso, const pid_options* opt,
+                           double* depth, double* in_in, double* in_out, int32_t* rank,
+                           void* stream);
+
+/*
+ * One ensemble of a batch. `data` are soft masks (is_field = 0) or scalar fields mapped
+ * through `iso` (is_field = 1). Outputs as in pid_full; `mass` receives m_i and
+ * `mean_depth` the PID-mean depth (both free by-products of every mode).
+ */
+typedef struct pid_ensemble {
+  const float* data;
+  int64_t N, M, ld;
+  const float* w;           /* [M] or NULL */
+  int32_t is_field;
+  int32_t reserved;
+  pid_iso iso;
+  pid_options opt;
+  double* depth;
+  double* in_in;
+  double* in_out;
+  int32_t* rank;
+  double* mass;
+  double* mean_depth;
+  double* P;                /* PID_MODE_FULL only */
+  double* err_est;          /* PID_MODE_FULL only */
+} pid_ensemble;
+
+/*
+ * pid_batch — many ensembles of uneven N and M in one persistent launch per kernel class,
+ * recorded as one CUDA graph (fork/join over the classes) and replayed while the batch
+ * layout is unchanged. Results are bitwise identical to the single-ensemble calls.
+ */
+pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PID_H_ */

@@ -1,0 +1,265 @@
+"""Thin ctypes binding of libpid.so (argument marshalling only).
+
+The functions named pid_* mirror the C ABI of include/pid.h one to one and take raw
+device pointers (ints) and sizes. `Handle` adds the same calls on torch CUDA tensors:
+it reads data pointers and strides, allocates the output tensors on the device and
+passes the current torch stream. Every computation runs in the library's CUDA kernels;
+if libpid.so is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t, c_void_p
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libpid.so")
+
+PID_OK, PID_ERR_INVALID_ARG, PID_ERR_DOMAIN, PID_ERR_OOM, PID_ERR_CUDA = 0, 1, 2, 3, 4
+PID_ERR_TIMEOUT, PID_ERR_BUSY, PID_ERR_CANCELLED, PID_ERR_UNSUPPORTED = 5, 6, 7, 8
+PID_MODE_MEAN, PID_MODE_FULL, PID_MODE_FULL_LINEAR = 0, 1, 2
+PID_FP32, PID_BF16, PID_SPLIT_BF16, PID_FP8 = 0, 1, 2, 3
+PID_ISO_NORMAL = 0
+
+MODES = {"mean": PID_MODE_MEAN, "full": PID_MODE_FULL, "gram": PID_MODE_FULL,
+         "linear": PID_MODE_FULL_LINEAR, "full_linear": PID_MODE_FULL_LINEAR}
+PRECISIONS = {"fp32": PID_FP32, "bf16": PID_BF16, "split_bf16": PID_SPLIT_BF16, "fp8": PID_FP8}
+
+EXPORTS = [
+    "pid_create", "pid_destroy", "pid_sync", "pid_status_string", "pid_last_error",
+    "pid_workspace_bytes", "pid_soft_masks", "pid_mean", "pid_full", "pid_from_fields",
+    "pid_batch",
+]
+
+
+class PidError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[pid status {status}] {message}")
+        self.status = status
+
+
+class pid_iso(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("superlevel", c_int32), ("mu", c_double), ("sigma", c_double)]
+
+
+class pid_options(ctypes.Structure):
+    _fields_ = [("mode", c_int32), ("precision", c_int32), ("validate", c_int32),
+                ("reserved", c_int32)]
+
+
+class pid_ensemble(ctypes.Structure):
+    _fields_ = [("data", c_void_p), ("N", c_int64), ("M", c_int64), ("ld", c_int64),
+                ("w", c_void_p), ("is_field", c_int32), ("reserved", c_int32),
+                ("iso", pid_iso), ("opt", pid_options),
+                ("depth", c_void_p), ("in_in", c_void_p), ("in_out", c_void_p),
+                ("rank", c_void_p), ("mass", c_void_p), ("mean_depth", c_void_p),
+                ("P", c_void_p), ("err_est", c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpid.so (raises if it is missing: there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpid.so not found at {path}; build it with "
+                           "`python -m paper_2512_15187_gb300.build`")
+    lib = ctypes.CDLL(path)
+    P = c_void_p
+    sig = {
+        "pid_create": ([POINTER(c_void_p), c_int, c_size_t], c_int),
+        "pid_destroy": ([P], c_int),
+        "pid_sync": ([P, P], c_int),
+        "pid_status_string": ([c_int], c_char_p),
+        "pid_last_error": ([P], c_char_p),
+        "pid_workspace_bytes": ([P], c_size_t),
+        "pid_soft_masks": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, c_int64, P], c_int),
+        "pid_mean": ([P, P, c_int64, c_int64, c_int64, P, P, P, P, P, P], c_int),
+        "pid_full": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_options), P, P, P, P, P, P, P],
+                     c_int),
+        "pid_from_fields": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_iso),
+                             POINTER(pid_options), P, P, P, P, P], c_int),
+        "pid_batch": ([P, POINTER(pid_ensemble), c_int32, P], c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(h, status: int):
+    if status != PID_OK:
+        lib = load()
+        msg = lib.pid_last_error(h).decode() if h else lib.pid_status_string(status).decode()
+        raise PidError(status, msg or lib.pid_status_string(status).decode())
+
+
+# --- raw C-ABI mirrors (device pointers as ints) -------------------------------------------
+
+def pid_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = c_void_p()
+    st = load().pid_create(ctypes.byref(h), device, hbm_budget_bytes)
+    if st != PID_OK:
+        raise PidError(st, load().pid_status_string(st).decode())
+    return h
+
+
+def pid_destroy(h):
+    _check(None, load().pid_destroy(h))
+
+
+def pid_sync(h, stream=None):
+    _check(h, load().pid_sync(h, stream))
+
+
+def pid_soft_masks(h, F, N, M, ld, iso: pid_iso, U_out, ld_out, stream=None):
+    _check(h, load().pid_soft_masks(h, F, N, M, ld, ctypes.byref(iso), U_out, ld_out, stream))
+
+
+def pid_mean(h, U, N, M, ld, w, depth, in_in, in_out, rank, stream=None):
+    _check(h, load().pid_mean(h, U, N, M, ld, w, depth, in_in, in_out, rank, stream))
+
+
+def pid_full(h, U, N, M, ld, w, opt: pid_options, depth, in_in, in_out, rank, P, err_est,
+             stream=None):
+    _check(h, load().pid_full(h, U, N, M, ld, w, ctypes.byref(opt) if opt else None, depth, in_in,
+                              in_out, rank, P, err_est, stream))
+
+
+def pid_from_fields(h, F, N, M, ld, w, iso: pid_iso, opt: pid_options, depth, in_in, in_out, rank,
+                    stream=None):
+    _check(h, load().pid_from_fields(h, F, N, M, ld, w, ctypes.byref(iso),
+                                     ctypes.byref(opt) if opt else None, depth, in_in, in_out,
+                                     rank, stream))
+
+
+def pid_batch(h, ensembles, stream=None):
+    arr = (pid_ensemble * len(ensembles))(*ensembles)
+    _check(h, load().pid_batch(h, arr, len(ensembles), stream))
+
+
+# --- torch tensor convenience -----------------------------------------------------------------
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _check_matrix(x, name):
+    if x.dim() != 2 or x.dtype.__repr__() != "torch.float32" or not x.is_cuda or x.stride(1) != 1:
+        raise ValueError(f"{name} must be a 2-D float32 CUDA tensor with unit cell stride")
+    return x.shape[0], x.shape[1], x.stride(0)
+
+
+class Handle:
+    """A libpid handle bound to one CUDA device; methods take and return torch tensors."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.h = pid_create(device, hbm_budget_bytes)
+
+    def close(self):
+        if self.h:
+            pid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sync(self, stream=None):
+        pid_sync(self.h, _stream(stream))
+
+    def workspace_bytes(self) -> int:
+        return int(load().pid_workspace_bytes(self.h))
+
+    def _outputs(self, N, want_P=False, extras=False):
+        import torch
+        dev = torch.device("cuda", self.device)
+        o = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("depth", "in_in", "in_out")}
+        o["rank"] = torch.empty(N, dtype=torch.int32, device=dev)
+        if want_P:
+            o["P"] = torch.empty((N, N), dtype=torch.float64, device=dev)
+            o["err_est"] = torch.empty(1, dtype=torch.float64, device=dev)
+        if extras:
+            o["mass"] = torch.empty(N, dtype=torch.float64, device=dev)
+            o["mean_depth"] = torch.empty(N, dtype=torch.float64, device=dev)
+        return o
+
+    def soft_masks(self, F, mu, sigma, superlevel=False, out=None, stream=None):
+        import torch
+        N, M, ld = _check_matrix(F, "F")
+        if out is None:
+            out = torch.empty((N, M), dtype=torch.float32, device=F.device)
+        iso = pid_iso(PID_ISO_NORMAL, int(superlevel), float(mu), float(sigma))
+        pid_soft_masks(self.h, F.data_ptr(), N, M, ld, iso, out.data_ptr(), out.stride(0),
+                       _stream(stream))
+        return out
+
+    def mean(self, U, w=None, stream=None):
+        N, M, ld = _check_matrix(U, "U")
+        o = self._outputs(N)
+        pid_mean(self.h, U.data_ptr(), N, M, ld, _ptr(w), o["depth"].data_ptr(),
+                 o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
+                 _stream(stream))
+        return o
+
+    def full(self, U, w=None, mode="linear", precision="fp32", want_P=False, validate=False,
+             stream=None):
+        N, M, ld = _check_matrix(U, "U")
+        gram = MODES[mode] == PID_MODE_FULL and PRECISIONS[precision] != PID_FP32
+        o = self._outputs(N, want_P=want_P and gram)
+        opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
+        pid_full(self.h, U.data_ptr(), N, M, ld, _ptr(w), opt, o["depth"].data_ptr(),
+                 o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
+                 _ptr(o.get("P")), _ptr(o.get("err_est")), _stream(stream))
+        return o
+
+    def from_fields(self, F, mu, sigma, superlevel=False, w=None, mode="mean", precision="fp32",
+                    validate=False, stream=None):
+        N, M, ld = _check_matrix(F, "F")
+        o = self._outputs(N)
+        iso = pid_iso(PID_ISO_NORMAL, int(superlevel), float(mu), float(sigma))
+        opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
+        pid_from_fields(self.h, F.data_ptr(), N, M, ld, _ptr(w), iso, opt, o["depth"].data_ptr(),
+                        o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
+                        _stream(stream))
+        return o
+
+    def batch(self, items, stream=None):
+        """items: list of dicts with keys data (tensor), w, iso=(mu, sigma, superlevel) or None,
+        mode, precision, want_P. Returns a list of output dicts (with mass and mean_depth)."""
+        ens, outs = [], []
+        for it in items:
+            x = it["data"]
+            N, M, ld = _check_matrix(x, "data")
+            mode = MODES[it.get("mode", "mean")]
+            prec = PRECISIONS[it.get("precision", "fp32")]
+            gram = mode == PID_MODE_FULL and prec != PID_FP32
+            o = self._outputs(N, want_P=it.get("want_P", False) and gram, extras=True)
+            iso = it.get("iso")
+            e = pid_ensemble()
+            e.data, e.N, e.M, e.ld = x.data_ptr(), N, M, ld
+            e.w = _ptr(it.get("w"))
+            e.is_field = int(iso is not None)
+            if iso is not None:
+                e.iso = pid_iso(PID_ISO_NORMAL, int(iso[2]) if len(iso) > 2 else 0, float(iso[0]),
+                                float(iso[1]))
+            e.opt = pid_options(mode, prec, int(it.get("validate", False)), 0)
+            for k in ("depth", "in_in", "in_out", "rank", "mass", "mean_depth", "P", "err_est"):
+                setattr(e, k, _ptr(o.get(k)))
+            ens.append(e)
+            outs.append(o)
+        pid_batch(self.h, ens, _stream(stream))
+        return outs

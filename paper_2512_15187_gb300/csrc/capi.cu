@@ -1,0 +1,524 @@
+// C ABI of the PID library: handle, argument checks, planning and launch sequences.
+// The computation itself lives in stream.cu (PID-mean, exact full PID, isovalue map,
+// finalisation) and gram.cu (tensor-core Gram for full PID).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pid.h"
+#include "capi_internal.h"
+#include "internal.h"
+
+using namespace pidk;
+
+namespace pidh {
+
+// ---------------------------------------------------------------------------------------
+// Status helpers
+// ---------------------------------------------------------------------------------------
+
+pid_status fail(pid_handle h, pid_status s, const std::string& msg) {
+  if (h) h->last_error = msg;
+  return s;
+}
+
+pid_status cuda_fail(pid_handle h, cudaError_t e, const char* where) {
+  if (h) h->last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return PID_ERR_CUDA;
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+  cudaGetDevice(&prev_);
+  if (prev_ != dev) cudaSetDevice(dev);
+  dev_ = dev;
+}
+DeviceGuard::~DeviceGuard() {
+  if (prev_ != dev_) cudaSetDevice(prev_);
+}
+
+// ---------------------------------------------------------------------------------------
+// TMA descriptor encoding through the runtime's driver entry point (no libcuda link).
+// ---------------------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
+               uint64_t row_bytes, uint32_t box_inner, uint32_t box_outer) {
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[1] = {n};
+  cuuint64_t strides[1] = {0};
+  cuuint32_t bx[1] = {box};
+  cuuint32_t es[1] = {1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<void*>(base), dims, strides, bx, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// ---------------------------------------------------------------------------------------
+// Planning
+// ---------------------------------------------------------------------------------------
+
+// Tile class of the streaming kernel as a function of N alone, so that an ensemble is
+// always processed with the same arithmetic order, alone or inside a batch.
+StreamCfg stream_cfg(int64_t N) {
+  if (N <= 8) return {4, 1, 128};
+  if (N <= 16) return {4, 2, 128};
+  if (N <= 32) return {4, 4, 128};
+  if (N <= 64) return {4, 8, 128};
+  if (N <= 128) return {4, 16, 128};
+  if (N <= 256) return {2, 16, 64};
+  return {1, 16, 32};
+}
+
+static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t) {
+  if (!iso) { *mode = ISO_NONE; *mu = 0.f; *inv = 0.f; *t = 0.f; return; }
+  *mu = static_cast<float>(iso->mu);
+  if (iso->sigma > 0.0) {
+    *mode = ISO_NORMAL;
+    const double inv_d = 1.0 / (iso->sigma * std::sqrt(2.0));
+    *inv = static_cast<float>(iso->superlevel ? -inv_d : inv_d);
+    *t = 0.f;
+  } else {
+    // F < mu (exact, in double) <=> F < t with t the smallest float >= mu;
+    // F > mu <=> F > t with t the largest float <= mu.
+    float t32 = static_cast<float>(iso->mu);
+    if (!iso->superlevel) {
+      if (static_cast<double>(t32) < iso->mu) t32 = std::nextafter(t32, INFINITY);
+      *mode = ISO_STEP_BELOW;
+    } else {
+      if (static_cast<double>(t32) > iso->mu) t32 = std::nextafter(t32, -INFINITY);
+      *mode = ISO_STEP_ABOVE;
+    }
+    *t = t32;
+    *inv = 0.f;
+  }
+}
+
+pid_status check_iso(pid_handle h, const pid_iso* iso) {
+  if (!iso) return fail(h, PID_ERR_INVALID_ARG, "iso must not be NULL");
+  if (iso->kind != PID_ISO_NORMAL) return fail(h, PID_ERR_UNSUPPORTED, "unknown iso kind");
+  if (!std::isfinite(iso->mu) || !std::isfinite(iso->sigma) || iso->sigma < 0.0)
+    return fail(h, PID_ERR_INVALID_ARG, "iso needs finite mu and sigma >= 0");
+  if (iso->superlevel != 0 && iso->superlevel != 1)
+    return fail(h, PID_ERR_INVALID_ARG, "iso.superlevel must be 0 or 1");
+  return PID_OK;
+}
+
+pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  if (!data) return fail(h, PID_ERR_INVALID_ARG, "data pointer is NULL");
+  if (N < 1 || M < 1) return fail(h, PID_ERR_INVALID_ARG, "N and M must be >= 1");
+  if (ld < M) return fail(h, PID_ERR_INVALID_ARG, "ld must be >= M");
+  if (M > (int64_t(1) << 31) - 4096) return fail(h, PID_ERR_UNSUPPORTED, "M must be < 2^31 - 4096");
+  if (ld > (int64_t(1) << 37)) return fail(h, PID_ERR_UNSUPPORTED, "ld too large");
+  if (N > kMaxMembers) return fail(h, PID_ERR_UNSUPPORTED, "N above the supported maximum (512)");
+  return PID_OK;
+}
+
+pid_status check_opt(pid_handle h, const pid_options* o) {
+  if (!o) return PID_OK;
+  if (o->mode < PID_MODE_MEAN || o->mode > PID_MODE_FULL_LINEAR)
+    return fail(h, PID_ERR_INVALID_ARG, "unknown mode");
+  if (o->precision < PID_FP32 || o->precision > PID_FP8)
+    return fail(h, PID_ERR_INVALID_ARG, "unknown precision");
+  if (o->validate != 0 && o->validate != 1)
+    return fail(h, PID_ERR_INVALID_ARG, "validate must be 0 or 1");
+  if (o->reserved != 0) return fail(h, PID_ERR_INVALID_ARG, "reserved must be 0");
+  return PID_OK;
+}
+
+// Plan one ensemble for the streaming kernel. Pointers into the workspace are filled later.
+pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
+  std::memset(pl, 0, sizeof(*pl));
+  const StreamCfg cfg = stream_cfg(in.N);
+  pl->cfg = cfg;
+  EnsDesc& d = pl->desc;
+  d.data = in.data;
+  d.w = in.w;
+  d.ld = in.ld;
+  d.N = static_cast<int32_t>(in.N);
+  d.M = static_cast<int32_t>(in.M);
+  const int n_groups = kStreamWarps / cfg.G;
+  const int64_t total_groups = static_cast<int64_t>(h->sms) * n_groups;
+  int64_t chunk = round_up((in.M + total_groups - 1) / total_groups, cfg.T);
+  chunk = std::max<int64_t>(cfg.T, std::min<int64_t>(chunk, 256 * cfg.T));
+  d.chunk_cells = static_cast<int32_t>(chunk);
+  d.n_chunks = static_cast<int32_t>((in.M + chunk - 1) / chunk);
+  d.n_boxes = static_cast<int32_t>((in.N + 255) / 256);
+  d.box_rows = static_cast<int32_t>((in.N + d.n_boxes - 1) / d.n_boxes);
+  iso_fill(in.is_field ? &in.iso : nullptr, &d.iso_mode, &d.iso_mu, &d.iso_inv, &d.iso_t);
+  d.validate = in.validate;
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in.data);
+  const bool tma_ok = (in.ld % 4 == 0) && (a % 16 == 0) &&
+                      (in.w == nullptr || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
+  pl->use_tma = false;
+  if (tma_ok && get_encode_fn()) {
+    bool ok = encode_2d(&d.tmap, in.data, static_cast<uint64_t>(in.M), static_cast<uint64_t>(in.N),
+                        static_cast<uint64_t>(in.ld) * 4, static_cast<uint32_t>(cfg.T),
+                        static_cast<uint32_t>(d.box_rows));
+    if (ok && in.w) ok = encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), cfg.T);
+    pl->use_tma = ok;
+  }
+  pl->stage_floats = static_cast<int32_t>(round_up(int64_t(d.n_boxes) * d.box_rows * cfg.T + cfg.T, 32));
+  pl->part_bytes = round_up(static_cast<int64_t>(d.n_chunks) * 2 * in.N * 8, 256);
+  pl->sums_bytes = round_up((4 * in.N + in.N * in.N) * 8, 256);
+  pl->coef_bytes = round_up(in.N * 4, 256);
+  return PID_OK;
+}
+
+// Choose ring depth and smem size for a launch whose largest stage has `stage_floats`.
+void stream_launch_geometry(const StreamCfg& cfg, int32_t stage_floats, int* depth, size_t* smem) {
+  const int n_groups = kStreamWarps / cfg.G;
+  const size_t red = static_cast<size_t>(n_groups) * 2 * cfg.G * cfg.T * 4;
+  const size_t budget = 220 * 1024 - red;
+  const size_t per_stage = static_cast<size_t>(n_groups) * stage_floats * 4;
+  int dpt = static_cast<int>(budget / per_stage);
+  dpt = std::max(1, std::min(dpt, 8));
+  *depth = dpt;
+  *smem = stream_smem_bytes(cfg.vec, cfg.G, dpt, stage_floats);
+}
+
+// ---------------------------------------------------------------------------------------
+// Workspace
+// ---------------------------------------------------------------------------------------
+
+pid_status ensure_workspace(pid_handle h, size_t bytes, cudaStream_t s) {
+  if (bytes <= h->ws_bytes) return PID_OK;
+  if (h->budget && bytes + h->fixed_bytes > h->budget)
+    return fail(h, PID_ERR_OOM, "workspace would exceed the handle's HBM budget");
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(h, PID_ERR_OOM, "workspace must grow, but the stream is being captured");
+  if (h->ws) {
+    cudaStreamSynchronize(s);
+    cudaFree(h->ws);
+    h->ws = nullptr;
+    h->ws_bytes = 0;
+  }
+  const size_t alloc = round_up(static_cast<int64_t>(bytes), 1 << 20);
+  cudaError_t e = cudaMalloc(&h->ws, alloc);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, PID_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  h->ws_bytes = alloc;
+  return PID_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Launch sequences for one ensemble (single calls)
+// ---------------------------------------------------------------------------------------
+
+static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef, cudaStream_t s) {
+  StreamParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.one = pl.desc;
+  sp.one.coef = coef;
+  sp.one.unit_begin = 0;
+  sp.descs = nullptr;
+  sp.n_ens = 1;
+  sp.total_units = pl.desc.n_chunks;
+  sp.G = pl.cfg.G;
+  sp.use_tma = pl.use_tma ? 1 : 0;
+  sp.err = h->err_word;
+  int depth;
+  size_t smem;
+  stream_launch_geometry(pl.cfg, pl.stage_floats, &depth, &smem);
+  sp.depth = depth;
+  sp.stage_floats = pl.stage_floats;
+  const int n_groups = kStreamWarps / pl.cfg.G;
+  int grid = std::min<int>(h->sms, (sp.total_units + n_groups - 1) / n_groups);
+  grid = std::max(grid, 1);
+  cudaError_t e = launch_stream(sp, pl.cfg.vec, grid, smem, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream kernel launch");
+  return PID_OK;
+}
+
+static pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
+  const int nb_stream = (2 * fd.N + 31) / 32;
+  const int nb_gram = fd.kind == FIN_GRAM ? (fd.N * fd.N + 31) / 32 : 0;
+  fd.slices = std::max(1, std::min(nb_stream + nb_gram, 2 * h->sms));
+  FinParams fp;
+  std::memset(&fp, 0, sizeof(fp));
+  fp.one = fd;
+  fp.descs = nullptr;
+  fp.n_ens = 1;
+  fp.err = h->err_word;
+  cudaError_t e = launch_finalize(fp, fd.slices, 1, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "finalize launch");
+  return PID_OK;
+}
+
+pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s) {
+  EnsPlan pl;
+  pid_status st = plan_stream(h, in, &pl);
+  if (st != PID_OK) return st;
+  const bool gram = in.mode == PID_MODE_FULL && in.precision != PID_FP32;
+  const bool linear = in.mode == PID_MODE_FULL_LINEAR || (in.mode == PID_MODE_FULL && !gram);
+  size_t gram_bytes = 0;
+  GramPlan gp;
+  if (gram) {
+    st = plan_gram(h, in, &gp);
+    if (st != PID_OK) return st;
+    gram_bytes = gp.gpart_bytes;
+  }
+  const size_t need = pl.part_bytes + pl.sums_bytes + pl.coef_bytes + gram_bytes;
+  st = ensure_workspace(h, need, s);
+  if (st != PID_OK) return st;
+  char* ws = static_cast<char*>(h->ws);
+  double* part = reinterpret_cast<double*>(ws);
+  double* sums = reinterpret_cast<double*>(ws + pl.part_bytes);
+  float* coef = reinterpret_cast<float*>(ws + pl.part_bytes + pl.sums_bytes);
+  float* gpart = reinterpret_cast<float*>(ws + pl.part_bytes + pl.sums_bytes + pl.coef_bytes);
+  pl.desc.part = part;
+
+  FinDesc fd;
+  std::memset(&fd, 0, sizeof(fd));
+  fd.part = part;
+  fd.N = pl.desc.N;
+  fd.n_chunks = pl.desc.n_chunks;
+  fd.sums = sums;
+  fd.coef = coef;
+  fd.ticket = h->tickets;
+  fd.depth = out.depth;
+  fd.in_in = out.in_in;
+  fd.in_out = out.in_out;
+  fd.rank = out.rank;
+  fd.mass = out.mass;
+  fd.mean_depth = out.mean_depth;
+
+  if (gram) {
+    st = launch_gram_one(h, in, gp, pl, gpart, s);
+    if (st != PID_OK) return st;
+    fd.kind = FIN_GRAM;
+    fd.gpart = gpart;
+    fd.n_gchunks = gp.n_gchunks;
+    fd.P = out.P;
+    fd.err_est = out.err_est;
+    return launch_fin_one(h, fd, s);
+  }
+  st = launch_stream_one(h, pl, nullptr, s);
+  if (st != PID_OK) return st;
+  if (!linear) {
+    fd.kind = FIN_MEAN;
+    return launch_fin_one(h, fd, s);
+  }
+  FinDesc f1 = fd;
+  f1.kind = FIN_LIN1;
+  f1.depth = nullptr; f1.in_in = nullptr; f1.in_out = nullptr; f1.rank = nullptr;
+  st = launch_fin_one(h, f1, s);
+  if (st != PID_OK) return st;
+  st = launch_stream_one(h, pl, coef, s);
+  if (st != PID_OK) return st;
+  FinDesc f2 = fd;
+  f2.kind = FIN_LIN2;
+  f2.mass = nullptr; f2.mean_depth = nullptr;
+  return launch_fin_one(h, f2, s);
+}
+
+}  // namespace pidh
+
+using namespace pidh;
+
+// =======================================================================================
+// Exported C ABI
+// =======================================================================================
+
+extern "C" {
+
+const char* pid_status_string(pid_status s) {
+  switch (s) {
+    case PID_OK: return "ok";
+    case PID_ERR_INVALID_ARG: return "invalid argument";
+    case PID_ERR_DOMAIN: return "input outside the domain (u not in [0,1], NaN, or w <= 0)";
+    case PID_ERR_OOM: return "out of device memory or over the HBM budget";
+    case PID_ERR_CUDA: return "CUDA error";
+    case PID_ERR_TIMEOUT: return "bounded device wait timed out";
+    case PID_ERR_BUSY: return "busy";
+    case PID_ERR_CANCELLED: return "cancelled";
+    case PID_ERR_UNSUPPORTED: return "unsupported size or option";
+  }
+  return "unknown status";
+}
+
+pid_status pid_create(pid_handle* out, int device, size_t hbm_budget_bytes) {
+  if (!out) return PID_ERR_INVALID_ARG;
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return e != cudaSuccess ? PID_ERR_CUDA : PID_ERR_INVALID_ARG;
+  }
+  pid_handle h = new pid_handle_s();
+  h->device = device;
+  h->budget = hbm_budget_bytes;
+  DeviceGuard g(device);
+  cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
+  h->cc = major * 10 + minor;
+  h->fixed_bytes = sizeof(uint32_t) * (1 + kMaxTickets) + 256;
+  e = cudaMalloc(&h->fixed, h->fixed_bytes);
+  if (e != cudaSuccess) {
+    delete h;
+    return PID_ERR_OOM;
+  }
+  cudaMemset(h->fixed, 0, h->fixed_bytes);
+  h->err_word = static_cast<uint32_t*>(h->fixed);
+  h->tickets = reinterpret_cast<unsigned int*>(static_cast<char*>(h->fixed) + 256);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(h->fixed);
+    delete h;
+    return PID_ERR_CUDA;
+  }
+  *out = h;
+  return PID_OK;
+}
+
+pid_status pid_destroy(pid_handle h) {
+  if (!h) return PID_OK;
+  {
+    DeviceGuard g(h->device);
+    destroy_batch_cache(h);
+    if (h->ws) cudaFree(h->ws);
+    if (h->fixed) cudaFree(h->fixed);
+    if (h->desc_dev) cudaFree(h->desc_dev);
+    if (h->desc_host) cudaFreeHost(h->desc_host);
+  }
+  delete h;
+  return PID_OK;
+}
+
+pid_status pid_sync(pid_handle h, void* stream) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+  uint32_t word = 0;
+  e = cudaMemcpy(&word, h->err_word, sizeof(word), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reading the device error word");
+  if (word == 0) return PID_OK;
+  cudaMemset(h->fixed, 0, h->fixed_bytes);  // clear the word and any ticket left by an early exit
+  cudaDeviceSynchronize();
+  if (word & ERR_TIMEOUT) return fail(h, PID_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (word & ERR_DOMAIN) return fail(h, PID_ERR_DOMAIN, "validation: u outside [0,1], NaN, or w <= 0");
+  return fail(h, PID_ERR_CUDA, "internal device error");
+}
+
+const char* pid_last_error(pid_handle h) { return h ? h->last_error.c_str() : "no handle"; }
+
+size_t pid_workspace_bytes(pid_handle h) { return h ? h->ws_bytes : 0; }
+
+pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                          const pid_iso* iso, float* U_out, int64_t ld_out, void* stream) {
+  pid_status st = check_shape(h, F, N, M, ld);
+  if (st == PID_ERR_UNSUPPORTED && N > kMaxMembers) st = PID_OK;  // elementwise: any N
+  if (st != PID_OK) return st;
+  if ((st = check_iso(h, iso)) != PID_OK) return st;
+  if (!U_out || ld_out < M) return fail(h, PID_ERR_INVALID_ARG, "U_out must be non-NULL with ld_out >= M");
+  DeviceGuard g(h->device);
+  IsoParams p;
+  p.F = F; p.U = U_out; p.N = N; p.M = M; p.ld = ld; p.ld_out = ld_out;
+  iso_fill(iso, &p.iso_mode, &p.iso_mu, &p.iso_inv, &p.iso_t);
+  cudaError_t e = launch_iso(p, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(h, e, "iso kernel launch");
+  return PID_OK;
+}
+
+static pid_status common_call(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,
+                              const float* w, const pid_iso* iso, int mode, int prec, int validate,
+                              const EnsOutputs& out, void* stream) {
+  EnsInput in;
+  in.data = data; in.N = N; in.M = M; in.ld = ld; in.w = w;
+  in.is_field = iso != nullptr;
+  if (iso) in.iso = *iso;
+  in.mode = mode; in.precision = prec; in.validate = validate;
+  DeviceGuard g(h->device);
+  return run_single(h, in, out, static_cast<cudaStream_t>(stream));
+}
+
+pid_status pid_mean(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
+                    const float* w, double* depth, double* in_in, double* in_out, int32_t* rank,
+                    void* stream) {
+  pid_status st = check_shape(h, U, N, M, ld);
+  if (st != PID_OK) return st;
+  EnsOutputs out{};
+  out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
+  return common_call(h, U, N, M, ld, w, nullptr, PID_MODE_MEAN, PID_FP32, 0, out, stream);
+}
+
+pid_status pid_full(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
+                    const float* w, const pid_options* opt, double* depth, double* in_in,
+                    double* in_out, int32_t* rank, double* P, double* err_est, void* stream) {
+  pid_status st = check_shape(h, U, N, M, ld);
+  if (st != PID_OK) return st;
+  if ((st = check_opt(h, opt)) != PID_OK) return st;
+  pid_options o{PID_MODE_FULL_LINEAR, PID_FP32, 0, 0};
+  if (opt) o = *opt;
+  if (o.mode == PID_MODE_MEAN) return fail(h, PID_ERR_INVALID_ARG, "pid_full needs a full-PID mode");
+  EnsOutputs out{};
+  out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
+  out.P = P; out.err_est = err_est;
+  return common_call(h, U, N, M, ld, w, nullptr, o.mode, o.precision, o.validate, out, stream);
+}
+
+pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                           const float* w, const pid_iso* iso, const pid_options* opt,
+                           double* depth, double* in_in, double* in_out, int32_t* rank,
+                           void* stream) {
+  pid_status st = check_shape(h, F, N, M, ld);
+  if (st != PID_OK) return st;
+  if ((st = check_iso(h, iso)) != PID_OK) return st;
+  if ((st = check_opt(h, opt)) != PID_OK) return st;
+  pid_options o{PID_MODE_MEAN, PID_FP32, 0, 0};
+  if (opt) o = *opt;
+  EnsOutputs out{};
+  out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
+  return common_call(h, F, N, M, ld, w, iso, o.mode, o.precision, o.validate, out, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,118 @@
+// Host-side internals of the C ABI (handle, plans). Not part of the public interface.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pid.h"
+#include "internal.h"
+
+namespace pidh {
+
+constexpr int64_t kMaxMembers = 512;   // largest N of the fused single-pass kernels
+constexpr int kMaxTickets = 8192;      // ensembles per batch (one finalisation ticket each)
+
+struct BatchCache;  // batch.cu
+
+}  // namespace pidh
+
+struct pid_handle_s {
+  int device = 0;
+  int sms = 148;
+  int cc = 0;
+  size_t budget = 0;
+  void* ws = nullptr;          // growable workspace
+  size_t ws_bytes = 0;
+  void* fixed = nullptr;       // error word + tickets (zeroed at creation)
+  size_t fixed_bytes = 0;
+  uint32_t* err_word = nullptr;
+  unsigned int* tickets = nullptr;
+  void* desc_dev = nullptr;    // batch descriptor arrays (device)
+  void* desc_host = nullptr;   // pinned mirror
+  size_t desc_bytes = 0;
+  pidh::BatchCache* batch = nullptr;
+  std::string last_error;
+};
+
+namespace pidh {
+
+struct StreamCfg {
+  int vec;  // cells per lane per stage (4, 2, 1)
+  int G;    // warps per group
+  int T;    // cells per stage (32 * vec)
+};
+
+struct EnsInput {
+  const float* data = nullptr;
+  int64_t N = 0, M = 0, ld = 0;
+  const float* w = nullptr;
+  int is_field = 0;
+  pid_iso iso{};
+  int mode = PID_MODE_MEAN;
+  int precision = PID_FP32;
+  int validate = 0;
+};
+
+struct EnsOutputs {
+  double* depth = nullptr;
+  double* in_in = nullptr;
+  double* in_out = nullptr;
+  int32_t* rank = nullptr;
+  double* mass = nullptr;
+  double* mean_depth = nullptr;
+  double* P = nullptr;
+  double* err_est = nullptr;
+};
+
+struct EnsPlan {
+  pidk::EnsDesc desc;
+  StreamCfg cfg;
+  bool use_tma;
+  int32_t stage_floats;
+  size_t part_bytes, sums_bytes, coef_bytes;
+};
+
+struct GramPlan {
+  int n_gchunks = 0;
+  size_t gpart_bytes = 0;
+  int prec = 0;
+  int n_pad = 0;
+  int64_t chunk_cells = 0;
+};
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev);
+  ~DeviceGuard();
+ private:
+  int prev_ = 0, dev_ = 0;
+};
+
+pid_status fail(pid_handle h, pid_status s, const std::string& msg);
+pid_status cuda_fail(pid_handle h, cudaError_t e, const char* where);
+StreamCfg stream_cfg(int64_t N);
+void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t);
+pid_status check_iso(pid_handle h, const pid_iso* iso);
+pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld);
+pid_status check_opt(pid_handle h, const pid_options* o);
+pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl);
+void stream_launch_geometry(const StreamCfg& cfg, int32_t stage_floats, int* depth, size_t* smem);
+pid_status ensure_workspace(pid_handle h, size_t bytes, cudaStream_t s);
+pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s);
+bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
+               uint32_t box_inner, uint32_t box_outer);
+bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
+
+// gram.cu
+pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
+pid_status launch_gram_one(pid_handle h, const EnsInput& in, const GramPlan& gp, EnsPlan& pl,
+                           float* gpart, cudaStream_t s);
+
+// batch.cu
+void destroy_batch_cache(pid_handle h);
+
+}  // namespace pidh

@@ -1,0 +1,112 @@
+// Internal descriptors shared by the host planner and the kernels (not part of the ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace pidk {
+
+// How a kernel turns an input element into a soft-mask value (Sec. 3.5).
+enum IsoMode : int32_t {
+  ISO_NONE = 0,        // data are soft masks already
+  ISO_NORMAL = 1,      // u = erfc((F - mu) * inv) / 2, inv = +-1 / (sigma sqrt 2)
+  ISO_STEP_BELOW = 2,  // sigma = 0, sub-level:   u = 1[F < t]
+  ISO_STEP_ABOVE = 3   // sigma = 0, super-level: u = 1[F > t]
+};
+
+// Bits of the device error word.
+enum ErrBits : uint32_t { ERR_DOMAIN = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
+
+// Bounded device waits give up after this many nanoseconds of %globaltimer.
+constexpr uint64_t kWaitTimeoutNs = 1000000000ull;
+
+// Streaming pass: 16 consumer warps per CTA, grouped G warps per cell tile.
+constexpr int kStreamWarps = 16;
+constexpr int kStreamThreads = kStreamWarps * 32;
+
+// One ensemble as seen by the streaming kernel.
+struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
+  CUtensorMap tmap;     // data [N][ld] float32; box {T cells, box_rows members}
+  CUtensorMap tmap_w;   // weights [M] float32; box {T}
+  const float* data;    // [N][ld]
+  const float* w;       // [M] or nullptr (unit cell measure)
+  const float* coef;    // [N] column-sum coefficients c_j; nullptr = 1/N for every member
+  double* part;         // [n_chunks][2N] partial sums: m_i, then A_i (or B_i)
+  int64_t ld;
+  int32_t N, M;
+  int32_t chunk_cells;  // multiple of the tile width T
+  int32_t n_chunks;
+  int32_t unit_begin;   // index of chunk 0 in the launch's flat unit list
+  int32_t box_rows;     // members per TMA box (<= 256)
+  int32_t n_boxes;      // boxes per stage along the member axis
+  int32_t iso_mode;     // IsoMode
+  float iso_mu, iso_inv, iso_t;
+  int32_t validate;
+  int32_t pad0, pad1;
+};
+
+struct StreamParams {
+  EnsDesc one;             // used when descs == nullptr (single ensemble)
+  const EnsDesc* descs;    // device array of n_ens descriptors (batch)
+  int32_t n_ens;
+  int32_t total_units;     // chunks over all ensembles
+  int32_t G;               // warps per group (1, 2, 4, 8, 16)
+  int32_t depth;           // stages in each group's ring
+  int32_t stage_floats;    // floats per stage; the last T floats hold the weights
+  int32_t use_tma;
+  uint32_t* err;           // device error word
+};
+
+// Finalisation of one ensemble: fixed-order FP64 reduction of the chunk partials, then
+// inclusion fractions, depth and rank.
+enum FinKind : int32_t {
+  FIN_MEAN = 0,   // PID-mean outputs from (m, A)
+  FIN_LIN1 = 1,   // first pass of exact full PID: keep (m, A), emit coefficients 1/(N m_j)
+  FIN_LIN2 = 2,   // second pass: B_i = IN_out(i); full-PID outputs
+  FIN_GRAM = 3    // full PID from the Gram partials plus (m, A)
+};
+
+struct FinDesc {
+  const double* part;      // [n_chunks][2N]
+  const float* gpart;      // FIN_GRAM: [n_gchunks][N][N] float32 Gram partials (col-major)
+  int32_t N, n_chunks;
+  int32_t n_gchunks, kind;
+  int32_t slices;          // CTAs working on this ensemble
+  int32_t pad0;
+  double* sums;            // workspace [4N + N*N] FP64: m, A, (second-pass m), B, then G
+  float* coef;             // FIN_LIN1 writes [N] coefficients here
+  unsigned int* ticket;    // zero before the launch; the last CTA resets it
+  double* depth;
+  double* in_in;
+  double* in_out;
+  int32_t* rank;
+  double* mass;
+  double* mean_depth;
+  double* P;               // FIN_GRAM: [N][N] inclusion matrix
+  double* err_est;         // FIN_GRAM: max |IN_in(Gram) - A_i/m_i|
+};
+
+struct FinParams {
+  FinDesc one;
+  const FinDesc* descs;
+  int32_t n_ens;
+  int32_t pad;
+  uint32_t* err;
+};
+
+struct IsoParams {
+  const float* F;
+  float* U;
+  int64_t N, M, ld, ld_out;
+  int32_t iso_mode;
+  float iso_mu, iso_inv, iso_t;
+};
+
+// Launchers (stream.cu).
+cudaError_t launch_stream(const StreamParams& p, int vec, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
+cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
+size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
+
+}  // namespace pidk

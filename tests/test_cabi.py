@@ -1,0 +1,57 @@
+"""CPU checks of the C ABI: the library loads, exports every declared symbol, and the
+host-side argument checks answer without touching a GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "pid.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pid_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2512_15187_gb300 import build, binding
+    build.build()
+    return binding.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("pid_soft_masks", "pid_from_fields", "pid_mean", "pid_batch", "pid_full"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_binding_mirrors_every_export(lib):
+    from paper_2512_15187_gb300 import binding
+    for n in _declared():
+        assert n in binding.EXPORTS, n
+
+
+def test_null_handle_is_rejected_on_the_host(lib):
+    from paper_2512_15187_gb300 import binding as B
+    assert lib.pid_mean(None, None, 4, 10, 10, None, None, None, None, None, None) == \
+        B.PID_ERR_INVALID_ARG
+    assert lib.pid_full(None, None, 4, 10, 10, None, None, None, None, None, None, None, None,
+                        None) == B.PID_ERR_INVALID_ARG
+    assert lib.pid_status_string(B.PID_ERR_DOMAIN).startswith(b"input outside")
+    assert lib.pid_destroy(None) == B.PID_OK
+
+
+def test_struct_layout_matches_header():
+    from paper_2512_15187_gb300 import binding as B
+    assert ctypes.sizeof(B.pid_iso) == 24
+    assert ctypes.sizeof(B.pid_options) == 16
+    # data, N, M, ld, w, is_field+reserved, iso, opt, 8 output pointers
+    assert ctypes.sizeof(B.pid_ensemble) == 8 * 5 + 8 + 24 + 16 + 8 * 8
