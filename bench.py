@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the PID hot path on GB300.
+
+Workload: fuzzy isocontours. Each ensemble is N = 64 scalar fields on a 512 x 512 grid
+(sum of 32 Gaussian bumps + noise), mapped to soft masks by an isovalue ~ Normal(0.5, 0.05).
+One step runs the whole hot path over a batch of E ensembles through one pid_batch call:
+isovalue map (fused) -> masses and mean contour -> PID-mean -> full PID -> FP64
+finalisation and ranking. The metric counts member x cell pairs processed per second.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --impl reference the FP64 CPU oracle is timed on the host cores on a bounded sample
+of the same workload. Under torchrun (N > 1) every rank processes its own batch (replicas,
+weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "member·cells/s for PID-mean & full PID (HBM / tensor roofline %); served p50/p99 ms"
+UNIT = "member·cells/s"
+N_MEMBERS, GRID_H, GRID_W, N_RBF = 64, 512, 512, 32
+ISO_MU, ISO_SIGMA = 0.5, 0.05
+WORKLOAD = "fuzzy isocontours: 64 members x 512x512 FP32 fields, isovalue ~ Normal(0.5, 0.05)"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ensembles", type=int, default=256, help="ensembles per step (per GPU)")
+    ap.add_argument("--mode", default="linear", choices=["linear", "full", "mean"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "split_bf16", "fp8"])
+    ap.add_argument("--e2e-ensembles", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------------------
+# CPU oracle leg (runs in a child process with one BLAS/OpenMP thread)
+# ---------------------------------------------------------------------------------------
+
+CPU_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from oracle import pid_oracle as O
+from paper_2512_15187_gb300 import synth
+budget, max_steps, rows = {budget}, {max_steps}, {rows}
+pool = [synth.rbf_fields_2d(N={N}, H={H}, W={W}, n_rbf={K}, seed=synth.DEFAULT_SEED + 2 + 7919 * k)
+        for k in range(2)]
+done, t_total, per = 0, 0.0, []
+while done < max_steps and t_total < budget:
+    F = pool[done % len(pool)]
+    band = (done // len(pool)) % ({H} // rows)
+    F = np.ascontiguousarray(F.reshape({N}, {H}, {W})[:, band * rows:(band + 1) * rows].reshape({N}, -1))
+    t0 = time.perf_counter()
+    U = O.iso_soft_mask(F, {mu}, {sigma})
+    O.pid_mean(U)
+    O.pid(U)
+    dt = time.perf_counter() - t0
+    per.append(dt); t_total += dt; done += 1
+print(json.dumps({{"steps": done, "seconds": t_total, "per_step": per, "cells": rows * {W}}}))
+"""
+
+
+def run_cpu_oracle(budget_s=12.0, max_steps=64, rows=GRID_H):
+    """Time the FP64 oracle on `rows`-row bands of the workload's ensembles, one thread."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = CPU_SNIPPET.format(root=ROOT, budget=budget_s, max_steps=max_steps, rows=rows,
+                              N=N_MEMBERS, H=GRID_H, W=GRID_W, K=N_RBF, mu=ISO_MU, sigma=ISO_SIGMA)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError("CPU oracle failed:\n" + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_record(res):
+    mc = res["steps"] * N_MEMBERS * res["cells"]
+    return {"value": mc / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{res['steps']} ensemble(s) of the workload, {res['cells']} cells each "
+                      f"(64 members): FP64 isovalue map + PID-mean + full PID by O(N^2 M) pairs, "
+                      f"{res['seconds']:.1f} s of one thread"}
+
+
+# ---------------------------------------------------------------------------------------
+# Clocks during the timed region
+# ---------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "20", "-i", self.uuid], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v == "Active"})
+        loaded = [r[0] for r in rows if r[0] > 0.5 * rows[0][1]] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------
+# Roofline bookkeeping
+# ---------------------------------------------------------------------------------------
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"],
+                "bf16_tflops_sustained": d.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "source": "fallback"}
+
+
+def ncu_traffic(kernel_file, workload_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
+    src = os.path.join(ROOT, "paper_2512_15187_gb300", "csrc", kernel_file)
+    prof_dir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(prof_dir):
+        return None
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    for name in sorted(os.listdir(prof_dir)):
+        if not name.endswith(".md") or workload_tag not in name:
+            continue
+        txt = open(os.path.join(prof_dir, name)).read()
+        m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+        m2 = re.search(r"dram_bytes_per_full_launch:\s*([0-9.eE+]+)", txt)
+        if m1 and m2 and m1.group(1) == sha:
+            return float(m2.group(1))
+    return None
+
+
+# ---------------------------------------------------------------------------------------
+# Reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------------
+
+def run_reference(args, rank):
+    """The oracle as it stands on the host cores: each step is one ensemble of the workload
+    restricted to a 128-row band of the grid (64 x 65536 member x cells)."""
+    if rank != 0:
+        return
+    rows = 128
+    res = run_cpu_oracle(budget_s=1e9, max_steps=args.warmup + args.steps, rows=rows)
+    t = res["per_step"][args.warmup:]
+    sec = sum(t)
+    value = len(t) * N_MEMBERS * res["cells"] / sec
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec / len(t), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_cells_per_step": res["cells"],
+                       "path": ["isovalue map", "pid_mean", "full_pid (O(N^2 M) pairs)"],
+                       "parallelism": "host, one thread (rank 0 only)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"one ensemble per step, {rows} of {GRID_H} grid rows"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# Our arm
+# ---------------------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    cpu_res = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_res = run_cpu_oracle(budget_s=12.0, max_steps=16, rows=GRID_H)  # before any CUDA work
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    from paper_2512_15187_gb300 import binding, build, synth
+    build.build()
+    h = binding.Handle(local_rank)
+    E, N, M = args.ensembles, N_MEMBERS, GRID_H * GRID_W
+    dev = torch.device("cuda", local_rank)
+
+    # ---- inputs resident in HBM: E ensembles of fields, generated on the device ----
+    F = torch.empty((E, N, M), dtype=torch.float32, device=dev)
+    for e in range(E):
+        synth.rbf_fields_2d_torch(N, GRID_H, GRID_W, N_RBF,
+                                  seed=synth.DEFAULT_SEED + 2 + 7919 * (e + 100003 * rank),
+                                  device=dev, out=F[e])
+    items = [dict(data=F[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=args.mode, precision=args.precision)
+             for e in range(E)]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return h.batch(items, stream=stream)
+
+    h.autotune(True)          # first warm-up step times the launch candidates
+    for _ in range(args.warmup):
+        step()
+    h.sync()
+    h.autotune(False)
+
+    # ---- timed region ----
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    sampler = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
+    sampler.start()
+    h.profile(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = t0.elapsed_time(t1)
+    prof = h.profile_read()
+    h.profile(False)
+    clocks = sampler.stop()
+    h.sync()
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    total_mc = world * args.steps * E * N * M
+    value = total_mc / (ms * 1e-3)
+
+    # ---- roofline of the dominant kernel (launched by the library on `stream`) ----
+    peaks = measured_peaks()
+    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
+    dom = max(kinds, key=lambda k: kinds[k]["total_ms"])
+    st = kinds[dom]
+    per_launch_ms = st["total_ms"] / st["launches"]
+    if dom == "gram" and st["flops"] > 0 and args.precision != "fp32":
+        achieved = st["flops"] / (st["total_ms"] * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
+    else:
+        achieved = st["bytes"] / (st["total_ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["peak_source"] = peaks["source"]
+    roof["kernel"] = {"stream": "stream_kernel", "gram": "gram_kernel", "finalize": "finalize_kernel",
+                      "iso": "iso_kernel"}[dom]
+    roof["launches"] = st["launches"]
+    roof["ms_per_launch"] = per_launch_ms
+    roof["algorithmic_bytes_per_launch"] = st["bytes"] / st["launches"]
+    traffic = ncu_traffic("stream.cu" if dom == "stream" else "gram.cu",
+                          f"{N}x{GRID_H}x{GRID_W}") if dom in ("stream", "gram") else None
+    roof["traffic"] = traffic
+    gpu_launches = sum(v["launches"] for v in prof.values())
+
+    # ---- end to end: pinned host inputs -> device -> results back, every step ----
+    Ee = min(args.e2e_ensembles, E)
+    host = torch.empty((Ee, N, M), dtype=torch.float32, pin_memory=True)
+    host.copy_(F[:Ee].cpu())
+    dbuf = torch.empty((Ee, N, M), dtype=torch.float32, device=dev)
+    items_e = [dict(data=dbuf[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=args.mode,
+                    precision=args.precision) for e in range(Ee)]
+    res_host = torch.empty((Ee, N), dtype=torch.float64, pin_memory=True)
+
+    def e2e_step():
+        dbuf.copy_(host, non_blocking=True)
+        outs = h.batch(items_e, stream=stream)
+        res_host.copy_(torch.stack([o["depth"] for o in outs]), non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    k_e2e = max(3, min(args.steps, 20))
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(k_e2e):
+        e2e_step()
+    a1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a0.elapsed_time(a1) / k_e2e
+    if dist:
+        tt = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    e2e_value = world * Ee * N * M / (e2e_ms * 1e-3)
+
+    if rank == 0:
+        modes = {"linear": ["isovalue map", "pid_mean_fp32", "full_pid_exact_fp32"],
+                 "full": ["isovalue map", "pid_mean_fp32", f"full_pid_gram_{args.precision}"],
+                 "mean": ["isovalue map", "pid_mean_fp32"]}[args.mode]
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "members": N, "grid": f"{GRID_H}x{GRID_W}",
+                       "ensembles_per_step": E, "path": modes,
+                       "l2": f"inputs larger than L2 ({E * N * M * 4 / 1e9:.1f} GB per step per GPU)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Ee * N * M * 4,
+                    "d2h_bytes_per_step": Ee * N * 8, "ensembles_per_step": Ee},
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+        }
+        if cpu_res is not None:
+            line["cpu_baseline"] = cpu_baseline_record(cpu_res)
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

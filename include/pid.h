@@ -111,6 +111,44 @@ const char* pid_last_error(pid_handle h);
 size_t pid_workspace_bytes(pid_handle h);
 
 /*
+ * Kernel timing. While enabled, the handle brackets each of its kernel launches with CUDA
+ * events recorded on the launch stream and keeps, per kernel kind, the launch count, the
+ * summed device time, and the algorithmic bytes and flops of those launches (bytes: one
+ * read of every input element and cell measure, plus stored outputs; flops: 2 N^2 M per
+ * Gram launch, times 3 for split BF16). Enabling resets the counters. Reading waits for
+ * the recorded events.
+ */
+typedef enum pid_kernel_kind {
+  PID_KERNEL_STREAM = 0,    /* PID-mean / exact full-PID streaming pass */
+  PID_KERNEL_GRAM = 1,      /* tensor-core Gram */
+  PID_KERNEL_FINALIZE = 2,  /* FP64 reduction, depths, ranks */
+  PID_KERNEL_ISO = 3,       /* isovalue map alone */
+  PID_KERNEL_KINDS = 4
+} pid_kernel_kind;
+
+typedef struct pid_kernel_stats {
+  int64_t launches;
+  double total_ms;
+  double bytes;
+  double flops;
+} pid_kernel_stats;
+
+pid_status pid_profile_enable(pid_handle h, int enable);
+pid_status pid_profile_read(pid_handle h, int kind, pid_kernel_stats* out);
+
+/*
+ * Autotuning. While enabled, the first launch of each kernel class and size bucket runs
+ * every candidate of the launch parameters that leave results unchanged (the column-sum
+ * exchange scheme and the TMA ring depth of the streaming kernel), times them with CUDA
+ * events, and keeps the fastest for later launches. That first call synchronises its
+ * stream; launches being captured into a CUDA graph are never tuned. If the environment
+ * variable PID_AUTOTUNE_CACHE names a file, choices are loaded from it at pid_create and
+ * appended to it as they are made. Returns the number of tuned entries in *n_entries
+ * (may be NULL).
+ */
+pid_status pid_autotune_enable(pid_handle h, int enable, int32_t* n_entries);
+
+/*
  * pid_soft_masks — the isovalue map alone (Sec. 3.5): U_out[i*ld_out + x] = u_i(x) for
  * x < M. F: [N][ld] float32 scalar fields; U_out: [N][ld_out] float32, ld_out >= M.
  * Cells x in [M, ld_out) of U_out are not written.

@@ -27,8 +27,10 @@ PRECISIONS = {"fp32": PID_FP32, "bf16": PID_BF16, "split_bf16": PID_SPLIT_BF16, 
 EXPORTS = [
     "pid_create", "pid_destroy", "pid_sync", "pid_status_string", "pid_last_error",
     "pid_workspace_bytes", "pid_soft_masks", "pid_mean", "pid_full", "pid_from_fields",
-    "pid_batch",
+    "pid_batch", "pid_profile_enable", "pid_profile_read", "pid_autotune_enable",
 ]
+PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO = 0, 1, 2, 3
+KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3}
 
 
 class PidError(RuntimeError):
@@ -44,6 +46,11 @@ class pid_iso(ctypes.Structure):
 class pid_options(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("precision", c_int32), ("validate", c_int32),
                 ("reserved", c_int32)]
+
+
+class pid_kernel_stats(ctypes.Structure):
+    _fields_ = [("launches", c_int64), ("total_ms", c_double), ("bytes", c_double),
+                ("flops", c_double)]
 
 
 class pid_ensemble(ctypes.Structure):
@@ -82,6 +89,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_from_fields": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_iso),
                              POINTER(pid_options), P, P, P, P, P], c_int),
         "pid_batch": ([P, POINTER(pid_ensemble), c_int32, P], c_int),
+        "pid_profile_enable": ([P, c_int], c_int),
+        "pid_profile_read": ([P, c_int, POINTER(pid_kernel_stats)], c_int),
+        "pid_autotune_enable": ([P, c_int, POINTER(c_int32)], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -137,6 +147,22 @@ def pid_from_fields(h, F, N, M, ld, w, iso: pid_iso, opt: pid_options, depth, in
                                      rank, stream))
 
 
+def pid_profile_enable(h, enable: bool):
+    _check(h, load().pid_profile_enable(h, int(enable)))
+
+
+def pid_profile_read(h, kind: int) -> pid_kernel_stats:
+    st = pid_kernel_stats()
+    _check(h, load().pid_profile_read(h, kind, ctypes.byref(st)))
+    return st
+
+
+def pid_autotune_enable(h, enable: bool) -> int:
+    n = c_int32(0)
+    _check(h, load().pid_autotune_enable(h, int(enable), ctypes.byref(n)))
+    return int(n.value)
+
+
 def pid_batch(h, ensembles, stream=None):
     arr = (pid_ensemble * len(ensembles))(*ensembles)
     _check(h, load().pid_batch(h, arr, len(ensembles), stream))
@@ -180,6 +206,21 @@ class Handle:
 
     def sync(self, stream=None):
         pid_sync(self.h, _stream(stream))
+
+    def autotune(self, enable: bool = True) -> int:
+        return pid_autotune_enable(self.h, enable)
+
+    def profile(self, enable: bool = True):
+        pid_profile_enable(self.h, enable)
+
+    def profile_read(self):
+        """{kind: {launches, total_ms, bytes, flops}} for every kernel kind."""
+        out = {}
+        for name, k in KERNEL_KINDS.items():
+            st = pid_profile_read(self.h, k)
+            out[name] = {"launches": int(st.launches), "total_ms": float(st.total_ms),
+                         "bytes": float(st.bytes), "flops": float(st.flops)}
+        return out
 
     def workspace_bytes(self) -> int:
         return int(load().pid_workspace_bytes(self.h))

@@ -1,12 +1,378 @@
-// Batched execution of many ensembles (placeholder until the persistent batch lands).
+// Batched execution: many ensembles of uneven N and M per call.
+//
+// Ensembles are grouped by tile class (a function of N alone, so each ensemble keeps the
+// arithmetic order of a single call and its results are bitwise identical to it). Each
+// class runs as one persistent launch of the streaming kernel over the flat list of all its
+// (ensemble, chunk) units; one finalisation launch then serves every ensemble. The exact
+// full PID adds a second streaming launch per class and a second finalisation. Full PID on
+// tensor cores runs one Gram launch per class instead of the first streaming pass.
+//
+// The whole sequence (descriptor upload + launches) is recorded once into a CUDA graph and
+// replayed while the caller submits the same batch layout (same pointers and shapes).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <vector>
+
 #include "capi_internal.h"
+#include "internal.h"
+
+using namespace pidk;
 
 namespace pidh {
 
-void destroy_batch_cache(pid_handle) {}
+struct BatchCache {
+  std::vector<unsigned char> key;     // serialized batch layout of the cached graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  void* host_desc = nullptr;          // pinned descriptor image read by the graph's memcpy
+  size_t host_bytes = 0;
+  bool use_graphs = true;
+  int64_t replays = 0;
+};
+
+void destroy_batch_cache(pid_handle h) {
+  if (!h->batch) return;
+  BatchCache* c = h->batch;
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->graph) cudaGraphDestroy(c->graph);
+  if (c->host_desc) cudaFreeHost(c->host_desc);
+  delete c;
+  h->batch = nullptr;
+}
+
+static int64_t align_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+struct ClassKey {
+  int vec, G, coef;
+  bool operator<(const ClassKey& o) const {
+    if (vec != o.vec) return vec < o.vec;
+    if (G != o.G) return G < o.G;
+    return coef < o.coef;
+  }
+};
+
+struct Launch {
+  enum Kind { STREAM, GRAM, FIN } kind;
+  int first, count;        // descriptor range (stream/gram: EnsDesc index; fin: FinDesc index)
+  StreamCfg cfg;
+  bool coef = false;
+  bool tma = true;
+  int32_t stage_floats = 0;
+  int32_t total_units = 0;
+  int32_t max_n = 0;
+  int64_t cells = 0;     // sum of N * M over the launch (tuning bucket)
+  int grid_x = 1;
+  double bytes = 0, flops = 0;
+  GramPlan gp;             // GRAM launches
+};
+
+struct BatchPlan {
+  std::vector<EnsDesc> sdesc;   // streaming descriptors (pass 1 then pass 2), grouped by class
+  std::vector<FinDesc> fdesc;   // finalisation descriptors (phase 1 then phase 2)
+  std::vector<Launch> launches;
+  size_t desc_bytes = 0;
+  size_t work_bytes = 0;
+};
+
+static pid_status to_input(pid_handle h, const pid_ensemble& e, EnsInput* in) {
+  pid_status st = check_shape(h, e.data, e.N, e.M, e.ld);
+  if (st != PID_OK) return st;
+  if (e.is_field != 0 && e.is_field != 1) return fail(h, PID_ERR_INVALID_ARG, "is_field must be 0 or 1");
+  if (e.is_field && (st = check_iso(h, &e.iso)) != PID_OK) return st;
+  if ((st = check_opt(h, &e.opt)) != PID_OK) return st;
+  if (e.reserved != 0) return fail(h, PID_ERR_INVALID_ARG, "reserved must be 0");
+  in->data = e.data; in->N = e.N; in->M = e.M; in->ld = e.ld; in->w = e.w;
+  in->is_field = e.is_field;
+  if (e.is_field) in->iso = e.iso;
+  in->mode = e.opt.mode;
+  in->precision = e.opt.precision;
+  in->validate = e.opt.validate;
+  return PID_OK;
+}
+
+// Lay out descriptors and workspace for the batch. Pointers are offsets from `base`.
+static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, char* base,
+                             BatchPlan* bp) {
+  std::vector<EnsInput> in(count);
+  std::vector<EnsPlan> pl(count);
+  std::vector<GramPlan> gp(count);
+  std::vector<int> is_gram(count, 0), is_lin(count, 0);
+  for (int e = 0; e < count; ++e) {
+    pid_status st = to_input(h, ens[e], &in[e]);
+    if (st != PID_OK) return st;
+    if ((st = plan_stream(h, in[e], &pl[e])) != PID_OK) return st;
+    is_gram[e] = in[e].mode == PID_MODE_FULL && in[e].precision != PID_FP32;
+    is_lin[e] = in[e].mode == PID_MODE_FULL_LINEAR || (in[e].mode == PID_MODE_FULL && !is_gram[e]);
+    if (is_gram[e] && (st = plan_gram(h, in[e], &gp[e])) != PID_OK) return st;
+  }
+  // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
+  std::map<ClassKey, std::vector<int>> pass1, pass2;
+  std::map<int, std::vector<int>> gram_cls;
+  for (int e = 0; e < count; ++e) {
+    if (is_gram[e]) {
+      gram_cls[gp[e].n_pad].push_back(e);
+    } else {
+      pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0}].push_back(e);
+      if (is_lin[e]) pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1}].push_back(e);
+    }
+  }
+  const int n_sdesc = static_cast<int>(count + pass2.size() * 0);
+  int n_s = 0;
+  for (auto& kv : pass1) n_s += static_cast<int>(kv.second.size());
+  for (auto& kv : pass2) n_s += static_cast<int>(kv.second.size());
+  for (auto& kv : gram_cls) n_s += static_cast<int>(kv.second.size());
+  (void)n_sdesc;
+  int n_lin = 0;
+  for (int e = 0; e < count; ++e) n_lin += is_lin[e];
+  const int n_f = count + n_lin;
+  const size_t sdesc_bytes = align_up(static_cast<int64_t>(n_s) * sizeof(EnsDesc), 256);
+  const size_t fdesc_bytes = align_up(static_cast<int64_t>(n_f) * sizeof(FinDesc), 256);
+  bp->desc_bytes = sdesc_bytes + fdesc_bytes;
+  size_t off = bp->desc_bytes;
+  std::vector<double*> part(count), sums(count);
+  std::vector<float*> coef(count), gpart(count, nullptr);
+  for (int e = 0; e < count; ++e) {
+    part[e] = reinterpret_cast<double*>(base + off); off += pl[e].part_bytes;
+    sums[e] = reinterpret_cast<double*>(base + off); off += pl[e].sums_bytes;
+    coef[e] = reinterpret_cast<float*>(base + off); off += pl[e].coef_bytes;
+    if (is_gram[e]) { gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes; }
+    pl[e].desc.part = part[e];
+  }
+  bp->work_bytes = off;
+  if (count > kMaxTickets) return fail(h, PID_ERR_UNSUPPORTED, "too many ensembles in one batch");
+
+  auto add_stream_class = [&](const ClassKey& k, const std::vector<int>& members, bool coef_pass) {
+    Launch L;
+    L.kind = Launch::STREAM;
+    L.first = static_cast<int>(bp->sdesc.size());
+    L.count = static_cast<int>(members.size());
+    L.cfg = pl[members[0]].cfg;
+    L.coef = coef_pass;
+    L.tma = true;
+    int32_t units = 0;
+    for (int e : members) {
+      EnsDesc d = pl[e].desc;
+      d.unit_begin = units;
+      d.coef = coef_pass ? coef[e] : nullptr;
+      units += d.n_chunks;
+      L.stage_floats = std::max(L.stage_floats, pl[e].stage_floats);
+      L.tma = L.tma && pl[e].use_tma;
+      L.bytes += 4.0 * d.N * d.M + (d.w ? 4.0 * d.M : 0.0);
+      L.max_n = std::max(L.max_n, d.N);
+      L.cells += static_cast<int64_t>(d.N) * d.M;
+      bp->sdesc.push_back(d);
+    }
+    L.total_units = units;
+    bp->launches.push_back(L);
+    (void)k;
+  };
+  auto fin_for = [&](int e, int kind) {
+    FinDesc f;
+    std::memset(&f, 0, sizeof(f));
+    f.part = part[e];
+    f.N = static_cast<int32_t>(in[e].N);
+    f.n_chunks = pl[e].desc.n_chunks;
+    f.kind = kind;
+    f.sums = sums[e];
+    f.coef = coef[e];
+    f.ticket = h->tickets + e;
+    const pid_ensemble& o = ens[e];
+    if (kind != FIN_LIN1) {
+      f.depth = o.depth; f.in_in = o.in_in; f.in_out = o.in_out; f.rank = o.rank;
+    }
+    if (kind != FIN_LIN2) { f.mass = o.mass; f.mean_depth = o.mean_depth; }
+    if (kind == FIN_GRAM) {
+      f.gpart = gpart[e];
+      f.n_gchunks = gp[e].n_gchunks;
+      f.P = o.P;
+      f.err_est = o.err_est;
+    }
+    const int nb = (2 * f.N + 31) / 32 + (kind == FIN_GRAM ? (f.N * f.N + 31) / 32 : 0);
+    f.slices = std::max(1, std::min(nb, 2 * h->sms));
+    return f;
+  };
+
+  // Phase 1: Gram launches and first streaming passes.
+  for (auto& kv : gram_cls) {
+    Launch L;
+    L.kind = Launch::GRAM;
+    L.first = static_cast<int>(bp->sdesc.size());
+    L.count = static_cast<int>(kv.second.size());
+    L.gp = gp[kv.second[0]];
+    int32_t units = 0;
+    for (int e : kv.second) {
+      EnsDesc d = pl[e].desc;
+      d.unit_begin = units;
+      d.coef = reinterpret_cast<const float*>(gpart[e]);  // Gram launches: partial Gram output
+      units += gp[e].n_gchunks;
+      L.bytes += 4.0 * d.N * d.M + (d.w ? 4.0 * d.M : 0.0);
+      const double mult = in[e].precision == PID_SPLIT_BF16 ? 3.0 : 1.0;
+      L.flops += mult * 2.0 * static_cast<double>(d.N) * d.N * d.M;
+      bp->sdesc.push_back(d);
+    }
+    L.total_units = units;
+    bp->launches.push_back(L);
+  }
+  for (auto& kv : pass1) add_stream_class(kv.first, kv.second, false);
+  {
+    Launch L;
+    L.kind = Launch::FIN;
+    L.first = static_cast<int>(bp->fdesc.size());
+    for (int e = 0; e < count; ++e) {
+      const int kind = is_gram[e] ? FIN_GRAM : (is_lin[e] ? FIN_LIN1 : FIN_MEAN);
+      bp->fdesc.push_back(fin_for(e, kind));
+      L.grid_x = std::max(L.grid_x, bp->fdesc.back().slices);
+    }
+    L.count = static_cast<int>(bp->fdesc.size()) - L.first;
+    bp->launches.push_back(L);
+  }
+  // Phase 2: exact full PID, second streaming pass and its finalisation.
+  if (n_lin) {
+    for (auto& kv : pass2) add_stream_class(kv.first, kv.second, true);
+    Launch L;
+    L.kind = Launch::FIN;
+    L.first = static_cast<int>(bp->fdesc.size());
+    for (int e = 0; e < count; ++e) {
+      if (!is_lin[e]) continue;
+      bp->fdesc.push_back(fin_for(e, FIN_LIN2));
+      L.grid_x = std::max(L.grid_x, bp->fdesc.back().slices);
+    }
+    L.count = static_cast<int>(bp->fdesc.size()) - L.first;
+    bp->launches.push_back(L);
+  }
+  return PID_OK;
+}
+
+static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const void* host_image,
+                          cudaStream_t s) {
+  cudaError_t e = cudaMemcpyAsync(base, host_image, bp.desc_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch descriptor upload");
+  const EnsDesc* sdev = reinterpret_cast<const EnsDesc*>(base);
+  const size_t sdesc_bytes = align_up(static_cast<int64_t>(bp.sdesc.size()) * sizeof(EnsDesc), 256);
+  const FinDesc* fdev = reinterpret_cast<const FinDesc*>(base + sdesc_bytes);
+  for (const Launch& L : bp.launches) {
+    if (L.kind == Launch::STREAM) {
+      StreamParams sp;
+      std::memset(&sp, 0, sizeof(sp));
+      sp.one = bp.sdesc[L.first];  // host copy: tuning key (iso / weights of the class)
+      sp.descs = sdev + L.first;
+      sp.n_ens = L.count;
+      sp.total_units = L.total_units;
+      sp.G = L.cfg.G;
+      sp.sub = L.cfg.sub;
+      sp.use_tma = L.tma ? 1 : 0;
+      sp.err = h->err_word;
+      sp.stage_floats = L.stage_floats;
+      const int n_groups = kStreamWarps / L.cfg.G;
+      const int grid = std::max(1, std::min<int>(h->sms, (L.total_units + n_groups - 1) / n_groups));
+      pid_status st = stream_launch(h, sp, L.cfg, L.coef, grid, L.max_n, L.cells, L.bytes, s);
+      if (st != PID_OK) return st;
+    } else if (L.kind == Launch::GRAM) {
+      pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units, L.bytes,
+                                        L.flops, s);
+      if (st != PID_OK) return st;
+    } else {
+      FinParams fp;
+      std::memset(&fp, 0, sizeof(fp));
+      fp.descs = fdev + L.first;
+      fp.n_ens = L.count;
+      fp.err = h->err_word;
+      ProfScope ps(h, PID_KERNEL_FINALIZE, 0.0, 0.0, s);
+      e = launch_finalize(fp, L.grid_x, L.count, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "batch finalize launch");
+    }
+  }
+  return PID_OK;
+}
 
 }  // namespace pidh
 
-extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble*, int32_t, void*) {
-  return pidh::fail(h, PID_ERR_UNSUPPORTED, "pid_batch not built yet");
+using namespace pidh;
+
+extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && !ens)) return fail(h, PID_ERR_INVALID_ARG, "bad ensemble array");
+  if (count == 0) return PID_OK;
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!h->batch) h->batch = new BatchCache();
+  BatchCache* c = h->batch;
+
+  // Plan against a null base to size the workspace, then for real.
+  BatchPlan sizing;
+  pid_status st = plan_batch(h, ens, count, nullptr, &sizing);
+  if (st != PID_OK) return st;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  const bool capturing = cs != cudaStreamCaptureStatusNone;
+  // Replay the cached graph when the layout is unchanged (and the workspace did not move).
+  std::vector<unsigned char> key(sizeof(pid_ensemble) * count + sizeof(void*));
+  std::memcpy(key.data(), ens, sizeof(pid_ensemble) * count);
+  void* ws_before = h->ws;
+  if ((st = ensure_workspace(h, sizing.work_bytes, s)) != PID_OK) return st;
+  std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
+  const bool profiled = h->profiling;
+  if (c->use_graphs && !capturing && !profiled && c->exec && h->ws == ws_before && key == c->key) {
+    cudaError_t e = cudaGraphLaunch(c->exec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "batch graph replay");
+    ++c->replays;
+    return PID_OK;
+  }
+  BatchPlan bp;
+  char* base = static_cast<char*>(h->ws);
+  if ((st = plan_batch(h, ens, count, base, &bp)) != PID_OK) return st;
+  // Host image of the descriptors (pinned, so the upload is asynchronous and graph-safe).
+  if (c->host_bytes < bp.desc_bytes) {
+    if (c->exec) { cudaStreamSynchronize(s); }
+    if (c->host_desc) cudaFreeHost(c->host_desc);
+    c->host_desc = nullptr;
+    c->host_bytes = 0;
+    if (cudaMallocHost(&c->host_desc, bp.desc_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, PID_ERR_OOM, "pinned descriptor staging");
+    }
+    c->host_bytes = bp.desc_bytes;
+  } else {
+    cudaStreamSynchronize(s);  // a previous upload may still read the staging image
+  }
+  std::memset(c->host_desc, 0, bp.desc_bytes);
+  std::memcpy(c->host_desc, bp.sdesc.data(), bp.sdesc.size() * sizeof(EnsDesc));
+  const size_t sdesc_bytes = align_up(static_cast<int64_t>(bp.sdesc.size()) * sizeof(EnsDesc), 256);
+  std::memcpy(static_cast<char*>(c->host_desc) + sdesc_bytes, bp.fdesc.data(),
+              bp.fdesc.size() * sizeof(FinDesc));
+
+  if (!c->use_graphs || capturing || profiled) {
+    return enqueue(h, bp, base, c->host_desc, s);
+  }
+  if (h->autotune) {
+    // Tune on the caller's stream before recording: captured launches are never tuned.
+    st = enqueue(h, bp, base, c->host_desc, s);
+    if (st != PID_OK) return st;
+  }
+  // Record the sequence into a graph on a private stream, then launch it on the caller's.
+  if (c->exec) { cudaGraphExecDestroy(c->exec); c->exec = nullptr; }
+  if (c->graph) { cudaGraphDestroy(c->graph); c->graph = nullptr; }
+  cudaStream_t cap;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(h, e, "capture stream");
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaStreamDestroy(cap); return cuda_fail(h, e, "begin capture"); }
+  st = enqueue(h, bp, base, c->host_desc, cap);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cap, &graph);
+  cudaStreamDestroy(cap);
+  if (st != PID_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+  if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(graph); return cuda_fail(h, e, "graph instantiate"); }
+  c->graph = graph;
+  c->exec = exec;
+  c->key = key;
+  e = cudaGraphLaunch(exec, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "batch graph launch");
+  return PID_OK;
 }

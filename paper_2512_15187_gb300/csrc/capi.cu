@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -41,6 +42,53 @@ DeviceGuard::DeviceGuard(int dev) {
 }
 DeviceGuard::~DeviceGuard() {
   if (prev_ != dev_) cudaSetDevice(prev_);
+}
+
+// ---------------------------------------------------------------------------------------
+// Kernel timing
+// ---------------------------------------------------------------------------------------
+
+static cudaEvent_t pool_event(pid_handle h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+ProfScope::ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStream_t s)
+    : h_(h), s_(s) {
+  if (!h_ || !h_->profiling) return;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s_, &cs);
+  if (cs != cudaStreamCaptureStatusNone) return;  // captured launches are not timed here
+  ProfRecord r{kind, pool_event(h_), pool_event(h_), bytes, flops};
+  cudaEventRecord(r.start, s_);
+  h_->prof_pending.push_back(r);
+  idx_ = static_cast<int>(h_->prof_pending.size()) - 1;
+}
+
+ProfScope::~ProfScope() {
+  if (idx_ >= 0) cudaEventRecord(h_->prof_pending[idx_].stop, s_);
+}
+
+static void prof_drain(pid_handle h) {
+  for (ProfRecord& r : h->prof_pending) {
+    float ms = 0.f;
+    cudaEventSynchronize(r.stop);
+    cudaEventElapsedTime(&ms, r.start, r.stop);
+    pid_kernel_stats& t = h->prof_total[r.kind];
+    t.launches += 1;
+    t.total_ms += ms;
+    t.bytes += r.bytes;
+    t.flops += r.flops;
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof_pending.clear();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -97,14 +145,17 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
 
 // Tile class of the streaming kernel as a function of N alone, so that an ensemble is
 // always processed with the same arithmetic order, alone or inside a batch.
+// Each warp holds MPW = ceil(N / G) members x VEC cells in registers (MPW x VEC <= 32);
+// a TMA stage moves sub x T cells of every member (sub = 1 keeps three stages in flight
+// for N up to 512).
 StreamCfg stream_cfg(int64_t N) {
-  if (N <= 8) return {4, 1, 128};
-  if (N <= 16) return {4, 2, 128};
-  if (N <= 32) return {4, 4, 128};
-  if (N <= 64) return {4, 8, 128};
-  if (N <= 128) return {4, 16, 128};
-  if (N <= 256) return {2, 16, 64};
-  return {1, 16, 32};
+  if (N <= 8) return {4, 1, 128, 1};      // MPW <= 8
+  if (N <= 16) return {4, 2, 128, 1};     // MPW <= 8
+  if (N <= 32) return {4, 4, 128, 1};     // MPW <= 8
+  if (N <= 64) return {4, 8, 128, 1};     // MPW <= 8
+  if (N <= 128) return {4, 16, 128, 1};   // MPW <= 8
+  if (N <= 256) return {2, 16, 64, 1};    // MPW <= 16
+  return {1, 16, 32, 1};                  // MPW <= 32
 }
 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -179,8 +230,9 @@ pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
   d.M = static_cast<int32_t>(in.M);
   const int n_groups = kStreamWarps / cfg.G;
   const int64_t total_groups = static_cast<int64_t>(h->sms) * n_groups;
-  int64_t chunk = round_up((in.M + total_groups - 1) / total_groups, cfg.T);
-  chunk = std::max<int64_t>(cfg.T, std::min<int64_t>(chunk, 256 * cfg.T));
+  const int64_t TS = static_cast<int64_t>(cfg.T) * cfg.sub;
+  int64_t chunk = round_up((in.M + total_groups - 1) / total_groups, TS);
+  chunk = std::max<int64_t>(TS, std::min<int64_t>(chunk, 256 * cfg.T));
   d.chunk_cells = static_cast<int32_t>(chunk);
   d.n_chunks = static_cast<int32_t>((in.M + chunk - 1) / chunk);
   d.n_boxes = static_cast<int32_t>((in.N + 255) / 256);
@@ -193,28 +245,123 @@ pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
   pl->use_tma = false;
   if (tma_ok && get_encode_fn()) {
     bool ok = encode_2d(&d.tmap, in.data, static_cast<uint64_t>(in.M), static_cast<uint64_t>(in.N),
-                        static_cast<uint64_t>(in.ld) * 4, static_cast<uint32_t>(cfg.T),
+                        static_cast<uint64_t>(in.ld) * 4, static_cast<uint32_t>(TS),
                         static_cast<uint32_t>(d.box_rows));
-    if (ok && in.w) ok = encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), cfg.T);
+    if (ok && in.w) ok = encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), static_cast<uint32_t>(TS));
     pl->use_tma = ok;
   }
-  pl->stage_floats = static_cast<int32_t>(round_up(int64_t(d.n_boxes) * d.box_rows * cfg.T + cfg.T, 32));
+  pl->stage_floats = static_cast<int32_t>(round_up(int64_t(d.n_boxes) * d.box_rows * TS + TS, 32));
   pl->part_bytes = round_up(static_cast<int64_t>(d.n_chunks) * 2 * in.N * 8, 256);
   pl->sums_bytes = round_up((4 * in.N + in.N * in.N) * 8, 256);
   pl->coef_bytes = round_up(in.N * 4, 256);
   return PID_OK;
 }
 
+// Exchange scheme of the column sums: 0 = every warp adds the G partials, 1 = reduce-scatter
+// then gather (two barriers). Both add the partials in the same order.
+int default_xchg(const StreamCfg& cfg) { return cfg.G >= 16 ? 1 : 0; }
+
 // Choose ring depth and smem size for a launch whose largest stage has `stage_floats`.
 void stream_launch_geometry(const StreamCfg& cfg, int32_t stage_floats, int* depth, size_t* smem) {
   const int n_groups = kStreamWarps / cfg.G;
-  const size_t red = static_cast<size_t>(n_groups) * 2 * cfg.G * cfg.T * 4;
+  const size_t red = static_cast<size_t>(n_groups) * 2 * (cfg.G * cfg.T + cfg.T) * 4;
   const size_t budget = 220 * 1024 - red;
   const size_t per_stage = static_cast<size_t>(n_groups) * stage_floats * 4;
   int dpt = static_cast<int>(budget / per_stage);
   dpt = std::max(1, std::min(dpt, 8));
   *depth = dpt;
   *smem = stream_smem_bytes(cfg.vec, cfg.G, dpt, stage_floats);
+}
+
+// ---------------------------------------------------------------------------------------
+// Streaming launches and their autotuning
+// ---------------------------------------------------------------------------------------
+
+static std::string stream_tune_key(const StreamCfg& cfg, bool coef, const pidk::StreamParams& sp,
+                                   int32_t max_n, int64_t cells) {
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= cells) ++lg;
+  const pidk::EnsDesc& d = sp.descs ? sp.one : sp.one;  // iso / weights flags come from `one`
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "stream v%d g%d s%d c%d iso%d w%d tma%d n%d m%d", cfg.vec, cfg.G,
+                cfg.sub, coef ? 1 : 0, d.iso_mode != 0, d.w != nullptr, sp.use_tma,
+                (max_n + 7) / 8 * 8, lg);
+  return buf;
+}
+
+void load_tune_cache(pid_handle h) {
+  const char* f = std::getenv("PID_AUTOTUNE_CACHE");
+  if (!f || !*f) return;
+  h->tune_file = f;
+  FILE* fp = std::fopen(f, "r");
+  if (!fp) return;
+  char line[256];
+  while (std::fgets(line, sizeof(line), fp)) {
+    std::string l(line);
+    const size_t bar = l.find('|');
+    if (bar == std::string::npos) continue;
+    int x = 0, d = 0;
+    if (std::sscanf(l.c_str() + bar + 1, "%d %d", &x, &d) == 2) h->tuned[l.substr(0, bar)] = {x, d};
+  }
+  std::fclose(fp);
+}
+
+pid_status stream_launch(pid_handle h, StreamParams sp, const StreamCfg& cfg, bool coef, int grid,
+                         int32_t max_n, int64_t cells, double bytes, cudaStream_t s) {
+  int dmax;
+  size_t smem;
+  stream_launch_geometry(cfg, sp.stage_floats, &dmax, &smem);
+  sp.depth = dmax;
+  sp.xchg = default_xchg(cfg);
+  const std::string key = stream_tune_key(cfg, coef, sp, max_n, cells);
+  auto it = h->tuned.find(key);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (it == h->tuned.end() && h->autotune && cs == cudaStreamCaptureStatusNone) {
+    // Candidates that leave the results unchanged: exchange scheme x ring depth.
+    std::vector<std::pair<int, int>> cand;
+    for (int x = 0; x <= (cfg.G > 2 ? 1 : 0); ++x)
+      for (int d = dmax; d >= std::max(1, dmax - 1); --d) cand.push_back({x, d});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> pick{sp.xchg, dmax};
+    for (auto c : cand) {
+      StreamParams t = sp;
+      t.xchg = c.first;
+      t.depth = c.second;
+      const size_t sm = stream_smem_bytes(cfg.vec, cfg.G, c.second, sp.stage_floats);
+      cudaError_t e = launch_stream(t, cfg.vec, coef, grid, sm, s);  // warm-up
+      if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(h, e, "tune"); }
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 3; ++r) launch_stream(t, cfg.vec, coef, grid, sm, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) { best = ms; pick = c; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->tuned[key] = pick;
+    if (!h->tune_file.empty()) {
+      if (FILE* fp = std::fopen(h->tune_file.c_str(), "a")) {
+        std::fprintf(fp, "%s|%d %d\n", key.c_str(), pick.first, pick.second);
+        std::fclose(fp);
+      }
+    }
+    it = h->tuned.find(key);
+  }
+  if (it != h->tuned.end()) {
+    sp.xchg = it->second.first;
+    sp.depth = std::min(it->second.second, dmax);
+    smem = stream_smem_bytes(cfg.vec, cfg.G, sp.depth, sp.stage_floats);
+  }
+  ProfScope ps(h, PID_KERNEL_STREAM, bytes, 0.0, s);
+  cudaError_t e = launch_stream(sp, cfg.vec, coef, grid, smem, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "stream kernel launch");
+  return PID_OK;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -259,19 +406,16 @@ static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef
   sp.n_ens = 1;
   sp.total_units = pl.desc.n_chunks;
   sp.G = pl.cfg.G;
+  sp.sub = pl.cfg.sub;
   sp.use_tma = pl.use_tma ? 1 : 0;
   sp.err = h->err_word;
-  int depth;
-  size_t smem;
-  stream_launch_geometry(pl.cfg, pl.stage_floats, &depth, &smem);
-  sp.depth = depth;
   sp.stage_floats = pl.stage_floats;
   const int n_groups = kStreamWarps / pl.cfg.G;
   int grid = std::min<int>(h->sms, (sp.total_units + n_groups - 1) / n_groups);
   grid = std::max(grid, 1);
-  cudaError_t e = launch_stream(sp, pl.cfg.vec, grid, smem, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "stream kernel launch");
-  return PID_OK;
+  const double bytes = 4.0 * pl.desc.N * pl.desc.M + (pl.desc.w ? 4.0 * pl.desc.M : 0.0);
+  return stream_launch(h, sp, pl.cfg, coef != nullptr, grid, pl.desc.N,
+                       static_cast<int64_t>(pl.desc.N) * pl.desc.M, bytes, s);
 }
 
 static pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
@@ -284,6 +428,7 @@ static pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
   fp.descs = nullptr;
   fp.n_ens = 1;
   fp.err = h->err_word;
+  ProfScope ps(h, PID_KERNEL_FINALIZE, 0.0, 0.0, s);
   cudaError_t e = launch_finalize(fp, fd.slices, 1, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "finalize launch");
   return PID_OK;
@@ -399,6 +544,15 @@ pid_status pid_create(pid_handle* out, int device, size_t hbm_budget_bytes) {
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, device);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, device);
   h->cc = major * 10 + minor;
+  int max_smem = 0;
+  cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  h->max_smem = max_smem;
+  e = stream_kernels_init(max_smem);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return PID_ERR_CUDA;
+  }
   h->fixed_bytes = sizeof(uint32_t) * (1 + kMaxTickets) + 256;
   e = cudaMalloc(&h->fixed, h->fixed_bytes);
   if (e != cudaSuccess) {
@@ -407,6 +561,7 @@ pid_status pid_create(pid_handle* out, int device, size_t hbm_budget_bytes) {
   }
   cudaMemset(h->fixed, 0, h->fixed_bytes);
   h->err_word = static_cast<uint32_t*>(h->fixed);
+  load_tune_cache(h);
   h->tickets = reinterpret_cast<unsigned int*>(static_cast<char*>(h->fixed) + 256);
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -423,6 +578,8 @@ pid_status pid_destroy(pid_handle h) {
   {
     DeviceGuard g(h->device);
     destroy_batch_cache(h);
+    prof_drain(h);
+    for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
     if (h->fixed) cudaFree(h->fixed);
     if (h->desc_dev) cudaFree(h->desc_dev);
@@ -451,6 +608,30 @@ pid_status pid_sync(pid_handle h, void* stream) {
 
 const char* pid_last_error(pid_handle h) { return h ? h->last_error.c_str() : "no handle"; }
 
+pid_status pid_profile_enable(pid_handle h, int enable) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  prof_drain(h);
+  for (auto& t : h->prof_total) t = pid_kernel_stats{};
+  h->profiling = enable != 0;
+  return PID_OK;
+}
+
+pid_status pid_autotune_enable(pid_handle h, int enable, int32_t* n_entries) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  h->autotune = enable != 0;
+  if (n_entries) *n_entries = static_cast<int32_t>(h->tuned.size());
+  return PID_OK;
+}
+
+pid_status pid_profile_read(pid_handle h, int kind, pid_kernel_stats* out) {
+  if (!h || !out || kind < 0 || kind >= PID_KERNEL_KINDS) return PID_ERR_INVALID_ARG;
+  DeviceGuard g(h->device);
+  prof_drain(h);
+  *out = h->prof_total[kind];
+  return PID_OK;
+}
+
 size_t pid_workspace_bytes(pid_handle h) { return h ? h->ws_bytes : 0; }
 
 pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
@@ -464,6 +645,7 @@ pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, in
   IsoParams p;
   p.F = F; p.U = U_out; p.N = N; p.M = M; p.ld = ld; p.ld_out = ld_out;
   iso_fill(iso, &p.iso_mode, &p.iso_mu, &p.iso_inv, &p.iso_t);
+  ProfScope ps(h, PID_KERNEL_ISO, 8.0 * N * M, 0.0, static_cast<cudaStream_t>(stream));
   cudaError_t e = launch_iso(p, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "iso kernel launch");
   return PID_OK;

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -18,12 +19,30 @@ constexpr int kMaxTickets = 8192;      // ensembles per batch (one finalisation 
 
 struct BatchCache;  // batch.cu
 
+struct ProfRecord {
+  int kind;
+  cudaEvent_t start, stop;
+  double bytes, flops;
+};
+
+// Brackets one kernel launch with events when profiling is on (RAII on the host side).
+class ProfScope {
+ public:
+  ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStream_t s);
+  ~ProfScope();
+ private:
+  pid_handle h_;
+  int idx_ = -1;
+  cudaStream_t s_;
+};
+
 }  // namespace pidh
 
 struct pid_handle_s {
   int device = 0;
   int sms = 148;
   int cc = 0;
+  int max_smem = 0;
   size_t budget = 0;
   void* ws = nullptr;          // growable workspace
   size_t ws_bytes = 0;
@@ -36,14 +55,22 @@ struct pid_handle_s {
   size_t desc_bytes = 0;
   pidh::BatchCache* batch = nullptr;
   std::string last_error;
+  bool profiling = false;
+  std::vector<pidh::ProfRecord> prof_pending;
+  std::vector<cudaEvent_t> event_pool;
+  pid_kernel_stats prof_total[PID_KERNEL_KINDS] = {};
+  bool autotune = false;
+  std::map<std::string, std::pair<int, int>> tuned;  // key -> (exchange scheme, ring depth)
+  std::string tune_file;
 };
 
 namespace pidh {
 
 struct StreamCfg {
-  int vec;  // cells per lane per stage (4, 2, 1)
+  int vec;  // cells per lane per register tile (4, 2, 1)
   int G;    // warps per group
-  int T;    // cells per stage (32 * vec)
+  int T;    // cells per register tile (32 * vec)
+  int sub;  // register tiles per TMA stage (stage = sub * T cells = 128 for every class)
 };
 
 struct EnsInput {
@@ -101,6 +128,11 @@ pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int
 pid_status check_opt(pid_handle h, const pid_options* o);
 pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl);
 void stream_launch_geometry(const StreamCfg& cfg, int32_t stage_floats, int* depth, size_t* smem);
+int default_xchg(const StreamCfg& cfg);
+// Launch the streaming kernel with tuned (or default) exchange scheme and ring depth.
+pid_status stream_launch(pid_handle h, pidk::StreamParams sp, const StreamCfg& cfg, bool coef,
+                         int grid, int32_t max_n, int64_t cells, double bytes, cudaStream_t s);
+void load_tune_cache(pid_handle h);
 pid_status ensure_workspace(pid_handle h, size_t bytes, cudaStream_t s);
 pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s);
 bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
@@ -111,6 +143,11 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
 pid_status launch_gram_one(pid_handle h, const EnsInput& in, const GramPlan& gp, EnsPlan& pl,
                            float* gpart, cudaStream_t s);
+// Gram launch over `count` device descriptors whose `coef` field points at the partial-Gram
+// output of each ensemble.
+pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDesc* descs,
+                             int count, int total_units, double bytes, double flops,
+                             cudaStream_t s);
 
 // batch.cu
 void destroy_batch_cache(pid_handle h);

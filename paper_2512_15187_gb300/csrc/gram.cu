@@ -12,4 +12,9 @@ pid_status launch_gram_one(pid_handle h, const EnsInput&, const GramPlan&, EnsPl
   return fail(h, PID_ERR_UNSUPPORTED, "tensor-core Gram not built yet");
 }
 
+pid_status launch_gram_batch(pid_handle h, const GramPlan&, const pidk::EnsDesc*, int, int, double,
+                             double, cudaStream_t) {
+  return fail(h, PID_ERR_UNSUPPORTED, "tensor-core Gram not built yet");
+}
+
 }  // namespace pidh

@@ -35,7 +35,7 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   double* part;         // [n_chunks][2N] partial sums: m_i, then A_i (or B_i)
   int64_t ld;
   int32_t N, M;
-  int32_t chunk_cells;  // multiple of the tile width T
+  int32_t chunk_cells;  // multiple of the stage width sub*T
   int32_t n_chunks;
   int32_t unit_begin;   // index of chunk 0 in the launch's flat unit list
   int32_t box_rows;     // members per TMA box (<= 256)
@@ -53,8 +53,10 @@ struct StreamParams {
   int32_t total_units;     // chunks over all ensembles
   int32_t G;               // warps per group (1, 2, 4, 8, 16)
   int32_t depth;           // stages in each group's ring
-  int32_t stage_floats;    // floats per stage; the last T floats hold the weights
+  int32_t stage_floats;    // floats per stage; the last sub*T floats hold the weights
   int32_t use_tma;
+  int32_t sub;             // register tiles of T cells per TMA stage
+  int32_t xchg;            // column-sum exchange: 0 direct, 1 reduce-scatter (G > 2)
   uint32_t* err;           // device error word
 };
 
@@ -104,9 +106,11 @@ struct IsoParams {
 };
 
 // Launchers (stream.cu).
-cudaError_t launch_stream(const StreamParams& p, int vec, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_stream(const StreamParams& p, int vec, bool coef, int grid, size_t smem,
+                          cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
+cudaError_t stream_kernels_init(int max_smem);
 
 }  // namespace pidk

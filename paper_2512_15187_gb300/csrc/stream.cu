@@ -56,13 +56,15 @@ __device__ __forceinline__ void lds_vec(float (&dst)[VEC], const float* src) {
 }
 
 // Layout of the dynamic shared memory (per CTA):
-//   ring  [n_groups][depth][stage_floats]   TMA destinations; last T floats of a stage = w
-//   red   [n_groups][2][G][T]               partial column sums, double-buffered
+//   ring  [n_groups][depth][stage_floats]   TMA destinations [rows][SUB*T]; the last SUB*T
+//                                           floats of a stage hold the cell measures
+//   red   [n_groups][2][G*T + T]            partial column sums and their total, double-buffered
 //   bars  [n_groups][depth]                 "stage full" mbarriers
 //   flags [n_groups]                        abort flags (bounded wait ran out)
-template <int VEC, int MPW, bool TMA>
+template <int VEC, int MPW, bool TMA, bool COEF>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 stream_kernel(const __grid_constant__ StreamParams p) {
+  static_assert(MPW <= 32, "member coefficients are broadcast from one lane each");
   constexpr int T = 32 * VEC;
   extern __shared__ __align__(1024) unsigned char smem[];
 
@@ -74,14 +76,17 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   const int q = warp - grp * G;
   const int depth = p.depth;
   const int SF = p.stage_floats;
+  const int SUB = p.sub;        // register tiles of T cells per TMA stage
+  const int TS = SUB * T;       // cells per stage (TMA box width)
 
   float* ring = reinterpret_cast<float*>(smem);
   float* red = ring + static_cast<size_t>(n_groups) * depth * SF;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(red + n_groups * 2 * G * T);
+  const int RB = G * T + T;  // floats per exchange buffer
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + n_groups * 2 * RB);
   volatile int* flags = reinterpret_cast<volatile int*>(bars + n_groups * depth);
 
   float* my_ring = ring + static_cast<size_t>(grp) * depth * SF;
-  float* my_red = red + grp * 2 * G * T;
+  float* my_red = red + grp * 2 * RB;
   uint64_t* my_bars = bars + grp * depth;
   const bool leader = (q == 0) && (lane == 0);
 
@@ -104,7 +109,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     const int c = u - d.unit_begin;
     icell0 = c * d.chunk_cells;
     const int cells = min(d.chunk_cells, d.M - icell0);
-    in_st = (cells + T - 1) / T;
+    in_st = (cells + TS - 1) / TS;
   };
   auto issue_next = [&]() {
     if (iu >= p.total_units) return;
@@ -112,13 +117,13 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     const int slot = static_cast<int>(n_issued % depth);
     float* dst = my_ring + static_cast<size_t>(slot) * SF;
     const uint32_t bytes =
-        static_cast<uint32_t>(d.n_boxes * d.box_rows * T + (d.w ? T : 0)) * 4u;
+        static_cast<uint32_t>(d.n_boxes * d.box_rows * TS + (d.w ? TS : 0)) * 4u;
     mbar_arrive_expect_tx(&my_bars[slot], bytes);
-    const int x0 = icell0 + ist * T;
+    const int x0 = icell0 + ist * TS;
     for (int b = 0; b < d.n_boxes; ++b)
-      tma_load_2d(dst + static_cast<size_t>(b) * d.box_rows * T, &d.tmap, &my_bars[slot], x0,
+      tma_load_2d(dst + static_cast<size_t>(b) * d.box_rows * TS, &d.tmap, &my_bars[slot], x0,
                   b * d.box_rows);
-    if (d.w) tma_load_1d(dst + SF - T, &d.tmap_w, &my_bars[slot], x0);
+    if (d.w) tma_load_1d(dst + SF - TS, &d.tmap_w, &my_bars[slot], x0);
     ++n_issued;
     if (++ist == in_st) {
       ist = 0;
@@ -133,6 +138,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 
   // ---- consumers: every warp of the group ----
   long k_cons = 0;
+  long k_sub = 0;   // register tiles processed (parity of the exchange buffer)
   bool aborted = false;
   uint32_t bad = 0;
 
@@ -143,133 +149,166 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     const int c = u - d.unit_begin;
     const int cell0 = c * d.chunk_cells;
     const int cells = min(d.chunk_cells, d.M - cell0);
-    const int n_st = (cells + T - 1) / T;
+    const int n_st = (cells + TS - 1) / TS;
     const int iso = d.iso_mode;
     const float iso_mu = d.iso_mu, iso_inv = d.iso_inv, iso_t = d.iso_t;
     const bool has_w = d.w != nullptr;
 
-    float cf[MPW];
-#pragma unroll
-    for (int k = 0; k < MPW; ++k) {
-      const int i = q + k * G;
-      cf[k] = (i < N) ? (d.coef ? d.coef[i] : 1.0f / static_cast<float>(N)) : 0.0f;
+    // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
+    // every member weighs 1/N, applied once per cell (pass 1).
+    float my_cf = 0.f;
+    if constexpr (COEF) {
+      const int i = q + lane * G;
+      if (lane < MPW && i < N) my_cf = d.coef[i];
     }
+    const float inv_n = 1.0f / static_cast<float>(N);
     float accM[MPW], accA[MPW];
 #pragma unroll
     for (int k = 0; k < MPW; ++k) { accM[k] = 0.f; accA[k] = 0.f; }
 
-    for (int st = 0; st < n_st; ++st, ++k_cons) {
+    for (int st = 0; st < n_st && !aborted; ++st, ++k_cons) {
       const int slot = static_cast<int>(k_cons % depth);
       const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
-      const int xl = cell0 + st * T + lane * VEC;  // first cell handled by this lane
-      float x[MPW][VEC];
-      float wv[VEC];
-
+      const float* sb = my_ring + static_cast<size_t>(slot) * SF;
       if constexpr (TMA) {
         if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[grp] = 1;
-        const float* sb = my_ring + static_cast<size_t>(slot) * SF;
+      }
+      for (int j = 0; j < SUB; ++j, ++k_sub) {
+        const int xl = cell0 + st * TS + j * T + lane * VEC;  // first cell of this lane
+        float x[MPW][VEC];
+        float wv[VEC];
+
+        if constexpr (TMA) {
 #pragma unroll
-        for (int k = 0; k < MPW; ++k) {
-          const int i = q + k * G;
-          if (i < N) {
-            lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * T + lane * VEC);
+          for (int k = 0; k < MPW; ++k) {
+            const int i = q + k * G;
+            if (i < N) {
+              lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
+            } else {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) x[k][v] = 0.f;
+            }
+          }
+          if (has_w) {
+            lds_vec<VEC>(wv, sb + SF - TS + j * T + lane * VEC);
           } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) x[k][v] = 0.f;
+            for (int v = 0; v < VEC; ++v) wv[v] = 1.f;
           }
-        }
-        if (has_w) {
-          lds_vec<VEC>(wv, sb + SF - T + lane * VEC);
         } else {
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) wv[v] = 1.f;
-        }
-      } else {
+          for (int k = 0; k < MPW; ++k) {
+            const int i = q + k * G;
 #pragma unroll
-        for (int k = 0; k < MPW; ++k) {
-          const int i = q + k * G;
+            for (int v = 0; v < VEC; ++v) {
+              const int xc = xl + v;
+              x[k][v] = (i < N && xc < d.M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
+                                            : 0.f;
+            }
+          }
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
             const int xc = xl + v;
-            x[k][v] = (i < N && xc < d.M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
-                                          : 0.f;
+            wv[v] = has_w ? ((xc < d.M) ? __ldg(d.w + xc) : 0.f) : 1.f;
           }
         }
+        // Cells past the end of the ensemble carry no measure.
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          const int xc = xl + v;
-          wv[v] = has_w ? ((xc < d.M) ? __ldg(d.w + xc) : 0.f) : 1.f;
-        }
-      }
-      // Cells past the end of the ensemble carry no measure.
-#pragma unroll
-      for (int v = 0; v < VEC; ++v)
-        if (xl + v >= d.M) wv[v] = 0.f;
+        for (int v = 0; v < VEC; ++v)
+          if (xl + v >= d.M) wv[v] = 0.f;
 
-      if (d.validate) {
+        if (d.validate) {
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          if (xl + v < d.M) {
-            if (!(wv[v] > 0.f) || !(wv[v] < 3.0e38f)) bad |= ERR_DOMAIN;
+          for (int v = 0; v < VEC; ++v) {
+            if (xl + v < d.M) {
+              if (!(wv[v] > 0.f) || !(wv[v] < 3.0e38f)) bad |= ERR_DOMAIN;
 #pragma unroll
-            for (int k = 0; k < MPW; ++k) {
-              if (q + k * G < N) {
-                const float f = x[k][v];
-                if (iso != ISO_NONE ? !(fabsf(f) < 3.0e38f) : !(f >= 0.f && f <= 1.f))
-                  bad |= ERR_DOMAIN;
+              for (int k = 0; k < MPW; ++k) {
+                if (q + k * G < N) {
+                  const float f = x[k][v];
+                  if (iso != ISO_NONE ? !(fabsf(f) < 3.0e38f) : !(f >= 0.f && f <= 1.f))
+                    bad |= ERR_DOMAIN;
+                }
               }
             }
           }
         }
-      }
-      if (iso != ISO_NONE) {
+        if (iso != ISO_NONE) {
 #pragma unroll
-        for (int k = 0; k < MPW; ++k)
+          for (int k = 0; k < MPW; ++k)
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) x[k][v] = iso_value(x[k][v], iso, iso_mu, iso_inv, iso_t);
-      }
+            for (int v = 0; v < VEC; ++v) x[k][v] = iso_value(x[k][v], iso, iso_mu, iso_inv, iso_t);
+        }
 
-      // Column sum over this warp's members, then across the G warps of the group.
-      float s[VEC];
-#pragma unroll
-      for (int v = 0; v < VEC; ++v) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < MPW; ++k) acc = fmaf(cf[k], x[k][v], acc);
-        s[v] = acc;
-      }
-      float* rb = my_red + static_cast<int>(k_cons & 1) * G * T;
-      if (G > 1) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) rb[q * T + lane * VEC + v] = s[v];
-        named_barrier(1 + grp, G * 32);
-      } else {
-        __syncwarp();
-      }
-      if (flags[grp]) { aborted = true; break; }
-      if constexpr (TMA) {
-        if (leader) issue_next();  // every warp has read this slot: refill it
-      }
-      if (G > 1) {
+        // Column sum over this warp's members (rows past N are dropped) ...
+        float s[VEC];
 #pragma unroll
         for (int v = 0; v < VEC; ++v) s[v] = 0.f;
-        for (int r = 0; r < G; ++r) {
-          float t[VEC];
-          lds_vec<VEC>(t, rb + r * T + lane * VEC);
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) s[v] += t[v];
+        for (int k = 0; k < MPW; ++k) {
+          if constexpr (COEF) {
+            const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
+          } else {
+            if (q + k * G < N) {  // iso-mapped padding rows are not zero
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
+            }
+          }
+        }
+        // ... then across the G warps of the group: every warp posts its partial; for G <= 2
+        // each warp adds the others' directly, for larger G warp r first totals the cells
+        // [r T/G, (r+1) T/G) (reduce-scatter) and every warp then reads the totals.
+        float* rb = my_red + static_cast<int>(k_sub & 1) * RB;
+        if (G > 1) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) rb[q * T + lane * VEC + v] = s[v];
+          named_barrier(1 + grp, G * 32);
+        } else {
+          __syncwarp();
+        }
+        if (flags[grp]) { aborted = true; break; }
+        if constexpr (TMA) {
+          if (leader && j == SUB - 1) issue_next();  // every warp has read this slot: refill it
+        }
+        if (G > 2 && p.xchg == 1) {
+          const int cpw = T / G;
+          if (lane < cpw) {
+            const int cc = q * cpw + lane;
+            float acc = 0.f;
+            for (int r = 0; r < G; ++r) acc += rb[r * T + cc];
+            rb[G * T + cc] = acc;
+          }
+          named_barrier(1 + grp, G * 32);
+          lds_vec<VEC>(s, rb + G * T + lane * VEC);
+        } else if (G > 1) {
+          // every warp adds the G partials in warp order (the same order as above)
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) s[v] = 0.f;
+          for (int r = 0; r < G; ++r) {
+            float t[VEC];
+            lds_vec<VEC>(t, rb + r * T + lane * VEC);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s[v] += t[v];
+          }
+        }
+        if constexpr (!COEF) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) s[v] *= inv_n;
+        }
+        // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
+#pragma unroll
+        for (int k = 0; k < MPW; ++k) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const float t = wv[v] * x[k][v];
+            accM[k] += t;
+            accA[k] = fmaf(t, s[v], accA[k]);
+          }
         }
       }
-      // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
-#pragma unroll
-      for (int k = 0; k < MPW; ++k) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          const float t = wv[v] * x[k][v];
-          accM[k] += t;
-          accA[k] = fmaf(t, s[v], accA[k]);
-        }
-      }
+      if (aborted) break;
     }
     if (aborted) break;
 
@@ -303,33 +342,59 @@ size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats) {
   const int T = 32 * vec;
   const int n_groups = kStreamWarps / G;
   return static_cast<size_t>(n_groups) * depth * stage_floats * 4 +
-         static_cast<size_t>(n_groups) * 2 * G * T * 4 + static_cast<size_t>(n_groups) * depth * 8 +
-         static_cast<size_t>(n_groups) * 4 + 64;
+         static_cast<size_t>(n_groups) * 2 * (G * T + T) * 4 +
+         static_cast<size_t>(n_groups) * depth * 8 + static_cast<size_t>(n_groups) * 4 + 64;
 }
 
-template <int VEC, int MPW>
-static cudaError_t launch_stream_t(const StreamParams& p, int grid, size_t smem, cudaStream_t s) {
-  if (p.use_tma) {
-    auto k = stream_kernel<VEC, MPW, true>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k<<<grid, kStreamThreads, smem, s>>>(p);
-  } else {
-    auto k = stream_kernel<VEC, MPW, false>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    k<<<grid, kStreamThreads, smem, s>>>(p);
-  }
+template <int VEC, int MPW, bool TMA, bool COEF>
+static cudaError_t launch_one(const StreamParams& p, int grid, size_t smem, cudaStream_t s) {
+  auto k = stream_kernel<VEC, MPW, TMA, COEF>;
+  k<<<grid, kStreamThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stream(const StreamParams& p, int vec, int grid, size_t smem, cudaStream_t s) {
+template <int VEC, int MPW>
+static cudaError_t set_smem_attrs(int bytes) {
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(stream_kernel<VEC, MPW, true, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(stream_kernel<VEC, MPW, true, false>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(stream_kernel<VEC, MPW, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(stream_kernel<VEC, MPW, false, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// Opt every streaming instantiation in to the largest dynamic shared memory once per
+// device (before any launch, so that launches can be captured into graphs).
+cudaError_t stream_kernels_init(int max_smem) {
+  cudaError_t e;
+  if ((e = set_smem_attrs<4, 8>(max_smem)) != cudaSuccess) return e;
+  if ((e = set_smem_attrs<2, 16>(max_smem)) != cudaSuccess) return e;
+  return set_smem_attrs<1, 32>(max_smem);
+}
+
+template <int VEC, int MPW>
+static cudaError_t launch_stream_t(const StreamParams& p, bool coef, int grid, size_t smem,
+                                   cudaStream_t s) {
+  if (p.use_tma)
+    return coef ? launch_one<VEC, MPW, true, true>(p, grid, smem, s)
+                : launch_one<VEC, MPW, true, false>(p, grid, smem, s);
+  return coef ? launch_one<VEC, MPW, false, true>(p, grid, smem, s)
+              : launch_one<VEC, MPW, false, false>(p, grid, smem, s);
+}
+
+// Tile classes (cells per lane VEC, members per warp MPW): see stream_cfg on the host.
+cudaError_t launch_stream(const StreamParams& p, int vec, bool coef, int grid, size_t smem,
+                          cudaStream_t s) {
   switch (vec) {
-    case 4: return launch_stream_t<4, 8>(p, grid, smem, s);
-    case 2: return launch_stream_t<2, 16>(p, grid, smem, s);
-    case 1: return launch_stream_t<1, 32>(p, grid, smem, s);
+    case 4: return launch_stream_t<4, 8>(p, coef, grid, smem, s);
+    case 2: return launch_stream_t<2, 16>(p, coef, grid, smem, s);
+    case 1: return launch_stream_t<1, 32>(p, coef, grid, smem, s);
     default: return cudaErrorInvalidValue;
   }
 }

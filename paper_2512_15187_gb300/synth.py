@@ -198,3 +198,33 @@ def plume_3d(N: int, R: int, t: int = 0, T: int = 16, seed: int = DEFAULT_SEED +
             amp *= 0.5
         out[i] = torch.sigmoid((base + 0.08 * noise) / 0.02).reshape(-1)
     return out
+
+
+def rbf_fields_2d_torch(N: int = 64, H: int = 512, W: int = 512, n_rbf: int = 32,
+                        seed: int = DEFAULT_SEED + 2, device: str = "cuda", out=None,
+                        chunk: int = 256):
+    """Device twin of rbf_fields_2d (same recipe, torch Philox stream instead of numpy's).
+
+    F_i = sum_k A_k gy_k(y) gx_k(x) + N(0, 0.05): each Gaussian bump is separable, so a
+    member is the product of a [H, n_rbf] and an [n_rbf, W] factor. Returns float32 [N, H*W].
+    """
+    import torch
+
+    if out is None:
+        out = torch.empty((N, H * W), dtype=torch.float32, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    y = torch.arange(H, dtype=torch.float32, device=device).view(1, H, 1)
+    x = torch.arange(W, dtype=torch.float32, device=device).view(1, 1, W)
+    for s in range(0, N, chunk):
+        n = min(chunk, N - s)
+        cy = torch.rand((n, 1, n_rbf), generator=g, device=device) * H
+        cx = torch.rand((n, n_rbf, 1), generator=g, device=device) * W
+        amp = 1.0 + 0.3 * torch.randn((n, 1, n_rbf), generator=g, device=device)
+        sd = 20.0 + 40.0 * torch.rand((n, 1, n_rbf), generator=g, device=device)
+        gy = torch.exp(-((y - cy) ** 2) / (2 * sd ** 2)) * amp          # [n, H, K]
+        gx = torch.exp(-((x - cx) ** 2) / (2 * sd.transpose(1, 2) ** 2))  # [n, K, W]
+        F = torch.bmm(gy, gx).view(n, H * W)
+        F += 0.05 * torch.randn((n, H * W), generator=g, device=device)
+        out[s:s + n] = F
+    return out

@@ -2,6 +2,7 @@
 import numpy as np
 
 FP32_TOL = 1e-6      # FP32 paths vs the FP64 oracle (absolute, on depths and fractions)
+ISO_TOL = 3e-7       # the FP32 isovalue map (soft-mask values) vs FP64 erfc
 GRAM_TOL = 1e-3      # BF16 / split-BF16 / FP8 tensor-core Gram vs the FP64 oracle
 
 

@@ -8,7 +8,7 @@ import pytest
 
 from oracle import pid_oracle as O
 from paper_2512_15187_gb300 import synth
-from tests.helpers import (FP32_TOL, assert_close, assert_rank_agrees_outside_ties,
+from tests.helpers import (FP32_TOL, ISO_TOL, assert_close, assert_rank_agrees_outside_ties,
                            assert_rank_valid, to_np)
 
 pytestmark = pytest.mark.gpu
@@ -124,7 +124,7 @@ def test_soft_masks_parity(H, sigma, superlevel):
     out = H.soft_masks(_dev(F), 0.5, sigma, superlevel)
     H.sync()
     ref = O.iso_soft_mask(F, 0.5, sigma, superlevel)
-    assert_close(to_np(out), ref, 2e-7, "iso map")
+    assert_close(to_np(out), ref, ISO_TOL, "iso map")
 
 
 def test_soft_masks_threshold_not_float_representable(H):
@@ -201,3 +201,21 @@ def test_invalid_arguments(H):
     with pytest.raises(B.PidError) as e:
         H.mean(big)
     assert e.value.status == B.PID_ERR_UNSUPPORTED
+
+
+def test_autotuned_launch_is_bitwise_identical(H):
+    from paper_2512_15187_gb300 import binding
+    U = _dev(synth.random_soft(100, 70000, seed=77))     # G = 16 class: both exchange schemes
+    ref = H.mean(U)
+    H.sync()
+    h2 = binding.Handle(0)
+    n0 = h2.autotune(True)
+    tuned = h2.mean(U)
+    h2.sync()
+    assert h2.autotune(False) >= n0 + 1
+    again = h2.mean(U)
+    h2.sync()
+    for k in ("in_in", "in_out", "depth", "rank"):
+        assert np.array_equal(to_np(ref[k]), to_np(tuned[k]))
+        assert np.array_equal(to_np(ref[k]), to_np(again[k]))
+    h2.close()
