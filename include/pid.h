@@ -217,6 +217,40 @@ typedef struct pid_ensemble {
  */
 pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
 
+/*
+ * pid_mean_noalloc — PID-mean (the same result as pid_mean) for callers that cannot
+ * allocate device memory: code recording a CUDA graph, real-time loops in which a
+ * cudaMalloc would synchronise the device, and host applications whose own allocator owns
+ * all device memory. The paper has no counterpart; this is an interface convenience.
+ *
+ * No handle is needed and nothing is allocated: the scratch (per-chunk partial sums, FP64
+ * totals, a finalisation ticket and an error word) lives in one fixed 4 MiB array inside
+ * the library, which every GPU that loads the library holds until the process exits. The
+ * caller still provides U (and w) and the outputs, all device pointers as for pid_mean.
+ *
+ * Limits: N <= 512 and 8 * (4 N + 2 N * n_chunks) + 256 bytes <= 4 MiB, where n_chunks is
+ * the number of cell chunks the library splits M into (at most the device's SM count times
+ * the members' group count, more only for very large M). Larger problems return
+ * PID_ERR_UNSUPPORTED before anything is enqueued.
+ *
+ * The first call on a device (with that device current) performs a one-time set-up: it
+ * looks up the device address of the scratch array and opts the kernels in to their shared
+ * memory; make that first call before any stream capture. Later calls only enqueue work
+ * on `stream` and can be captured.
+ *
+ * Every call on a device shares the one scratch array, which keeps the previous call's
+ * contents; each call clears the parts that must start at zero. Calls whose work overlaps
+ * on the GPU (different streams, or graphs replayed concurrently) race on the scratch and
+ * produce wrong results: serialise them.
+ *
+ * device_status (device pointer to one uint32, may be NULL) receives the call's device
+ * error word once the stream reaches it: 0 = success, bit 1 = a bounded device wait ran
+ * out (the outputs are then not valid).
+ */
+pid_status pid_mean_noalloc(const float* U, int64_t N, int64_t M, int64_t ld, const float* w,
+                            double* depth, double* in_in, double* in_out, int32_t* rank,
+                            uint32_t* device_status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

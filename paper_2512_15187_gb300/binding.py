@@ -28,6 +28,7 @@ EXPORTS = [
     "pid_create", "pid_destroy", "pid_sync", "pid_status_string", "pid_last_error",
     "pid_workspace_bytes", "pid_soft_masks", "pid_mean", "pid_full", "pid_from_fields",
     "pid_batch", "pid_profile_enable", "pid_profile_read", "pid_autotune_enable",
+    "pid_mean_noalloc",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO = 0, 1, 2, 3
 KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3}
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_profile_enable": ([P, c_int], c_int),
         "pid_profile_read": ([P, c_int, POINTER(pid_kernel_stats)], c_int),
         "pid_autotune_enable": ([P, c_int, POINTER(c_int32)], c_int),
+        "pid_mean_noalloc": ([P, c_int64, c_int64, c_int64, P, P, P, P, P, P, P], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -161,6 +163,13 @@ def pid_autotune_enable(h, enable: bool) -> int:
     n = c_int32(0)
     _check(h, load().pid_autotune_enable(h, int(enable), ctypes.byref(n)))
     return int(n.value)
+
+
+def pid_mean_noalloc(U, N, M, ld, w, depth, in_in, in_out, rank, device_status=None,
+                     stream=None):
+    """PID-mean through the allocation-free entry point (no handle; fixed internal scratch)."""
+    _check(None, load().pid_mean_noalloc(U, N, M, ld, w, depth, in_in, in_out, rank,
+                                         device_status, stream))
 
 
 def pid_batch(h, ensembles, stream=None):
