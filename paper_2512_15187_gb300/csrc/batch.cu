@@ -46,11 +46,12 @@ void destroy_batch_cache(pid_handle h) {
 static int64_t align_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 struct ClassKey {
-  int vec, G, coef;
+  int vec, G, coef, iso;
   bool operator<(const ClassKey& o) const {
     if (vec != o.vec) return vec < o.vec;
     if (G != o.G) return G < o.G;
-    return coef < o.coef;
+    if (coef != o.coef) return coef < o.coef;
+    return iso < o.iso;
   }
 };
 
@@ -115,8 +116,9 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     if (is_gram[e]) {
       gram_cls[gp[e].n_pad].push_back(e);
     } else {
-      pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0}].push_back(e);
-      if (is_lin[e]) pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1}].push_back(e);
+      const int ik = iso_kind(pl[e].desc.iso_mode);
+      pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik}].push_back(e);
+      if (is_lin[e]) pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1, ik}].push_back(e);
     }
   }
   const int n_sdesc = static_cast<int>(count + pass2.size() * 0);

@@ -16,6 +16,7 @@
 #include "../../include/pid.h"
 #include "capi_internal.h"
 #include "internal.h"
+#include "device.cuh"
 
 using namespace pidk;
 
@@ -165,7 +166,7 @@ void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t
   *mu = static_cast<float>(iso->mu);
   if (iso->sigma > 0.0) {
     *mode = ISO_NORMAL;
-    const double inv_d = 1.0 / (iso->sigma * std::sqrt(2.0));
+    const double inv_d = kSqrtLog2e / (iso->sigma * std::sqrt(2.0));
     *inv = static_cast<float>(iso->superlevel ? -inv_d : inv_d);
     *t = 0.f;
   } else {
@@ -313,6 +314,7 @@ pid_status stream_launch(pid_handle h, StreamParams sp, const StreamCfg& cfg, bo
   stream_launch_geometry(cfg, sp.stage_floats, &dmax, &smem);
   sp.depth = dmax;
   sp.xchg = default_xchg(cfg);
+  const int ik = iso_kind(sp.one.iso_mode);
   const std::string key = stream_tune_key(cfg, coef, sp, max_n, cells);
   auto it = h->tuned.find(key);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
@@ -332,10 +334,10 @@ pid_status stream_launch(pid_handle h, StreamParams sp, const StreamCfg& cfg, bo
       t.xchg = c.first;
       t.depth = c.second;
       const size_t sm = stream_smem_bytes(cfg.vec, cfg.G, c.second, sp.stage_floats);
-      cudaError_t e = launch_stream(t, cfg.vec, coef, grid, sm, s);  // warm-up
+      cudaError_t e = launch_stream(t, cfg.vec, cfg.G, ik, coef, grid, sm, s);  // warm-up
       if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(h, e, "tune"); }
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) launch_stream(t, cfg.vec, coef, grid, sm, s);
+      for (int r = 0; r < 3; ++r) launch_stream(t, cfg.vec, cfg.G, ik, coef, grid, sm, s);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -359,7 +361,7 @@ pid_status stream_launch(pid_handle h, StreamParams sp, const StreamCfg& cfg, bo
     smem = stream_smem_bytes(cfg.vec, cfg.G, sp.depth, sp.stage_floats);
   }
   ProfScope ps(h, PID_KERNEL_STREAM, bytes, 0.0, s);
-  cudaError_t e = launch_stream(sp, cfg.vec, coef, grid, smem, s);
+  cudaError_t e = launch_stream(sp, cfg.vec, cfg.G, ik, coef, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "stream kernel launch");
   return PID_OK;
 }

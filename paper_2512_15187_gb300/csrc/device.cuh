@@ -113,36 +113,40 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return r;
 }
 
-// erfc(a) / 2 for a >= 0 in about 15 FP32 operations, relative error below 3e-7 down to
-// FP32's smallest normal number (a ~ 9.3). Form after the Chebyshev-fitted erfc of
-// Numerical Recipes (2nd ed., Sec. 6.2): with t = 1 / (1 + a/2),
-//   erfc(a) / 2 = t * 2^(Q(t) - log2(e) a^2),
+// sqrt(log2 e): the isovalue scale carries it, so that log2(e) a^2 = a'^2 below.
+constexpr double kSqrtLog2e = 1.2011224087864498;
+
+// erfc(a) / 2 for a >= 0, given a' = sqrt(log2 e) a, in 16 FP32 operations (two of them
+// MUFU). Relative error below 3e-7 down to FP32's smallest normal number (a ~ 9.3); beyond
+// that the result flushes to 0. Form after the Chebyshev-fitted erfc of Numerical Recipes
+// (2nd ed., Sec. 6.2): with t = 1 / (1 + a/2),
+//   erfc(a) / 2 = t * 2^(Q(t) - log2(e) a^2) = t * 2^(Q(t) - a'^2),
 // where Q is a degree-9 polynomial whose coefficients were fitted for this library by
-// csrc/fit_erfc.py (least squares on Chebyshev nodes of t, float64).
-__device__ __forceinline__ float half_erfc_pos(float a) {
-  const float t = rcp_approx(fmaf(0.5f, a, 1.0f));
-  float q = 1.998988667e-01f;
-  q = fmaf(q, t, -9.318530720e-01f);
-  q = fmaf(q, t, 1.549441905e+00f);
-  q = fmaf(q, t, -8.443616250e-01f);
-  q = fmaf(q, t, -2.494008395e-01f);
-  q = fmaf(q, t, 7.348592341e-02f);
-  q = fmaf(q, t, 2.528491611e-02f);
-  q = fmaf(q, t, 5.630220750e-01f);
-  q = fmaf(q, t, 1.440106667e+00f);
-  q = fmaf(q, t, -2.825624756e+00f);
-  const float e = fmaf(-1.4426950408889634f * a, a, q);
-  return t * ex2_approx(e);
+// csrc/fit_erfc.py (float64 near-minimax fit on Chebyshev nodes of t).
+__device__ __forceinline__ float half_erfc_scaled(float as) {
+  const float t = rcp_approx(fmaf(static_cast<float>(0.5 / kSqrtLog2e), as, 1.0f));
+  float q = 1.966346219e-01f;
+  q = fmaf(q, t, -9.140366267e-01f);
+  q = fmaf(q, t, 1.507482838e+00f);
+  q = fmaf(q, t, -7.885746771e-01f);
+  q = fmaf(q, t, -2.953876851e-01f);
+  q = fmaf(q, t, 9.776866458e-02f);
+  q = fmaf(q, t, 1.710338295e-02f);
+  q = fmaf(q, t, 5.647117482e-01f);
+  q = fmaf(q, t, 1.439913215e+00f);
+  q = fmaf(q, t, -2.825615422e+00f);
+  return t * ex2_approx(fmaf(-as, as, q));
 }
 
-// Soft-mask value of one input element (Sec. 3.5). mode is uniform across the launch.
-//   mode 1: u = P(F < q), q ~ Normal(mu, sigma): u = erfc((F - mu) * inv) / 2 with
-//           inv = 1 / (sigma sqrt 2) (negated for the super-level set P(F > q)).
+// Soft-mask value of one input element (Sec. 3.5); used by the standalone map.
+//   mode 1: u = P(F < q), q ~ Normal(mu, sigma): u = erfc(a)/2 with a = (F - mu) / (sigma
+//           sqrt 2), from xs = (F - mu) * inv, inv = +-sqrt(log2 e) / (sigma sqrt 2)
+//           (negated for the super-level set P(F > q)).
 //   mode 2/3: sigma = 0, the indicator of F < t or F > t.
 __device__ __forceinline__ float iso_value(float f, int32_t mode, float mu, float inv, float t) {
   if (mode == 1) {
     const float xs = (f - mu) * inv;
-    const float h = half_erfc_pos(fabsf(xs));
+    const float h = half_erfc_scaled(fabsf(xs));
     return xs >= 0.f ? h : 1.0f - h;
   }
   if (mode == 2) return f < t ? 1.0f : 0.0f;

@@ -6,7 +6,8 @@ coefficients fitted here): for a >= 0 and t = 1 / (1 + P_SCALE a),
     erfc(a) / 2 = t * 2^( Q(t) - log2(e) a^2 ),    Q(t) = log2(e) * g(t) - 1,
 
 where g(t) = ln(erfcx(a)) - ln(t) is smooth on t in (0, 1]. Q is a polynomial fitted in
-float64 by least squares on Chebyshev nodes of t in [T_MIN, 1]; T_MIN corresponds to
+float64 on Chebyshev nodes of t in [T_MIN, 1] by Lawson's iteratively reweighted least
+squares, which converges to the minimax (equioscillating) fit; T_MIN corresponds to
 a = 9.3, beyond which erfc(a)/2 is below FP32's smallest normal number. Prints the
 coefficients (constant term first) and the maximum relative error of the fit.
 
@@ -29,7 +30,13 @@ def fit(deg: int):
     g = np.log(erfcx(a)) - np.log(tt)
     target = g / np.log(2.0) - 1.0
     V = np.vander(tt, deg + 1, increasing=True)
-    c, *_ = np.linalg.lstsq(V, target, rcond=None)
+    wts = np.ones_like(tt)
+    for _ in range(200):  # Lawson: weights grow where the error is largest
+        sw = np.sqrt(wts)
+        c, *_ = np.linalg.lstsq(V * sw[:, None], target * sw, rcond=None)
+        err = np.abs(V @ c - target)
+        wts = wts * err
+        wts /= wts.sum()
     a_chk = np.linspace(0, A_MAX, 200001)
     t_chk = 1.0 / (1.0 + P_SCALE * a_chk)
     q = np.polynomial.polynomial.polyval(t_chk, c)

@@ -106,8 +106,11 @@ struct IsoParams {
 };
 
 // Launchers (stream.cu).
-cudaError_t launch_stream(const StreamParams& p, int vec, bool coef, int grid, size_t smem,
-                          cudaStream_t s);
+// Kernel family of an isovalue mode: 0 none, 1 normal, 2 step (either direction).
+inline int iso_kind(int32_t iso_mode) { return iso_mode == ISO_NONE ? 0 : (iso_mode == ISO_NORMAL ? 1 : 2); }
+
+cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, bool coef, int grid,
+                          size_t smem, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);

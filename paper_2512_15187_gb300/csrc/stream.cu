@@ -1,15 +1,8 @@
-// Streaming kernels of the PID library (sm_103a):
-//   * stream_kernel  — one pass over an ensemble [N][M]: per cell tile the column sum
-//                      s(x) = sum_j c_j u_j(x) is formed on chip, then every member's
-//                      m_i = sum_x w u_i and A_i = sum_x w u_i s are accumulated.
-//                      With c_j = 1/N this is PID-mean (Eq. 15-16): s = u_bar and
-//                      IN_in = A_i / m_i, IN_out = A_i / m_bar. With c_j = 1/(N m_j) it is
-//                      the second pass of the exact O(NM) full PID: A_i = IN_out(i).
-//                      The isovalue map of Sec. 3.5 is optionally applied to each element
-//                      as it is read. Tiles arrive by TMA into a per-group shared-memory ring.
+// Host-side dispatch of the streaming pass (kernel in stream_kernel.cuh, instantiated per
+// tile class in stream_c*.cu) and the two small kernels of the library:
 //   * finalize_kernel — fixed-order FP64 reduction of the per-chunk partials, then the
 //                      inclusion fractions, depths and ranks of Eq. 10 / Eq. 16.
-//   * iso_kernel      — the isovalue map alone (pid_soft_masks).
+//   * iso_kernel      — the isovalue map alone (pid_soft_masks, Sec. 3.5).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -19,323 +12,52 @@
 namespace pidk {
 
 // ---------------------------------------------------------------------------------------
-// Streaming pass
+// Streaming pass: dispatch to the per-class instantiations (stream_c*.cu)
 // ---------------------------------------------------------------------------------------
 
-__device__ __forceinline__ const EnsDesc& stream_desc(const StreamParams& p, int e) {
-  return p.descs ? p.descs[e] : p.one;
+#define PIDK_CLASS(V, M, G)                                                                  \
+  cudaError_t launch_stream_c##V##_##M##_##G(const StreamParams&, int, bool, int, size_t,  \
+                                             cudaStream_t);                                \
+  cudaError_t init_stream_c##V##_##M##_##G(int);
+PIDK_CLASS(4, 8, 1)
+PIDK_CLASS(4, 8, 2)
+PIDK_CLASS(4, 8, 4)
+PIDK_CLASS(4, 8, 8)
+PIDK_CLASS(4, 8, 16)
+PIDK_CLASS(2, 16, 16)
+PIDK_CLASS(1, 32, 16)
+#undef PIDK_CLASS
+
+cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, bool coef, int grid,
+                          size_t smem, cudaStream_t s) {
+  if (vec == 4) {
+    switch (G) {
+      case 1: return launch_stream_c4_8_1(p, iso_kind, coef, grid, smem, s);
+      case 2: return launch_stream_c4_8_2(p, iso_kind, coef, grid, smem, s);
+      case 4: return launch_stream_c4_8_4(p, iso_kind, coef, grid, smem, s);
+      case 8: return launch_stream_c4_8_8(p, iso_kind, coef, grid, smem, s);
+      case 16: return launch_stream_c4_8_16(p, iso_kind, coef, grid, smem, s);
+    }
+  } else if (vec == 2 && G == 16) {
+    return launch_stream_c2_16_16(p, iso_kind, coef, grid, smem, s);
+  } else if (vec == 1 && G == 16) {
+    return launch_stream_c1_32_16(p, iso_kind, coef, grid, smem, s);
+  }
+  return cudaErrorInvalidValue;
 }
 
-// Ensemble owning flat unit u (unit_begin is increasing across the descriptor array).
-__device__ __forceinline__ int stream_find_ens(const StreamParams& p, int u) {
-  if (p.descs == nullptr) return 0;
-  int lo = 0, hi = p.n_ens - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (p.descs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-template <int VEC>
-struct VecT;
-template <> struct VecT<1> { using T = float; };
-template <> struct VecT<2> { using T = float2; };
-template <> struct VecT<4> { using T = float4; };
-
-template <int VEC>
-__device__ __forceinline__ void lds_vec(float (&dst)[VEC], const float* src) {
-  const typename VecT<VEC>::T v = *reinterpret_cast<const typename VecT<VEC>::T*>(src);
-  if constexpr (VEC == 1) {
-    dst[0] = v;
-  } else if constexpr (VEC == 2) {
-    dst[0] = v.x; dst[1] = v.y;
-  } else {
-    dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
-  }
-}
-
-// Layout of the dynamic shared memory (per CTA):
-//   ring  [n_groups][depth][stage_floats]   TMA destinations [rows][SUB*T]; the last SUB*T
-//                                           floats of a stage hold the cell measures
-//   red   [n_groups][2][G*T + T]            partial column sums and their total, double-buffered
-//   bars  [n_groups][depth]                 "stage full" mbarriers
-//   flags [n_groups]                        abort flags (bounded wait ran out)
-template <int VEC, int MPW, bool TMA, bool COEF>
-__global__ void __launch_bounds__(kStreamThreads, 1)
-stream_kernel(const __grid_constant__ StreamParams p) {
-  static_assert(MPW <= 32, "member coefficients are broadcast from one lane each");
-  constexpr int T = 32 * VEC;
-  extern __shared__ __align__(1024) unsigned char smem[];
-
-  const int warp = threadIdx.x >> 5;
-  const int lane = threadIdx.x & 31;
-  const int G = p.G;
-  const int n_groups = kStreamWarps / G;
-  const int grp = warp / G;
-  const int q = warp - grp * G;
-  const int depth = p.depth;
-  const int SF = p.stage_floats;
-  const int SUB = p.sub;        // register tiles of T cells per TMA stage
-  const int TS = SUB * T;       // cells per stage (TMA box width)
-
-  float* ring = reinterpret_cast<float*>(smem);
-  float* red = ring + static_cast<size_t>(n_groups) * depth * SF;
-  const int RB = G * T + T;  // floats per exchange buffer
-  uint64_t* bars = reinterpret_cast<uint64_t*>(red + n_groups * 2 * RB);
-  volatile int* flags = reinterpret_cast<volatile int*>(bars + n_groups * depth);
-
-  float* my_ring = ring + static_cast<size_t>(grp) * depth * SF;
-  float* my_red = red + grp * 2 * RB;
-  uint64_t* my_bars = bars + grp * depth;
-  const bool leader = (q == 0) && (lane == 0);
-
-  if (TMA && leader) {
-    for (int s = 0; s < depth; ++s) mbar_init(&my_bars[s], 1);
-    fence_mbar_init();
-  }
-  if (threadIdx.x < n_groups) flags[threadIdx.x] = 0;
-  __syncthreads();
-
-  const int gid = blockIdx.x * n_groups + grp;
-  const int total_groups = gridDim.x * n_groups;
-
-  // ---- producer cursor (leader lane of the group only) ----
-  int iu = gid, ist = 0, ie = 0, icell0 = 0, in_st = 0;
-  long n_issued = 0;
-  auto set_unit = [&](int u) {
-    ie = stream_find_ens(p, u);
-    const EnsDesc& d = stream_desc(p, ie);
-    const int c = u - d.unit_begin;
-    icell0 = c * d.chunk_cells;
-    const int cells = min(d.chunk_cells, d.M - icell0);
-    in_st = (cells + TS - 1) / TS;
-  };
-  auto issue_next = [&]() {
-    if (iu >= p.total_units) return;
-    const EnsDesc& d = stream_desc(p, ie);
-    const int slot = static_cast<int>(n_issued % depth);
-    float* dst = my_ring + static_cast<size_t>(slot) * SF;
-    const uint32_t bytes =
-        static_cast<uint32_t>(d.n_boxes * d.box_rows * TS + (d.w ? TS : 0)) * 4u;
-    mbar_arrive_expect_tx(&my_bars[slot], bytes);
-    const int x0 = icell0 + ist * TS;
-    for (int b = 0; b < d.n_boxes; ++b)
-      tma_load_2d(dst + static_cast<size_t>(b) * d.box_rows * TS, &d.tmap, &my_bars[slot], x0,
-                  b * d.box_rows);
-    if (d.w) tma_load_1d(dst + SF - TS, &d.tmap_w, &my_bars[slot], x0);
-    ++n_issued;
-    if (++ist == in_st) {
-      ist = 0;
-      iu += total_groups;
-      if (iu < p.total_units) set_unit(iu);
-    }
-  };
-  if (TMA && leader) {
-    if (iu < p.total_units) set_unit(iu);
-    for (int s = 0; s < depth; ++s) issue_next();
-  }
-
-  // ---- consumers: every warp of the group ----
-  long k_cons = 0;
-  long k_sub = 0;   // register tiles processed (parity of the exchange buffer)
-  bool aborted = false;
-  uint32_t bad = 0;
-
-  for (int u = gid; u < p.total_units && !aborted; u += total_groups) {
-    const int e = stream_find_ens(p, u);
-    const EnsDesc& d = stream_desc(p, e);
-    const int N = d.N;
-    const int c = u - d.unit_begin;
-    const int cell0 = c * d.chunk_cells;
-    const int cells = min(d.chunk_cells, d.M - cell0);
-    const int n_st = (cells + TS - 1) / TS;
-    const int iso = d.iso_mode;
-    const float iso_mu = d.iso_mu, iso_inv = d.iso_inv, iso_t = d.iso_t;
-    const bool has_w = d.w != nullptr;
-
-    // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
-    // every member weighs 1/N, applied once per cell (pass 1).
-    float my_cf = 0.f;
-    if constexpr (COEF) {
-      const int i = q + lane * G;
-      if (lane < MPW && i < N) my_cf = d.coef[i];
-    }
-    const float inv_n = 1.0f / static_cast<float>(N);
-    float accM[MPW], accA[MPW];
-#pragma unroll
-    for (int k = 0; k < MPW; ++k) { accM[k] = 0.f; accA[k] = 0.f; }
-
-    for (int st = 0; st < n_st && !aborted; ++st, ++k_cons) {
-      const int slot = static_cast<int>(k_cons % depth);
-      const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
-      const float* sb = my_ring + static_cast<size_t>(slot) * SF;
-      if constexpr (TMA) {
-        if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[grp] = 1;
-      }
-      for (int j = 0; j < SUB; ++j, ++k_sub) {
-        const int xl = cell0 + st * TS + j * T + lane * VEC;  // first cell of this lane
-        float x[MPW][VEC];
-        float wv[VEC];
-
-        if constexpr (TMA) {
-#pragma unroll
-          for (int k = 0; k < MPW; ++k) {
-            const int i = q + k * G;
-            if (i < N) {
-              lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
-            } else {
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) x[k][v] = 0.f;
-            }
-          }
-          if (has_w) {
-            lds_vec<VEC>(wv, sb + SF - TS + j * T + lane * VEC);
-          } else {
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) wv[v] = 1.f;
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < MPW; ++k) {
-            const int i = q + k * G;
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              const int xc = xl + v;
-              x[k][v] = (i < N && xc < d.M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
-                                            : 0.f;
-            }
-          }
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            const int xc = xl + v;
-            wv[v] = has_w ? ((xc < d.M) ? __ldg(d.w + xc) : 0.f) : 1.f;
-          }
-        }
-        // Cells past the end of the ensemble carry no measure.
-#pragma unroll
-        for (int v = 0; v < VEC; ++v)
-          if (xl + v >= d.M) wv[v] = 0.f;
-
-        if (d.validate) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            if (xl + v < d.M) {
-              if (!(wv[v] > 0.f) || !(wv[v] < 3.0e38f)) bad |= ERR_DOMAIN;
-#pragma unroll
-              for (int k = 0; k < MPW; ++k) {
-                if (q + k * G < N) {
-                  const float f = x[k][v];
-                  if (iso != ISO_NONE ? !(fabsf(f) < 3.0e38f) : !(f >= 0.f && f <= 1.f))
-                    bad |= ERR_DOMAIN;
-                }
-              }
-            }
-          }
-        }
-        if (iso != ISO_NONE) {
-#pragma unroll
-          for (int k = 0; k < MPW; ++k)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) x[k][v] = iso_value(x[k][v], iso, iso_mu, iso_inv, iso_t);
-        }
-
-        // Column sum over this warp's members (rows past N are dropped) ...
-        float s[VEC];
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) s[v] = 0.f;
-#pragma unroll
-        for (int k = 0; k < MPW; ++k) {
-          if constexpr (COEF) {
-            const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
-          } else {
-            if (q + k * G < N) {  // iso-mapped padding rows are not zero
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
-            }
-          }
-        }
-        // ... then across the G warps of the group: every warp posts its partial; for G <= 2
-        // each warp adds the others' directly, for larger G warp r first totals the cells
-        // [r T/G, (r+1) T/G) (reduce-scatter) and every warp then reads the totals.
-        float* rb = my_red + static_cast<int>(k_sub & 1) * RB;
-        if (G > 1) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) rb[q * T + lane * VEC + v] = s[v];
-          named_barrier(1 + grp, G * 32);
-        } else {
-          __syncwarp();
-        }
-        if (flags[grp]) { aborted = true; break; }
-        if constexpr (TMA) {
-          if (leader && j == SUB - 1) issue_next();  // every warp has read this slot: refill it
-        }
-        if (G > 2 && p.xchg == 1) {
-          const int cpw = T / G;
-          if (lane < cpw) {
-            const int cc = q * cpw + lane;
-            float acc = 0.f;
-            for (int r = 0; r < G; ++r) acc += rb[r * T + cc];
-            rb[G * T + cc] = acc;
-          }
-          named_barrier(1 + grp, G * 32);
-          lds_vec<VEC>(s, rb + G * T + lane * VEC);
-        } else if (G > 1) {
-          // every warp adds the G partials in warp order (the same order as above)
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) s[v] = 0.f;
-          for (int r = 0; r < G; ++r) {
-            float t[VEC];
-            lds_vec<VEC>(t, rb + r * T + lane * VEC);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] += t[v];
-          }
-        }
-        if constexpr (!COEF) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) s[v] *= inv_n;
-        }
-        // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
-#pragma unroll
-        for (int k = 0; k < MPW; ++k) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            const float t = wv[v] * x[k][v];
-            accM[k] += t;
-            accA[k] = fmaf(t, s[v], accA[k]);
-          }
-        }
-      }
-      if (aborted) break;
-    }
-    if (aborted) break;
-
-    // Chunk done: reduce lanes, write this chunk's partials.
-#pragma unroll
-    for (int k = 0; k < MPW; ++k) {
-      const float m = warp_sum(accM[k]);
-      const float a = warp_sum(accA[k]);
-      const int i = q + k * G;
-      if (lane == 0 && i < N) {
-        d.part[static_cast<size_t>(c) * 2 * N + i] = static_cast<double>(m);
-        d.part[static_cast<size_t>(c) * 2 * N + N + i] = static_cast<double>(a);
-      }
-    }
-  }
-
-  if (bad) atomicOr(p.err, bad);
-  if (aborted && lane == 0 && q == 0) atomicOr(p.err, ERR_TIMEOUT);
-  // On an early exit, let this group's copies in flight land before the CTA retires.
-  if (TMA && leader) {
-    while (k_cons < n_issued) {
-      const int slot = static_cast<int>(k_cons % depth);
-      const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
-      if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) break;
-      ++k_cons;
-    }
-  }
+// Opt every streaming instantiation in to the largest dynamic shared memory once per
+// device (before any launch, so that launches can be captured into graphs).
+cudaError_t stream_kernels_init(int max_smem) {
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = init_stream_c4_8_1(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_8_2(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_8_4(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_8_8(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_8_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c2_16_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c1_32_16(max_smem);
+  return e;
 }
 
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats) {
@@ -344,59 +66,6 @@ size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats) {
   return static_cast<size_t>(n_groups) * depth * stage_floats * 4 +
          static_cast<size_t>(n_groups) * 2 * (G * T + T) * 4 +
          static_cast<size_t>(n_groups) * depth * 8 + static_cast<size_t>(n_groups) * 4 + 64;
-}
-
-template <int VEC, int MPW, bool TMA, bool COEF>
-static cudaError_t launch_one(const StreamParams& p, int grid, size_t smem, cudaStream_t s) {
-  auto k = stream_kernel<VEC, MPW, TMA, COEF>;
-  k<<<grid, kStreamThreads, smem, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <int VEC, int MPW>
-static cudaError_t set_smem_attrs(int bytes) {
-  cudaError_t e;
-  if ((e = cudaFuncSetAttribute(stream_kernel<VEC, MPW, true, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(stream_kernel<VEC, MPW, true, false>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(stream_kernel<VEC, MPW, false, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
-    return e;
-  return cudaFuncSetAttribute(stream_kernel<VEC, MPW, false, false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-// Opt every streaming instantiation in to the largest dynamic shared memory once per
-// device (before any launch, so that launches can be captured into graphs).
-cudaError_t stream_kernels_init(int max_smem) {
-  cudaError_t e;
-  if ((e = set_smem_attrs<4, 8>(max_smem)) != cudaSuccess) return e;
-  if ((e = set_smem_attrs<2, 16>(max_smem)) != cudaSuccess) return e;
-  return set_smem_attrs<1, 32>(max_smem);
-}
-
-template <int VEC, int MPW>
-static cudaError_t launch_stream_t(const StreamParams& p, bool coef, int grid, size_t smem,
-                                   cudaStream_t s) {
-  if (p.use_tma)
-    return coef ? launch_one<VEC, MPW, true, true>(p, grid, smem, s)
-                : launch_one<VEC, MPW, true, false>(p, grid, smem, s);
-  return coef ? launch_one<VEC, MPW, false, true>(p, grid, smem, s)
-              : launch_one<VEC, MPW, false, false>(p, grid, smem, s);
-}
-
-// Tile classes (cells per lane VEC, members per warp MPW): see stream_cfg on the host.
-cudaError_t launch_stream(const StreamParams& p, int vec, bool coef, int grid, size_t smem,
-                          cudaStream_t s) {
-  switch (vec) {
-    case 4: return launch_stream_t<4, 8>(p, coef, grid, smem, s);
-    case 2: return launch_stream_t<2, 16>(p, coef, grid, smem, s);
-    case 1: return launch_stream_t<1, 32>(p, coef, grid, smem, s);
-    default: return cudaErrorInvalidValue;
-  }
 }
 
 // ---------------------------------------------------------------------------------------

@@ -1,0 +1,434 @@
+// The streaming pass of PID-mean / exact full PID (included by the per-class translation
+// units stream_c*.cu, each of which instantiates one tile class).
+//
+// One pass over an ensemble U [N][M]: per tile of T cells the column sum
+// s(x) = sum_j c_j u_j(x) is formed on chip, then every member accumulates
+//   m_i = sum_x w u_i  and  A_i = sum_x w u_i s.
+// With c_j = 1/N, s is the mean contour u_bar (Eq. 15) and IN_in = A_i / m_i,
+// IN_out = A_i / m_bar (Eq. 16). With c_j = 1/(N m_j) the same pass yields IN_out of full
+// PID exactly: A_i = (1/N) sum_j G_ij / m_j (Eq. 10 with the sums of Eq. 14). The
+// isovalue map of Sec. 3.5 can be applied to each element as it is read.
+//
+// Work decomposition: groups of G warps share a TMA-fed shared-memory ring of stages; a
+// stage holds [N rows][sub*T cells] of one chunk; warp q of a group owns members
+// q, q+G, q+2G, ... (MPW of them) and lane l owns VEC consecutive cells of each T-cell
+// register tile. Each group processes whole chunks and writes one partial (m_i, A_i) per
+// member per chunk; a separate finalisation reduces the chunks in a fixed order.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace pidk {
+
+__device__ __forceinline__ const EnsDesc& stream_desc(const StreamParams& p, int e) {
+  return p.descs ? p.descs[e] : p.one;
+}
+
+// Ensemble owning flat unit u (unit_begin is increasing across the descriptor array).
+__device__ __forceinline__ int stream_find_ens(const StreamParams& p, int u) {
+  if (p.descs == nullptr) return 0;
+  int lo = 0, hi = p.n_ens - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.descs[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int VEC> struct VecT;
+template <> struct VecT<1> { using T = float; };
+template <> struct VecT<2> { using T = float2; };
+template <> struct VecT<4> { using T = float4; };
+
+template <int VEC>
+__device__ __forceinline__ void lds_vec(float (&dst)[VEC], const float* src) {
+  const typename VecT<VEC>::T v = *reinterpret_cast<const typename VecT<VEC>::T*>(src);
+  if constexpr (VEC == 1) {
+    dst[0] = v;
+  } else if constexpr (VEC == 2) {
+    dst[0] = v.x; dst[1] = v.y;
+  } else {
+    dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
+  }
+}
+
+// Isovalue map kinds compiled into a kernel.
+enum IsoKind : int { ISOK_NONE = 0, ISOK_NORMAL = 1, ISOK_STEP = 2 };
+
+// Soft-mask value of one element for a compile-time isovalue kind (Sec. 3.5).
+//   NORMAL: u = erfc(xs) / 2, xs = (F - mu) * inv with inv = +-sqrt(log2 e) / (sigma sqrt 2)
+//   STEP:   u = 1[(F - t) * dir < 0], dir = +1 (F < t) or -1 (F > t)
+template <int ISO>
+__device__ __forceinline__ float iso_map(float f, float mu, float inv, float t, float dir) {
+  if constexpr (ISO == ISOK_NORMAL) {
+    const float xs = (f - mu) * inv;
+    const float h = half_erfc_scaled(fabsf(xs));
+    return xs >= 0.f ? h : 1.0f - h;
+  } else if constexpr (ISO == ISOK_STEP) {
+    return (f - t) * dir < 0.f ? 1.0f : 0.0f;
+  } else {
+    return f;
+  }
+}
+
+// Layout of the dynamic shared memory (per CTA):
+//   ring  [n_groups][depth][stage_floats]   TMA destinations [rows][sub*T]; the last sub*T
+//                                           floats of a stage hold the cell measures
+//   red   [n_groups][2][G*T + T]            partial column sums and their total, double-buffered
+//   bars  [n_groups][depth]                 "stage full" mbarriers
+//   flags [n_groups]                        abort flags (bounded wait ran out)
+template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
+__global__ void __launch_bounds__(kStreamThreads, 1)
+stream_kernel(const __grid_constant__ StreamParams p) {
+  static_assert(MPW <= 32, "member coefficients are broadcast from one lane each");
+  constexpr int T = 32 * VEC;
+  constexpr int NG = kStreamWarps / G;
+  constexpr int RB = G * T + T;  // floats per exchange buffer
+  extern __shared__ __align__(1024) unsigned char smem[];
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int grp = warp / G;
+  const int q = warp - grp * G;
+  const int depth = p.depth;
+  const int SF = p.stage_floats;
+  const int SUB = p.sub;
+  const int TS = SUB * T;
+
+  float* ring = reinterpret_cast<float*>(smem);
+  float* red = ring + static_cast<size_t>(NG) * depth * SF;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(red + NG * 2 * RB);
+  volatile int* flags = reinterpret_cast<volatile int*>(bars + NG * depth);
+
+  float* my_ring = ring + static_cast<size_t>(grp) * depth * SF;
+  float* my_red = red + grp * 2 * RB;
+  uint64_t* my_bars = bars + grp * depth;
+  const bool leader = (q == 0) && (lane == 0);
+
+  if (TMA && leader) {
+    for (int s = 0; s < depth; ++s) mbar_init(&my_bars[s], 1);
+    fence_mbar_init();
+  }
+  if (threadIdx.x < NG) flags[threadIdx.x] = 0;
+  __syncthreads();
+
+  const int gid = blockIdx.x * NG + grp;
+  const int total_groups = gridDim.x * NG;
+
+  // ---- producer cursor (leader lane of the group only) ----
+  int iu = gid, ist = 0, ie = 0, icell0 = 0, in_st = 0;
+  long n_issued = 0;
+  auto set_unit = [&](int u) {
+    ie = stream_find_ens(p, u);
+    const EnsDesc& d = stream_desc(p, ie);
+    const int c = u - d.unit_begin;
+    icell0 = c * d.chunk_cells;
+    const int cells = min(d.chunk_cells, d.M - icell0);
+    in_st = (cells + TS - 1) / TS;
+  };
+  auto issue_next = [&]() {
+    if (iu >= p.total_units) return;
+    const EnsDesc& d = stream_desc(p, ie);
+    const int slot = static_cast<int>(n_issued % depth);
+    float* dst = my_ring + static_cast<size_t>(slot) * SF;
+    const uint32_t bytes =
+        static_cast<uint32_t>(d.n_boxes * d.box_rows * TS + (d.w ? TS : 0)) * 4u;
+    mbar_arrive_expect_tx(&my_bars[slot], bytes);
+    const int x0 = icell0 + ist * TS;
+    for (int b = 0; b < d.n_boxes; ++b)
+      tma_load_2d(dst + static_cast<size_t>(b) * d.box_rows * TS, &d.tmap, &my_bars[slot], x0,
+                  b * d.box_rows);
+    if (d.w) tma_load_1d(dst + SF - TS, &d.tmap_w, &my_bars[slot], x0);
+    ++n_issued;
+    if (++ist == in_st) {
+      ist = 0;
+      iu += total_groups;
+      if (iu < p.total_units) set_unit(iu);
+    }
+  };
+  if (TMA && leader) {
+    if (iu < p.total_units) set_unit(iu);
+    for (int s = 0; s < depth; ++s) issue_next();
+  }
+
+  // ---- consumers: every warp of the group ----
+  long k_cons = 0;
+  long k_sub = 0;   // register tiles processed (parity of the exchange buffer)
+  bool aborted = false;
+  uint32_t bad = 0;
+
+  for (int u = gid; u < p.total_units && !aborted; u += total_groups) {
+    const int e = stream_find_ens(p, u);
+    const EnsDesc& d = stream_desc(p, e);
+    const int N = d.N;
+    const int c = u - d.unit_begin;
+    const int cell0 = c * d.chunk_cells;
+    const int cells = min(d.chunk_cells, d.M - cell0);
+    const int n_st = (cells + TS - 1) / TS;
+    const float iso_mu = d.iso_mu, iso_inv = d.iso_inv, iso_t = d.iso_t;
+    // Rows past N read this value, which every isovalue kind maps to exactly 0.
+    const float dir = (d.iso_mode == ISO_STEP_ABOVE) ? -1.f : 1.f;
+    const float pad = ISO == ISOK_NONE ? 0.f
+                      : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
+                                            : dir * __int_as_float(0x7f800000));
+    const bool has_w = d.w != nullptr;
+
+    // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
+    // every member weighs 1/N, applied once per cell (pass 1).
+    float my_cf = 0.f;
+    if constexpr (COEF) {
+      const int i = q + lane * G;
+      if (lane < MPW && i < N) my_cf = d.coef[i];
+    }
+    const float inv_n = 1.0f / static_cast<float>(N);
+    float accM[MPW], accA[MPW];
+#pragma unroll
+    for (int k = 0; k < MPW; ++k) { accM[k] = 0.f; accA[k] = 0.f; }
+
+    for (int st = 0; st < n_st && !aborted; ++st, ++k_cons) {
+      const int slot = static_cast<int>(k_cons % depth);
+      const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
+      const float* sb = my_ring + static_cast<size_t>(slot) * SF;
+      if constexpr (TMA) {
+        if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[grp] = 1;
+      }
+      for (int j = 0; j < SUB; ++j, ++k_sub) {
+        const int x0 = cell0 + st * TS + j * T;     // first cell of this register tile
+        const int xl = x0 + lane * VEC;             // first cell of this lane
+        const bool full = x0 + T <= d.M;            // no cell past the end of the ensemble
+        float x[MPW][VEC];
+        float wv[VEC];
+
+        if constexpr (TMA) {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k) {
+            const int i = q + k * G;
+            if (i < N) {
+              lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
+            } else {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) x[k][v] = pad;
+            }
+          }
+          if (has_w) lds_vec<VEC>(wv, sb + SF - TS + j * T + lane * VEC);
+        } else {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k) {
+            const int i = q + k * G;
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              const int xc = xl + v;
+              x[k][v] = (i < N && xc < d.M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
+                                            : (i < N ? 0.f : pad);
+            }
+          }
+          if (has_w) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) wv[v] = (xl + v < d.M) ? __ldg(d.w + xl + v) : 0.f;
+          }
+        }
+
+        if (d.validate) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            if (xl + v < d.M) {
+              if (has_w && (!(wv[v] > 0.f) || !(wv[v] < 3.0e38f))) bad |= ERR_DOMAIN;
+#pragma unroll
+              for (int k = 0; k < MPW; ++k) {
+                if (q + k * G < N) {
+                  const float f = x[k][v];
+                  if (ISO != ISOK_NONE ? !(fabsf(f) < 3.0e38f) : !(f >= 0.f && f <= 1.f))
+                    bad |= ERR_DOMAIN;
+                }
+              }
+            }
+          }
+        }
+        if constexpr (ISO != ISOK_NONE) {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], iso_mu, iso_inv, iso_t, dir);
+        }
+        if (!full) {  // only the ensemble's last tile: cells past M carry no mass
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            if (xl + v >= d.M) {
+#pragma unroll
+              for (int k = 0; k < MPW; ++k) x[k][v] = 0.f;
+            }
+          }
+        }
+
+        // Column sum over this warp's members (padding rows hold zeros) ...
+        float s[VEC];
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) s[v] = 0.f;
+#pragma unroll
+        for (int k = 0; k < MPW; ++k) {
+          if constexpr (COEF) {
+            const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
+          }
+        }
+        // ... then across the G warps of the group: every warp posts its partial; either
+        // every warp adds the G partials (xchg 0), or warp r first totals the cells
+        // [r T/G, (r+1) T/G) and every warp then reads the totals (xchg 1). Both add the
+        // partials in warp order, so both give the same bits.
+        float* rb = my_red + static_cast<int>(k_sub & 1) * RB;
+        if constexpr (G > 1) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) rb[q * T + lane * VEC + v] = s[v];
+          named_barrier(1 + grp, G * 32);
+        } else {
+          __syncwarp();
+        }
+        if (flags[grp]) { aborted = true; break; }
+        if constexpr (TMA) {
+          if (leader && j == SUB - 1) issue_next();  // every warp has read this slot: refill it
+        }
+        if constexpr (G > 2) {
+          if (p.xchg == 1) {
+            constexpr int cpw = T / G;
+            if (lane < cpw) {
+              const int cc = q * cpw + lane;
+              float acc = 0.f;
+#pragma unroll
+              for (int r = 0; r < G; ++r) acc += rb[r * T + cc];
+              rb[G * T + cc] = acc;
+            }
+            named_barrier(1 + grp, G * 32);
+            lds_vec<VEC>(s, rb + G * T + lane * VEC);
+          } else {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s[v] = 0.f;
+#pragma unroll
+            for (int r = 0; r < G; ++r) {
+              float t[VEC];
+              lds_vec<VEC>(t, rb + r * T + lane * VEC);
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) s[v] += t[v];
+            }
+          }
+        } else if constexpr (G == 2) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) s[v] = 0.f;
+#pragma unroll
+          for (int r = 0; r < G; ++r) {
+            float t[VEC];
+            lds_vec<VEC>(t, rb + r * T + lane * VEC);
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) s[v] += t[v];
+          }
+        }
+        if constexpr (!COEF) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) s[v] *= inv_n;
+        }
+        // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
+        if (has_w) {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              const float t = wv[v] * x[k][v];
+              accM[k] += t;
+              accA[k] = fmaf(t, s[v], accA[k]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k) {
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) {
+              accM[k] += x[k][v];
+              accA[k] = fmaf(x[k][v], s[v], accA[k]);
+            }
+          }
+        }
+      }
+      if (aborted) break;
+    }
+    if (aborted) break;
+
+    // Chunk done: reduce lanes, write this chunk's partials.
+#pragma unroll
+    for (int k = 0; k < MPW; ++k) {
+      const float m = warp_sum(accM[k]);
+      const float a = warp_sum(accA[k]);
+      const int i = q + k * G;
+      if (lane == 0 && i < N) {
+        d.part[static_cast<size_t>(c) * 2 * N + i] = static_cast<double>(m);
+        d.part[static_cast<size_t>(c) * 2 * N + N + i] = static_cast<double>(a);
+      }
+    }
+  }
+
+  if (bad) atomicOr(p.err, bad);
+  if (aborted && lane == 0 && q == 0) atomicOr(p.err, ERR_TIMEOUT);
+  // On an early exit, let this group's copies in flight land before the CTA retires.
+  if (TMA && leader) {
+    while (k_cons < n_issued) {
+      const int slot = static_cast<int>(k_cons % depth);
+      const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
+      if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) break;
+      ++k_cons;
+    }
+  }
+}
+
+template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
+cudaError_t launch_stream_inst(const StreamParams& p, int grid, size_t smem, cudaStream_t s) {
+  stream_kernel<VEC, MPW, G, ISO, COEF, TMA><<<grid, kStreamThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
+cudaError_t init_stream_inst(int smem) {
+  return cudaFuncSetAttribute(stream_kernel<VEC, MPW, G, ISO, COEF, TMA>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+// All instantiations of one tile class (isovalue kind x coefficient pass x TMA).
+template <int VEC, int MPW, int G>
+struct StreamClass {
+  static cudaError_t launch(const StreamParams& p, int iso, bool coef, int grid, size_t smem,
+                            cudaStream_t s) {
+    const bool tma = p.use_tma != 0;
+#define PIDK_STREAM_CASE(ISO)                                                           \
+  if (iso == ISO) {                                                                     \
+    if (tma) return coef ? launch_stream_inst<VEC, MPW, G, ISO, true, true>(p, grid, smem, s)  \
+                         : launch_stream_inst<VEC, MPW, G, ISO, false, true>(p, grid, smem, s); \
+    return coef ? launch_stream_inst<VEC, MPW, G, ISO, true, false>(p, grid, smem, s)          \
+                : launch_stream_inst<VEC, MPW, G, ISO, false, false>(p, grid, smem, s);        \
+  }
+    PIDK_STREAM_CASE(ISOK_NONE)
+    PIDK_STREAM_CASE(ISOK_NORMAL)
+    PIDK_STREAM_CASE(ISOK_STEP)
+#undef PIDK_STREAM_CASE
+    return cudaErrorInvalidValue;
+  }
+  static cudaError_t init(int smem) {
+    cudaError_t e = cudaSuccess;
+#define PIDK_STREAM_INIT(ISO)                                                                \
+  if (e == cudaSuccess) e = init_stream_inst<VEC, MPW, G, ISO, true, true>(smem);           \
+  if (e == cudaSuccess) e = init_stream_inst<VEC, MPW, G, ISO, false, true>(smem);          \
+  if (e == cudaSuccess) e = init_stream_inst<VEC, MPW, G, ISO, true, false>(smem);          \
+  if (e == cudaSuccess) e = init_stream_inst<VEC, MPW, G, ISO, false, false>(smem);
+    PIDK_STREAM_INIT(ISOK_NONE)
+    PIDK_STREAM_INIT(ISOK_NORMAL)
+    PIDK_STREAM_INIT(ISOK_STEP)
+#undef PIDK_STREAM_INIT
+    return e;
+  }
+};
+
+}  // namespace pidk
