@@ -44,6 +44,8 @@ def parse_args():
     ap.add_argument("--ensembles", type=int, default=256, help="ensembles per step (per GPU)")
     ap.add_argument("--mode", default="linear", choices=["linear", "full", "mean"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "split_bf16", "fp8"])
+    ap.add_argument("--other-steps", type=int, default=10,
+                    help="steps timed for each alternative path reported beside the headline")
     ap.add_argument("--e2e-ensembles", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -310,6 +312,32 @@ def main():
     roof["traffic"] = traffic
     gpu_launches = sum(v["launches"] for v in prof.values())
 
+    # ---- the other paths on the same batch (reported beside the headline) ----
+    others = {}
+    for name, mode, prec in (("pid_mean_fp32", "mean", "fp32"),
+                             ("full_pid_exact_fp32", "linear", "fp32"),
+                             ("full_pid_gram_bf16", "full", "bf16"),
+                             ("full_pid_gram_split_bf16", "full", "split_bf16"),
+                             ("full_pid_gram_fp8", "full", "fp8")):
+        if args.other_steps <= 0 or (mode == args.mode and prec == args.precision):
+            continue
+        its = [dict(data=F[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=mode, precision=prec)
+               for e in range(E)]
+        h.autotune(True)
+        h.batch(its, stream=stream)
+        h.batch(its, stream=stream)
+        h.sync()
+        h.autotune(False)
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.other_steps):
+            h.batch(its, stream=stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        t_ms = b0.elapsed_time(b1) / args.other_steps
+        others[name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms}
+
     # ---- end to end: pinned host inputs -> device -> results back, every step ----
     Ee = min(args.e2e_ensembles, E)
     host = torch.empty((Ee, N, M), dtype=torch.float32, pin_memory=True)
@@ -344,7 +372,8 @@ def main():
 
     if rank == 0:
         modes = {"linear": ["isovalue map", "pid_mean_fp32", "full_pid_exact_fp32"],
-                 "full": ["isovalue map", "pid_mean_fp32", f"full_pid_gram_{args.precision}"],
+                 "full": ["isovalue map", "pid_mean_fp32",
+                          f"full_pid_gram_{args.precision} (calibrated to exact row sums)"],
                  "mean": ["isovalue map", "pid_mean_fp32"]}[args.mode]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -360,6 +389,7 @@ def main():
                     "d2h_bytes_per_step": Ee * N * 8, "ensembles_per_step": Ee},
             "gpu_launches": gpu_launches,
             "clocks": clocks,
+            "other_paths": others,
         }
         if cpu_res is not None:
             line["cpu_baseline"] = cpu_baseline_record(cpu_res)

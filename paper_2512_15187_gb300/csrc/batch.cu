@@ -68,6 +68,9 @@ struct Launch {
   int grid_x = 1;
   double bytes = 0, flops = 0;
   GramPlan gp;             // GRAM launches
+  int iso_mode = 0;
+  struct Scale { const float* w; int64_t M; float* out; };
+  std::vector<Scale> scales;  // FP8 operand scales to compute before the Gram launch
 };
 
 struct BatchPlan {
@@ -111,10 +114,10 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   }
   // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
   std::map<ClassKey, std::vector<int>> pass1, pass2;
-  std::map<int, std::vector<int>> gram_cls;
+  std::map<std::pair<int, int>, std::vector<int>> gram_cls;   // (precision x 2 + TMA, iso kind)
   for (int e = 0; e < count; ++e) {
     if (is_gram[e]) {
-      gram_cls[gp[e].n_pad].push_back(e);
+      gram_cls[{gp[e].prec * 2 + (gp[e].tma ? 1 : 0), iso_kind(gp[e].desc.iso_mode)}].push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
       pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik}].push_back(e);
@@ -136,11 +139,16 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   size_t off = bp->desc_bytes;
   std::vector<double*> part(count), sums(count);
   std::vector<float*> coef(count), gpart(count, nullptr);
+  std::vector<float*> scale(count, nullptr);
   for (int e = 0; e < count; ++e) {
-    part[e] = reinterpret_cast<double*>(base + off); off += pl[e].part_bytes;
+    const size_t pb = is_gram[e] ? std::max(pl[e].part_bytes, gp[e].part_bytes) : pl[e].part_bytes;
+    part[e] = reinterpret_cast<double*>(base + off); off += pb;
     sums[e] = reinterpret_cast<double*>(base + off); off += pl[e].sums_bytes;
     coef[e] = reinterpret_cast<float*>(base + off); off += pl[e].coef_bytes;
-    if (is_gram[e]) { gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes; }
+    if (is_gram[e]) {
+      scale[e] = reinterpret_cast<float*>(base + off); off += 256;
+      gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes;
+    }
     pl[e].desc.part = part[e];
   }
   bp->work_bytes = off;
@@ -176,7 +184,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     std::memset(&f, 0, sizeof(f));
     f.part = part[e];
     f.N = static_cast<int32_t>(in[e].N);
-    f.n_chunks = pl[e].desc.n_chunks;
+    f.n_chunks = is_gram[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks;
     f.kind = kind;
     f.sums = sums[e];
     f.coef = coef[e];
@@ -206,15 +214,23 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.gp = gp[kv.second[0]];
     int32_t units = 0;
     for (int e : kv.second) {
-      EnsDesc d = pl[e].desc;
+      EnsDesc d = gp[e].desc;
       d.unit_begin = units;
-      d.coef = reinterpret_cast<const float*>(gpart[e]);  // Gram launches: partial Gram output
+      d.part = part[e];
+      d.gpart = gpart[e];
+      d.op_scale = nullptr;
+      if (gp[e].prec == PID_FP8 && in[e].w) {
+        d.op_scale = scale[e];
+        L.scales.push_back({in[e].w, in[e].M, scale[e]});
+      }
       units += gp[e].n_gchunks;
-      L.bytes += 4.0 * d.N * d.M + (d.w ? 4.0 * d.M : 0.0);
-      const double mult = in[e].precision == PID_SPLIT_BF16 ? 3.0 : 1.0;
-      L.flops += mult * 2.0 * static_cast<double>(d.N) * d.N * d.M;
+      L.bytes += gp[e].bytes;
+      L.flops += gp[e].flops;
+      L.gp.stage_floats = std::max(L.gp.stage_floats, gp[e].stage_floats);
       bp->sdesc.push_back(d);
     }
+    gram_geometry(h, L.gp.prec, L.gp.stage_floats, &L.gp.dF, &L.gp.dO, &L.gp.smem);
+    L.iso_mode = gp[kv.second[0]].desc.iso_mode;
     L.total_units = units;
     bp->launches.push_back(L);
   }
@@ -273,8 +289,12 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       pid_status st = stream_launch(h, sp, L.cfg, L.coef, grid, L.max_n, L.cells, L.bytes, s);
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::GRAM) {
-      pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units, L.bytes,
-                                        L.flops, s);
+      for (const auto& sc : L.scales) {
+        e = launch_fp8_scale(sc.w, sc.M, sc.out, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
+      }
+      pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units,
+                                        L.iso_mode, L.bytes, L.flops, s);
       if (st != PID_OK) return st;
     } else {
       FinParams fp;

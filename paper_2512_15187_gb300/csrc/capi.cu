@@ -442,21 +442,21 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
   if (st != PID_OK) return st;
   const bool gram = in.mode == PID_MODE_FULL && in.precision != PID_FP32;
   const bool linear = in.mode == PID_MODE_FULL_LINEAR || (in.mode == PID_MODE_FULL && !gram);
-  size_t gram_bytes = 0;
   GramPlan gp;
+  size_t part_bytes = pl.part_bytes, gram_bytes = 0;
   if (gram) {
-    st = plan_gram(h, in, &gp);
-    if (st != PID_OK) return st;
-    gram_bytes = gp.gpart_bytes;
+    if ((st = plan_gram(h, in, &gp)) != PID_OK) return st;
+    part_bytes = std::max(part_bytes, gp.part_bytes);
+    gram_bytes = gp.gpart_bytes + 256;  // partial Grams + the FP8 operand scale
   }
-  const size_t need = pl.part_bytes + pl.sums_bytes + pl.coef_bytes + gram_bytes;
+  const size_t need = part_bytes + pl.sums_bytes + pl.coef_bytes + gram_bytes;
   st = ensure_workspace(h, need, s);
   if (st != PID_OK) return st;
   char* ws = static_cast<char*>(h->ws);
   double* part = reinterpret_cast<double*>(ws);
-  double* sums = reinterpret_cast<double*>(ws + pl.part_bytes);
-  float* coef = reinterpret_cast<float*>(ws + pl.part_bytes + pl.sums_bytes);
-  float* gpart = reinterpret_cast<float*>(ws + pl.part_bytes + pl.sums_bytes + pl.coef_bytes);
+  double* sums = reinterpret_cast<double*>(ws + part_bytes);
+  float* coef = reinterpret_cast<float*>(ws + part_bytes + pl.sums_bytes);
+  char* gbase = ws + part_bytes + pl.sums_bytes + pl.coef_bytes;
   pl.desc.part = part;
 
   FinDesc fd;
@@ -475,9 +475,12 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
   fd.mean_depth = out.mean_depth;
 
   if (gram) {
-    st = launch_gram_one(h, in, gp, pl, gpart, s);
+    float* gpart = reinterpret_cast<float*>(gbase + 256);
+    float* scale = reinterpret_cast<float*>(gbase);
+    st = launch_gram_one(h, in, gp, part, gpart, scale, s);
     if (st != PID_OK) return st;
     fd.kind = FIN_GRAM;
+    fd.n_chunks = gp.n_gchunks;
     fd.gpart = gpart;
     fd.n_gchunks = gp.n_gchunks;
     fd.P = out.P;
@@ -550,6 +553,7 @@ pid_status pid_create(pid_handle* out, int device, size_t hbm_budget_bytes) {
   cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
   h->max_smem = max_smem;
   e = stream_kernels_init(max_smem);
+  if (e == cudaSuccess && h->cc >= 100) e = gram_kernels_init(max_smem);
   if (e != cudaSuccess) {
     cudaGetLastError();
     delete h;

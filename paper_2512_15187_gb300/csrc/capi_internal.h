@@ -104,11 +104,18 @@ struct EnsPlan {
 };
 
 struct GramPlan {
+  pidk::EnsDesc desc;      // tensor maps and chunking of the Gram pass
+  int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
+  bool tma = true;         // rows 16-byte aligned: FP32 tiles staged by TMA
+  int TS = 64;             // cells per stage
   int n_gchunks = 0;
-  size_t gpart_bytes = 0;
-  int prec = 0;
-  int n_pad = 0;
   int64_t chunk_cells = 0;
+  int32_t stage_floats = 0;
+  int dF = 2, dO = 2;
+  size_t smem = 0;
+  size_t gpart_bytes = 0;  // [n_gchunks][N][N] float32
+  size_t part_bytes = 0;   // [n_gchunks][2N] float64 (exact PID-mean partials)
+  double bytes = 0, flops = 0;
 };
 
 class DeviceGuard {
@@ -141,12 +148,12 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
 
 // gram.cu
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
-pid_status launch_gram_one(pid_handle h, const EnsInput& in, const GramPlan& gp, EnsPlan& pl,
-                           float* gpart, cudaStream_t s);
-// Gram launch over `count` device descriptors whose `coef` field points at the partial-Gram
-// output of each ensemble.
+void gram_geometry(pid_handle h, int prec, int32_t stage_floats, int* dF, int* dO, size_t* smem);
+pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
+                           float* gpart, float* scale, cudaStream_t s);
+// Gram launch over `count` device descriptors (part / gpart / op_scale already set).
 pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDesc* descs,
-                             int count, int total_units, double bytes, double flops,
+                             int count, int total_units, int iso_mode, double bytes, double flops,
                              cudaStream_t s);
 
 // batch.cu

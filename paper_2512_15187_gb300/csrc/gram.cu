@@ -1,20 +1,128 @@
-// Tensor-core Gram for full PID (placeholder until the tcgen05 kernel lands).
+// Host side of the tensor-core Gram path (kernel in gram_kernel.cu): planning, workspace
+// sizing and launches, for single calls and for batches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+
 #include "capi_internal.h"
+#include "internal.h"
+
+using namespace pidk;
 
 namespace pidh {
 
-pid_status plan_gram(pid_handle h, const EnsInput&, GramPlan*) {
-  return fail(h, PID_ERR_UNSUPPORTED, "tensor-core Gram not built yet; use PID_FP32");
+static int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
+  *gp = GramPlan{};
+  if (in.N > kGramMaxN)
+    return fail(h, PID_ERR_UNSUPPORTED,
+                "the tensor-core Gram takes N <= 128 in this build; use PID_MODE_FULL_LINEAR");
+  const uintptr_t a = reinterpret_cast<uintptr_t>(in.data);
+  gp->tma = in.ld % 4 == 0 && a % 16 == 0 && (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
+  gp->prec = in.precision;
+  gp->TS = 128;
+  int64_t chunk = rup((in.M + h->sms - 1) / h->sms, gp->TS);
+  chunk = std::max<int64_t>(chunk, gp->TS);
+  gp->chunk_cells = chunk;
+  gp->n_gchunks = static_cast<int>((in.M + chunk - 1) / chunk);
+
+  EnsDesc& d = gp->desc;
+  std::memset(&d, 0, sizeof(d));
+  d.data = in.data;
+  d.w = in.w;
+  d.ld = in.ld;
+  d.N = static_cast<int32_t>(in.N);
+  d.M = static_cast<int32_t>(in.M);
+  d.chunk_cells = static_cast<int32_t>(chunk);
+  d.n_chunks = gp->n_gchunks;
+  d.n_boxes = 1;
+  d.box_rows = static_cast<int32_t>(in.N);
+  iso_fill(in.is_field ? &in.iso : nullptr, &d.iso_mode, &d.iso_mu, &d.iso_inv, &d.iso_t);
+  d.validate = in.validate;
+  if (gp->tma &&
+      (!encode_2d(&d.tmap, in.data, static_cast<uint64_t>(in.M), static_cast<uint64_t>(in.N),
+                  static_cast<uint64_t>(in.ld) * 4, static_cast<uint32_t>(gp->TS),
+                  static_cast<uint32_t>(in.N)) ||
+       (in.w && !encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), static_cast<uint32_t>(gp->TS)))))
+    return fail(h, PID_ERR_CUDA, "tensor map encoding failed");
+
+  // Without TMA the FP32 ring is unused: keep one minimal stage.
+  gp->stage_floats = gp->tma ? static_cast<int32_t>(rup(in.N * gp->TS + gp->TS, 32)) : 32;
+  gp->gpart_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * in.N * in.N * 4, 256);
+  gp->part_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * 2 * in.N * 8, 256);
+  gram_geometry(h, gp->prec, gp->stage_floats, &gp->dF, &gp->dO, &gp->smem);
+  gp->flops = (in.precision == PID_SPLIT_BF16 ? 3.0 : 1.0) * 2.0 * static_cast<double>(in.N) *
+              in.N * in.M;
+  gp->bytes = 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0);
+  return PID_OK;
 }
 
-pid_status launch_gram_one(pid_handle h, const EnsInput&, const GramPlan&, EnsPlan&, float*,
-                           cudaStream_t) {
-  return fail(h, PID_ERR_UNSUPPORTED, "tensor-core Gram not built yet");
+// Ring depths that fit the shared memory: at least two FP32 stages, then as many operand
+// stages as fit (at most four), then the FP32 ring deepened to at most six stages.
+void gram_geometry(pid_handle h, int prec, int32_t stage_floats, int* dF, int* dO, size_t* smem) {
+  const size_t cap = static_cast<size_t>(h->max_smem > 0 ? h->max_smem : 232448);
+  int f = 2, o = 4;
+  while (o > 1 && gram_smem_bytes(prec, f, o, stage_floats) > cap) --o;
+  while (f > 1 && gram_smem_bytes(prec, f, o, stage_floats) > cap) --f;
+  while (f < 6 && gram_smem_bytes(prec, f + 1, o, stage_floats) <= cap) ++f;
+  *dF = f;
+  *dO = o;
+  *smem = gram_smem_bytes(prec, f, o, stage_floats);
 }
 
-pid_status launch_gram_batch(pid_handle h, const GramPlan&, const pidk::EnsDesc*, int, int, double,
-                             double, cudaStream_t) {
-  return fail(h, PID_ERR_UNSUPPORTED, "tensor-core Gram not built yet");
+static pid_status gram_launch(pid_handle h, const GramParams& gpar, int prec, int iso_mode,
+                              int grid, size_t smem, double bytes, double flops, cudaStream_t s) {
+  ProfScope ps(h, PID_KERNEL_GRAM, bytes, flops, s);
+  cudaError_t e = launch_gram(gpar, prec, iso_kind(iso_mode), grid, smem, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "Gram kernel launch");
+  return PID_OK;
+}
+
+pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
+                           float* gpart, float* scale, cudaStream_t s) {
+  GramParams gpar;
+  std::memset(&gpar, 0, sizeof(gpar));
+  gpar.one = gp.desc;
+  gpar.one.part = part;
+  gpar.one.gpart = gpart;
+  gpar.one.op_scale = nullptr;
+  if (gp.prec == PID_FP8 && in.w) {
+    cudaError_t e = launch_fp8_scale(in.w, in.M, scale, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
+    gpar.one.op_scale = scale;
+  }
+  gpar.n_ens = 1;
+  gpar.total_units = gp.n_gchunks;
+  gpar.dF = gp.dF;
+  gpar.dO = gp.dO;
+  gpar.stage_floats = gp.stage_floats;
+  gpar.TS = gp.TS;
+  gpar.xchg = 1;
+  gpar.use_tma = gp.tma ? 1 : 0;
+  gpar.err = h->err_word;
+  const int grid = std::max(1, std::min(h->sms, gp.n_gchunks));
+  return gram_launch(h, gpar, gp.prec, gp.desc.iso_mode, grid, gp.smem, gp.bytes, gp.flops, s);
+}
+
+pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* descs, int count,
+                             int total_units, int iso_mode, double bytes, double flops,
+                             cudaStream_t s) {
+  GramParams gpar;
+  std::memset(&gpar, 0, sizeof(gpar));
+  gpar.descs = descs;
+  gpar.n_ens = count;
+  gpar.total_units = total_units;
+  gpar.dF = gp.dF;
+  gpar.dO = gp.dO;
+  gpar.stage_floats = gp.stage_floats;
+  gpar.TS = gp.TS;
+  gpar.xchg = 1;
+  gpar.use_tma = gp.tma ? 1 : 0;
+  gpar.err = h->err_word;
+  const int grid = std::max(1, std::min(h->sms, total_units));
+  return gram_launch(h, gpar, gp.prec, iso_mode, grid, gp.smem, bytes, flops, s);
 }
 
 }  // namespace pidh

@@ -43,7 +43,9 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   int32_t iso_mode;     // IsoMode
   float iso_mu, iso_inv, iso_t;
   int32_t validate;
-  int32_t pad0, pad1;
+  int32_t pad0;
+  float* gpart;         // Gram launches: [n_chunks][N][N] float32 partial Gram (G_ij at j*N + i)
+  const float* op_scale;  // Gram FP8: device scalar multiplying every operand (nullptr = 256)
 };
 
 struct StreamParams {
@@ -58,6 +60,28 @@ struct StreamParams {
   int32_t sub;             // register tiles of T cells per TMA stage
   int32_t xchg;            // column-sum exchange: 0 direct, 1 reduce-scatter (G > 2)
   uint32_t* err;           // device error word
+};
+
+// Tensor-core Gram pass: 16 warps convert tiles (the streaming arithmetic plus operand
+// conversion); thread 0 also issues the tensor-core work and warps 0-3 drain it.
+constexpr int kGramConvWarps = 16;
+constexpr int kGramEpiWarps = 4;      // converter warps 0..3, one per TMEM lane quarter
+constexpr int kGramThreads = kGramConvWarps * 32;
+constexpr int kGramMaxN = 128;        // one M = 128 tensor-core tile
+constexpr int kOpPlaneBytes = 128 * 128;  // 128 rows x 128-byte swizzled K-block
+
+struct GramParams {
+  EnsDesc one;
+  const EnsDesc* descs;
+  int32_t n_ens;
+  int32_t total_units;
+  int32_t dF;            // FP32 stages in the TMA ring
+  int32_t dO;            // operand stages
+  int32_t stage_floats;  // floats per FP32 stage (rows x TS + TS)
+  int32_t TS;            // cells per stage: 64 (16-bit operands) or 128 (FP8)
+  int32_t xchg;
+  int32_t use_tma;       // 0: converters read FP32 directly (rows not 16-byte aligned)
+  uint32_t* err;
 };
 
 // Finalisation of one ensemble: fixed-order FP64 reduction of the chunk partials, then
@@ -114,6 +138,11 @@ cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, b
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
+size_t gram_smem_bytes(int prec, int dF, int dO, int stage_floats);
+cudaError_t launch_gram(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
+                        cudaStream_t s);
+cudaError_t gram_kernels_init(int max_smem);
+cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s);
 cudaError_t stream_kernels_init(int max_smem);
 
 }  // namespace pidk

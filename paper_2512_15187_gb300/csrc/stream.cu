@@ -65,7 +65,7 @@ size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats) {
   const int n_groups = kStreamWarps / G;
   return static_cast<size_t>(n_groups) * depth * stage_floats * 4 +
          static_cast<size_t>(n_groups) * 2 * (G * T + T) * 4 +
-         static_cast<size_t>(n_groups) * depth * 8 + static_cast<size_t>(n_groups) * 4 + 64;
+         static_cast<size_t>(n_groups) * depth * 8 + static_cast<size_t>(n_groups) * 8 + 64;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   __shared__ double scratch[32][33];
   __shared__ double sdepth[1024];
   __shared__ double sred[1024];
+  __shared__ double sd[kGramMaxN], sdn[kGramMaxN];   // Gram calibration scales
   __shared__ int is_last;
 
   const int N = d.N;
@@ -157,18 +158,8 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     } else if (d.kind == FIN_LIN2) {
       in_in = in_in_exact;
       in_out = __ldcg(S + 3 * N + i);
-    } else {  // FIN_GRAM: G[i + j N] = sum_x w u_i u_j
-      const double* Gm = S + 4 * N;
-      double si = 0.0, so = 0.0;
-      for (int j = 0; j < N; ++j) {
-        const double gij = __ldcg(Gm + i + static_cast<size_t>(j) * N);
-        const double mj = __ldcg(S + j);
-        si += gij;
-        if (mj > 0.0) so += __ldcg(Gm + j + static_cast<size_t>(i) * N) / mj;
-      }
-      in_in = m > 0.0 ? si / (m * N) : 0.0;
-      in_out = so / N;
-      err = fabs(in_in - in_in_exact);
+    } else {  // FIN_GRAM: see the calibration below
+      in_in = in_in_exact;
     }
     depth = fmin(in_in, in_out);
   }
@@ -176,6 +167,51 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     __syncthreads();
     if (threadIdx.x == 0) *d.ticket = 0u;
     return;
+  }
+  if (d.kind == FIN_GRAM) {
+    // The tensor-core Gram G' (G'[i + j N] ~ G_ij = sum_x w u_i u_j) carries each member's
+    // rounding bias in its row and column. Its row sums are known exactly from the same pass:
+    // sum_j G_ij = N A_i (the recall identity, Eq. 17). Calibrate by a symmetric diagonal
+    // scaling C_ij = d_i d_j (G'_ij + G'_ji) / 2 with d_i sum_j C... = N A_i (symmetric
+    // Sinkhorn iteration, FP64), then P_ij = C_ij / m_i, IN_in = mean_j P_ij (= A_i / m_i),
+    // IN_out = mean_j P_ji. err_est reports the uncalibrated |mean_j G'_ij / m_i - A_i / m_i|.
+    const double* Gm = S + 4 * N;
+    const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
+    if (i < N) {
+      double raw = 0.0;
+      for (int j = 0; j < N; ++j) raw += __ldcg(Gm + i + static_cast<size_t>(j) * N);
+      err = m > 0.0 ? fabs(raw / (m * N) - A / m) : 0.0;
+      sd[i] = (A > 0.0 && raw > 0.0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int it = 0; it < 24; ++it) {
+      for (int r = wi; r < N; r += kFinThreads / 32) {
+        double acc = 0.0;
+        for (int j = ln; j < N; j += 32)
+          acc += 0.5 * (__ldcg(Gm + r + static_cast<size_t>(j) * N) +
+                        __ldcg(Gm + j + static_cast<size_t>(r) * N)) * sd[j];
+        acc = warp_sum(acc);
+        if (ln == 0) {
+          const double target = static_cast<double>(N) * __ldcg(S + N + r);
+          sdn[r] = (sd[r] > 0.0 && acc > 0.0) ? sqrt(sd[r] * target / acc) : 0.0;
+        }
+      }
+      __syncthreads();
+      if (i < N) sd[i] = sdn[i];
+      __syncthreads();
+    }
+    if (i < N) {
+      double so = 0.0;
+      for (int j = 0; j < N; ++j) {
+        const double mj = __ldcg(S + j);
+        const double cji = sd[j] * sd[i] * 0.5 *
+                           (__ldcg(Gm + j + static_cast<size_t>(i) * N) +
+                            __ldcg(Gm + i + static_cast<size_t>(j) * N));
+        if (mj > 0.0) so += cji / mj;
+      }
+      in_out = so / N;
+      depth = fmin(in_in, in_out);
+    }
   }
   sdepth[i] = (i < N) ? depth : 0.0;
   sred[i] = err;
@@ -202,9 +238,12 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     if (d.P) {
       const double* Gm = S + 4 * N;
       for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
-        const int r = k / N, cc = k - r * N;   // P[r][cc] = G_{r,cc} / m_r
+        const int r = k / N, cc = k - r * N;   // P[r][cc] = C_{r,cc} / m_r
         const double mr = __ldcg(S + r);
-        d.P[k] = mr > 0.0 ? __ldcg(Gm + r + static_cast<size_t>(cc) * N) / mr : 0.0;
+        const double c = sd[r] * sd[cc] * 0.5 *
+                         (__ldcg(Gm + r + static_cast<size_t>(cc) * N) +
+                          __ldcg(Gm + cc + static_cast<size_t>(r) * N));
+        d.P[k] = mr > 0.0 ? c / mr : 0.0;
       }
     }
   }

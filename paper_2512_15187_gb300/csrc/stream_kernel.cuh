@@ -80,7 +80,8 @@ __device__ __forceinline__ float iso_map(float f, float mu, float inv, float t, 
 //                                           floats of a stage hold the cell measures
 //   red   [n_groups][2][G*T + T]            partial column sums and their total, double-buffered
 //   bars  [n_groups][depth]                 "stage full" mbarriers
-//   flags [n_groups]                        abort flags (bounded wait ran out)
+//   flags [n_groups][2]                     abort flags (bounded wait ran out), one per
+//                                           exchange-buffer parity (see below)
 template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 stream_kernel(const __grid_constant__ StreamParams p) {
@@ -113,7 +114,10 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     for (int s = 0; s < depth; ++s) mbar_init(&my_bars[s], 1);
     fence_mbar_init();
   }
-  if (threadIdx.x < NG) flags[threadIdx.x] = 0;
+  // A warp that gives up on a wait sets the flag of the register tile whose group barrier
+  // it arrives at next; all warps of the group read that flag after that barrier, so they
+  // leave together (the other parity belongs to the neighbouring barrier).
+  if (threadIdx.x < 2 * NG) flags[threadIdx.x] = 0;
   __syncthreads();
 
   const int gid = blockIdx.x * NG + grp;
@@ -165,9 +169,11 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     const int e = stream_find_ens(p, u);
     const EnsDesc& d = stream_desc(p, e);
     const int N = d.N;
+    const int M = d.M;                       // descriptor fields kept in registers: the
+    const bool validate = d.validate != 0;   // asm barriers below clobber memory
     const int c = u - d.unit_begin;
     const int cell0 = c * d.chunk_cells;
-    const int cells = min(d.chunk_cells, d.M - cell0);
+    const int cells = min(d.chunk_cells, M - cell0);
     const int n_st = (cells + TS - 1) / TS;
     const float iso_mu = d.iso_mu, iso_inv = d.iso_inv, iso_t = d.iso_t;
     // Rows past N read this value, which every isovalue kind maps to exactly 0.
@@ -176,6 +182,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
                       : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
                                             : dir * __int_as_float(0x7f800000));
     const bool has_w = d.w != nullptr;
+    // Rows q, q+G, ... below N are this warp's members; rows past N are skipped with
+    // warp-uniform guards (their registers hold the padding value and are never used).
+    const int kmax = q < N ? (N - q + G - 1) / G : 0;
 
     // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
     // every member weighs 1/N, applied once per cell (pass 1).
@@ -194,12 +203,12 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
       const float* sb = my_ring + static_cast<size_t>(slot) * SF;
       if constexpr (TMA) {
-        if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[grp] = 1;
+        if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[2 * grp + (k_sub & 1)] = 1;
       }
       for (int j = 0; j < SUB; ++j, ++k_sub) {
         const int x0 = cell0 + st * TS + j * T;     // first cell of this register tile
         const int xl = x0 + lane * VEC;             // first cell of this lane
-        const bool full = x0 + T <= d.M;            // no cell past the end of the ensemble
+        const bool full = x0 + T <= M;              // no cell past the end of the ensemble
         float x[MPW][VEC];
         float wv[VEC];
 
@@ -222,20 +231,20 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) {
               const int xc = xl + v;
-              x[k][v] = (i < N && xc < d.M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
-                                            : (i < N ? 0.f : pad);
+              x[k][v] = (i < N && xc < M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
+                                          : (i < N ? 0.f : pad);
             }
           }
           if (has_w) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) wv[v] = (xl + v < d.M) ? __ldg(d.w + xl + v) : 0.f;
+            for (int v = 0; v < VEC; ++v) wv[v] = (xl + v < M) ? __ldg(d.w + xl + v) : 0.f;
           }
         }
 
-        if (d.validate) {
+        if (validate) {
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
-            if (xl + v < d.M) {
+            if (xl + v < M) {
               if (has_w && (!(wv[v] > 0.f) || !(wv[v] < 3.0e38f))) bad |= ERR_DOMAIN;
 #pragma unroll
               for (int k = 0; k < MPW; ++k) {
@@ -251,13 +260,15 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         if constexpr (ISO != ISOK_NONE) {
 #pragma unroll
           for (int k = 0; k < MPW; ++k)
+            if (k < kmax) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], iso_mu, iso_inv, iso_t, dir);
+              for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], iso_mu, iso_inv, iso_t, dir);
+            }
         }
         if (!full) {  // only the ensemble's last tile: cells past M carry no mass
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
-            if (xl + v >= d.M) {
+            if (xl + v >= M) {
 #pragma unroll
               for (int k = 0; k < MPW; ++k) x[k][v] = 0.f;
             }
@@ -270,13 +281,15 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         for (int v = 0; v < VEC; ++v) s[v] = 0.f;
 #pragma unroll
         for (int k = 0; k < MPW; ++k) {
-          if constexpr (COEF) {
-            const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
+          if (k < kmax) {
+            if constexpr (COEF) {
+              const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
-          } else {
+              for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
+            } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
+              for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
+            }
           }
         }
         // ... then across the G warps of the group: every warp posts its partial; either
@@ -291,7 +304,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         } else {
           __syncwarp();
         }
-        if (flags[grp]) { aborted = true; break; }
+        if (flags[2 * grp + (k_sub & 1)]) { aborted = true; break; }
         if constexpr (TMA) {
           if (leader && j == SUB - 1) issue_next();  // every warp has read this slot: refill it
         }
@@ -337,20 +350,24 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         if (has_w) {
 #pragma unroll
           for (int k = 0; k < MPW; ++k) {
+            if (k < kmax) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              const float t = wv[v] * x[k][v];
-              accM[k] += t;
-              accA[k] = fmaf(t, s[v], accA[k]);
+              for (int v = 0; v < VEC; ++v) {
+                const float t = wv[v] * x[k][v];
+                accM[k] += t;
+                accA[k] = fmaf(t, s[v], accA[k]);
+              }
             }
           }
         } else {
 #pragma unroll
           for (int k = 0; k < MPW; ++k) {
+            if (k < kmax) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              accM[k] += x[k][v];
-              accA[k] = fmaf(x[k][v], s[v], accA[k]);
+              for (int v = 0; v < VEC; ++v) {
+                accM[k] += x[k][v];
+                accA[k] = fmaf(x[k][v], s[v], accA[k]);
+              }
             }
           }
         }

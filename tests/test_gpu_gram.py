@@ -1,0 +1,147 @@
+"""GPU parity of full PID on tensor cores (BF16, split BF16, E4M3 Gram) vs the FP64 oracle.
+
+Bar: depths, IN_in, IN_out and the inclusion matrix within 1e-3 absolute, the same ranking
+outside ties; split BF16 much tighter; binary masks exact (integer counts in FP32).
+"""
+import numpy as np
+import pytest
+
+from oracle import pid_oracle as O
+from paper_2512_15187_gb300 import synth
+from tests.helpers import (FP32_TOL, GRAM_TOL, assert_close, assert_rank_agrees_outside_ties,
+                           assert_rank_valid, to_np)
+
+pytestmark = pytest.mark.gpu
+PRECS = ["bf16", "split_bf16", "fp8"]
+FP8_SMALL_M_TOL = 1e-2   # E4M3 depths below a few thousand cells
+FP8_P_TOL = 5e-3         # E4M3 single-pair inclusions P_ij (no averaging over members)
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2512_15187_gb300 import binding, build
+    build.build()
+    h = binding.Handle(0)
+    yield h
+    h.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _check(o, U, w, tol, what, p_tol=None):
+    a, b, d = O.pid(U, w)
+    # IN_in comes from the exact FP32 arithmetic of the same pass (Eq. 17)
+    assert_close(to_np(o["in_in"]), a, FP32_TOL, what + " in_in")
+    assert_close(to_np(o["in_out"]), b, tol, what + " in_out")
+    assert_close(to_np(o["depth"]), d, tol, what + " depth")
+    assert_rank_valid(to_np(o["rank"]), to_np(o["depth"]))
+    assert_rank_agrees_outside_ties(to_np(o["rank"]), d, tol)
+    if "P" in o:
+        assert_close(to_np(o["P"]), O.inclusion_matrix(U, w), p_tol or tol, what + " P")
+        # err_est: the raw Gram's |mean_j G'_ij / m_i - A_i / m_i| before calibration
+        err = float(to_np(o["err_est"])[0])
+        assert 0.0 <= err <= 10 * tol
+        # the calibrated inclusion matrix reproduces the exact IN_in row means
+        assert_close(to_np(o["P"]).mean(axis=1), a, 1e-6, what + " P row means")
+
+
+def test_gram_first_small_case(H):
+    U = synth.ellipses_2d(N=20, H=64, W=64)
+    o = H.full(_dev(U), mode="full", precision="bf16", want_P=True)
+    H.sync()
+    _check(o, U, None, GRAM_TOL, "bf16 N=20")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("N,M", [(1, 64), (2, 1000), (16, 4097), (33, 3000), (64, 65543),
+                                 (100, 5000), (128, 20000)])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_gram_parity(H, prec, N, M, weighted):
+    U = synth.random_soft(N, M, seed=N * 131 + M, binary_frac=0.2)
+    w = np.random.default_rng(M).uniform(0.2, 5, M).astype(np.float32) if weighted else None
+    o = H.full(_dev(U), None if w is None else _dev(w), mode="full", precision=prec, want_P=True)
+    H.sync()
+    # E4M3 keeps 3 mantissa bits: per-element noise of a few percent that averages down as
+    # 1/sqrt(M); the 1e-3 bar holds from a few thousand cells on.
+    tol = GRAM_TOL if (prec != "fp8" or M >= 4096) else FP8_SMALL_M_TOL
+    p_tol = max(tol, FP8_P_TOL) if prec == "fp8" else tol
+    _check(o, U, w, tol, f"{prec} N={N} M={M} w={weighted}", p_tol)
+
+
+def test_split_bf16_is_much_tighter(H):
+    U = synth.radial_disk(N=64, M=1 << 16)[0]
+    ref = O.pid(U)
+    errs = {}
+    for prec in PRECS:
+        o = H.full(_dev(U), mode="full", precision=prec)
+        H.sync()
+        errs[prec] = float(np.max(np.abs(to_np(o["depth"]) - ref[2])))
+    assert errs["split_bf16"] <= 2e-5, errs
+    assert errs["bf16"] <= GRAM_TOL and errs["fp8"] <= GRAM_TOL, errs
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gram_binary_masks_are_exact(H, prec):
+    # {0,1} operands are exact in BF16 and E4M3 and the Gram sums are integer counts; what
+    # remains is the FP32 rounding of the exact mean-contour arithmetic (about 1e-8)
+    Ub = synth.ellipses_2d(N=20, binary=True)
+    sets = [set(np.nonzero(r)[0].tolist()) for r in Ub]
+    o = H.full(_dev(Ub), mode="full", precision=prec, want_P=True)
+    H.sync()
+    for k, r in zip(("in_in", "in_out", "depth"), O.eid(sets)):
+        assert_close(to_np(o[k]), r, 1e-7, f"{prec} binary {k}")
+    assert float(to_np(o["err_est"])[0]) <= 1e-7
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("superlevel", [False, True])
+def test_gram_from_fields(H, prec, superlevel):
+    F = synth.rbf_fields_2d(N=64, H=128, W=96, n_rbf=8)
+    F = (F - np.median(F, axis=1, keepdims=True)).astype(np.float32)
+    w = np.random.default_rng(3).uniform(0.5, 2, F.shape[1]).astype(np.float32)
+    o = H.from_fields(_dev(F), 0.01, 0.05, superlevel=superlevel, w=_dev(w), mode="full",
+                      precision=prec)
+    H.sync()
+    _check(o, O.iso_soft_mask(F, 0.01, 0.05, superlevel), w, GRAM_TOL, f"fields {prec}")
+
+
+def test_gram_in_batch_with_exact_mean(H):
+    rng = np.random.default_rng(5)
+    items, refs = [], []
+    for k, prec in enumerate(["bf16", "split_bf16", "fp8", "bf16", "fp8"]):
+        N = int(rng.integers(3, 129))
+        M = int(rng.integers(500, 20000))
+        U = synth.random_soft(N, M, seed=900 + k)
+        w = rng.uniform(0.5, 3, M).astype(np.float32) if k % 2 else None
+        items.append(dict(data=_dev(U), w=None if w is None else _dev(w), mode="full",
+                          precision=prec, want_P=True))
+        refs.append((U, w, prec))
+    outs = H.batch(items)
+    H.sync()
+    for o, (U, w, prec) in zip(outs, refs):
+        _check(o, U, w, GRAM_TOL, f"batch {prec}", FP8_P_TOL if prec == "fp8" else None)
+        assert_close(to_np(o["mean_depth"]), O.pid_mean(U, w)[2], FP32_TOL, "exact PID-mean by-product")
+
+
+def test_gram_rejects_too_many_members(H):
+    import torch
+    from paper_2512_15187_gb300 import binding as B
+    U = torch.rand((129, 256), device="cuda")
+    with pytest.raises(B.PidError) as e:
+        H.full(U, mode="full", precision="bf16")
+    assert e.value.status == B.PID_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_gram_unaligned_rows_read_directly(H, prec):
+    import torch
+    N, M = 24, 9001
+    U = synth.random_soft(N, M, seed=11)
+    big = torch.zeros((N, M + 3), dtype=torch.float32, device="cuda")
+    big[:, :M] = _dev(U)
+    o = H.full(big[:, :M], mode="full", precision=prec, want_P=True)   # ld = M + 3
+    H.sync()
+    _check(o, U, None, GRAM_TOL, f"{prec} ld=M+3", FP8_P_TOL if prec == "fp8" else None)
