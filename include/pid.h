@@ -218,6 +218,65 @@ typedef struct pid_ensemble {
 pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
 
 /*
+ * Serving. A server keeps ensembles resident on one GPU and answers depth requests that
+ * arrive from any number of host threads. A scheduler thread forms batched steps from the
+ * requests waiting at that moment and launches each step as one pid_batch on one of
+ * `max_inflight` slots (each with its own stream and workspace) as soon as a slot is free,
+ * so requests that arrive while others are on the GPU join the next step and steps overlap
+ * on the device (continuous batching). A request's results do not depend on the requests
+ * it is batched with (pid_batch results are bitwise identical to single calls).
+ * Admission: ensembles are registered against an HBM budget; submissions beyond
+ * max_queue are refused with PID_ERR_BUSY.
+ */
+typedef struct pid_serve_cfg {
+  int32_t device;
+  int32_t max_inflight;            /* concurrent steps (slots), >= 1 */
+  int32_t max_batch;               /* requests per step, >= 1 */
+  int32_t max_queue;               /* waiting requests before PID_ERR_BUSY, >= 1 */
+  size_t hbm_budget_bytes;         /* resident ensembles + slot workspaces (0 = no cap) */
+  size_t workspace_reserve_bytes;  /* per slot, counted against the budget */
+  int64_t max_step_member_cells;   /* cap on sum N*M per step (0 = none) */
+} pid_serve_cfg;
+
+typedef struct pid_serve_stats {
+  int64_t submitted, completed, failed, steps;
+  double mean_batch;               /* requests per step */
+  double p50_ms, p99_ms, max_ms;   /* submit -> results on the host */
+  double requests_per_s;           /* completed / (last completion - first submit) */
+  double member_cells_per_s;
+  size_t resident_bytes;
+} pid_serve_stats;
+
+typedef struct pid_server_s* pid_server;
+
+pid_status pid_serve_start(pid_server* out, const pid_serve_cfg* cfg);
+/* Stop the scheduler: waiting requests complete with PID_ERR_CANCELLED, steps in flight
+ * finish. Frees everything the server owns. */
+pid_status pid_serve_stop(pid_server s);
+/* Register an ensemble [N][ld] float32 (soft masks, or fields with `iso`), cell measures w
+ * [M] (or NULL). copy = 1: data (and w) are HOST pointers copied into device memory the
+ * server owns (counted against the budget; PID_ERR_OOM if it does not fit); copy = 0: DEVICE
+ * pointers the caller keeps alive until pid_serve_unregister. */
+pid_status pid_serve_register(pid_server s, const float* data, int64_t N, int64_t M, int64_t ld,
+                              const float* w, int32_t is_field, const pid_iso* iso, int32_t copy,
+                              int64_t* ensemble_id);
+/* Replace the data of a server-owned ensemble (a new time step) from host memory; waits for
+ * steps in flight that read it. */
+pid_status pid_serve_update(pid_server s, int64_t ensemble_id, const float* data_host);
+pid_status pid_serve_unregister(pid_server s, int64_t ensemble_id);
+/* Queue a request; returns a ticket for pid_serve_wait. */
+pid_status pid_serve_submit(pid_server s, int64_t ensemble_id, const pid_options* opt,
+                            uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: forever) for a request; copies its results into the HOST
+ * arrays given (any may be NULL; each N long) and retires the ticket. Returns the request's
+ * status, or PID_ERR_TIMEOUT (ticket kept) if it is not done in time. */
+pid_status pid_serve_wait(pid_server s, uint64_t ticket, int64_t timeout_ms, double* depth_host,
+                          double* in_in_host, double* in_out_host, int32_t* rank_host,
+                          double* mean_depth_host);
+pid_status pid_serve_stats_get(pid_server s, pid_serve_stats* out);
+pid_status pid_serve_stats_reset(pid_server s);
+
+/*
  * pid_mean_noalloc — PID-mean (the same result as pid_mean) for callers that cannot
  * allocate device memory: code recording a CUDA graph, real-time loops in which a
  * cudaMalloc would synchronise the device, and host applications whose own allocator owns

@@ -28,7 +28,9 @@ EXPORTS = [
     "pid_create", "pid_destroy", "pid_sync", "pid_status_string", "pid_last_error",
     "pid_workspace_bytes", "pid_soft_masks", "pid_mean", "pid_full", "pid_from_fields",
     "pid_batch", "pid_profile_enable", "pid_profile_read", "pid_autotune_enable",
-    "pid_mean_noalloc",
+    "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
+    "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
+    "pid_serve_stats_get", "pid_serve_stats_reset",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO = 0, 1, 2, 3
 KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3}
@@ -63,6 +65,19 @@ class pid_ensemble(ctypes.Structure):
                 ("P", c_void_p), ("err_est", c_void_p)]
 
 
+class pid_serve_cfg(ctypes.Structure):
+    _fields_ = [("device", c_int32), ("max_inflight", c_int32), ("max_batch", c_int32),
+                ("max_queue", c_int32), ("hbm_budget_bytes", c_size_t),
+                ("workspace_reserve_bytes", c_size_t), ("max_step_member_cells", c_int64)]
+
+
+class pid_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("failed", c_int64),
+                ("steps", c_int64), ("mean_batch", c_double), ("p50_ms", c_double),
+                ("p99_ms", c_double), ("max_ms", c_double), ("requests_per_s", c_double),
+                ("member_cells_per_s", c_double), ("resident_bytes", c_size_t)]
+
+
 _lib = None
 
 
@@ -94,6 +109,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_profile_read": ([P, c_int, POINTER(pid_kernel_stats)], c_int),
         "pid_autotune_enable": ([P, c_int, POINTER(c_int32)], c_int),
         "pid_mean_noalloc": ([P, c_int64, c_int64, c_int64, P, P, P, P, P, P, P], c_int),
+        "pid_serve_start": ([POINTER(c_void_p), POINTER(pid_serve_cfg)], c_int),
+        "pid_serve_stop": ([P], c_int),
+        "pid_serve_register": ([P, P, c_int64, c_int64, c_int64, P, c_int32, POINTER(pid_iso),
+                                c_int32, POINTER(c_int64)], c_int),
+        "pid_serve_update": ([P, c_int64, P], c_int),
+        "pid_serve_unregister": ([P, c_int64], c_int),
+        "pid_serve_submit": ([P, c_int64, POINTER(pid_options), POINTER(ctypes.c_uint64)], c_int),
+        "pid_serve_wait": ([P, ctypes.c_uint64, c_int64, P, P, P, P, P], c_int),
+        "pid_serve_stats_get": ([P, POINTER(pid_serve_stats)], c_int),
+        "pid_serve_stats_reset": ([P], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -313,3 +338,97 @@ class Handle:
             outs.append(o)
         pid_batch(self.h, ens, _stream(stream))
         return outs
+
+
+# --- serving --------------------------------------------------------------------------------
+
+class Server:
+    """Continuous-batching depth server (pid_serve_*): resident ensembles, queued requests."""
+
+    def __init__(self, device=0, max_inflight=2, max_batch=32, max_queue=4096,
+                 hbm_budget_bytes=0, workspace_reserve_bytes=0, max_step_member_cells=0):
+        cfg = pid_serve_cfg(device, max_inflight, max_batch, max_queue, hbm_budget_bytes,
+                            workspace_reserve_bytes, max_step_member_cells)
+        self.s = c_void_p()
+        st = load().pid_serve_start(ctypes.byref(self.s), ctypes.byref(cfg))
+        if st != PID_OK:
+            raise PidError(st, load().pid_status_string(st).decode())
+
+    def _chk(self, st):
+        if st != PID_OK:
+            raise PidError(st, load().pid_status_string(st).decode())
+
+    def stop(self):
+        if self.s:
+            self._chk(load().pid_serve_stop(self.s))
+            self.s = None
+
+    def __del__(self):
+        try:
+            self.stop()
+        except Exception:
+            pass
+
+    def register(self, data, w=None, iso=None, copy=None):
+        """data: numpy float32 [N, M] (copied to the device) or a torch CUDA tensor (adopted)."""
+        import numpy as np
+        ens = ctypes.c_int64(0)
+        is_dev = hasattr(data, "is_cuda") and data.is_cuda
+        if copy is None:
+            copy = not is_dev
+        if is_dev:
+            N, M = data.shape
+            ld = data.stride(0)
+            dptr = data.data_ptr()
+            wptr = None if w is None else w.data_ptr()
+            keep = (data, w)
+        else:
+            data = np.ascontiguousarray(data, dtype=np.float32)
+            N, M = data.shape
+            ld = M
+            dptr = data.ctypes.data
+            w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
+            wptr = None if w is None else w.ctypes.data
+            keep = None
+        iso_s = pid_iso(PID_ISO_NORMAL, int(iso[2]) if iso and len(iso) > 2 else 0,
+                        float(iso[0]), float(iso[1])) if iso else pid_iso()
+        self._chk(load().pid_serve_register(self.s, dptr, N, M, ld, wptr, int(iso is not None),
+                                            ctypes.byref(iso_s), int(bool(copy)),
+                                            ctypes.byref(ens)))
+        if keep is not None:
+            self.__dict__.setdefault("_keep", {})[ens.value] = keep
+        return ens.value
+
+    def update(self, ens_id, data_host):
+        import numpy as np
+        data_host = np.ascontiguousarray(data_host, dtype=np.float32)
+        self._chk(load().pid_serve_update(self.s, ens_id, data_host.ctypes.data))
+
+    def unregister(self, ens_id):
+        self._chk(load().pid_serve_unregister(self.s, ens_id))
+        self.__dict__.get("_keep", {}).pop(ens_id, None)
+
+    def submit(self, ens_id, mode="mean", precision="fp32"):
+        t = ctypes.c_uint64(0)
+        opt = pid_options(MODES[mode], PRECISIONS[precision], 0, 0)
+        self._chk(load().pid_serve_submit(self.s, ens_id, ctypes.byref(opt), ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket, N, timeout_ms=-1):
+        """Returns a dict of numpy arrays (depth, in_in, in_out, rank, mean_depth)."""
+        import numpy as np
+        out = {k: np.empty(N, dtype=np.float64) for k in ("depth", "in_in", "in_out", "mean_depth")}
+        out["rank"] = np.empty(N, dtype=np.int32)
+        st = load().pid_serve_wait(self.s, ticket, timeout_ms, out["depth"].ctypes.data,
+                                   out["in_in"].ctypes.data, out["in_out"].ctypes.data,
+                                   out["rank"].ctypes.data, out["mean_depth"].ctypes.data)
+        self._chk(st)
+        return out
+
+    def stats(self):
+        st = pid_serve_stats()
+        self._chk(load().pid_serve_stats_get(self.s, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in pid_serve_stats._fields_}
+
+    def reset_stats(self):
+        self._chk(load().pid_serve_stats_reset(self.s))

@@ -33,6 +33,11 @@ struct BatchCache {
   int64_t replays = 0;
 };
 
+void batch_use_graphs(pid_handle h, bool on) {
+  if (!h->batch) h->batch = new BatchCache();
+  h->batch->use_graphs = on;
+}
+
 void destroy_batch_cache(pid_handle h) {
   if (!h->batch) return;
   BatchCache* c = h->batch;

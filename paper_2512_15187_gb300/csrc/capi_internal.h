@@ -158,5 +158,7 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDe
 
 // batch.cu
 void destroy_batch_cache(pid_handle h);
+// Record batches into CUDA graphs and replay them while the layout repeats (default on).
+void batch_use_graphs(pid_handle h, bool on);
 
 }  // namespace pidh

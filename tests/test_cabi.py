@@ -55,3 +55,15 @@ def test_struct_layout_matches_header():
     assert ctypes.sizeof(B.pid_options) == 16
     # data, N, M, ld, w, is_field+reserved, iso, opt, 8 output pointers
     assert ctypes.sizeof(B.pid_ensemble) == 8 * 5 + 8 + 24 + 16 + 8 * 8
+
+
+def test_serving_structs_and_host_checks(lib):
+    import ctypes
+    from paper_2512_15187_gb300 import binding as B
+    assert ctypes.sizeof(B.pid_serve_cfg) == 40
+    assert ctypes.sizeof(B.pid_serve_stats) == 88
+    out = ctypes.c_void_p()
+    assert lib.pid_serve_start(ctypes.byref(out), None) == B.PID_ERR_INVALID_ARG
+    bad = B.pid_serve_cfg(0, 0, 1, 1, 0, 0, 0)           # max_inflight < 1
+    assert lib.pid_serve_start(ctypes.byref(out), ctypes.byref(bad)) == B.PID_ERR_INVALID_ARG
+    assert lib.pid_serve_stop(None) == B.PID_OK
