@@ -48,6 +48,8 @@ def parse_args():
                     help="steps timed for each alternative path reported beside the headline")
     ap.add_argument("--e2e-ensembles", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=3.0,
+                    help="seconds of Poisson arrivals per serving scenario (0 = skip serving)")
     return ap.parse_args()
 
 
@@ -179,6 +181,87 @@ def ncu_traffic(kernel_file, workload_tag):
         if m1 and m2 and m1.group(1) == sha:
             return float(m2.group(1))
     return None
+
+
+# ---------------------------------------------------------------------------------------
+# Serving: Poisson arrivals against resident ensembles (continuous batching vs one launch
+# per request)
+# ---------------------------------------------------------------------------------------
+
+SERVE_GRIDS = [(256, 256), (512, 512), (1024, 1024), (64 * 8, 64 * 8 * 8 // 8),
+               (128 * 16, 128 * 128 // 16), (192 * 24, 192 * 192 // 24)]   # 2D grids, 3D grids flattened
+
+
+def run_serving(device, seconds, rate_hz, budget_bytes=150 << 30, n_ens=24, seed=5):
+    """Resident ensembles drawn from the 2D / non-Cartesian / 3D shape mix: N ~ U{16..256},
+    grids 256^2..1024^2 or 64^3..192^3 (flattened), fields (isovalue Normal(0.5, 0.05)) or
+    soft masks. Requests arrive as a Poisson process and ask for PID-mean, exact full PID
+    or the BF16 tensor-core full PID. Returns per-scenario latency and throughput."""
+    import math
+    import threading
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_2512_15187_gb300 import binding, synth
+
+    rng = np.random.default_rng(seed)
+    dev = torch.device("cuda", device)
+    pool = []
+    for k in range(n_ens):
+        N = int(rng.integers(16, 257))
+        H, W = SERVE_GRIDS[int(rng.integers(0, len(SERVE_GRIDS)))]
+        t = synth.rbf_fields_2d_torch(N, H, W, 32, seed=synth.DEFAULT_SEED + 77 + k, device=dev)
+        field = bool(k % 2)
+        if not field:
+            t = torch.sigmoid((t - 0.5) / 0.05)
+        pool.append((t, field))
+    out = {}
+    for name, inflight, batch in (("continuous_batching", 2, 32), ("one_launch_per_request", 1, 1)):
+        for load_name, hz in (("poisson_%d_per_s" % int(rate_hz), rate_hz),
+                              ("poisson_%d_per_s" % int(rate_hz * 15), rate_hz * 15)):
+            srv = binding.Server(device=device, max_inflight=inflight, max_batch=batch,
+                                 max_queue=1 << 16, hbm_budget_bytes=budget_bytes)
+            ids = [(srv.register(t, iso=(0.5, 0.05, 0) if f else None), t.shape[0]) for t, f in pool]
+            # warm-up: every ensemble once in every mode
+            for i, n in ids:
+                for mode, prec in (("mean", "fp32"), ("linear", "fp32")):
+                    srv.wait(srv.submit(i, mode, prec), n)
+            srv.reset_stats()
+            tickets = []
+            stop_at = time.perf_counter() + seconds
+            r = np.random.default_rng(seed + 1)
+
+            def submitter():
+                nxt = time.perf_counter()
+                while True:
+                    nxt += r.exponential(1.0 / hz)
+                    now = time.perf_counter()
+                    if nxt > stop_at:
+                        break
+                    if nxt > now:
+                        time.sleep(nxt - now)
+                    i, n = ids[int(r.integers(0, len(ids)))]
+                    u = r.uniform()
+                    mode, prec = ("mean", "fp32") if u < 0.5 else (
+                        ("linear", "fp32") if (u < 0.75 or n > 128) else ("full", "bf16"))
+                    tickets.append((srv.submit(i, mode, prec), n))
+
+            th = threading.Thread(target=submitter)
+            th.start()
+            th.join()
+            for tk, n in tickets:
+                srv.wait(tk, n)
+            st = srv.stats()
+            out.setdefault(name, {})[load_name] = {
+                "requests": st["completed"], "failed": st["failed"], "p50_ms": st["p50_ms"],
+                "p99_ms": st["p99_ms"], "max_ms": st["max_ms"],
+                "requests_per_s": st["requests_per_s"],
+                "member_cells_per_s": st["member_cells_per_s"], "mean_batch": st["mean_batch"],
+                "resident_gb": st["resident_bytes"] / 1e9}
+            srv.stop()
+    return out
 
 
 # ---------------------------------------------------------------------------------------
@@ -338,10 +421,17 @@ def main():
         t_ms = b0.elapsed_time(b1) / args.other_steps
         others[name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms}
 
+    serving = None
+    if rank == 0 and args.serve_seconds > 0:
+        serving = run_serving(local_rank, args.serve_seconds, 200.0)
+
     # ---- end to end: pinned host inputs -> device -> results back, every step ----
     Ee = min(args.e2e_ensembles, E)
     host = torch.empty((Ee, N, M), dtype=torch.float32, pin_memory=True)
-    host.copy_(F[:Ee].cpu())
+    for e in range(Ee):
+        host[e].copy_(synth.rbf_fields_2d_torch(N, GRID_H, GRID_W, N_RBF,
+                                                seed=synth.DEFAULT_SEED + 2 + 7919 * (e + 100003 * rank),
+                                                device=dev).cpu())
     dbuf = torch.empty((Ee, N, M), dtype=torch.float32, device=dev)
     items_e = [dict(data=dbuf[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=args.mode,
                     precision=args.precision) for e in range(Ee)]
@@ -391,6 +481,8 @@ def main():
             "clocks": clocks,
             "other_paths": others,
         }
+        if serving is not None:
+            line["serving"] = serving
         if cpu_res is not None:
             line["cpu_baseline"] = cpu_baseline_record(cpu_res)
         print(json.dumps(line), flush=True)

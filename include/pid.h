@@ -255,8 +255,8 @@ pid_status pid_serve_start(pid_server* out, const pid_serve_cfg* cfg);
 pid_status pid_serve_stop(pid_server s);
 /* Register an ensemble [N][ld] float32 (soft masks, or fields with `iso`), cell measures w
  * [M] (or NULL). copy = 1: data (and w) are HOST pointers copied into device memory the
- * server owns (counted against the budget; PID_ERR_OOM if it does not fit); copy = 0: DEVICE
- * pointers the caller keeps alive until pid_serve_unregister. */
+ * server owns; copy = 0: DEVICE pointers the caller keeps alive until pid_serve_unregister.
+ * Either way its footprint counts against the budget (PID_ERR_OOM if it does not fit). */
 pid_status pid_serve_register(pid_server s, const float* data, int64_t N, int64_t M, int64_t ld,
                               const float* w, int32_t is_field, const pid_iso* iso, int32_t copy,
                               int64_t* ensemble_id);

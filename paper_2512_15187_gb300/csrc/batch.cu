@@ -119,10 +119,12 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   }
   // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
   std::map<ClassKey, std::vector<int>> pass1, pass2;
-  std::map<std::pair<int, int>, std::vector<int>> gram_cls;   // (precision x 2 + TMA, iso kind)
+  // ((precision x 2 + TMA) x 32 + group size, isovalue kind)
+  std::map<std::pair<int, int>, std::vector<int>> gram_cls;
   for (int e = 0; e < count; ++e) {
     if (is_gram[e]) {
-      gram_cls[{gp[e].prec * 2 + (gp[e].tma ? 1 : 0), iso_kind(gp[e].desc.iso_mode)}].push_back(e);
+      gram_cls[{(gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 32 + gp[e].G, iso_kind(gp[e].desc.iso_mode)}]
+          .push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
       pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik}].push_back(e);
@@ -234,7 +236,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       L.gp.stage_floats = std::max(L.gp.stage_floats, gp[e].stage_floats);
       bp->sdesc.push_back(d);
     }
-    gram_geometry(h, L.gp.prec, L.gp.stage_floats, &L.gp.dF, &L.gp.dO, &L.gp.smem);
+    gram_geometry(h, L.gp.G, L.gp.prec, L.gp.stage_floats, &L.gp.dF, &L.gp.dO, &L.gp.smem);
     L.iso_mode = gp[kv.second[0]].desc.iso_mode;
     L.total_units = units;
     bp->launches.push_back(L);

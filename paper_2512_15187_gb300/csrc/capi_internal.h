@@ -107,6 +107,7 @@ struct GramPlan {
   pidk::EnsDesc desc;      // tensor maps and chunking of the Gram pass
   int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
   bool tma = true;         // rows 16-byte aligned: FP32 tiles staged by TMA
+  int G = 16;              // warps per group (8: two groups per CTA for N <= 64)
   int TS = 64;             // cells per stage
   int n_gchunks = 0;
   int64_t chunk_cells = 0;
@@ -148,7 +149,8 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
 
 // gram.cu
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
-void gram_geometry(pid_handle h, int prec, int32_t stage_floats, int* dF, int* dO, size_t* smem);
+void gram_geometry(pid_handle h, int G, int prec, int32_t stage_floats, int* dF, int* dO,
+                   size_t* smem);
 pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
                            float* gpart, float* scale, cudaStream_t s);
 // Gram launch over `count` device descriptors (part / gpart / op_scale already set).

@@ -22,8 +22,10 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(in.data);
   gp->tma = in.ld % 4 == 0 && a % 16 == 0 && (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
   gp->prec = in.precision;
+  gp->G = in.N <= 64 ? 8 : 16;        // two independent 8-warp groups when N <= 64
   gp->TS = 128;
-  int64_t chunk = rup((in.M + h->sms - 1) / h->sms, gp->TS);
+  const int64_t groups = static_cast<int64_t>(h->sms) * (kGramConvWarps / gp->G);
+  int64_t chunk = rup((in.M + groups - 1) / groups, gp->TS);
   chunk = std::max<int64_t>(chunk, gp->TS);
   gp->chunk_cells = chunk;
   gp->n_gchunks = static_cast<int>((in.M + chunk - 1) / chunk);
@@ -52,7 +54,7 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   gp->stage_floats = gp->tma ? static_cast<int32_t>(rup(in.N * gp->TS + gp->TS, 32)) : 32;
   gp->gpart_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * in.N * in.N * 4, 256);
   gp->part_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * 2 * in.N * 8, 256);
-  gram_geometry(h, gp->prec, gp->stage_floats, &gp->dF, &gp->dO, &gp->smem);
+  gram_geometry(h, gp->G, gp->prec, gp->stage_floats, &gp->dF, &gp->dO, &gp->smem);
   gp->flops = (in.precision == PID_SPLIT_BF16 ? 3.0 : 1.0) * 2.0 * static_cast<double>(in.N) *
               in.N * in.M;
   gp->bytes = 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0);
@@ -61,21 +63,22 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
 
 // Ring depths that fit the shared memory: at least two FP32 stages, then as many operand
 // stages as fit (at most four), then the FP32 ring deepened to at most six stages.
-void gram_geometry(pid_handle h, int prec, int32_t stage_floats, int* dF, int* dO, size_t* smem) {
+void gram_geometry(pid_handle h, int G, int prec, int32_t stage_floats, int* dF, int* dO,
+                   size_t* smem) {
   const size_t cap = static_cast<size_t>(h->max_smem > 0 ? h->max_smem : 232448);
   int f = 2, o = 4;
-  while (o > 1 && gram_smem_bytes(prec, f, o, stage_floats) > cap) --o;
-  while (f > 1 && gram_smem_bytes(prec, f, o, stage_floats) > cap) --f;
-  while (f < 6 && gram_smem_bytes(prec, f + 1, o, stage_floats) <= cap) ++f;
+  while (o > 1 && gram_smem_bytes(G, prec, f, o, stage_floats) > cap) --o;
+  while (f > 1 && gram_smem_bytes(G, prec, f, o, stage_floats) > cap) --f;
+  while (f < 6 && gram_smem_bytes(G, prec, f + 1, o, stage_floats) <= cap) ++f;
   *dF = f;
   *dO = o;
-  *smem = gram_smem_bytes(prec, f, o, stage_floats);
+  *smem = gram_smem_bytes(G, prec, f, o, stage_floats);
 }
 
-static pid_status gram_launch(pid_handle h, const GramParams& gpar, int prec, int iso_mode,
+static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, int prec, int iso_mode,
                               int grid, size_t smem, double bytes, double flops, cudaStream_t s) {
   ProfScope ps(h, PID_KERNEL_GRAM, bytes, flops, s);
-  cudaError_t e = launch_gram(gpar, prec, iso_kind(iso_mode), grid, smem, s);
+  cudaError_t e = launch_gram(gpar, G, prec, iso_kind(iso_mode), grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "Gram kernel launch");
   return PID_OK;
 }
@@ -99,11 +102,12 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   gpar.dO = gp.dO;
   gpar.stage_floats = gp.stage_floats;
   gpar.TS = gp.TS;
-  gpar.xchg = 1;
+  gpar.xchg = gp.G >= 16 ? 1 : 0;   // one group barrier per stage for 8-warp groups
   gpar.use_tma = gp.tma ? 1 : 0;
   gpar.err = h->err_word;
-  const int grid = std::max(1, std::min(h->sms, gp.n_gchunks));
-  return gram_launch(h, gpar, gp.prec, gp.desc.iso_mode, grid, gp.smem, gp.bytes, gp.flops, s);
+  const int ng = kGramConvWarps / gp.G;
+  const int grid = std::max(1, std::min(h->sms, (gp.n_gchunks + ng - 1) / ng));
+  return gram_launch(h, gpar, gp.G, gp.prec, gp.desc.iso_mode, grid, gp.smem, gp.bytes, gp.flops, s);
 }
 
 pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* descs, int count,
@@ -118,11 +122,12 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* de
   gpar.dO = gp.dO;
   gpar.stage_floats = gp.stage_floats;
   gpar.TS = gp.TS;
-  gpar.xchg = 1;
+  gpar.xchg = gp.G >= 16 ? 1 : 0;
   gpar.use_tma = gp.tma ? 1 : 0;
   gpar.err = h->err_word;
-  const int grid = std::max(1, std::min(h->sms, total_units));
-  return gram_launch(h, gpar, gp.prec, iso_mode, grid, gp.smem, bytes, flops, s);
+  const int ng = kGramConvWarps / gp.G;
+  const int grid = std::max(1, std::min(h->sms, (total_units + ng - 1) / ng));
+  return gram_launch(h, gpar, gp.G, gp.prec, iso_mode, grid, gp.smem, bytes, flops, s);
 }
 
 }  // namespace pidh

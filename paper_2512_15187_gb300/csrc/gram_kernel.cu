@@ -34,10 +34,8 @@ namespace {
 
 constexpr int VEC = 4;                  // cells per lane per register tile
 constexpr int T = 32 * VEC;             // cells per register tile (= one TMA stage)
-constexpr int G = kGramConvWarps;       // converter warps sharing every tile
-constexpr int MPW = kGramMaxN / G;      // members per converter warp
-constexpr int RB = G * T + T;           // exchange buffer floats
-constexpr uint32_t kTmemCols = 256;     // two accumulators of up to 128 columns
+constexpr int MPW = 8;                  // members per warp: a group of G warps covers 8 G rows
+constexpr uint32_t kTmemCols = 256;     // per CTA: each group's two accumulators of 8 G columns
 
 __device__ __forceinline__ const EnsDesc& gdesc(const GramParams& p, int e) {
   return p.descs ? p.descs[e] : p.one;
@@ -53,7 +51,7 @@ __device__ __forceinline__ int gram_find_ens(const GramParams& p, int u) {
   return lo;
 }
 
-// Byte offset of (member row i, byte b of the 128-byte K-block row) in the swizzled plane.
+// Byte offset of (member row i, byte b of the 128-byte K-block row) in a swizzled plane.
 __device__ __forceinline__ uint32_t sw128_offset(int i, int b) {
   return static_cast<uint32_t>((i >> 3) * 1024 + (i & 7) * 128 + ((((b >> 4) ^ (i & 7))) << 4) +
                                (b & 15));
@@ -72,36 +70,50 @@ __device__ __forceinline__ uint32_t sw128_offset(int i, int b) {
 // it to the stage's "operand free" mbarrier and, at a chunk's end, to the accumulator's
 // "ready" mbarrier; warps 0-3 drain the previous chunk's accumulator halfway through the
 // next chunk.
-template <int ISO, int PREC, bool TMA>
+template <int G, int ISO, int PREC, bool TMA>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams p) {
+  constexpr int NG = kGramConvWarps / G;             // independent groups per CTA
+  constexpr int ROWS = MPW * G;                      // operand rows a group writes (>= N)
+  constexpr uint32_t PLANE = ROWS * 128;             // one K-block: [ROWS][128 bytes]
   constexpr int PLANES = PREC == 2 ? 2 : 1;          // hi (+ lo)
   constexpr int KBLK = PREC == 3 ? 1 : 2;            // K-blocks per stage
-  constexpr uint32_t OP_STAGE = PLANES * KBLK * kOpPlaneBytes;
+  constexpr uint32_t OP_STAGE = PLANES * KBLK * PLANE;
   constexpr uint32_t FMT = PREC == 3 ? 0u : 1u;      // E4M3 : BF16
+  constexpr int RB = G * T + T;                      // exchange buffer floats
+  constexpr uint32_t BUFC = ROWS;                    // TMEM columns per accumulator
   extern __shared__ __align__(1024) unsigned char smem_raw[];
 
-  const int q = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const bool leader = threadIdx.x == 0;
+  const int grp = warp / G;
+  const int q = warp - grp * G;
+  const bool leader = (q == 0) && (lane == 0);
   const int dF = p.dF, dO = p.dO, SF = p.stage_floats, TS = p.TS;
 
-  // ---- shared memory carve-up (operand ring first, 1024-byte aligned) ----
+  // ---- shared memory carve-up: all operand rings first (1024-byte aligned) ----
+  // An M = 128 MMA reads 128 rows from a plane's base; with 64-row planes the upper rows
+  // come from the bytes that follow (garbage rows of D that are never read).
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
-  unsigned char* op_ring = smem;
-  float* f_ring = reinterpret_cast<float*>(op_ring + static_cast<size_t>(dO) * OP_STAGE);
-  float* red = f_ring + static_cast<size_t>(dF) * SF;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(red + 2 * RB);
+  float* f_all = reinterpret_cast<float*>(smem + static_cast<size_t>(NG) * dO * OP_STAGE);
+  float* red_all = f_all + static_cast<size_t>(NG) * dF * SF;
+  uint64_t* bars_all = reinterpret_cast<uint64_t*>(red_all + NG * 2 * RB);
+  int* flags_all = reinterpret_cast<int*>(bars_all + NG * (dF + dO + 5));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags_all + 2 * NG);
+
+  unsigned char* op_ring = smem + static_cast<size_t>(grp) * dO * OP_STAGE;
+  float* f_ring = f_all + static_cast<size_t>(grp) * dF * SF;
+  float* red = red_all + grp * 2 * RB;
+  uint64_t* bars = bars_all + grp * (dF + dO + 5);
   uint64_t* fF = bars;              // FP32 stage landed (TMA)
   uint64_t* opE = fF + dF;          // operand stage consumed (tcgen05.commit)
   uint64_t* accF = opE + dO;        // accumulator ready (tcgen05.commit)
-  uint64_t* accE = accF + 2;        // accumulator drained (warps 0-3)
-  uint64_t* finB = accE + 2;        // all tensor-core work done
+  uint64_t* accE = accF + 2;        // accumulator drained (the group's warps 0-3)
+  uint64_t* finB = accE + 2;        // all of the group's tensor-core work done
   // Abort flags, one per exchange-buffer parity: a warp that gives up on a wait sets the
-  // flag of the group barrier it reaches next, and every warp reads that flag after that
-  // barrier, so all of them leave together.
-  volatile int* cflag = reinterpret_cast<volatile int*>(finB + 1);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(finB + 1) + 2;
+  // flag of the group barrier it reaches next, and every warp of the group reads that flag
+  // after that barrier, so all of them leave together.
+  volatile int* cflag = flags_all + 2 * grp;
 
   if (leader) {
     for (int s = 0; s < dF; ++s) mbar_init(&fF[s], 1);
@@ -112,21 +124,23 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     cflag[1] = 0;
     fence_mbar_init();
   }
-  // Rows past N of the first operand use must be finite: clear the whole operand ring.
-  for (uint32_t o = threadIdx.x * 16; o < static_cast<uint32_t>(dO) * OP_STAGE; o += kGramThreads * 16)
-    *reinterpret_cast<uint4*>(op_ring + o) = make_uint4(0, 0, 0, 0);
+  // Operand rows past N must be finite on first use: clear every operand ring.
+  for (uint32_t o = threadIdx.x * 16; o < static_cast<uint32_t>(NG) * dO * OP_STAGE; o += kGramThreads * 16)
+    *reinterpret_cast<uint4*>(smem + o) = make_uint4(0, 0, 0, 0);
   fence_proxy_async_smem();
-  if (q == 0) {
+  if (warp == 0) {
     tmem_alloc(tmem_slot, kTmemCols);
     tmem_relinquish();
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t tmem_base = *tmem_slot + static_cast<uint32_t>(grp) * 2 * BUFC;
+  const int gid = blockIdx.x * NG + grp;
+  const int total_groups = gridDim.x * NG;
 
   // ---- TMA producer cursor (leader) ----
-  int iu = blockIdx.x, ist = 0, ie = 0, icell0 = 0, in_st = 0;
+  int iu = gid, ist = 0, ie = 0, icell0 = 0, in_st = 0;
   long n_issued = 0;
   auto set_unit = [&](int u) {
     ie = gram_find_ens(p, u);
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     ++n_issued;
     if (++ist == in_st) {
       ist = 0;
-      iu += gridDim.x;
+      iu += total_groups;
       if (iu < p.total_units) set_unit(iu);
     }
   };
@@ -171,21 +185,21 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                            kWaitTimeoutNs))
       return false;
     tc_fence_after();
-    const uint32_t dt = tmem_base + static_cast<uint32_t>(pend_buf) * 128;
-    const uint32_t base = smem_u32(op_ring) + static_cast<uint32_t>(pend_slot) * OP_STAGE;
+    const uint32_t dt = tmem_base + static_cast<uint32_t>(pend_buf) * BUFC;
+    // descriptor of the stage's first K-block; K steps advance its 16-byte address field
+    const uint64_t d0 = umma_desc_sw128(smem_u32(op_ring) + static_cast<uint32_t>(pend_slot) * OP_STAGE);
 #pragma unroll
     for (int kb = 0; kb < KBLK; ++kb) {
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {   // 4 x 32 bytes along K in the 128-byte row
-        const uint32_t a_addr = base + kb * kOpPlaneBytes + ks * 32;
-        const uint64_t hi = umma_desc_sw128(a_addr);
+        const uint64_t hi = d0 + static_cast<uint64_t>((kb * PLANE + ks * 32) >> 4);
         const uint32_t acc = (pend_first && kb == 0 && ks == 0) ? 0u : 1u;
         if constexpr (PREC == 3) {
           umma_f8(dt, hi, hi, pend_idesc, acc);
         } else {
           umma_f16(dt, hi, hi, pend_idesc, acc);
           if constexpr (PREC == 2) {
-            const uint64_t lo = umma_desc_sw128(a_addr + KBLK * kOpPlaneBytes);
+            const uint64_t lo = hi + static_cast<uint64_t>((KBLK * PLANE) >> 4);
             umma_f16(dt, hi, lo, pend_idesc, 1u);
             umma_f16(dt, lo, hi, pend_idesc, 1u);
           }
@@ -216,7 +230,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     float* gp = d.gpart + static_cast<size_t>(c) * N * N;
     for (int j0 = 0; j0 < nmma; j0 += 32) {
       float v[32];
-      tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * q) << 16) + b * 128 + j0, v);
+      tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * q) << 16) + b * BUFC + j0, v);
       if (row < N) {
 #pragma unroll
         for (int jj = 0; jj < 32; ++jj)
@@ -229,12 +243,17 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     return true;
   };
 
+  // Swizzled byte offset of this lane's piece of row q; row q + m G adds m G 128 bytes
+  // (G is a multiple of 8, so every owned row has the same row-in-atom q & 7).
+  const uint32_t lane_off = PREC == 3 ? sw128_offset(q, lane * 4)
+                                      : static_cast<uint32_t>(lane >> 4) * PLANE +
+                                            sw128_offset(q, (lane & 15) * 8);
   long k = 0, kt = 0, kc = 0;
   int prev_u = -1;
   long prev_kc = -1;
   bool aborted = false;
   uint32_t bad = 0;
-  for (int u = blockIdx.x; u < p.total_units && !aborted; u += gridDim.x, ++kc) {
+  for (int u = gid; u < p.total_units && !aborted; u += total_groups, ++kc) {
     const EnsDesc& d = gdesc(p, gram_find_ens(p, u));
     const int N = d.N;
     const int M = d.M;                       // descriptor fields kept in registers: the
@@ -338,9 +357,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 #pragma unroll
           for (int v = 0; v < VEC; ++v) s[v] += x[m][v];
         }
-      float* rb = red + static_cast<int>(kt & 1) * RB;
+      float* rb = red + static_cast<int>(kt & 1) * RB;  // this group's exchange buffer
       *reinterpret_cast<float4*>(rb + q * T + lane * VEC) = make_float4(s[0], s[1], s[2], s[3]);
-      named_barrier(1, kGramThreads);
+      named_barrier(1 + grp, G * 32);
       if (cflag[kt & 1]) { aborted = true; break; }
       if (leader) {
         if (!issue_pending()) cflag[(kt + 1) & 1] = 1;   // stage k-1 to the tensor cores
@@ -355,7 +374,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
           for (int r = 0; r < G; ++r) acc += rb[r * T + cc];
           rb[G * T + cc] = acc;
         }
-        named_barrier(1, kGramThreads);
+        named_barrier(1 + grp, G * 32);
         lds_vec<VEC>(s, rb + G * T + lane * VEC);
       } else {
 #pragma unroll
@@ -405,26 +424,24 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       // E4M3:   lane l holds bytes 4l..4l+3 of the single K-block.
 #pragma unroll
       for (int m = 0; m < MPW; ++m) {
-        const int i = q + m * G;
         if (m < mlive) {
           float a[VEC];
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) a[v] = x[m][v] * sw[v];
+          for (int v = 0; v < VEC; ++v) a[v] = has_w ? x[m][v] * sw[v] : x[m][v];
+          unsigned char* dst = ob + lane_off + static_cast<uint32_t>(m * G * 128);
           if constexpr (PREC == 3) {
             const uint32_t lo2 = __nv_cvt_float2_to_fp8x2(make_float2(a[0] * scale, a[1] * scale),
                                                           __NV_SATFINITE, __NV_E4M3);
             const uint32_t hi2 = __nv_cvt_float2_to_fp8x2(make_float2(a[2] * scale, a[3] * scale),
                                                           __NV_SATFINITE, __NV_E4M3);
-            *reinterpret_cast<uint32_t*>(ob + sw128_offset(i, lane * 4)) = lo2 | (hi2 << 16);
+            *reinterpret_cast<uint32_t*>(dst) = lo2 | (hi2 << 16);
           } else {
-            const uint32_t off = static_cast<uint32_t>(lane >> 4) * kOpPlaneBytes +
-                                 sw128_offset(i, (lane & 15) * 8);
             const __nv_bfloat162 h01 = __floats2bfloat162_rn(a[0], a[1]);
             const __nv_bfloat162 h23 = __floats2bfloat162_rn(a[2], a[3]);
             uint2 hv;
             hv.x = *reinterpret_cast<const uint32_t*>(&h01);
             hv.y = *reinterpret_cast<const uint32_t*>(&h23);
-            *reinterpret_cast<uint2*>(ob + off) = hv;
+            *reinterpret_cast<uint2*>(dst) = hv;
             if constexpr (PREC == 2) {
               const float2 f01 = __bfloat1622float2(h01), f23 = __bfloat1622float2(h23);
               const __nv_bfloat162 l01 = __floats2bfloat162_rn(a[0] - f01.x, a[1] - f01.y);
@@ -432,7 +449,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
               uint2 lv;
               lv.x = *reinterpret_cast<const uint32_t*>(&l01);
               lv.y = *reinterpret_cast<const uint32_t*>(&l23);
-              *reinterpret_cast<uint2*>(ob + KBLK * kOpPlaneBytes + off) = lv;
+              *reinterpret_cast<uint2*>(dst + KBLK * PLANE) = lv;
             }
           }
         }
@@ -469,7 +486,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   if (!aborted) {
     // The last stage goes to the tensor cores after one more group barrier; then the last
     // chunk's accumulator is drained.
-    named_barrier(1, kGramThreads);
+    named_barrier(1 + grp, G * 32);
     if (cflag[kt & 1]) aborted = true;
     if (!aborted && leader && !issue_pending()) aborted = true;
     if (!aborted && q < kGramEpiWarps && prev_u >= 0 && !drain(prev_u, prev_kc)) aborted = true;
@@ -491,32 +508,35 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (q == 0) tmem_dealloc(tmem_base, kTmemCols);
+  if (warp == 0) tmem_dealloc(*tmem_slot, kTmemCols);
 }
 
-size_t gram_smem_bytes(int prec, int dF, int dO, int stage_floats) {
-  const size_t planes = (prec == 2 ? 2 : 1) * (prec == 3 ? 1 : 2);
-  return 1024 + static_cast<size_t>(dO) * planes * kOpPlaneBytes +
-         static_cast<size_t>(dF) * stage_floats * 4 + 2 * RB * 4 +
-         (static_cast<size_t>(dF) + dO + 5) * 8 + 32;
+size_t gram_smem_bytes(int G, int prec, int dF, int dO, int stage_floats) {
+  const size_t NG = kGramConvWarps / G;
+  const size_t plane = static_cast<size_t>(MPW) * G * 128;
+  const size_t op_stage = (prec == 2 ? 2 : 1) * (prec == 3 ? 1 : 2) * plane;
+  const size_t rb = static_cast<size_t>(G) * T + T;
+  return 1024 + NG * (dO * op_stage + static_cast<size_t>(dF) * stage_floats * 4 + 2 * rb * 4 +
+                      (static_cast<size_t>(dF) + dO + 5) * 8 + 8) + 16;
 }
 
-template <int ISO, int PREC>
+template <int G, int ISO, int PREC>
 static cudaError_t gram_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
   if (p.use_tma)
-    gram_kernel<ISO, PREC, true><<<grid, kGramThreads, smem, s>>>(p);
+    gram_kernel<G, ISO, PREC, true><<<grid, kGramThreads, smem, s>>>(p);
   else
-    gram_kernel<ISO, PREC, false><<<grid, kGramThreads, smem, s>>>(p);
+    gram_kernel<G, ISO, PREC, false><<<grid, kGramThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
-                        cudaStream_t s) {
+template <int G>
+static cudaError_t launch_gram_g(const GramParams& p, int prec, int iso_kind, int grid,
+                                 size_t smem, cudaStream_t s) {
 #define PIDK_GRAM_CASE(ISO)                                                  \
   if (iso_kind == ISO) {                                                     \
-    if (prec == 1) return gram_launch_t<ISO, 1>(p, grid, smem, s);           \
-    if (prec == 2) return gram_launch_t<ISO, 2>(p, grid, smem, s);           \
-    if (prec == 3) return gram_launch_t<ISO, 3>(p, grid, smem, s);           \
+    if (prec == 1) return gram_launch_t<G, ISO, 1>(p, grid, smem, s);        \
+    if (prec == 2) return gram_launch_t<G, ISO, 2>(p, grid, smem, s);        \
+    if (prec == 3) return gram_launch_t<G, ISO, 3>(p, grid, smem, s);        \
   }
   PIDK_GRAM_CASE(ISOK_NONE)
   PIDK_GRAM_CASE(ISOK_NORMAL)
@@ -525,20 +545,33 @@ cudaError_t launch_gram(const GramParams& p, int prec, int iso_kind, int grid, s
   return cudaErrorInvalidValue;
 }
 
-cudaError_t gram_kernels_init(int max_smem) {
+cudaError_t launch_gram(const GramParams& p, int G, int prec, int iso_kind, int grid, size_t smem,
+                        cudaStream_t s) {
+  if (G == 8) return launch_gram_g<8>(p, prec, iso_kind, grid, smem, s);
+  if (G == 16) return launch_gram_g<16>(p, prec, iso_kind, grid, smem, s);
+  return cudaErrorInvalidValue;
+}
+
+template <int G>
+static cudaError_t gram_init_g(int max_smem) {
   cudaError_t e = cudaSuccess;
 #define PIDK_GRAM_INIT(ISO, PREC)                                                            \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(gram_kernel<ISO, PREC, true>,                                   \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, true>,                                \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);         \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(gram_kernel<ISO, PREC, false>,                                  \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, false>,                               \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   PIDK_GRAM_INIT(ISOK_NONE, 1) PIDK_GRAM_INIT(ISOK_NONE, 2) PIDK_GRAM_INIT(ISOK_NONE, 3)
   PIDK_GRAM_INIT(ISOK_NORMAL, 1) PIDK_GRAM_INIT(ISOK_NORMAL, 2) PIDK_GRAM_INIT(ISOK_NORMAL, 3)
   PIDK_GRAM_INIT(ISOK_STEP, 1) PIDK_GRAM_INIT(ISOK_STEP, 2) PIDK_GRAM_INIT(ISOK_STEP, 3)
 #undef PIDK_GRAM_INIT
   return e;
+}
+
+cudaError_t gram_kernels_init(int max_smem) {
+  cudaError_t e = gram_init_g<8>(max_smem);
+  return e == cudaSuccess ? gram_init_g<16>(max_smem) : e;
 }
 
 // Power-of-two E4M3 operand scale for weighted ensembles: the largest operand is

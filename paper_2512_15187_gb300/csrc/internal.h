@@ -68,7 +68,6 @@ constexpr int kGramConvWarps = 16;
 constexpr int kGramEpiWarps = 4;      // converter warps 0..3, one per TMEM lane quarter
 constexpr int kGramThreads = kGramConvWarps * 32;
 constexpr int kGramMaxN = 128;        // one M = 128 tensor-core tile
-constexpr int kOpPlaneBytes = 128 * 128;  // 128 rows x 128-byte swizzled K-block
 
 struct GramParams {
   EnsDesc one;
@@ -138,8 +137,8 @@ cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, b
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
-size_t gram_smem_bytes(int prec, int dF, int dO, int stage_floats);
-cudaError_t launch_gram(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
+size_t gram_smem_bytes(int G, int prec, int dF, int dO, int stage_floats);
+cudaError_t launch_gram(const GramParams& p, int G, int prec, int iso_kind, int grid, size_t smem,
                         cudaStream_t s);
 cudaError_t gram_kernels_init(int max_smem);
 cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s);

@@ -338,7 +338,8 @@ pid_status pid_serve_register(pid_server s, const float* data, int64_t N, int64_
   e->N = N; e->M = M; e->ld = ld; e->is_field = is_field;
   if (is_field) e->iso = *iso;
   e->owned = copy != 0;
-  if (e->owned) e->bytes = static_cast<size_t>(N) * ld * 4 + (w ? static_cast<size_t>(M) * 4 : 0);
+  // HBM footprint of the resident ensemble, owned or adopted
+  e->bytes = static_cast<size_t>(N) * ld * 4 + (w ? static_cast<size_t>(M) * 4 : 0);
   DeviceGuard g(s->cfg.device);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stopping) return PID_ERR_CANCELLED;

@@ -182,9 +182,6 @@ stream_kernel(const __grid_constant__ StreamParams p) {
                       : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
                                             : dir * __int_as_float(0x7f800000));
     const bool has_w = d.w != nullptr;
-    // Rows q, q+G, ... below N are this warp's members; rows past N are skipped with
-    // warp-uniform guards (their registers hold the padding value and are never used).
-    const int kmax = q < N ? (N - q + G - 1) / G : 0;
 
     // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
     // every member weighs 1/N, applied once per cell (pass 1).
@@ -260,10 +257,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         if constexpr (ISO != ISOK_NONE) {
 #pragma unroll
           for (int k = 0; k < MPW; ++k)
-            if (k < kmax) {
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], iso_mu, iso_inv, iso_t, dir);
-            }
+            for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], iso_mu, iso_inv, iso_t, dir);
         }
         if (!full) {  // only the ensemble's last tile: cells past M carry no mass
 #pragma unroll
@@ -281,15 +276,13 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         for (int v = 0; v < VEC; ++v) s[v] = 0.f;
 #pragma unroll
         for (int k = 0; k < MPW; ++k) {
-          if (k < kmax) {
-            if constexpr (COEF) {
-              const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
+          if constexpr (COEF) {
+            const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
-            } else {
+            for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
+          } else {
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
-            }
+            for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
           }
         }
         // ... then across the G warps of the group: every warp posts its partial; either
@@ -350,24 +343,20 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         if (has_w) {
 #pragma unroll
           for (int k = 0; k < MPW; ++k) {
-            if (k < kmax) {
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) {
-                const float t = wv[v] * x[k][v];
-                accM[k] += t;
-                accA[k] = fmaf(t, s[v], accA[k]);
-              }
+            for (int v = 0; v < VEC; ++v) {
+              const float t = wv[v] * x[k][v];
+              accM[k] += t;
+              accA[k] = fmaf(t, s[v], accA[k]);
             }
           }
         } else {
 #pragma unroll
           for (int k = 0; k < MPW; ++k) {
-            if (k < kmax) {
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) {
-                accM[k] += x[k][v];
-                accA[k] = fmaf(x[k][v], s[v], accA[k]);
-              }
+            for (int v = 0; v < VEC; ++v) {
+              accM[k] += x[k][v];
+              accA[k] = fmaf(x[k][v], s[v], accA[k]);
             }
           }
         }
