@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson arrivals per serving scenario (0 = skip serving)")
+    ap.add_argument("--source-hash", action="store_true",
+                    help="print the kernel-source stamp that ncu summaries carry, and exit")
     return ap.parse_args()
 
 
@@ -164,16 +166,27 @@ def measured_peaks():
             "source": "fallback"}
 
 
-def ncu_traffic(kernel_file, workload_tag):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current source."""
-    src = os.path.join(ROOT, "paper_2512_15187_gb300", "csrc", kernel_file)
+def kernel_sources_sha16():
+    """First 16 hex digits of the SHA-256 over every CUDA/C++ source of the library (in name
+    order): an ncu summary stamped with it describes exactly the kernels built from them."""
+    csrc = os.path.join(ROOT, "paper_2512_15187_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel, workload_tag):
+    """DRAM bytes per launch from the committed ncu summary profiles/<kernel>_*<tag>*.md, if
+    it was taken from the current sources (else None)."""
     prof_dir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(prof_dir):
         return None
-    with open(src, "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    sha = kernel_sources_sha16()
     for name in sorted(os.listdir(prof_dir)):
-        if not name.endswith(".md") or workload_tag not in name:
+        if not (name.endswith(".md") and name.startswith(kernel) and workload_tag in name):
             continue
         txt = open(os.path.join(prof_dir, name)).read()
         m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
@@ -298,6 +311,9 @@ def run_reference(args, rank):
 
 def main():
     args = parse_args()
+    if args.source_hash:
+        print(kernel_sources_sha16())
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -390,8 +406,8 @@ def main():
     roof["launches"] = st["launches"]
     roof["ms_per_launch"] = per_launch_ms
     roof["algorithmic_bytes_per_launch"] = st["bytes"] / st["launches"]
-    traffic = ncu_traffic("stream.cu" if dom == "stream" else "gram.cu",
-                          f"{N}x{GRID_H}x{GRID_W}") if dom in ("stream", "gram") else None
+    traffic = ncu_traffic(roof["kernel"], f"{N}x{GRID_H}x{GRID_W}") if dom in ("stream", "gram") \
+        else None
     roof["traffic"] = traffic
     gpu_launches = sum(v["launches"] for v in prof.values())
 

@@ -1,0 +1,57 @@
+"""Run one small, fixed case of one path of the library, for a profiler to capture.
+
+    python -m paper_2512_15187_gb300.profile_case fields        # isovalue map + PID-mean
+    python -m paper_2512_15187_gb300.profile_case mean          # PID-mean of soft masks
+    python -m paper_2512_15187_gb300.profile_case linear        # exact full PID, O(N M)
+    python -m paper_2512_15187_gb300.profile_case gram --precision bf16 --ensembles 4
+
+Each case builds its inputs on the device (seeded), runs the call three times and prints
+one line. Sizes default to N = 64 members and M = 2^20 cells (256 MiB of FP32 masks, larger
+than the 129 MB L2, so DRAM counters stay meaningful) and stay a few GB at most.
+"""
+from __future__ import annotations
+
+import argparse
+
+
+def main(argv=None) -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["fields", "mean", "linear", "gram"])
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--cells", type=int, default=1 << 20)
+    ap.add_argument("--ensembles", type=int, default=1,
+                    help="ensembles per call (more than one goes through pid_batch)")
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "split_bf16", "fp8"])
+    ap.add_argument("--repeat", type=int, default=3)
+    a = ap.parse_args(argv)
+
+    import torch
+
+    from . import binding, build, synth
+    build.build()
+    N, M, E = a.members, a.cells, a.ensembles
+    if 4.0 * N * M * E > 4e9:
+        raise SystemExit("profile cases stay below 4 GB of input")
+    h = binding.Handle(0)
+    X = torch.empty((E, N, M), device="cuda")
+    side = int(round(M ** 0.5))
+    for e in range(E):
+        if a.case in ("fields", "gram") and side * side == M:
+            synth.rbf_fields_2d_torch(N, side, side, 32, seed=7 + e, device="cuda", out=X[e])
+        else:
+            g = torch.Generator(device="cuda").manual_seed(7 + e)
+            X[e].uniform_(0.0, 1.0, generator=g)
+    is_field = a.case in ("fields", "gram") and side * side == M
+    mode = {"fields": "mean", "mean": "mean", "linear": "linear", "gram": "full"}[a.case]
+    prec = a.precision if mode == "full" else "fp32"
+    items = [dict(data=X[e], iso=(0.5, 0.05, 0) if is_field else None, mode=mode, precision=prec)
+             for e in range(E)]
+    for _ in range(a.repeat):
+        outs = h.batch(items)
+    h.sync()
+    print("ok", a.case, mode, prec, f"N={N} M={M} E={E}", float(outs[0]["depth"].sum()))
+    h.close()
+
+
+if __name__ == "__main__":
+    main()
