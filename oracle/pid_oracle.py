@@ -17,6 +17,8 @@ Every function cites the passage it follows:
   Eq. 15, Eq. 16   mean contour and PID-mean (Sec. 4.1)
   Sec. 3.5         probabilistic mask from a scalar field and an isovalue distribution
   Sec. 5.1         ranking: higher rank = lower depth
+  (pid_chunked / pid_mean_chunked restate Eq. 6, 9, 10, 15, 16 with their sums over
+  cells accumulated block by block, for ensembles larger than host memory in float64)
 
 Readings where the paper is silent (each also listed in the design notes):
   * Zero-mass reference mask: u subset_p v = 0 (Sec. 3.2), unlike eID's 1 (Eq. 1).
@@ -48,6 +50,8 @@ __all__ = [
     "rank_by_depth",
     "eps_subset",
     "eid",
+    "pid_chunked",
+    "pid_mean_chunked",
 ]
 
 
@@ -135,6 +139,57 @@ def pid_mean(U, w=None):
     N = U.shape[0]
     in_in = np.array([inclusion(U[i], ubar, w) for i in range(N)])
     in_out = np.array([inclusion(ubar, U[i], w) for i in range(N)])
+    return in_in, in_out, np.minimum(in_in, in_out)
+
+
+# ---------------------------------------------------------------------------
+# The same definitions for ensembles too large to hold in float64 at once: every sum over
+# cells in Eq. 6, Eq. 9 and Eq. 15/16 is a sum of per-cell terms, so it can be accumulated
+# over consecutive blocks of cells. `chunks` yields (U_block [N, m], w_block [m] or None);
+# the blocks must cover the cells once.
+# ---------------------------------------------------------------------------
+
+def pid_chunked(chunks):
+    """Full PID (Eq. 10 with Eq. 14) from G_ij = sum_x w u_i u_j and m_i = sum_x w u_i,
+    both accumulated block by block; P_ij = G_ij / m_i (ratio form of Eq. 9, 0 if m_i = 0).
+    Returns (in_in, in_out, depth)."""
+    G = None
+    m = None
+    for Ub, wb in chunks:
+        Ub = np.atleast_2d(_f64(Ub))
+        wb = cell_measure(Ub.shape[1], wb)
+        if G is None:
+            G = np.zeros((Ub.shape[0], Ub.shape[0]))
+            m = np.zeros(Ub.shape[0])
+        G += (Ub * wb) @ Ub.T
+        m += Ub @ wb
+    N = G.shape[0]
+    P = np.zeros_like(G)
+    nz = m > 0
+    P[nz, :] = G[nz, :] / m[nz, None]
+    in_in = P.sum(axis=1) / N
+    in_out = P.sum(axis=0) / N
+    return in_in, in_out, np.minimum(in_in, in_out)
+
+
+def pid_mean_chunked(chunks):
+    """PID-mean (Eq. 16) with u_bar of Eq. 15 formed per block (it is cell-local):
+    IN_in(i) = sum_x w u_i u_bar / sum_x w u_i, IN_out(i) = sum_x w u_bar u_i / sum_x w u_bar,
+    each sum accumulated block by block. Returns (in_in, in_out, depth)."""
+    num = None
+    for Ub, wb in chunks:
+        Ub = np.atleast_2d(_f64(Ub))
+        wb = cell_measure(Ub.shape[1], wb)
+        ubar = mean_contour(Ub)
+        if num is None:
+            num = np.zeros(Ub.shape[0])
+            m = np.zeros(Ub.shape[0])
+            mbar = 0.0
+        num += Ub @ (wb * ubar)
+        m += Ub @ wb
+        mbar += float(wb @ ubar)
+    in_in = np.where(m > 0, num / np.where(m > 0, m, 1.0), 0.0)
+    in_out = num / mbar if mbar > 0 else np.zeros_like(num)
     return in_in, in_out, np.minimum(in_in, in_out)
 
 

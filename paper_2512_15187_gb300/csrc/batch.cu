@@ -123,7 +123,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   std::map<std::pair<int, int>, std::vector<int>> gram_cls;
   for (int e = 0; e < count; ++e) {
     if (is_gram[e]) {
-      gram_cls[{(gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 32 + gp[e].G, iso_kind(gp[e].desc.iso_mode)}]
+      gram_cls[{((gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 2 + (gp[e].wide ? 1 : 0)) * 32 + gp[e].G,
+                iso_kind(gp[e].desc.iso_mode)}]
           .push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
@@ -173,6 +174,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     for (int e : members) {
       EnsDesc d = pl[e].desc;
       d.unit_begin = units;
+      d.work_begin = L.cells;
       d.coef = coef_pass ? coef[e] : nullptr;
       units += d.n_chunks;
       L.stage_floats = std::max(L.stage_floats, pl[e].stage_floats);
@@ -207,7 +209,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       f.P = o.P;
       f.err_est = o.err_est;
     }
-    const int nb = (2 * f.N + 31) / 32 + (kind == FIN_GRAM ? (f.N * f.N + 31) / 32 : 0);
+    const int nb = (2 * f.N + 31) / 32 + (kind == FIN_GRAM ? fin_gram_items(f.N) : 0);
     f.slices = std::max(1, std::min(nb, 2 * h->sms));
     return f;
   };
@@ -223,6 +225,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     for (int e : kv.second) {
       EnsDesc d = gp[e].desc;
       d.unit_begin = units;
+      d.work_begin = L.cells;
+      L.cells += static_cast<int64_t>(d.N) * d.M;
       d.part = part[e];
       d.gpart = gpart[e];
       d.op_scale = nullptr;
@@ -236,7 +240,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       L.gp.stage_floats = std::max(L.gp.stage_floats, gp[e].stage_floats);
       bp->sdesc.push_back(d);
     }
-    gram_geometry(h, L.gp.G, L.gp.prec, L.gp.stage_floats, &L.gp.dF, &L.gp.dO, &L.gp.smem);
+    gram_geometry(h, L.gp.G, L.gp.wide, L.gp.prec, L.gp.stage_floats, &L.gp.dF, &L.gp.dO,
+                  &L.gp.smem);
     L.iso_mode = gp[kv.second[0]].desc.iso_mode;
     L.total_units = units;
     bp->launches.push_back(L);
@@ -286,6 +291,7 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       sp.descs = sdev + L.first;
       sp.n_ens = L.count;
       sp.total_units = L.total_units;
+      sp.total_work = L.cells;
       sp.G = L.cfg.G;
       sp.sub = L.cfg.sub;
       sp.use_tma = L.tma ? 1 : 0;
@@ -301,7 +307,7 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
         if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
       }
       pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units,
-                                        L.iso_mode, L.bytes, L.flops, s);
+                                        L.cells, L.iso_mode, L.bytes, L.flops, s);
       if (st != PID_OK) return st;
     } else {
       FinParams fp;

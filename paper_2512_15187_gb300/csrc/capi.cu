@@ -407,6 +407,8 @@ static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef
   sp.descs = nullptr;
   sp.n_ens = 1;
   sp.total_units = pl.desc.n_chunks;
+  sp.one.work_begin = 0;
+  sp.total_work = static_cast<int64_t>(pl.desc.N) * pl.desc.M;
   sp.G = pl.cfg.G;
   sp.sub = pl.cfg.sub;
   sp.use_tma = pl.use_tma ? 1 : 0;
@@ -422,7 +424,7 @@ static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef
 
 static pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
   const int nb_stream = (2 * fd.N + 31) / 32;
-  const int nb_gram = fd.kind == FIN_GRAM ? (fd.N * fd.N + 31) / 32 : 0;
+  const int nb_gram = fd.kind == FIN_GRAM ? fin_gram_items(fd.N) : 0;
   fd.slices = std::max(1, std::min(nb_stream + nb_gram, 2 * h->sms));
   FinParams fp;
   std::memset(&fp, 0, sizeof(fp));

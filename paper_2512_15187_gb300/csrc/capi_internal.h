@@ -108,7 +108,8 @@ struct GramPlan {
   int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
   bool tma = true;         // rows 16-byte aligned: FP32 tiles staged by TMA
   int G = 16;              // warps per group (8: two groups per CTA for N <= 64)
-  int TS = 64;             // cells per stage
+  bool wide = false;       // 128 < N <= 256: 16 warps on 256 rows, two M = 128 row blocks
+  int TS = 128;            // cells per FP32 stage (64 for the wide tile)
   int n_gchunks = 0;
   int64_t chunk_cells = 0;
   int32_t stage_floats = 0;
@@ -149,13 +150,14 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
 
 // gram.cu
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
-void gram_geometry(pid_handle h, int G, int prec, int32_t stage_floats, int* dF, int* dO,
+void gram_geometry(pid_handle h, int G, bool wide, int prec, int32_t stage_floats, int* dF, int* dO,
                    size_t* smem);
 pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
                            float* gpart, float* scale, cudaStream_t s);
 // Gram launch over `count` device descriptors (part / gpart / op_scale already set).
 pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDesc* descs,
-                             int count, int total_units, int iso_mode, double bytes, double flops,
+                             int count, int total_units, int64_t total_work, int iso_mode,
+                             double bytes, double flops,
                              cudaStream_t s);
 
 // batch.cu

@@ -224,6 +224,45 @@ __device__ __forceinline__ float half_erfc_scaled(float as) {
   return t * ex2_approx(fmaf(-as, as, q));
 }
 
+// Packed FP32 pairs: on the sm_100 family one FFMA2 / FADD2 / FMUL2 instruction does the
+// arithmetic of two FP32 lanes with the rounding of the scalar instruction (round to
+// nearest even, no flush), so a kernel bound by instruction issue does half the issues.
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// half_erfc_scaled for two arguments xs (of either sign: a' = |xs|), with the polynomial on
+// packed pairs. Bitwise equal to the scalar function: the polynomial is evaluated with
+// negated coefficients, p = -Q(t) at every step (round to nearest is symmetric), so that
+// fma(xs, xs, p) = -fma(-a', a', Q) exactly and 2^-(that) is the scalar's 2^(Q - a'^2).
+__device__ __forceinline__ float2 half_erfc_scaled2(float2 xs) {
+  constexpr float c = static_cast<float>(0.5 / kSqrtLog2e);
+  const float2 t = make_float2(rcp_approx(fmaf(c, fabsf(xs.x), 1.0f)),
+                               rcp_approx(fmaf(c, fabsf(xs.y), 1.0f)));
+  float2 p = f2(-1.966346219e-01f);
+  p = f2_fma(p, t, f2(9.140366267e-01f));
+  p = f2_fma(p, t, f2(-1.507482838e+00f));
+  p = f2_fma(p, t, f2(7.885746771e-01f));
+  p = f2_fma(p, t, f2(2.953876851e-01f));
+  p = f2_fma(p, t, f2(-9.776866458e-02f));
+  p = f2_fma(p, t, f2(-1.710338295e-02f));
+  p = f2_fma(p, t, f2(-5.647117482e-01f));
+  p = f2_fma(p, t, f2(-1.439913215e+00f));
+  p = f2_fma(p, t, f2(2.825615422e+00f));
+  const float2 r = f2_fma(xs, xs, p);
+  return f2_mul(t, make_float2(ex2_approx(-r.x), ex2_approx(-r.y)));
+}
+
+// Normal-isovalue soft masks of two field values (see iso_value, mode 1), bitwise equal to
+// two scalar evaluations: xs = (F - mu) * inv, u = h if xs >= 0 else 1 - h.
+__device__ __forceinline__ float2 iso_normal2(float2 f, float mu, float inv) {
+  const float2 xs = f2_mul(f2_add(f, f2(-mu)), f2(inv));
+  const float2 h = half_erfc_scaled2(xs);
+  const float2 g = f2_fma(h, f2(-1.0f), f2(1.0f));
+  return make_float2(xs.x >= 0.f ? h.x : g.x, xs.y >= 0.f ? h.y : g.y);
+}
+
 // Soft-mask value of one input element (Sec. 3.5); used by the standalone map.
 //   mode 1: u = P(F < q), q ~ Normal(mu, sigma): u = erfc(a)/2 with a = (F - mu) / (sigma
 //           sqrt 2), from xs = (F - mu) * inv, inv = +-sqrt(log2 e) / (sigma sqrt 2)

@@ -18,15 +18,21 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   *gp = GramPlan{};
   if (in.N > kGramMaxN)
     return fail(h, PID_ERR_UNSUPPORTED,
-                "the tensor-core Gram takes N <= 128 in this build; use PID_MODE_FULL_LINEAR");
+                "the tensor-core Gram takes N <= 256 in this build; use PID_MODE_FULL_LINEAR");
   const uintptr_t a = reinterpret_cast<uintptr_t>(in.data);
   gp->tma = in.ld % 4 == 0 && a % 16 == 0 && (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
   gp->prec = in.precision;
   gp->G = in.N <= 64 ? 8 : 16;        // two independent 8-warp groups when N <= 64
-  gp->TS = 128;
+  gp->wide = in.N > kGramNarrowMaxN;   // two M = 128 row blocks, 64-cell FP32 stages
+  gp->TS = gp->wide ? 64 : 128;
+  // Chunks (one FP32 partial Gram each) of 32 to 256 operand stages: every chunk costs a
+  // TMEM drain, an N x N partial written and read back, and the MMA pipeline's ramp, so a
+  // few large chunks per ensemble beat one per group (batches supply the parallelism); the
+  // upper bound keeps the exact FP32 PID-mean sums of a chunk short enough for 1e-6.
   const int64_t groups = static_cast<int64_t>(h->sms) * (kGramConvWarps / gp->G);
-  int64_t chunk = rup((in.M + groups - 1) / groups, gp->TS);
-  chunk = std::max<int64_t>(chunk, gp->TS);
+  int64_t chunk = rup((in.M + groups - 1) / groups, 128);
+  chunk = std::max<int64_t>(chunk, std::min<int64_t>(rup(in.M, 128), 32 * 128));
+  chunk = std::min<int64_t>(chunk, 256 * 128);
   gp->chunk_cells = chunk;
   gp->n_gchunks = static_cast<int>((in.M + chunk - 1) / chunk);
 
@@ -54,7 +60,7 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   gp->stage_floats = gp->tma ? static_cast<int32_t>(rup(in.N * gp->TS + gp->TS, 32)) : 32;
   gp->gpart_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * in.N * in.N * 4, 256);
   gp->part_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * 2 * in.N * 8, 256);
-  gram_geometry(h, gp->G, gp->prec, gp->stage_floats, &gp->dF, &gp->dO, &gp->smem);
+  gram_geometry(h, gp->G, gp->wide, gp->prec, gp->stage_floats, &gp->dF, &gp->dO, &gp->smem);
   gp->flops = (in.precision == PID_SPLIT_BF16 ? 3.0 : 1.0) * 2.0 * static_cast<double>(in.N) *
               in.N * in.M;
   gp->bytes = 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0);
@@ -63,22 +69,23 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
 
 // Ring depths that fit the shared memory: at least two FP32 stages, then as many operand
 // stages as fit (at most four), then the FP32 ring deepened to at most six stages.
-void gram_geometry(pid_handle h, int G, int prec, int32_t stage_floats, int* dF, int* dO,
+void gram_geometry(pid_handle h, int G, bool wide, int prec, int32_t stage_floats, int* dF, int* dO,
                    size_t* smem) {
   const size_t cap = static_cast<size_t>(h->max_smem > 0 ? h->max_smem : 232448);
   int f = 2, o = 4;
-  while (o > 1 && gram_smem_bytes(G, prec, f, o, stage_floats) > cap) --o;
-  while (f > 1 && gram_smem_bytes(G, prec, f, o, stage_floats) > cap) --f;
-  while (f < 6 && gram_smem_bytes(G, prec, f + 1, o, stage_floats) <= cap) ++f;
+  while (o > 1 && gram_smem_bytes(G, wide, prec, f, o, stage_floats) > cap) --o;
+  while (f > 1 && gram_smem_bytes(G, wide, prec, f, o, stage_floats) > cap) --f;
+  while (f < 6 && gram_smem_bytes(G, wide, prec, f + 1, o, stage_floats) <= cap) ++f;
   *dF = f;
   *dO = o;
-  *smem = gram_smem_bytes(G, prec, f, o, stage_floats);
+  *smem = gram_smem_bytes(G, wide, prec, f, o, stage_floats);
 }
 
-static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, int prec, int iso_mode,
-                              int grid, size_t smem, double bytes, double flops, cudaStream_t s) {
+static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, bool wide, int prec,
+                              int iso_mode, int grid, size_t smem, double bytes, double flops,
+                              cudaStream_t s) {
   ProfScope ps(h, PID_KERNEL_GRAM, bytes, flops, s);
-  cudaError_t e = launch_gram(gpar, G, prec, iso_kind(iso_mode), grid, smem, s);
+  cudaError_t e = launch_gram(gpar, G, wide, prec, iso_kind(iso_mode), grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "Gram kernel launch");
   return PID_OK;
 }
@@ -98,6 +105,8 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   }
   gpar.n_ens = 1;
   gpar.total_units = gp.n_gchunks;
+  gpar.one.work_begin = 0;
+  gpar.total_work = static_cast<int64_t>(in.N) * in.M;
   gpar.dF = gp.dF;
   gpar.dO = gp.dO;
   gpar.stage_floats = gp.stage_floats;
@@ -107,17 +116,19 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   gpar.err = h->err_word;
   const int ng = kGramConvWarps / gp.G;
   const int grid = std::max(1, std::min(h->sms, (gp.n_gchunks + ng - 1) / ng));
-  return gram_launch(h, gpar, gp.G, gp.prec, gp.desc.iso_mode, grid, gp.smem, gp.bytes, gp.flops, s);
+  return gram_launch(h, gpar, gp.G, gp.wide, gp.prec, gp.desc.iso_mode, grid, gp.smem, gp.bytes,
+                     gp.flops, s);
 }
 
 pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* descs, int count,
-                             int total_units, int iso_mode, double bytes, double flops,
-                             cudaStream_t s) {
+                             int total_units, int64_t total_work, int iso_mode, double bytes,
+                             double flops, cudaStream_t s) {
   GramParams gpar;
   std::memset(&gpar, 0, sizeof(gpar));
   gpar.descs = descs;
   gpar.n_ens = count;
   gpar.total_units = total_units;
+  gpar.total_work = total_work;
   gpar.dF = gp.dF;
   gpar.dO = gp.dO;
   gpar.stage_floats = gp.stage_floats;
@@ -127,7 +138,7 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* de
   gpar.err = h->err_word;
   const int ng = kGramConvWarps / gp.G;
   const int grid = std::max(1, std::min(h->sms, (total_units + ng - 1) / ng));
-  return gram_launch(h, gpar, gp.G, gp.prec, iso_mode, grid, gp.smem, bytes, flops, s);
+  return gram_launch(h, gpar, gp.G, gp.wide, gp.prec, iso_mode, grid, gp.smem, bytes, flops, s);
 }
 
 }  // namespace pidh

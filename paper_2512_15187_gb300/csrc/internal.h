@@ -32,7 +32,7 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   const float* data;    // [N][ld]
   const float* w;       // [M] or nullptr (unit cell measure)
   const float* coef;    // [N] column-sum coefficients c_j; nullptr = 1/N for every member
-  double* part;         // [n_chunks][2N] partial sums: m_i, then A_i (or B_i)
+  double* part;         // [n_chunks][2N] partial sums: m_i, then N A_i (pass 1) or B_i (pass 2)
   int64_t ld;
   int32_t N, M;
   int32_t chunk_cells;  // multiple of the stage width sub*T
@@ -46,6 +46,7 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   int32_t pad0;
   float* gpart;         // Gram launches: [n_chunks][N][N] float32 partial Gram (G_ij at j*N + i)
   const float* op_scale;  // Gram FP8: device scalar multiplying every operand (nullptr = 256)
+  int64_t work_begin;   // member-cells of the launch's earlier ensembles (0 for the first)
 };
 
 struct StreamParams {
@@ -53,6 +54,7 @@ struct StreamParams {
   const EnsDesc* descs;    // device array of n_ens descriptors (batch)
   int32_t n_ens;
   int32_t total_units;     // chunks over all ensembles
+  int64_t total_work;      // sum of N * M over all ensembles (groups split it evenly)
   int32_t G;               // warps per group (1, 2, 4, 8, 16)
   int32_t depth;           // stages in each group's ring
   int32_t stage_floats;    // floats per stage; the last sub*T floats hold the weights
@@ -67,17 +69,19 @@ struct StreamParams {
 constexpr int kGramConvWarps = 16;
 constexpr int kGramEpiWarps = 4;      // converter warps 0..3, one per TMEM lane quarter
 constexpr int kGramThreads = kGramConvWarps * 32;
-constexpr int kGramMaxN = 128;        // one M = 128 tensor-core tile
+constexpr int kGramMaxN = 256;        // two M = 128 tensor-core row blocks (the wide tile)
+constexpr int kGramNarrowMaxN = 128;  // one M = 128 row block
 
 struct GramParams {
   EnsDesc one;
   const EnsDesc* descs;
   int32_t n_ens;
   int32_t total_units;
+  int64_t total_work;    // sum of N * M over all ensembles (groups split it evenly)
   int32_t dF;            // FP32 stages in the TMA ring
   int32_t dO;            // operand stages
   int32_t stage_floats;  // floats per FP32 stage (rows x TS + TS)
-  int32_t TS;            // cells per stage: 64 (16-bit operands) or 128 (FP8)
+  int32_t TS;            // cells per FP32 stage: 128, or 64 for the wide tile (N > 128)
   int32_t xchg;
   int32_t use_tma;       // 0: converters read FP32 directly (rows not 16-byte aligned)
   uint32_t* err;
@@ -128,6 +132,10 @@ struct IsoParams {
   float iso_mu, iso_inv, iso_t;
 };
 
+// Work items of the finalisation's Gram reduction: 32 warps each sum one 32-column block
+// of the [n_gchunks][N*N] partials, so an item covers 1024 columns.
+constexpr int fin_gram_items(int N) { return (N * N + 1023) / 1024; }
+
 // Launchers (stream.cu).
 // Kernel family of an isovalue mode: 0 none, 1 normal, 2 step (either direction).
 inline int iso_kind(int32_t iso_mode) { return iso_mode == ISO_NONE ? 0 : (iso_mode == ISO_NORMAL ? 1 : 2); }
@@ -137,9 +145,9 @@ cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, b
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
-size_t gram_smem_bytes(int G, int prec, int dF, int dO, int stage_floats);
-cudaError_t launch_gram(const GramParams& p, int G, int prec, int iso_kind, int grid, size_t smem,
-                        cudaStream_t s);
+size_t gram_smem_bytes(int G, bool wide, int prec, int dF, int dO, int stage_floats);
+cudaError_t launch_gram(const GramParams& p, int G, bool wide, int prec, int iso_kind, int grid,
+                        size_t smem, cudaStream_t s);
 cudaError_t gram_kernels_init(int max_smem);
 cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s);
 cudaError_t stream_kernels_init(int max_smem);

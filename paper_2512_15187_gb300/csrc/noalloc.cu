@@ -104,6 +104,8 @@ extern "C" pid_status pid_mean_noalloc(const float* U, int64_t N, int64_t M, int
   sp.one.unit_begin = 0;
   sp.n_ens = 1;
   sp.total_units = pl.desc.n_chunks;
+  sp.one.work_begin = 0;
+  sp.total_work = static_cast<int64_t>(pl.desc.N) * pl.desc.M;
   sp.G = pl.cfg.G;
   sp.sub = pl.cfg.sub;
   sp.use_tma = pl.use_tma ? 1 : 0;

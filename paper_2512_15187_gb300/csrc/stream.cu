@@ -111,16 +111,27 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
 
   const int N = d.N;
   const int nb_stream = (2 * N + 31) / 32;
-  const int nb_gram = d.kind == FIN_GRAM ? (N * N + 31) / 32 : 0;
+  const int nb_gram = d.kind == FIN_GRAM ? fin_gram_items(N) : 0;
   const int nb = nb_stream + nb_gram;
   const int dst_off = d.kind == FIN_LIN2 ? 2 * N : 0;
 
-  // Phase 1: this CTA's share of the column blocks.
+  // Phase 1: this CTA's share of the work items: 32-column blocks of the (m, A) partials
+  // (all warps on one block, rows split across warps), then 1024-column items of the Gram
+  // partials (each warp sums one 32-column block over every chunk, in chunk order).
   for (int cb = blockIdx.x; cb < nb; cb += d.slices) {
-    if (cb < nb_stream)
+    if (cb < nb_stream) {
       reduce_columns<double>(d.part, d.n_chunks, 2 * N, cb, d.sums + dst_off, scratch);
-    else
-      reduce_columns<float>(d.gpart, d.n_gchunks, N * N, cb - nb_stream, d.sums + 4 * N, scratch);
+    } else {
+      const int col = (cb - nb_stream) * 1024 + static_cast<int>(threadIdx.x);
+      const int NN = N * N;
+      if (col < NN) {
+        double acc = 0.0;
+#pragma unroll 4
+        for (int r = 0; r < d.n_gchunks; ++r)
+          acc += static_cast<double>(__ldcs(d.gpart + static_cast<size_t>(r) * NN + col));
+        d.sums[4 * N + col] = acc;
+      }
+    }
   }
   __threadfence();
   __syncthreads();
@@ -133,7 +144,8 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   const int i = threadIdx.x;
   const double* S = d.sums;
   double m = 0.0, A = 0.0;
-  if (i < N) { m = __ldcg(S + i); A = __ldcg(S + N + i); }
+  // The kernels sum A_i against the column sum N u_bar: the 1/N of Eq. 15 is applied here.
+  if (i < N) { m = __ldcg(S + i); A = __ldcg(S + N + i) / N; }
   // m_bar = (1/N) sum_i m_i, a fixed-order tree over the thread index.
   sred[i] = (i < N) ? m : 0.0;
   __syncthreads();
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     // scaling C_ij = d_i d_j (G'_ij + G'_ji) / 2 with d_i sum_j C... = N A_i (symmetric
     // Sinkhorn iteration, FP64), then P_ij = C_ij / m_i, IN_in = mean_j P_ij (= A_i / m_i),
     // IN_out = mean_j P_ji. err_est reports the uncalibrated |mean_j G'_ij / m_i - A_i / m_i|.
-    const double* Gm = S + 4 * N;
+    double* Gm = d.sums + 4 * N;   // the FP64 Gram of this ensemble (workspace)
     const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
     if (i < N) {
       double raw = 0.0;
@@ -184,29 +196,42 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
       sd[i] = (A > 0.0 && raw > 0.0) ? 1.0 : 0.0;
     }
     __syncthreads();
+    // Symmetrise in place, (G' + G'^T) / 2, so that every row is contiguous in memory.
+    for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
+      const int r = k / N, c = k - r * N;
+      if (r < c) {
+        const double v = 0.5 * (__ldcg(Gm + r + static_cast<size_t>(c) * N) +
+                                __ldcg(Gm + c + static_cast<size_t>(r) * N));
+        __stcg(Gm + r + static_cast<size_t>(c) * N, v);
+        __stcg(Gm + c + static_cast<size_t>(r) * N, v);
+      }
+    }
+    __syncthreads();
+    // Symmetric Sinkhorn: d_r <- sqrt(d_r N A_r / sum_j C0_rj d_j), until no scale moves by
+    // more than 1e-15 relative (at most 24 sweeps).
     for (int it = 0; it < 24; ++it) {
       for (int r = wi; r < N; r += kFinThreads / 32) {
         double acc = 0.0;
-        for (int j = ln; j < N; j += 32)
-          acc += 0.5 * (__ldcg(Gm + r + static_cast<size_t>(j) * N) +
-                        __ldcg(Gm + j + static_cast<size_t>(r) * N)) * sd[j];
+        for (int j = ln; j < N; j += 32) acc += __ldcg(Gm + static_cast<size_t>(r) * N + j) * sd[j];
         acc = warp_sum(acc);
         if (ln == 0) {
-          const double target = static_cast<double>(N) * __ldcg(S + N + r);
+          const double target = __ldcg(S + N + r);   // the kernels' sum N A_r
           sdn[r] = (sd[r] > 0.0 && acc > 0.0) ? sqrt(sd[r] * target / acc) : 0.0;
         }
       }
       __syncthreads();
-      if (i < N) sd[i] = sdn[i];
-      __syncthreads();
+      bool moved = false;
+      if (i < N) {
+        moved = fabs(sdn[i] - sd[i]) > 1e-15 * sd[i];
+        sd[i] = sdn[i];
+      }
+      if (!__syncthreads_or(moved)) break;
     }
     if (i < N) {
       double so = 0.0;
       for (int j = 0; j < N; ++j) {
         const double mj = __ldcg(S + j);
-        const double cji = sd[j] * sd[i] * 0.5 *
-                           (__ldcg(Gm + j + static_cast<size_t>(i) * N) +
-                            __ldcg(Gm + i + static_cast<size_t>(j) * N));
+        const double cji = sd[j] * sd[i] * __ldcg(Gm + static_cast<size_t>(j) * N + i);
         if (mj > 0.0) so += cji / mj;
       }
       in_out = so / N;
@@ -236,13 +261,11 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     }
     if (i == 0 && d.err_est) d.err_est[0] = sred[0];
     if (d.P) {
-      const double* Gm = S + 4 * N;
+      const double* Gm = S + 4 * N;   // symmetrised above
       for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
-        const int r = k / N, cc = k - r * N;   // P[r][cc] = C_{r,cc} / m_r
+        const int r = k / N, cc = k - r * N;   // P[r][cc] = C_{r,cc} / m_r (Gm symmetric now)
         const double mr = __ldcg(S + r);
-        const double c = sd[r] * sd[cc] * 0.5 *
-                         (__ldcg(Gm + r + static_cast<size_t>(cc) * N) +
-                          __ldcg(Gm + cc + static_cast<size_t>(r) * N));
+        const double c = sd[r] * sd[cc] * __ldcg(Gm + k);
         d.P[k] = mr > 0.0 ? c / mr : 0.0;
       }
     }

@@ -4,10 +4,11 @@
 // One pass over an ensemble U [N][M]: per tile of T cells the column sum
 // s(x) = sum_j c_j u_j(x) is formed on chip, then every member accumulates
 //   m_i = sum_x w u_i  and  A_i = sum_x w u_i s.
-// With c_j = 1/N, s is the mean contour u_bar (Eq. 15) and IN_in = A_i / m_i,
-// IN_out = A_i / m_bar (Eq. 16). With c_j = 1/(N m_j) the same pass yields IN_out of full
-// PID exactly: A_i = (1/N) sum_j G_ij / m_j (Eq. 10 with the sums of Eq. 14). The
-// isovalue map of Sec. 3.5 can be applied to each element as it is read.
+// With c_j = 1, s = N u_bar (the mean contour of Eq. 15 times N: the 1/N is applied in
+// FP64 by the finalisation, so no rounded 1/N enters the FP32 sums) and IN_in = A_i /
+// (N m_i), IN_out = A_i / (N m_bar) (Eq. 16). With c_j = 1/(N m_j) the same pass yields
+// IN_out of full PID exactly: A_i = (1/N) sum_j G_ij / m_j (Eq. 10 with the sums of
+// Eq. 14). The isovalue map of Sec. 3.5 can be applied to each element as it is read.
 //
 // Work decomposition: groups of G warps share a TMA-fed shared-memory ring of stages; a
 // stage holds [N rows][sub*T cells] of one chunk; warp q of a group owns members
@@ -39,6 +40,27 @@ __device__ __forceinline__ int stream_find_ens(const StreamParams& p, int u) {
   return lo;
 }
 
+// First unit whose start lies at or after position w of the launch's work (member-cells,
+// counted along the ensembles and their chunks). Group g owns the units starting in
+// [W g / groups, W (g+1) / groups): equal work per group to within one unit, whatever the
+// mix of ensemble sizes, and contiguous units, so a group meets each ensemble once.
+template <typename Params>
+__device__ __forceinline__ int unit_at_work(const Params& p, int64_t w) {
+  if (w >= p.total_work) return p.total_units;
+  const EnsDesc* d = &p.one;
+  if (p.descs != nullptr) {
+    int lo = 0, hi = p.n_ens - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.descs[mid].work_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    d = p.descs + lo;
+  }
+  const int64_t per = static_cast<int64_t>(d->N) * d->chunk_cells;
+  const int64_t c = (w - d->work_begin + per - 1) / per;
+  return d->unit_begin + static_cast<int>(c < d->n_chunks ? c : d->n_chunks);
+}
+
 template <int VEC> struct VecT;
 template <> struct VecT<1> { using T = float; };
 template <> struct VecT<2> { using T = float2; };
@@ -56,12 +78,53 @@ __device__ __forceinline__ void lds_vec(float (&dst)[VEC], const float* src) {
   }
 }
 
+template <int VEC>
+__device__ __forceinline__ void sts_vec(float* dst, const float (&src)[VEC]) {
+  if constexpr (VEC == 1) {
+    *dst = src[0];
+  } else if constexpr (VEC == 2) {
+    *reinterpret_cast<float2*>(dst) = make_float2(src[0], src[1]);
+  } else {
+    *reinterpret_cast<float4*>(dst) = make_float4(src[0], src[1], src[2], src[3]);
+  }
+}
+
 // Isovalue map kinds compiled into a kernel.
 enum IsoKind : int { ISOK_NONE = 0, ISOK_NORMAL = 1, ISOK_STEP = 2 };
 
 // Soft-mask value of one element for a compile-time isovalue kind (Sec. 3.5).
 //   NORMAL: u = erfc(xs) / 2, xs = (F - mu) * inv with inv = +-sqrt(log2 e) / (sigma sqrt 2)
 //   STEP:   u = 1[(F - t) * dir < 0], dir = +1 (F < t) or -1 (F > t)
+// s[v] = sum over r < G of part[r * stride + v], added in order r = 0, 1, ... (packed pairs
+// when VEC is even; the order, and so the bits, are those of a scalar loop).
+template <int VEC, int G>
+__device__ __forceinline__ void sum_partials(float (&s)[VEC], const float* part, int stride) {
+  if constexpr (VEC % 2 == 0) {
+    float2 a[VEC / 2];
+#pragma unroll
+    for (int v = 0; v < VEC / 2; ++v) a[v] = f2(0.f);
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      float t[VEC];
+      lds_vec<VEC>(t, part + r * stride);
+#pragma unroll
+      for (int v = 0; v < VEC / 2; ++v) a[v] = f2_add(a[v], make_float2(t[2 * v], t[2 * v + 1]));
+    }
+#pragma unroll
+    for (int v = 0; v < VEC / 2; ++v) { s[2 * v] = a[v].x; s[2 * v + 1] = a[v].y; }
+  } else {
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) s[v] = 0.f;
+#pragma unroll
+    for (int r = 0; r < G; ++r) {
+      float t[VEC];
+      lds_vec<VEC>(t, part + r * stride);
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) s[v] += t[v];
+    }
+  }
+}
+
 template <int ISO>
 __device__ __forceinline__ float iso_map(float f, float mu, float inv, float t, float dir) {
   if constexpr (ISO == ISOK_NORMAL) {
@@ -72,6 +135,37 @@ __device__ __forceinline__ float iso_map(float f, float mu, float inv, float t, 
     return (f - t) * dir < 0.f ? 1.0f : 0.0f;
   } else {
     return f;
+  }
+}
+
+// The isovalue map over a lane's MPW x VEC values, two at a time (packed FP32) for the
+// normal kind: pairs of neighbouring cells, or of neighbouring members when VEC = 1.
+template <int ISO, int MPW, int VEC>
+__device__ __forceinline__ void iso_map_tile(float (&x)[MPW][VEC], float mu, float inv, float t,
+                                             float dir) {
+  if constexpr (ISO == ISOK_NORMAL && VEC % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < MPW; ++k)
+#pragma unroll
+      for (int v = 0; v < VEC; v += 2) {
+        const float2 u = iso_normal2(make_float2(x[k][v], x[k][v + 1]), mu, inv);
+        x[k][v] = u.x;
+        x[k][v + 1] = u.y;
+      }
+  } else if constexpr (ISO == ISOK_NORMAL && MPW % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < MPW; k += 2)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        const float2 u = iso_normal2(make_float2(x[k][v], x[k + 1][v]), mu, inv);
+        x[k][v] = u.x;
+        x[k + 1][v] = u.y;
+      }
+  } else {
+#pragma unroll
+    for (int k = 0; k < MPW; ++k)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], mu, inv, t, dir);
   }
 }
 
@@ -86,6 +180,7 @@ template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 stream_kernel(const __grid_constant__ StreamParams p) {
   static_assert(MPW <= 32, "member coefficients are broadcast from one lane each");
+  static_assert(VEC % 2 == 0 || MPW % 2 == 0, "values are processed in packed pairs");
   constexpr int T = 32 * VEC;
   constexpr int NG = kStreamWarps / G;
   constexpr int RB = G * T + T;  // floats per exchange buffer
@@ -120,42 +215,54 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   if (threadIdx.x < 2 * NG) flags[threadIdx.x] = 0;
   __syncthreads();
 
+  // Each group takes a contiguous run of the flat unit list (an equal share of the work).
+  // An ensemble's chunks are consecutive units, so a group looks an ensemble up (and
+  // reloads its descriptor) only when it crosses into the next one; the chunks, and so the
+  // results, do not depend on which group computes them.
   const int gid = blockIdx.x * NG + grp;
   const int total_groups = gridDim.x * NG;
+  const int u_begin = unit_at_work(p, p.total_work * gid / total_groups);
+  const int u_end = unit_at_work(p, p.total_work * (gid + 1) / total_groups);
 
   // ---- producer cursor (leader lane of the group only) ----
-  int iu = gid, ist = 0, ie = 0, icell0 = 0, in_st = 0;
+  int iu = u_begin, ist = 0, icell0 = 0, in_st = 0;
+  int pe_begin = 0, pe_end = 0, pe_chunk = 0, pe_M = 0, pe_boxes = 0, pe_rows = 0;
+  bool pe_w = false;
+  const EnsDesc* pd = nullptr;
   long n_issued = 0;
   auto set_unit = [&](int u) {
-    ie = stream_find_ens(p, u);
-    const EnsDesc& d = stream_desc(p, ie);
-    const int c = u - d.unit_begin;
-    icell0 = c * d.chunk_cells;
-    const int cells = min(d.chunk_cells, d.M - icell0);
-    in_st = (cells + TS - 1) / TS;
+    if (u >= pe_end) {
+      pd = &stream_desc(p, stream_find_ens(p, u));
+      pe_begin = pd->unit_begin;
+      pe_end = pe_begin + pd->n_chunks;
+      pe_chunk = pd->chunk_cells;
+      pe_M = pd->M;
+      pe_boxes = pd->n_boxes;
+      pe_rows = pd->box_rows;
+      pe_w = pd->w != nullptr;
+    }
+    icell0 = (u - pe_begin) * pe_chunk;
+    in_st = (min(pe_chunk, pe_M - icell0) + TS - 1) / TS;
   };
   auto issue_next = [&]() {
-    if (iu >= p.total_units) return;
-    const EnsDesc& d = stream_desc(p, ie);
+    if (iu >= u_end) return;
     const int slot = static_cast<int>(n_issued % depth);
     float* dst = my_ring + static_cast<size_t>(slot) * SF;
-    const uint32_t bytes =
-        static_cast<uint32_t>(d.n_boxes * d.box_rows * TS + (d.w ? TS : 0)) * 4u;
+    const uint32_t bytes = static_cast<uint32_t>(pe_boxes * pe_rows * TS + (pe_w ? TS : 0)) * 4u;
     mbar_arrive_expect_tx(&my_bars[slot], bytes);
     const int x0 = icell0 + ist * TS;
-    for (int b = 0; b < d.n_boxes; ++b)
-      tma_load_2d(dst + static_cast<size_t>(b) * d.box_rows * TS, &d.tmap, &my_bars[slot], x0,
-                  b * d.box_rows);
-    if (d.w) tma_load_1d(dst + SF - TS, &d.tmap_w, &my_bars[slot], x0);
+    for (int b = 0; b < pe_boxes; ++b)
+      tma_load_2d(dst + static_cast<size_t>(b) * pe_rows * TS, &pd->tmap, &my_bars[slot], x0,
+                  b * pe_rows);
+    if (pe_w) tma_load_1d(dst + SF - TS, &pd->tmap_w, &my_bars[slot], x0);
     ++n_issued;
     if (++ist == in_st) {
       ist = 0;
-      iu += total_groups;
-      if (iu < p.total_units) set_unit(iu);
+      if (++iu < u_end) set_unit(iu);
     }
   };
   if (TMA && leader) {
-    if (iu < p.total_units) set_unit(iu);
+    if (iu < u_end) set_unit(iu);
     for (int s = 0; s < depth; ++s) issue_next();
   }
 
@@ -165,32 +272,43 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   bool aborted = false;
   uint32_t bad = 0;
 
-  for (int u = gid; u < p.total_units && !aborted; u += total_groups) {
-    const int e = stream_find_ens(p, u);
-    const EnsDesc& d = stream_desc(p, e);
-    const int N = d.N;
-    const int M = d.M;                       // descriptor fields kept in registers: the
-    const bool validate = d.validate != 0;   // asm barriers below clobber memory
-    const int c = u - d.unit_begin;
-    const int cell0 = c * d.chunk_cells;
-    const int cells = min(d.chunk_cells, M - cell0);
-    const int n_st = (cells + TS - 1) / TS;
-    const float iso_mu = d.iso_mu, iso_inv = d.iso_inv, iso_t = d.iso_t;
-    // Rows past N read this value, which every isovalue kind maps to exactly 0.
-    const float dir = (d.iso_mode == ISO_STEP_ABOVE) ? -1.f : 1.f;
-    const float pad = ISO == ISOK_NONE ? 0.f
-                      : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
-                                            : dir * __int_as_float(0x7f800000));
-    const bool has_w = d.w != nullptr;
-
-    // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
-    // every member weighs 1/N, applied once per cell (pass 1).
-    float my_cf = 0.f;
-    if constexpr (COEF) {
-      const int i = q + lane * G;
-      if (lane < MPW && i < N) my_cf = d.coef[i];
+  // Descriptor fields of the current ensemble, kept in registers (the asm barriers below
+  // clobber memory, so reading them through the descriptor would reload them every tile).
+  const EnsDesc* dp = nullptr;
+  int N = 0, M = 0, e_begin = 0, e_end = 0, e_chunk = 0;
+  bool validate = false, has_w = false;
+  float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f, my_cf = 0.f;
+  for (int u = u_begin; u < u_end && !aborted; ++u) {
+    if (u >= e_end) {
+      dp = &stream_desc(p, stream_find_ens(p, u));
+      N = dp->N;
+      M = dp->M;
+      e_begin = dp->unit_begin;
+      e_end = e_begin + dp->n_chunks;
+      e_chunk = dp->chunk_cells;
+      validate = dp->validate != 0;
+      has_w = dp->w != nullptr;
+      iso_mu = dp->iso_mu;
+      iso_inv = dp->iso_inv;
+      iso_t = dp->iso_t;
+      dir = (dp->iso_mode == ISO_STEP_ABOVE) ? -1.f : 1.f;
+      // Rows past N read this value, which every isovalue kind maps to exactly 0.
+      pad = ISO == ISOK_NONE ? 0.f
+                             : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
+                                                   : dir * __int_as_float(0x7f800000));
+      // Column-sum coefficients: lane k holds c_j of this warp's k-th member (pass 2), or
+      // every member weighs 1 (pass 1).
+      my_cf = 0.f;
+      if constexpr (COEF) {
+        const int i = q + lane * G;
+        if (lane < MPW && i < N) my_cf = dp->coef[i];
+      }
     }
-    const float inv_n = 1.0f / static_cast<float>(N);
+    const EnsDesc& d = *dp;
+    const int c = u - e_begin;
+    const int cell0 = c * e_chunk;
+    const int cells = min(e_chunk, M - cell0);
+    const int n_st = (cells + TS - 1) / TS;
     float accM[MPW], accA[MPW];
 #pragma unroll
     for (int k = 0; k < MPW; ++k) { accM[k] = 0.f; accA[k] = 0.f; }
@@ -254,12 +372,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
             }
           }
         }
-        if constexpr (ISO != ISOK_NONE) {
-#pragma unroll
-          for (int k = 0; k < MPW; ++k)
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], iso_mu, iso_inv, iso_t, dir);
-        }
+        if constexpr (ISO != ISOK_NONE) iso_map_tile<ISO>(x, iso_mu, iso_inv, iso_t, dir);
         if (!full) {  // only the ensemble's last tile: cells past M carry no mass
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {
@@ -272,18 +385,38 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 
         // Column sum over this warp's members (padding rows hold zeros) ...
         float s[VEC];
+        if constexpr (VEC % 2 == 0) {
+          float2 s2[VEC / 2];
 #pragma unroll
-        for (int v = 0; v < VEC; ++v) s[v] = 0.f;
+          for (int v = 0; v < VEC / 2; ++v) s2[v] = f2(0.f);
 #pragma unroll
-        for (int k = 0; k < MPW; ++k) {
-          if constexpr (COEF) {
-            const float cfk = __shfl_sync(0xffffffffu, my_cf, k);
+          for (int k = 0; k < MPW; ++k) {
+            if constexpr (COEF) {
+              const float2 cfk = f2(__shfl_sync(0xffffffffu, my_cf, k));
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] = fmaf(cfk, x[k][v], s[v]);
-          } else {
+              for (int v = 0; v < VEC / 2; ++v)
+                s2[v] = f2_fma(cfk, make_float2(x[k][2 * v], x[k][2 * v + 1]), s2[v]);
+            } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] += x[k][v];
+              for (int v = 0; v < VEC / 2; ++v)
+                s2[v] = f2_add(s2[v], make_float2(x[k][2 * v], x[k][2 * v + 1]));
+            }
           }
+#pragma unroll
+          for (int v = 0; v < VEC / 2; ++v) { s[2 * v] = s2[v].x; s[2 * v + 1] = s2[v].y; }
+        } else {
+          float2 s2 = f2(0.f);
+#pragma unroll
+          for (int k = 0; k < MPW; k += 2) {
+            if constexpr (COEF) {
+              const float2 cfk = make_float2(__shfl_sync(0xffffffffu, my_cf, k),
+                                             __shfl_sync(0xffffffffu, my_cf, k + 1));
+              s2 = f2_fma(cfk, make_float2(x[k][0], x[k + 1][0]), s2);
+            } else {
+              s2 = f2_add(s2, make_float2(x[k][0], x[k + 1][0]));
+            }
+          }
+          s[0] = s2.x + s2.y;
         }
         // ... then across the G warps of the group: every warp posts its partial; either
         // every warp adds the G partials (xchg 0), or warp r first totals the cells
@@ -291,8 +424,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         // partials in warp order, so both give the same bits.
         float* rb = my_red + static_cast<int>(k_sub & 1) * RB;
         if constexpr (G > 1) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) rb[q * T + lane * VEC + v] = s[v];
+          sts_vec<VEC>(rb + q * T + lane * VEC, s);
           named_barrier(1 + grp, G * 32);
         } else {
           __syncwarp();
@@ -315,49 +447,20 @@ stream_kernel(const __grid_constant__ StreamParams p) {
             lds_vec<VEC>(s, rb + G * T + lane * VEC);
           } else {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] = 0.f;
-#pragma unroll
-            for (int r = 0; r < G; ++r) {
-              float t[VEC];
-              lds_vec<VEC>(t, rb + r * T + lane * VEC);
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) s[v] += t[v];
-            }
+            sum_partials<VEC, G>(s, rb + lane * VEC, T);
           }
         } else if constexpr (G == 2) {
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) s[v] = 0.f;
-#pragma unroll
-          for (int r = 0; r < G; ++r) {
-            float t[VEC];
-            lds_vec<VEC>(t, rb + r * T + lane * VEC);
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) s[v] += t[v];
-          }
-        }
-        if constexpr (!COEF) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) s[v] *= inv_n;
+          sum_partials<VEC, G>(s, rb + lane * VEC, T);
         }
         // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
-        if (has_w) {
 #pragma unroll
-          for (int k = 0; k < MPW; ++k) {
+        for (int k = 0; k < MPW; ++k) {
 #pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              const float t = wv[v] * x[k][v];
-              accM[k] += t;
-              accA[k] = fmaf(t, s[v], accA[k]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < MPW; ++k) {
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              accM[k] += x[k][v];
-              accA[k] = fmaf(x[k][v], s[v], accA[k]);
-            }
+          for (int v = 0; v < VEC; ++v) {
+            const float t = has_w ? wv[v] * x[k][v] : x[k][v];
+            accM[k] += t;
+            accA[k] = fmaf(t, s[v], accA[k]);
           }
         }
       }

@@ -5,9 +5,11 @@
     python -m paper_2512_15187_gb300.profile_case linear        # exact full PID, O(N M)
     python -m paper_2512_15187_gb300.profile_case gram --precision bf16 --ensembles 4
 
-Each case builds its inputs on the device (seeded), runs the call three times and prints
-one line. Sizes default to N = 64 members and M = 2^20 cells (256 MiB of FP32 masks, larger
-than the 129 MB L2, so DRAM counters stay meaningful) and stay a few GB at most.
+Each case builds its inputs on the device (seeded), makes one call (planning, tuning and
+graph capture), then `--repeat` timed calls, and prints the best call time (CUDA events,
+host work included) and each kernel's time per launch from the library's own profiler.
+Sizes default to N = 64 members and M = 2^20 cells (256 MiB of FP32 masks, larger than
+the 129 MB L2, so DRAM counters stay meaningful); `--max-gb` bounds the input.
 """
 from __future__ import annotations
 
@@ -23,6 +25,8 @@ def main(argv=None) -> None:
                     help="ensembles per call (more than one goes through pid_batch)")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "split_bf16", "fp8"])
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--max-gb", type=float, default=4.0,
+                    help="refuse inputs above this size (profilers save and restore memory)")
     a = ap.parse_args(argv)
 
     import torch
@@ -30,8 +34,8 @@ def main(argv=None) -> None:
     from . import binding, build, synth
     build.build()
     N, M, E = a.members, a.cells, a.ensembles
-    if 4.0 * N * M * E > 4e9:
-        raise SystemExit("profile cases stay below 4 GB of input")
+    if 4.0 * N * M * E > a.max_gb * 1e9:
+        raise SystemExit(f"input above --max-gb {a.max_gb}")
     h = binding.Handle(0)
     X = torch.empty((E, N, M), device="cuda")
     side = int(round(M ** 0.5))
@@ -46,10 +50,28 @@ def main(argv=None) -> None:
     prec = a.precision if mode == "full" else "fp32"
     items = [dict(data=X[e], iso=(0.5, 0.05, 0) if is_field else None, mode=mode, precision=prec)
              for e in range(E)]
-    for _ in range(a.repeat):
-        outs = h.batch(items)
+    outs = h.batch(items)          # first call: plans, tunes and records the graph
     h.sync()
-    print("ok", a.case, mode, prec, f"N={N} M={M} E={E}", float(outs[0]["depth"].sum()))
+    h.profile(True)
+    ms = []
+    for _ in range(a.repeat):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        outs = h.batch(items)
+        t1.record()
+        t1.synchronize()
+        ms.append(t0.elapsed_time(t1))
+    h.sync()
+    prof = h.profile_read()
+    h.profile(False)
+    print("ok", a.case, mode, prec, f"N={N} M={M} E={E}", float(outs[0]["depth"].sum()),
+          f"call best {min(ms):.3f} ms")
+    for kind, st in prof.items():
+        if st["launches"]:
+            per = st["total_ms"] / st["launches"]
+            print(f"  {kind:9s} {st['launches']:4d} launches  {per:8.3f} ms/launch  "
+                  f"{st['bytes'] / st['launches'] / per / 1e6:8.1f} GB/s algorithmic")
     h.close()
 
 

@@ -57,7 +57,8 @@ def test_gram_first_small_case(H):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("N,M", [(1, 64), (2, 1000), (16, 4097), (33, 3000), (64, 65543),
-                                 (100, 5000), (128, 20000)])
+                                 (100, 5000), (128, 20000), (129, 777), (200, 20011),
+                                 (256, 9000)])
 @pytest.mark.parametrize("weighted", [False, True])
 def test_gram_parity(H, prec, N, M, weighted):
     U = synth.random_soft(N, M, seed=N * 131 + M, binary_frac=0.2)
@@ -98,8 +99,9 @@ def test_gram_binary_masks_are_exact(H, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("superlevel", [False, True])
-def test_gram_from_fields(H, prec, superlevel):
-    F = synth.rbf_fields_2d(N=64, H=128, W=96, n_rbf=8)
+@pytest.mark.parametrize("N", [64, 200])
+def test_gram_from_fields(H, prec, superlevel, N):
+    F = synth.rbf_fields_2d(N=N, H=128, W=96, n_rbf=8)
     F = (F - np.median(F, axis=1, keepdims=True)).astype(np.float32)
     w = np.random.default_rng(3).uniform(0.5, 2, F.shape[1]).astype(np.float32)
     o = H.from_fields(_dev(F), 0.01, 0.05, superlevel=superlevel, w=_dev(w), mode="full",
@@ -112,7 +114,7 @@ def test_gram_in_batch_with_exact_mean(H):
     rng = np.random.default_rng(5)
     items, refs = [], []
     for k, prec in enumerate(["bf16", "split_bf16", "fp8", "bf16", "fp8"]):
-        N = int(rng.integers(3, 129))
+        N = int(rng.integers(3, 257))
         M = int(rng.integers(500, 20000))
         U = synth.random_soft(N, M, seed=900 + k)
         w = rng.uniform(0.5, 3, M).astype(np.float32) if k % 2 else None
@@ -129,16 +131,17 @@ def test_gram_in_batch_with_exact_mean(H):
 def test_gram_rejects_too_many_members(H):
     import torch
     from paper_2512_15187_gb300 import binding as B
-    U = torch.rand((129, 256), device="cuda")
+    U = torch.rand((257, 256), device="cuda")
     with pytest.raises(B.PidError) as e:
         H.full(U, mode="full", precision="bf16")
     assert e.value.status == B.PID_ERR_UNSUPPORTED
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_gram_unaligned_rows_read_directly(H, prec):
+@pytest.mark.parametrize("N", [24, 150])
+def test_gram_unaligned_rows_read_directly(H, prec, N):
     import torch
-    N, M = 24, 9001
+    M = 9001
     U = synth.random_soft(N, M, seed=11)
     big = torch.zeros((N, M + 3), dtype=torch.float32, device="cuda")
     big[:, :M] = _dev(U)

@@ -43,7 +43,7 @@ REQ_KINDS = [("mean", "fp32"), ("linear", "fp32"), ("full", "bf16"), ("full", "f
 
 
 def _kind_ok(ens, kind):
-    return not (kind[0] == "full" and ens["data"].shape[0] > 128)
+    return not (kind[0] == "full" and ens["data"].shape[0] > 256)
 
 
 def test_results_same_alone_and_in_the_mix(B):

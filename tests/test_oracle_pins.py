@@ -280,3 +280,54 @@ def test_eid_is_strictly_pinned_by_counts():
     a, b, d = O.eid(A)
     assert a[0] == pytest.approx((1 + 0.5 + 0.5) / 3)
     assert b[0] == pytest.approx((1 + 1 + 2 / 3) / 3)
+
+
+# --- the block-accumulated forms used at full workload sizes --------------------------
+
+def _blocks(U, w, edges):
+    return ((U[:, a:b], None if w is None else w[a:b]) for a, b in zip(edges[:-1], edges[1:]))
+
+
+def test_chunked_forms_match_closed_forms_and_set_counts():
+    # nested binary disks: the closed form above, through uneven blocks
+    radii = [4, 7, 10, 13, 16, 20]
+    U = synth.nested_disks(radii, 48, 48).astype(np.float64)
+    a_area = U.sum(axis=1)
+    N = len(radii)
+    in_in = np.array([((N - k) + sum(a_area[j] / a_area[k] for j in range(k))) / N
+                      for k in range(N)])
+    in_out = np.array([((k + 1) + sum(a_area[k] / a_area[j] for j in range(k + 1, N))) / N
+                       for k in range(N)])
+    edges = [0, 1, 700, 701, 1500, 48 * 48]
+    a, b, _ = O.pid_chunked(_blocks(U, None, edges))
+    np.testing.assert_allclose(a, in_in, atol=1e-14)
+    np.testing.assert_allclose(b, in_out, atol=1e-14)
+    # binary masks with an empty member: eID by set counts (zero-mass reading: P_i. = 0)
+    rng = np.random.default_rng(4)
+    Ub = (rng.uniform(0, 1, (6, 300)) < 0.4).astype(np.float64)
+    sets = [set(np.nonzero(r)[0].tolist()) for r in Ub]
+    a, b, d = O.pid_chunked(_blocks(Ub, None, [0, 77, 78, 300]))
+    ea, eb, ed = O.eid(sets)
+    np.testing.assert_allclose(a, ea, atol=1e-14)
+    np.testing.assert_allclose(b, eb, atol=1e-14)
+    # constant masks: PID-mean closed form min(mean c, c_i), weighted, uneven blocks
+    c = np.array([0.2, 0.9, 0.5, 0.7, 0.05])
+    Uc = np.repeat(c[:, None], 40, axis=1)
+    w = np.linspace(0.5, 3.0, 40)
+    a, b, d = O.pid_mean_chunked(_blocks(Uc, w, [0, 3, 39, 40]))
+    np.testing.assert_allclose(a, np.full(5, c.mean()), atol=1e-15)
+    np.testing.assert_allclose(b, c, atol=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_chunked_forms_do_not_depend_on_the_blocks(seed):
+    rng = np.random.default_rng(seed)
+    U = synth.random_soft(9, 2000, seed=seed, binary_frac=0.3).astype(np.float64)
+    U[3] = 0.0                                            # a zero-mass member
+    w = rng.uniform(0.1, 5, 2000)
+    full = np.array(O.pid(U, w))
+    mean = np.array(O.pid_mean(U, w))
+    for edges in ([0, 2000], [0, 1, 2, 1999, 2000], list(range(0, 2001, 250))):
+        np.testing.assert_allclose(np.array(O.pid_chunked(_blocks(U, w, edges))), full, atol=1e-13)
+        np.testing.assert_allclose(np.array(O.pid_mean_chunked(_blocks(U, w, edges))), mean,
+                                   atol=1e-13)
