@@ -25,6 +25,8 @@ def main(argv=None) -> None:
                     help="ensembles per call (more than one goes through pid_batch)")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16", "split_bf16", "fp8"])
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tiles (no timing of candidate tiles on the first call)")
     ap.add_argument("--max-gb", type=float, default=4.0,
                     help="refuse inputs above this size (profilers save and restore memory)")
     a = ap.parse_args(argv)
@@ -37,6 +39,8 @@ def main(argv=None) -> None:
     if 4.0 * N * M * E > a.max_gb * 1e9:
         raise SystemExit(f"input above --max-gb {a.max_gb}")
     h = binding.Handle(0)
+    if a.no_autotune:
+        h.autotune(False)
     X = torch.empty((E, N, M), device="cuda")
     side = int(round(M ** 0.5))
     for e in range(E):
