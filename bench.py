@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson arrivals per serving scenario (0 = skip serving)")
+    ap.add_argument("--no-workloads", action="store_true",
+                    help="skip the other benchmark workloads (ellipses, non-Cartesian, 3D plume batch)")
     ap.add_argument("--source-hash", action="store_true",
                     help="print the kernel-source stamp that ncu summaries carry, and exit")
     return ap.parse_args()
@@ -281,6 +283,111 @@ def run_serving(device, seconds, rate_hz, budget_bytes=150 << 30, n_ens=24, seed
 # Reference arm: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------------------
+# The other workloads, reported beside the headline: 2D ellipses (latency), non-Cartesian
+# weighted points (throughput), and a 3D plume batch with uneven extras in one pid_batch
+# call against the same work as one call per ensemble.
+# ---------------------------------------------------------------------------------------
+
+def run_workloads(h, dev, stream):
+    import math
+    import statistics
+
+    import numpy as np
+    import torch
+
+    from paper_2512_15187_gb300 import synth
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {}
+    # 2D ellipses, 20 x 128^2 (1.3 MB, fits in L2): latency per call, L2 flushed before each
+    U = torch.from_numpy(synth.ellipses_2d()).to(dev)
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(max(1, 2 * l2 // 4), dtype=torch.float32, device=dev)
+    lat = {}
+    for name, fn in (("pid_mean", lambda: h.mean(U, stream=stream)),
+                     ("full_exact_fp32", lambda: h.full(U, mode="linear", stream=stream)),
+                     ("full_gram_bf16", lambda: h.full(U, mode="full", precision="bf16", stream=stream))):
+        fn()
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            a, b = ev(), ev()
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b) * 1000.0)
+        lat[name] = statistics.median(ts)
+    out["ellipses_20x128x128"] = {"unit": "us per call (median of 20, L2 flushed before each)", **lat}
+    del U, flush
+
+    # non-Cartesian: 128 members on 2^20 weighted points, one call per path
+    Un, wn = synth.radial_disk(N=128, M=1 << 20)
+    Ud, wd = torch.from_numpy(Un).to(dev), torch.from_numpy(wn).to(dev)
+    work = 128 * (1 << 20)
+    thr = {}
+    for name, fn in (("pid_mean", lambda: h.mean(Ud, wd, stream=stream)),
+                     ("full_exact_fp32", lambda: h.full(Ud, wd, mode="linear", stream=stream)),
+                     ("full_gram_split_bf16",
+                      lambda: h.full(Ud, wd, mode="full", precision="split_bf16", stream=stream))):
+        thr[name] = work / (timed(fn, 10) * 1e-3)
+    out["noncartesian_128x1M_weighted"] = {"unit": "member-cells/s per call", **thr}
+    del Ud, wd, Un, wn
+
+    # 3D plume: 2 time steps of 200 x 256^3 plus 48 uneven ensembles (N in [10, 500],
+    # M log-uniform in [64^2, 128^3]); PID-mean, and the E4M3 / split-BF16 Gram for the
+    # plume steps, exact full PID for the extras
+    steps = [synth.plume_3d(200, 256, t=t) for t in (0, 8)]
+    rng = np.random.default_rng(4)
+    g = torch.Generator(device=dev)
+    g.manual_seed(4)
+    extras = []
+    for _ in range(48):
+        N = int(rng.integers(10, 501))
+        M = int(round(math.exp(rng.uniform(math.log(64 ** 2), math.log(128 ** 3)))))
+        extras.append(torch.rand((N, M), generator=g, device=dev))
+    items = [dict(data=U, mode="mean") for U in steps]
+    items += [dict(data=U, mode="full", precision=p) for U in steps for p in ("fp8", "split_bf16")]
+    items += [dict(data=X, mode=m) for X in extras for m in ("mean", "linear")]
+    passes = {"mean": 1, "full": 1, "linear": 2}
+    member_cells = sum(it["data"].shape[0] * it["data"].shape[1] for it in items)
+    read_bytes = sum(4.0 * it["data"].numel() * passes[it["mode"]] for it in items)
+
+    def loop():
+        for it in items:
+            if it["mode"] == "mean":
+                h.mean(it["data"], stream=stream)
+            else:
+                h.full(it["data"], mode=it["mode"], precision=it.get("precision", "fp32"),
+                       stream=stream)
+
+    t_batch = timed(lambda: h.batch(items, stream=stream), 3)
+    t_loop = timed(loop, 3)
+    out["plume_2x200x256cubed_plus_48_uneven"] = {
+        "items": len(items), "member_cells_per_call": member_cells,
+        "batched_ms": t_batch, "one_call_per_ensemble_ms": t_loop,
+        "batched_speedup": t_loop / t_batch,
+        "batched_member_cells_per_s": member_cells / (t_batch * 1e-3),
+        "batched_read_gb_per_s": read_bytes / (t_batch * 1e-3) / 1e9}
+    del steps, extras
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank):
     """The oracle as it stands on the host cores: each step is one ensemble of the workload
     restricted to a 128-row band of the grid (64 x 65536 member x cells)."""
@@ -440,6 +547,9 @@ def main():
     serving = None
     if rank == 0 and args.serve_seconds > 0:
         serving = run_serving(local_rank, args.serve_seconds, 200.0)
+    workloads = None
+    if rank == 0 and not args.no_workloads:
+        workloads = run_workloads(h, dev, stream)
 
     # ---- end to end: pinned host inputs -> device -> results back, every step ----
     Ee = min(args.e2e_ensembles, E)
@@ -499,6 +609,8 @@ def main():
         }
         if serving is not None:
             line["serving"] = serving
+        if workloads is not None:
+            line["workloads"] = workloads
         if cpu_res is not None:
             line["cpu_baseline"] = cpu_baseline_record(cpu_res)
         print(json.dumps(line), flush=True)

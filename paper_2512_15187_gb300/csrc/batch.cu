@@ -103,12 +103,15 @@ static pid_status to_input(pid_handle h, const pid_ensemble& e, EnsInput* in) {
 }
 
 // Lay out descriptors and workspace for the batch. Pointers are offsets from `base`.
+// store_u: for exact full PID of a field, pass 1 also writes the soft masks into the
+// workspace and pass 2 streams them (instead of repeating the isovalue map).
 static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, char* base,
-                             BatchPlan* bp) {
+                             bool store_u, BatchPlan* bp) {
   std::vector<EnsInput> in(count);
   std::vector<EnsPlan> pl(count);
   std::vector<GramPlan> gp(count);
-  std::vector<int> is_gram(count, 0), is_lin(count, 0);
+  std::vector<int> is_gram(count, 0), is_lin(count, 0), stored(count, 0);
+  std::vector<EnsPlan> pl2(count);   // pass 2 over the stored soft masks
   for (int e = 0; e < count; ++e) {
     pid_status st = to_input(h, ens[e], &in[e]);
     if (st != PID_OK) return st;
@@ -116,6 +119,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     is_gram[e] = in[e].mode == PID_MODE_FULL && in[e].precision != PID_FP32;
     is_lin[e] = in[e].mode == PID_MODE_FULL_LINEAR || (in[e].mode == PID_MODE_FULL && !is_gram[e]);
     if (is_gram[e] && (st = plan_gram(h, in[e], &gp[e])) != PID_OK) return st;
+    stored[e] = store_u && is_lin[e] && in[e].is_field;
   }
   // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
   std::map<ClassKey, std::vector<int>> pass1, pass2;
@@ -129,7 +133,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
       pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik}].push_back(e);
-      if (is_lin[e]) pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1, ik}].push_back(e);
+      if (is_lin[e]) pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1, stored[e] ? 0 : ik}].push_back(e);
     }
   }
   const int n_sdesc = static_cast<int>(count + pass2.size() * 0);
@@ -158,6 +162,20 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes;
     }
     pl[e].desc.part = part[e];
+    if (stored[e]) {
+      const int64_t ldu = (in[e].M + 3) / 4 * 4;
+      float* ub = reinterpret_cast<float*>(base + off);
+      off += align_up(in[e].N * ldu * 4, 256);
+      pl[e].desc.u_out = ub;
+      EnsInput u = in[e];
+      u.data = ub;
+      u.ld = ldu;
+      u.is_field = 0;
+      u.validate = 0;    // checked on the fields in pass 1
+      const pid_status st2 = plan_stream(h, u, &pl2[e]);
+      if (st2 != PID_OK) return st2;
+      pl2[e].desc.part = part[e];
+    }
   }
   bp->work_bytes = off;
   if (count > kMaxTickets) return fail(h, PID_ERR_UNSUPPORTED, "too many ensembles in one batch");
@@ -172,13 +190,15 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.tma = true;
     int32_t units = 0;
     for (int e : members) {
-      EnsDesc d = pl[e].desc;
+      const EnsPlan& p = (coef_pass && stored[e]) ? pl2[e] : pl[e];
+      EnsDesc d = p.desc;
+      if (coef_pass) d.u_out = nullptr;
       d.unit_begin = units;
       d.work_begin = L.cells;
       d.coef = coef_pass ? coef[e] : nullptr;
       units += d.n_chunks;
-      L.stage_floats = std::max(L.stage_floats, pl[e].stage_floats);
-      L.tma = L.tma && pl[e].use_tma;
+      L.stage_floats = std::max(L.stage_floats, p.stage_floats);
+      L.tma = L.tma && p.use_tma;
       L.bytes += 4.0 * d.N * d.M + (d.w ? 4.0 * d.M : 0.0);
       L.max_n = std::max(L.max_n, d.N);
       L.cells += static_cast<int64_t>(d.N) * d.M;
@@ -336,29 +356,47 @@ extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t c
   if (!h->batch) h->batch = new BatchCache();
   BatchCache* c = h->batch;
 
-  // Plan against a null base to size the workspace, then for real.
-  BatchPlan sizing;
-  pid_status st = plan_batch(h, ens, count, nullptr, &sizing);
-  if (st != PID_OK) return st;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s, &cs);
   const bool capturing = cs != cudaStreamCaptureStatusNone;
-  // Replay the cached graph when the layout is unchanged (and the workspace did not move).
+  const bool profiled = h->profiling;
+  // Replay the cached graph when the batch is the one it was recorded for (same ensemble
+  // records, same workspace): no planning, no tensor-map encoding, one graph launch.
   std::vector<unsigned char> key(sizeof(pid_ensemble) * count + sizeof(void*));
   std::memcpy(key.data(), ens, sizeof(pid_ensemble) * count);
-  void* ws_before = h->ws;
-  if ((st = ensure_workspace(h, sizing.work_bytes, s)) != PID_OK) return st;
   std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
-  const bool profiled = h->profiling;
-  if (c->use_graphs && !capturing && !profiled && c->exec && h->ws == ws_before && key == c->key) {
+  if (c->use_graphs && !capturing && !profiled && c->exec && key == c->key) {
     cudaError_t e = cudaGraphLaunch(c->exec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch graph replay");
     ++c->replays;
     return PID_OK;
   }
+  // Plan against a null base to size the workspace, then for real. Soft masks of fields in
+  // exact full PID are stored for the second pass when the extra workspace fits the
+  // handle's budget (or, without one, half of the free device memory).
+  BatchPlan sizing;
+  bool store_u = true;
+  pid_status st = plan_batch(h, ens, count, nullptr, store_u, &sizing);
+  if (st != PID_OK) return st;
+  {
+    BatchPlan lean;
+    if ((st = plan_batch(h, ens, count, nullptr, false, &lean)) != PID_OK) return st;
+    const size_t extra = sizing.work_bytes - lean.work_bytes;
+    size_t free_b = 0, total_b = 0;
+    if (extra > 0) cudaMemGetInfo(&free_b, &total_b);
+    const size_t have = h->ws_bytes;
+    const size_t grow = sizing.work_bytes > have ? sizing.work_bytes - have : 0;
+    if (extra > 0 && ((h->budget && sizing.work_bytes + h->fixed_bytes > h->budget) ||
+                      (!h->budget && grow > free_b / 2))) {
+      store_u = false;
+      sizing = lean;
+    }
+  }
+  if ((st = ensure_workspace(h, sizing.work_bytes, s)) != PID_OK) return st;
+  std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
   BatchPlan bp;
   char* base = static_cast<char*>(h->ws);
-  if ((st = plan_batch(h, ens, count, base, &bp)) != PID_OK) return st;
+  if ((st = plan_batch(h, ens, count, base, store_u, &bp)) != PID_OK) return st;
   // Host image of the descriptors (pinned, so the upload is asynchronous and graph-safe).
   if (c->host_bytes < bp.desc_bytes) {
     if (c->exec) { cudaStreamSynchronize(s); }

@@ -47,6 +47,8 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   float* gpart;         // Gram launches: [n_chunks][N][N] float32 partial Gram (G_ij at j*N + i)
   const float* op_scale;  // Gram FP8: device scalar multiplying every operand (nullptr = 256)
   int64_t work_begin;   // member-cells of the launch's earlier ensembles (0 for the first)
+  float* u_out;         // streaming pass 1 of a field: also store the soft masks here,
+                        // [N][round_up(M, 4)] float32, for pass 2 to read (nullptr = no)
 };
 
 struct StreamParams {
@@ -103,7 +105,7 @@ struct FinDesc {
   int32_t n_gchunks, kind;
   int32_t slices;          // CTAs working on this ensemble
   int32_t pad0;
-  double* sums;            // workspace [4N + N*N] FP64: m, A, (second-pass m), B, then G
+  double* sums;            // workspace [4N] FP64 m, A, (second-pass m), B; then FP32 G [N*N], C0 [N*N]
   float* coef;             // FIN_LIN1 writes [N] coefficients here
   unsigned int* ticket;    // zero before the launch; the last CTA resets it
   double* depth;

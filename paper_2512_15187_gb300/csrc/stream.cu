@@ -106,7 +106,8 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   __shared__ double scratch[32][33];
   __shared__ double sdepth[1024];
   __shared__ double sred[1024];
-  __shared__ double sd[kGramMaxN], sdn[kGramMaxN];   // Gram calibration scales
+  __shared__ float sd[kGramMaxN], sdn[kGramMaxN];   // Gram calibration scales
+  __shared__ float sdm[kGramMaxN];                  // d_j / m_j (0 for zero mass)
   __shared__ int is_last;
 
   const int N = d.N;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
 #pragma unroll 4
         for (int r = 0; r < d.n_gchunks; ++r)
           acc += static_cast<double>(__ldcs(d.gpart + static_cast<size_t>(r) * NN + col));
-        d.sums[4 * N + col] = acc;
+        reinterpret_cast<float*>(d.sums + 4 * N)[col] = static_cast<float>(acc);
       }
     }
   }
@@ -187,54 +188,62 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     // scaling C_ij = d_i d_j (G'_ij + G'_ji) / 2 with d_i sum_j C... = N A_i (symmetric
     // Sinkhorn iteration, FP64), then P_ij = C_ij / m_i, IN_in = mean_j P_ij (= A_i / m_i),
     // IN_out = mean_j P_ji. err_est reports the uncalibrated |mean_j G'_ij / m_i - A_i / m_i|.
-    double* Gm = d.sums + 4 * N;   // the FP64 Gram of this ensemble (workspace)
+    // GB300's FP64 rate is a small fraction of its FP32 rate, so the O(N^2) calibration
+    // runs in FP32 (the scales converge to FP32 precision, ~1e-7, far inside the Gram
+    // bound); only the per-member scalars stay in FP64.
+    const float* Cg = reinterpret_cast<const float*>(d.sums + 4 * N);   // G' (phase 1)
+    float* C0 = reinterpret_cast<float*>(d.sums + 4 * N) + N * N;       // (G' + G'^T) / 2
     const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
-    if (i < N) {
-      double raw = 0.0;
-      for (int j = 0; j < N; ++j) raw += __ldcg(Gm + i + static_cast<size_t>(j) * N);
-      err = m > 0.0 ? fabs(raw / (m * N) - A / m) : 0.0;
-      sd[i] = (A > 0.0 && raw > 0.0) ? 1.0 : 0.0;
+    // Every row loop below runs one warp per row with the lanes on contiguous columns.
+    // Raw sums: row r of the stored array is G'_{., r}, which equals row r of G' up to
+    // the rounding of the tensor-core sums.
+    for (int r = wi; r < N; r += kFinThreads / 32) {
+      float acc = 0.f;
+      for (int j = ln; j < N; j += 32) acc += __ldcg(Cg + r * N + j);
+      acc = warp_sum(acc);
+      if (ln == 0) sdn[r] = acc;
     }
-    __syncthreads();
-    // Symmetrise in place, (G' + G'^T) / 2, so that every row is contiguous in memory.
     for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
       const int r = k / N, c = k - r * N;
-      if (r < c) {
-        const double v = 0.5 * (__ldcg(Gm + r + static_cast<size_t>(c) * N) +
-                                __ldcg(Gm + c + static_cast<size_t>(r) * N));
-        __stcg(Gm + r + static_cast<size_t>(c) * N, v);
-        __stcg(Gm + c + static_cast<size_t>(r) * N, v);
-      }
+      C0[k] = 0.5f * (__ldcg(Cg + r + c * N) + __ldcg(Cg + k));
+    }
+    __syncthreads();
+    if (i < N) {
+      const double raw = sdn[i];
+      err = m > 0.0 ? fabs(raw / (m * N) - A / m) : 0.0;
+      sd[i] = (A > 0.0 && raw > 0.0) ? 1.0f : 0.0f;
+      sdm[i] = static_cast<float>(N * A);   // row-sum targets N A_i, kept here until IN_out
     }
     __syncthreads();
     // Symmetric Sinkhorn: d_r <- sqrt(d_r N A_r / sum_j C0_rj d_j), until no scale moves by
-    // more than 1e-15 relative (at most 24 sweeps).
+    // more than 2^-22 relative (at most 24 sweeps).
     for (int it = 0; it < 24; ++it) {
       for (int r = wi; r < N; r += kFinThreads / 32) {
-        double acc = 0.0;
-        for (int j = ln; j < N; j += 32) acc += __ldcg(Gm + static_cast<size_t>(r) * N + j) * sd[j];
+        float acc = 0.f;
+        for (int j = ln; j < N; j += 32) acc = fmaf(__ldcg(C0 + r * N + j), sd[j], acc);
         acc = warp_sum(acc);
-        if (ln == 0) {
-          const double target = __ldcg(S + N + r);   // the kernels' sum N A_r
-          sdn[r] = (sd[r] > 0.0 && acc > 0.0) ? sqrt(sd[r] * target / acc) : 0.0;
-        }
+        if (ln == 0) sdn[r] = (sd[r] > 0.f && acc > 0.f) ? sqrtf(sd[r] * sdm[r] / acc) : 0.f;
       }
       __syncthreads();
       bool moved = false;
       if (i < N) {
-        moved = fabs(sdn[i] - sd[i]) > 1e-15 * sd[i];
+        moved = fabsf(sdn[i] - sd[i]) > 2.4e-7f * sd[i];
         sd[i] = sdn[i];
       }
       if (!__syncthreads_or(moved)) break;
     }
+    // IN_out(i) = (1/N) sum_j C_ji / m_j = (d_i / N) sum_j (d_j / m_j) C0_ij (C0 symmetric).
+    if (i < N) sdm[i] = m > 0.0 ? static_cast<float>(sd[i] / m) : 0.f;
+    __syncthreads();
+    for (int r = wi; r < N; r += kFinThreads / 32) {
+      float acc = 0.f;
+      for (int j = ln; j < N; j += 32) acc = fmaf(__ldcg(C0 + r * N + j), sdm[j], acc);
+      acc = warp_sum(acc);
+      if (ln == 0) sdn[r] = sd[r] * acc;
+    }
+    __syncthreads();
     if (i < N) {
-      double so = 0.0;
-      for (int j = 0; j < N; ++j) {
-        const double mj = __ldcg(S + j);
-        const double cji = sd[j] * sd[i] * __ldcg(Gm + static_cast<size_t>(j) * N + i);
-        if (mj > 0.0) so += cji / mj;
-      }
-      in_out = so / N;
+      in_out = static_cast<double>(sdn[i]) / N;
       depth = fmin(in_in, in_out);
     }
   }
@@ -261,11 +270,11 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     }
     if (i == 0 && d.err_est) d.err_est[0] = sred[0];
     if (d.P) {
-      const double* Gm = S + 4 * N;   // symmetrised above
+      const float* C0 = reinterpret_cast<const float*>(S + 4 * N) + N * N;   // symmetrised above
       for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
-        const int r = k / N, cc = k - r * N;   // P[r][cc] = C_{r,cc} / m_r (Gm symmetric now)
+        const int r = k / N, cc = k - r * N;   // P[r][cc] = C_{r,cc} / m_r
         const double mr = __ldcg(S + r);
-        const double c = sd[r] * sd[cc] * __ldcg(Gm + k);
+        const double c = static_cast<double>(sd[r] * sd[cc] * __ldcg(C0 + k));
         d.P[k] = mr > 0.0 ? c / mr : 0.0;
       }
     }

@@ -78,6 +78,18 @@ __device__ __forceinline__ void lds_vec(float (&dst)[VEC], const float* src) {
   }
 }
 
+// Streaming (evict-first) global store of VEC consecutive floats.
+template <int VEC>
+__device__ __forceinline__ void stg_cs_vec(float* dst, const float (&src)[VEC]) {
+  if constexpr (VEC == 1) {
+    __stcs(dst, src[0]);
+  } else if constexpr (VEC == 2) {
+    __stcs(reinterpret_cast<float2*>(dst), make_float2(src[0], src[1]));
+  } else {
+    __stcs(reinterpret_cast<float4*>(dst), make_float4(src[0], src[1], src[2], src[3]));
+  }
+}
+
 template <int VEC>
 __device__ __forceinline__ void sts_vec(float* dst, const float (&src)[VEC]) {
   if constexpr (VEC == 1) {
@@ -277,6 +289,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   const EnsDesc* dp = nullptr;
   int N = 0, M = 0, e_begin = 0, e_end = 0, e_chunk = 0;
   bool validate = false, has_w = false;
+  float* u_out = nullptr;   // pass 1 of a field: soft masks stored for pass 2
   float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f, my_cf = 0.f;
   for (int u = u_begin; u < u_end && !aborted; ++u) {
     if (u >= e_end) {
@@ -288,6 +301,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       e_chunk = dp->chunk_cells;
       validate = dp->validate != 0;
       has_w = dp->w != nullptr;
+      if constexpr (ISO != ISOK_NONE && !COEF) u_out = dp->u_out;
       iso_mu = dp->iso_mu;
       iso_inv = dp->iso_inv;
       iso_t = dp->iso_t;
@@ -373,6 +387,27 @@ stream_kernel(const __grid_constant__ StreamParams p) {
           }
         }
         if constexpr (ISO != ISOK_NONE) iso_map_tile<ISO>(x, iso_mu, iso_inv, iso_t, dir);
+        if constexpr (ISO != ISOK_NONE && !COEF) {
+          // The soft masks of this tile, stored once so that pass 2 reads them instead of
+          // repeating the isovalue map (rows are round_up(M, 4) floats, 16-byte aligned).
+          if (u_out != nullptr) {
+            const int64_t ldu = (M + 3) & ~3;
+#pragma unroll
+            for (int k = 0; k < MPW; ++k) {
+              const int i = q + k * G;
+              if (i < N) {
+                float* dst = u_out + static_cast<int64_t>(i) * ldu + xl;
+                if (xl + VEC <= M) {
+                  stg_cs_vec<VEC>(dst, x[k]);
+                } else {
+#pragma unroll
+                  for (int v = 0; v < VEC; ++v)
+                    if (xl + v < M) __stcs(dst + v, x[k][v]);
+                }
+              }
+            }
+          }
+        }
         if (!full) {  // only the ensemble's last tile: cells past M carry no mass
 #pragma unroll
           for (int v = 0; v < VEC; ++v) {

@@ -35,7 +35,7 @@ def _mixed_batch(seed=0, n=14):
     for k, N in enumerate(Ns):
         M = int(rng.integers(50, 6000))
         weighted = bool(k % 3 == 1)
-        field = bool(k % 4 == 2)
+        field = bool(k % 4 in (2, 3))   # fields in both modes (linear stores the masks)
         mode = ["mean", "linear"][k % 2]
         w = rng.uniform(0.2, 4, M).astype(np.float32) if weighted else None
         if field:
