@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   using S = GramShape<WIDE>;
   constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, SPO = S::SPO, MB = S::MB, NBUF = S::NBUF;
   static_assert(!WIDE || G == 16, "the wide tile uses all 16 warps as one group");
+  static_assert(SPO == 1 || SPO == 2, "FP32 stages per operand stage");
   constexpr int NG = kGramConvWarps / G;             // independent groups per CTA
   constexpr int ROWS = MPW * G;                      // operand rows a group writes (>= N)
   constexpr uint32_t PLANE = ROWS * 128;             // one K-block: [ROWS][128 bytes]
@@ -106,7 +107,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   const int grp = warp / G;
   const int q = warp - grp * G;
   const bool leader = (q == 0) && (lane == 0);
-  const int dF = p.dF, dO = p.dO, SF = p.stage_floats, TS = p.TS;
+  const int dF = p.dF, dO = p.dO, SF = p.stage_floats;
+  constexpr int TS = T;   // cells per FP32 stage (the planner's TS)
 
   // ---- shared memory carve-up: all operand rings first (1024-byte aligned) ----
   // An M = 128 MMA reads 128 rows from a plane's base; with 64-row planes the upper rows
@@ -167,6 +169,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   bool pe_w = false;
   const EnsDesc* pd = nullptr;
   long n_issued = 0;
+  int p_slot = 0;   // n_issued % dF, kept incrementally (no 64-bit division per stage)
   auto set_unit = [&](int u) {
     if (u >= pe_end) {
       pd = &gdesc(p, gram_find_ens(p, u));
@@ -183,7 +186,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   };
   auto issue_next = [&]() {
     if (iu >= u_end) return;
-    const int slot = static_cast<int>(n_issued % dF);
+    const int slot = p_slot;
+    if (++p_slot == dF) p_slot = 0;
     float* dst = f_ring + static_cast<size_t>(slot) * SF;
     mbar_arrive_expect_tx(&fF[slot],
                           static_cast<uint32_t>(pe_boxes * pe_rows * TS + (pe_w ? TS : 0)) * 4u);
@@ -294,6 +298,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
                           : static_cast<uint32_t>(lane >> 4) * PLANE + sw128_offset(q, (lane & 15) * 8);
   }
   long k = 0, kt = 0, kc = 0;
+  int f_slot = 0, o_slot = 0;
+  uint32_t f_par = 0;
+  long o_round = 0;
   float* prev_gp = nullptr;          // partial Gram of the previous unit, still to drain
   int prev_N = 0;
   float prev_unscale = 1.0f;
@@ -345,11 +352,17 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     for (int m = 0; m < MPW; ++m) { accM[m] = 0.f; accA[m] = 0.f; }
 
     for (int st = 0; st < n_st; ++st, ++k, ++kt) {
-      const int fslot = static_cast<int>(k % dF);
-      const long ko = k / SPO;                 // operand stage of this FP32 stage
-      const int jh = static_cast<int>(k % SPO);   // which part of it
-      const int oslot = static_cast<int>(ko % dO);
-      if (TMA && !mbar_wait_bounded(&fF[fslot], static_cast<uint32_t>((k / dF) & 1), kWaitTimeoutNs))
+      // Ring positions, kept incrementally (no 64-bit division per stage):
+      // fslot = k % dF, f_par = (k / dF) & 1; operand stage ko = k / SPO, jh = k % SPO,
+      // oslot = ko % dO, o_round = ko / dO.
+      const int fslot = f_slot;
+      const uint32_t fpar = f_par;
+      const int jh = SPO == 1 ? 0 : static_cast<int>(k & (SPO - 1));
+      const int oslot = o_slot;
+      const long oround = o_round;
+      if (++f_slot == dF) { f_slot = 0; f_par ^= 1u; }
+      if (jh == SPO - 1 && ++o_slot == dO) { o_slot = 0; ++o_round; }
+      if (TMA && !mbar_wait_bounded(&fF[fslot], fpar, kWaitTimeoutNs))
         cflag[kt & 1] = 1;
       const float* sb = f_ring + static_cast<size_t>(fslot) * SF;
       unsigned char* ob = op_ring + static_cast<size_t>(oslot) * OP_STAGE;
@@ -465,8 +478,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         for (int v = 0; v < VEC; ++v) sw[v] = sqrtf(wv[v]);
       }
       // ---- operands: u sqrt(w) in the swizzled K-major layout, once the slot is free ----
-      if (jh == 0 && ko >= dO &&
-          !mbar_wait_bounded(&opE[oslot], static_cast<uint32_t>(((ko / dO) - 1) & 1), kWaitTimeoutNs))
+      if (jh == 0 && oround >= 1 &&
+          !mbar_wait_bounded(&opE[oslot], static_cast<uint32_t>((oround - 1) & 1), kWaitTimeoutNs))
         cflag[(kt + 1) & 1] = 1;
       const uint32_t loff = (SPO == 1 || jh == 0) ? lane_off0 : lane_off1;
 #pragma unroll

@@ -204,8 +204,10 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   const int q = warp - grp * G;
   const int depth = p.depth;
   const int SF = p.stage_floats;
-  const int SUB = p.sub;
-  const int TS = SUB * T;
+  // One register tile per TMA stage (every tile class is planned with sub = 1): the stage
+  // width is a compile-time constant, so row offsets fold into the shared-memory loads.
+  constexpr int SUB = 1;
+  constexpr int TS = SUB * T;
 
   float* ring = reinterpret_cast<float*>(smem);
   float* red = ring + static_cast<size_t>(NG) * depth * SF;
@@ -242,6 +244,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   bool pe_w = false;
   const EnsDesc* pd = nullptr;
   long n_issued = 0;
+  int p_slot = 0;   // n_issued % depth, kept incrementally (no 64-bit division per stage)
   auto set_unit = [&](int u) {
     if (u >= pe_end) {
       pd = &stream_desc(p, stream_find_ens(p, u));
@@ -258,7 +261,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   };
   auto issue_next = [&]() {
     if (iu >= u_end) return;
-    const int slot = static_cast<int>(n_issued % depth);
+    const int slot = p_slot;
+    if (++p_slot == depth) p_slot = 0;
     float* dst = my_ring + static_cast<size_t>(slot) * SF;
     const uint32_t bytes = static_cast<uint32_t>(pe_boxes * pe_rows * TS + (pe_w ? TS : 0)) * 4u;
     mbar_arrive_expect_tx(&my_bars[slot], bytes);
@@ -280,6 +284,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 
   // ---- consumers: every warp of the group ----
   long k_cons = 0;
+  int c_slot = 0;
+  uint32_t c_par = 0;
   long k_sub = 0;   // register tiles processed (parity of the exchange buffer)
   bool aborted = false;
   uint32_t bad = 0;
@@ -328,8 +334,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     for (int k = 0; k < MPW; ++k) { accM[k] = 0.f; accA[k] = 0.f; }
 
     for (int st = 0; st < n_st && !aborted; ++st, ++k_cons) {
-      const int slot = static_cast<int>(k_cons % depth);
-      const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
+      const int slot = c_slot;          // k_cons % depth
+      const uint32_t par = c_par;       // (k_cons / depth) & 1
+      if (++c_slot == depth) { c_slot = 0; c_par ^= 1u; }
       const float* sb = my_ring + static_cast<size_t>(slot) * SF;
       if constexpr (TMA) {
         if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[2 * grp + (k_sub & 1)] = 1;
