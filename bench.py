@@ -168,6 +168,17 @@ def measured_peaks():
             "source": "fallback"}
 
 
+def max_over_ranks(value, dist, device):
+    """The largest `value` over all ranks (the slowest replica sets the job's time); the
+    value itself without a process group."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def kernel_sources_sha16():
     """First 16 hex digits of the SHA-256 over every CUDA/C++ source of the library (in name
     order): an ncu summary stamped with it describes exactly the kernels built from them."""
@@ -488,10 +499,7 @@ def main():
     h.profile(False)
     clocks = sampler.stop()
     h.sync()
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(ms, dist, dev)
     total_mc = world * args.steps * E * N * M
     value = total_mc / (ms * 1e-3)
 
@@ -603,10 +611,7 @@ def main():
     a1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a0.elapsed_time(a1) / k_e2e
-    if dist:
-        tt = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     e2e_value = world * Ee * N * M / (e2e_ms * 1e-3)
 
     if rank == 0:

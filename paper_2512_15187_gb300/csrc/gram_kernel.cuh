@@ -41,6 +41,18 @@ namespace {
 // lane (the FP32 stage is then 64 KB), two FP32 stages fill one 128-cell operand stage,
 // and every K step issues two M = 128 MMAs (row blocks 0-127 and 128-255 against all
 // rows) into one 2 x 256-column accumulator that fills the tensor memory.
+// Leader-only state of a group (TMA cursor and the operand stage waiting for its MMAs),
+// kept in shared memory so that it takes no registers from the converter warps.
+struct GramLeader {
+  const EnsDesc* pd;   // descriptor of the ensemble being loaded
+  long n_issued;       // FP32 stages issued so far
+  long pend_kc;        // unit of the pending operand stage
+  int iu, u_end, ist, in_st, icell0, slot;
+  int e_begin, e_end, chunk, M, boxes, rows, has_w;
+  int pend, pend_first, pend_last, pend_slot, pend_buf;
+  uint32_t pend_idesc;
+};
+
 template <bool WIDE>
 struct GramShape {
   static constexpr int VEC = WIDE ? 2 : 4;             // cells per lane per register tile
@@ -120,6 +132,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   uint64_t* bars_all = reinterpret_cast<uint64_t*>(red_all + NG * 2 * RB);
   int* flags_all = reinterpret_cast<int*>(bars_all + NG * (dF + dO + 5));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags_all + 2 * NG);
+  GramLeader* lead_all = reinterpret_cast<GramLeader*>(
+      (reinterpret_cast<uintptr_t>(tmem_slot + 1) + 15) & ~static_cast<uintptr_t>(15));
 
   unsigned char* op_ring = smem + static_cast<size_t>(grp) * dO * OP_STAGE;
   float* f_ring = f_all + static_cast<size_t>(grp) * dF * SF;
@@ -163,95 +177,105 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   const int u_begin = unit_at_work(p, p.total_work * gid / total_groups);
   const int u_end = unit_at_work(p, p.total_work * (gid + 1) / total_groups);
 
-  // ---- TMA producer cursor (leader) ----
-  int iu = u_begin, ist = 0, icell0 = 0, in_st = 0;
-  int pe_begin = 0, pe_end = 0, pe_chunk = 0, pe_M = 0, pe_boxes = 0, pe_rows = 0;
-  bool pe_w = false;
-  const EnsDesc* pd = nullptr;
-  long n_issued = 0;
-  int p_slot = 0;   // n_issued % dF, kept incrementally (no 64-bit division per stage)
+  // ---- TMA producer cursor and pending MMA issue (leader only, in shared memory) ----
+  GramLeader& L = lead_all[grp];
   auto set_unit = [&](int u) {
-    if (u >= pe_end) {
-      pd = &gdesc(p, gram_find_ens(p, u));
-      pe_begin = pd->unit_begin;
-      pe_end = pe_begin + pd->n_chunks;
-      pe_chunk = pd->chunk_cells;
-      pe_M = pd->M;
-      pe_boxes = pd->n_boxes;
-      pe_rows = pd->box_rows;
-      pe_w = pd->w != nullptr;
+    if (u >= L.e_end) {
+      const EnsDesc* pd = &gdesc(p, gram_find_ens(p, u));
+      L.pd = pd;
+      L.e_begin = pd->unit_begin;
+      L.e_end = pd->unit_begin + pd->n_chunks;
+      L.chunk = pd->chunk_cells;
+      L.M = pd->M;
+      L.boxes = pd->n_boxes;
+      L.rows = pd->box_rows;
+      L.has_w = pd->w != nullptr;
     }
-    icell0 = (u - pe_begin) * pe_chunk;
-    in_st = SPO * ((min(pe_chunk, pe_M - icell0) + 127) / 128);
+    L.icell0 = (u - L.e_begin) * L.chunk;
+    L.in_st = SPO * ((min(L.chunk, L.M - L.icell0) + 127) / 128);
   };
   auto issue_next = [&]() {
-    if (iu >= u_end) return;
-    const int slot = p_slot;
-    if (++p_slot == dF) p_slot = 0;
+    if (L.iu >= L.u_end) return;
+    const int slot = L.slot;
+    L.slot = slot + 1 == dF ? 0 : slot + 1;
     float* dst = f_ring + static_cast<size_t>(slot) * SF;
-    mbar_arrive_expect_tx(&fF[slot],
-                          static_cast<uint32_t>(pe_boxes * pe_rows * TS + (pe_w ? TS : 0)) * 4u);
-    const int x0 = icell0 + ist * TS;
-    for (int b = 0; b < pe_boxes; ++b)
-      tma_load_2d(dst + static_cast<size_t>(b) * pe_rows * TS, &pd->tmap, &fF[slot], x0,
-                  b * pe_rows);
-    if (pe_w) tma_load_1d(dst + SF - TS, &pd->tmap_w, &fF[slot], x0);
-    ++n_issued;
-    if (++ist == in_st) {
-      ist = 0;
-      if (++iu < u_end) set_unit(iu);
+    const int boxes = L.boxes, rows = L.rows;
+    const bool hw = L.has_w != 0;
+    const EnsDesc* pd = L.pd;
+    mbar_arrive_expect_tx(&fF[slot], static_cast<uint32_t>(boxes * rows * TS + (hw ? TS : 0)) * 4u);
+    const int x0 = L.icell0 + L.ist * TS;
+    for (int b = 0; b < boxes; ++b)
+      tma_load_2d(dst + static_cast<size_t>(b) * rows * TS, &pd->tmap, &fF[slot], x0, b * rows);
+    if (hw) tma_load_1d(dst + SF - TS, &pd->tmap_w, &fF[slot], x0);
+    ++L.n_issued;
+    if (++L.ist == L.in_st) {
+      L.ist = 0;
+      if (++L.iu < L.u_end) set_unit(L.iu);
     }
   };
-  if (TMA && leader) {
-    if (iu < u_end) set_unit(iu);
-    for (int s = 0; s < dF; ++s) issue_next();
+  if (leader) {
+    L.pd = nullptr;
+    L.n_issued = 0;
+    L.pend_kc = 0;
+    L.iu = u_begin;
+    L.u_end = u_end;
+    L.ist = 0;
+    L.in_st = 0;
+    L.icell0 = 0;
+    L.slot = 0;
+    L.e_begin = 0;
+    L.e_end = 0;
+    L.pend = 0;
+    if (TMA) {
+      if (L.iu < L.u_end) set_unit(L.iu);
+      for (int s = 0; s < dF; ++s) issue_next();
+    }
   }
 
   // ---- tensor-core issue (leader): the stage written last, issued after the next barrier ----
-  bool pend = false, pend_first = false, pend_last = false;
-  int pend_slot = 0, pend_buf = 0;
-  long pend_kc = 0;
-  uint32_t pend_idesc = 0;
   auto issue_pending = [&]() -> bool {
-    if (!pend) return true;
-    pend = false;
+    if (!L.pend) return true;
+    L.pend = 0;
+    const bool first = L.pend_first != 0;
+    const int buf = L.pend_buf, slot = L.pend_slot;
+    const long pkc = L.pend_kc;
+    const uint32_t idsc = L.pend_idesc;
     // The unit's first MMA overwrites its accumulator buffer: the unit that used that
     // buffer before must have been drained (two units back, or one with a single buffer).
-    if (pend_first && pend_kc >= NBUF &&
-        !mbar_wait_bounded(&accE[pend_buf],
-                           static_cast<uint32_t>((pend_kc / NBUF - 1) & 1), kWaitTimeoutNs))
+    if (first && pkc >= NBUF &&
+        !mbar_wait_bounded(&accE[buf], static_cast<uint32_t>((pkc / NBUF - 1) & 1), kWaitTimeoutNs))
       return false;
     tc_fence_after();
-    const uint32_t dt = tmem_base + static_cast<uint32_t>(pend_buf) * BUFC;
+    const uint32_t dt = tmem_base + static_cast<uint32_t>(buf) * BUFC;
     // descriptor of the stage's first K-block; K steps advance its 16-byte address field,
     // row block b starts 128 rows (16 KB) into the plane
-    const uint64_t d0 = umma_desc_sw128(smem_u32(op_ring) + static_cast<uint32_t>(pend_slot) * OP_STAGE);
+    const uint64_t d0 = umma_desc_sw128(smem_u32(op_ring) + static_cast<uint32_t>(slot) * OP_STAGE);
 #pragma unroll
     for (int kb = 0; kb < KBLK; ++kb) {
 #pragma unroll
       for (int ks = 0; ks < 4; ++ks) {   // 4 x 32 bytes along K in the 128-byte row
         const uint64_t hi = d0 + static_cast<uint64_t>((kb * PLANE + ks * 32) >> 4);
-        const uint32_t acc = (pend_first && kb == 0 && ks == 0) ? 0u : 1u;
+        const uint32_t acc = (first && kb == 0 && ks == 0) ? 0u : 1u;
 #pragma unroll
         for (int mb = 0; mb < MB; ++mb) {
           const uint32_t dmb = dt + static_cast<uint32_t>(mb * 256);
           const uint64_t ha = hi + static_cast<uint64_t>((mb * 128 * 128) >> 4);
           if constexpr (PREC == 3) {
-            umma_f8(dmb, ha, hi, pend_idesc, acc);
+            umma_f8(dmb, ha, hi, idsc, acc);
           } else {
-            umma_f16(dmb, ha, hi, pend_idesc, acc);
+            umma_f16(dmb, ha, hi, idsc, acc);
             if constexpr (PREC == 2) {
               const uint64_t lo = hi + static_cast<uint64_t>((KBLK * PLANE) >> 4);
               const uint64_t la = ha + static_cast<uint64_t>((KBLK * PLANE) >> 4);
-              umma_f16(dmb, ha, lo, pend_idesc, 1u);
-              umma_f16(dmb, la, hi, pend_idesc, 1u);
+              umma_f16(dmb, ha, lo, idsc, 1u);
+              umma_f16(dmb, la, hi, idsc, 1u);
             }
           }
         }
       }
     }
-    tc_commit(&opE[pend_slot]);
-    if (pend_last) tc_commit(&accF[pend_buf]);
+    tc_commit(&opE[slot]);
+    if (L.pend_last) tc_commit(&accF[buf]);
     return true;
   };
 
@@ -518,13 +542,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       }
       fence_proxy_async_smem();
       if (leader && jh == SPO - 1) {   // a full operand stage: to the tensor cores after the next barrier
-        pend = true;
-        pend_slot = oslot;
-        pend_first = st < SPO;
-        pend_last = st == n_st - 1;
-        pend_buf = static_cast<int>(kc % NBUF);
-        pend_kc = kc;
-        pend_idesc = idesc;
+        L.pend = 1;
+        L.pend_slot = oslot;
+        L.pend_first = st < SPO;
+        L.pend_last = st == n_st - 1;
+        L.pend_buf = static_cast<int>(kc % NBUF);
+        L.pend_kc = kc;
+        L.pend_idesc = idesc;
       }
       // Double-buffered accumulators are drained halfway through the next chunk, when the
       // last products have long landed; a single buffer must be drained before the next
@@ -568,7 +592,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     tc_commit(finB);
     mbar_wait_bounded(finB, 0, kWaitTimeoutNs);
     if (TMA) {
-      while (k < n_issued) {
+      while (k < L.n_issued) {
         if (!mbar_wait_bounded(&fF[k % dF], static_cast<uint32_t>((k / dF) & 1), kWaitTimeoutNs)) break;
         ++k;
       }

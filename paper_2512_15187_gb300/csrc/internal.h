@@ -24,6 +24,7 @@ constexpr uint64_t kWaitTimeoutNs = 1000000000ull;
 // Streaming pass: 16 consumer warps per CTA, grouped G warps per cell tile.
 constexpr int kStreamWarps = 16;
 constexpr int kStreamThreads = kStreamWarps * 32;
+constexpr int kStreamProducerBytes = 96;   // shared-memory TMA cursor per group
 
 // One ensemble as seen by the streaming kernel.
 struct EnsDesc {  // 64-byte aligned through its CUtensorMap members

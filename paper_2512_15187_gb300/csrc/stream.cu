@@ -65,7 +65,8 @@ size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats) {
   const int n_groups = kStreamWarps / G;
   return static_cast<size_t>(n_groups) * depth * stage_floats * 4 +
          static_cast<size_t>(n_groups) * 2 * (G * T + T) * 4 +
-         static_cast<size_t>(n_groups) * depth * 8 + static_cast<size_t>(n_groups) * 8 + 64;
+         static_cast<size_t>(n_groups) * depth * 8 + static_cast<size_t>(n_groups) * 8 + 64 +
+         static_cast<size_t>(n_groups) * kStreamProducerBytes + 16;
 }
 
 // ---------------------------------------------------------------------------------------

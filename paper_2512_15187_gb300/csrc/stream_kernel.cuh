@@ -150,6 +150,18 @@ __device__ __forceinline__ float iso_map(float f, float mu, float inv, float t, 
   }
 }
 
+// TMA producer cursor of a group. It lives in shared memory: only the group's leader thread
+// uses it, so it takes no registers from the converter warps.
+struct StreamProducer {
+  const EnsDesc* pd;   // descriptor of the ensemble being loaded
+  long n_issued;       // stages issued so far
+  int iu, u_end;       // unit being loaded, end of the group's run
+  int ist, in_st;      // stage within the unit, stages of the unit
+  int icell0, slot;    // first cell of the unit, ring slot of the next stage
+  int e_begin, e_end, chunk, M, boxes, rows, has_w;
+};
+static_assert(sizeof(StreamProducer) <= kStreamProducerBytes, "producer cursor size");
+
 // The isovalue map over a lane's MPW x VEC values, two at a time (packed FP32) for the
 // normal kind: pairs of neighbouring cells, or of neighbouring members when VEC = 1.
 template <int ISO, int MPW, int VEC>
@@ -213,6 +225,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   float* red = ring + static_cast<size_t>(NG) * depth * SF;
   uint64_t* bars = reinterpret_cast<uint64_t*>(red + NG * 2 * RB);
   volatile int* flags = reinterpret_cast<volatile int*>(bars + NG * depth);
+  StreamProducer* prod = reinterpret_cast<StreamProducer*>(
+      (reinterpret_cast<uintptr_t>(flags + 2 * NG) + 15) & ~static_cast<uintptr_t>(15));
 
   float* my_ring = ring + static_cast<size_t>(grp) * depth * SF;
   float* my_red = red + grp * 2 * RB;
@@ -238,48 +252,58 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   const int u_begin = unit_at_work(p, p.total_work * gid / total_groups);
   const int u_end = unit_at_work(p, p.total_work * (gid + 1) / total_groups);
 
-  // ---- producer cursor (leader lane of the group only) ----
-  int iu = u_begin, ist = 0, icell0 = 0, in_st = 0;
-  int pe_begin = 0, pe_end = 0, pe_chunk = 0, pe_M = 0, pe_boxes = 0, pe_rows = 0;
-  bool pe_w = false;
-  const EnsDesc* pd = nullptr;
-  long n_issued = 0;
-  int p_slot = 0;   // n_issued % depth, kept incrementally (no 64-bit division per stage)
+  // ---- producer cursor (leader lane of the group only, in shared memory) ----
+  StreamProducer& P = prod[grp];
   auto set_unit = [&](int u) {
-    if (u >= pe_end) {
-      pd = &stream_desc(p, stream_find_ens(p, u));
-      pe_begin = pd->unit_begin;
-      pe_end = pe_begin + pd->n_chunks;
-      pe_chunk = pd->chunk_cells;
-      pe_M = pd->M;
-      pe_boxes = pd->n_boxes;
-      pe_rows = pd->box_rows;
-      pe_w = pd->w != nullptr;
+    if (u >= P.e_end) {
+      const EnsDesc* pd = &stream_desc(p, stream_find_ens(p, u));
+      P.pd = pd;
+      P.e_begin = pd->unit_begin;
+      P.e_end = pd->unit_begin + pd->n_chunks;
+      P.chunk = pd->chunk_cells;
+      P.M = pd->M;
+      P.boxes = pd->n_boxes;
+      P.rows = pd->box_rows;
+      P.has_w = pd->w != nullptr;
     }
-    icell0 = (u - pe_begin) * pe_chunk;
-    in_st = (min(pe_chunk, pe_M - icell0) + TS - 1) / TS;
+    P.icell0 = (u - P.e_begin) * P.chunk;
+    P.in_st = (min(P.chunk, P.M - P.icell0) + TS - 1) / TS;
   };
   auto issue_next = [&]() {
-    if (iu >= u_end) return;
-    const int slot = p_slot;
-    if (++p_slot == depth) p_slot = 0;
+    if (P.iu >= P.u_end) return;
+    const int slot = P.slot;
+    P.slot = slot + 1 == depth ? 0 : slot + 1;
     float* dst = my_ring + static_cast<size_t>(slot) * SF;
-    const uint32_t bytes = static_cast<uint32_t>(pe_boxes * pe_rows * TS + (pe_w ? TS : 0)) * 4u;
+    const int boxes = P.boxes, rows = P.rows;
+    const bool has_w_p = P.has_w != 0;
+    const EnsDesc* pd = P.pd;
+    const uint32_t bytes = static_cast<uint32_t>(boxes * rows * TS + (has_w_p ? TS : 0)) * 4u;
     mbar_arrive_expect_tx(&my_bars[slot], bytes);
-    const int x0 = icell0 + ist * TS;
-    for (int b = 0; b < pe_boxes; ++b)
-      tma_load_2d(dst + static_cast<size_t>(b) * pe_rows * TS, &pd->tmap, &my_bars[slot], x0,
-                  b * pe_rows);
-    if (pe_w) tma_load_1d(dst + SF - TS, &pd->tmap_w, &my_bars[slot], x0);
-    ++n_issued;
-    if (++ist == in_st) {
-      ist = 0;
-      if (++iu < u_end) set_unit(iu);
+    const int x0 = P.icell0 + P.ist * TS;
+    for (int b = 0; b < boxes; ++b)
+      tma_load_2d(dst + static_cast<size_t>(b) * rows * TS, &pd->tmap, &my_bars[slot], x0, b * rows);
+    if (has_w_p) tma_load_1d(dst + SF - TS, &pd->tmap_w, &my_bars[slot], x0);
+    ++P.n_issued;
+    if (++P.ist == P.in_st) {
+      P.ist = 0;
+      if (++P.iu < P.u_end) set_unit(P.iu);
     }
   };
-  if (TMA && leader) {
-    if (iu < u_end) set_unit(iu);
-    for (int s = 0; s < depth; ++s) issue_next();
+  if (leader) {
+    P.pd = nullptr;
+    P.n_issued = 0;
+    P.iu = u_begin;
+    P.u_end = u_end;
+    P.ist = 0;
+    P.in_st = 0;
+    P.icell0 = 0;
+    P.slot = 0;
+    P.e_begin = 0;
+    P.e_end = 0;
+    if (TMA) {
+      if (P.iu < P.u_end) set_unit(P.iu);
+      for (int s = 0; s < depth; ++s) issue_next();
+    }
   }
 
   // ---- consumers: every warp of the group ----
@@ -527,7 +551,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   if (aborted && lane == 0 && q == 0) atomicOr(p.err, ERR_TIMEOUT);
   // On an early exit, let this group's copies in flight land before the CTA retires.
   if (TMA && leader) {
-    while (k_cons < n_issued) {
+    while (k_cons < P.n_issued) {
       const int slot = static_cast<int>(k_cons % depth);
       const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
       if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) break;
