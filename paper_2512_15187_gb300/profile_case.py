@@ -1,6 +1,7 @@
 """Run one small, fixed case of one path of the library, for a profiler to capture.
 
     python -m paper_2512_15187_gb300.profile_case fields        # isovalue map + PID-mean
+    python -m paper_2512_15187_gb300.profile_case fields-full   # isovalue map + exact full PID
     python -m paper_2512_15187_gb300.profile_case mean          # PID-mean of soft masks
     python -m paper_2512_15187_gb300.profile_case linear        # exact full PID, O(N M)
     python -m paper_2512_15187_gb300.profile_case gram --precision bf16 --ensembles 4
@@ -18,7 +19,7 @@ import argparse
 
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fields", "mean", "linear", "gram"])
+    ap.add_argument("case", choices=["fields", "fields-full", "mean", "linear", "gram"])
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--cells", type=int, default=1 << 20)
     ap.add_argument("--ensembles", type=int, default=1,
@@ -44,13 +45,14 @@ def main(argv=None) -> None:
     X = torch.empty((E, N, M), device="cuda")
     side = int(round(M ** 0.5))
     for e in range(E):
-        if a.case in ("fields", "gram") and side * side == M:
+        if a.case in ("fields", "fields-full", "gram") and side * side == M:
             synth.rbf_fields_2d_torch(N, side, side, 32, seed=7 + e, device="cuda", out=X[e])
         else:
             g = torch.Generator(device="cuda").manual_seed(7 + e)
             X[e].uniform_(0.0, 1.0, generator=g)
-    is_field = a.case in ("fields", "gram") and side * side == M
-    mode = {"fields": "mean", "mean": "mean", "linear": "linear", "gram": "full"}[a.case]
+    is_field = a.case in ("fields", "fields-full", "gram") and side * side == M
+    mode = {"fields": "mean", "fields-full": "linear", "mean": "mean", "linear": "linear",
+            "gram": "full"}[a.case]
     prec = a.precision if mode == "full" else "fp32"
     items = [dict(data=X[e], iso=(0.5, 0.05, 0) if is_field else None, mode=mode, precision=prec)
              for e in range(E)]
