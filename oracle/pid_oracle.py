@@ -19,6 +19,8 @@ Every function cites the passage it follows:
   Sec. 5.1         ranking: higher rank = lower depth
   (pid_chunked / pid_mean_chunked restate Eq. 6, 9, 10, 15, 16 with their sums over
   cells accumulated block by block, for ensembles larger than host memory in float64)
+  Sec. 5.4         contour boxplots: unions and intersections of the binarised members
+                   of a depth-ordered population, and the median member
 
 Readings where the paper is silent (each also listed in the design notes):
   * Zero-mass reference mask: u subset_p v = 0 (Sec. 3.2), unlike eID's 1 (Eq. 1).
@@ -52,6 +54,7 @@ __all__ = [
     "eid",
     "pid_chunked",
     "pid_mean_chunked",
+    "contour_bands",
 ]
 
 
@@ -248,3 +251,43 @@ def eid(sets):
     in_in = np.array([sum(eps_subset(sets[i], sets[j]) for j in range(N)) / N for i in range(N)])
     in_out = np.array([sum(eps_subset(sets[j], sets[i]) for j in range(N)) / N for i in range(N)])
     return in_in, in_out, np.minimum(in_in, in_out)
+
+
+# ---------------------------------------------------------------------------
+# Contour boxplot bands (Sec. 5.4): binarise each soft mask at a probability threshold,
+# then take the union and the intersection over the deepest fraction of the members and
+# over all members; the median member is the deepest one.
+# ---------------------------------------------------------------------------
+
+BAND_INNER_UNION, BAND_INNER_INTERSECTION = 1, 2
+BAND_ALL_UNION, BAND_ALL_INTERSECTION = 4, 8
+BAND_MEDIAN = 16
+
+
+def contour_bands(U, rank, tau: float, inner_fraction: float = 0.5) -> np.ndarray:
+    """Per cell, a byte of band flags for the contour boxplot of Sec. 5.4.
+
+    b_i(x) = [u_i(x) > tau]; the inner population is the ceil(inner_fraction N) members of
+    lowest rank (rank 0 = deepest, Sec. 5.1), the outer population all N members.
+    bit 0: union over the inner population      bit 1: intersection over it
+    bit 2: union over all members               bit 3: intersection over all members
+    bit 4: b of the median (rank-0) member
+    """
+    U = np.atleast_2d(_f64(U))
+    rank = np.asarray(rank).reshape(-1)
+    N, M = U.shape
+    if rank.shape[0] != N:
+        raise ValueError("one rank per member")
+    n_inner = int(math.ceil(inner_fraction * N))
+    B = U > tau
+    inner = B[rank < n_inner]
+    out = np.zeros(M, dtype=np.uint8)
+    if inner.shape[0] > 0:
+        out |= inner.any(axis=0).astype(np.uint8) * BAND_INNER_UNION
+        out |= inner.all(axis=0).astype(np.uint8) * BAND_INNER_INTERSECTION
+    out |= B.any(axis=0).astype(np.uint8) * BAND_ALL_UNION
+    out |= B.all(axis=0).astype(np.uint8) * BAND_ALL_INTERSECTION
+    med = np.nonzero(rank == 0)[0]
+    if med.size:
+        out |= B[med[0]].astype(np.uint8) * BAND_MEDIAN
+    return out

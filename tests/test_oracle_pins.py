@@ -331,3 +331,48 @@ def test_chunked_forms_do_not_depend_on_the_blocks(seed):
         np.testing.assert_allclose(np.array(O.pid_chunked(_blocks(U, w, edges))), full, atol=1e-13)
         np.testing.assert_allclose(np.array(O.pid_mean_chunked(_blocks(U, w, edges))), mean,
                                    atol=1e-13)
+
+
+# --- contour boxplot bands (Sec. 5.4) -------------------------------------------------
+
+def test_bands_hand_example():
+    g = _load("hand_bands_3x6.json")
+    got = O.contour_bands(np.array(g["U"]), np.array(g["rank"]), g["tau"], g["inner_fraction"])
+    assert got.tolist() == g["bands"]
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bands_nesting_invariants(seed):
+    rng = np.random.default_rng(seed)
+    N, M = int(rng.integers(1, 12)), 500
+    U = synth.random_soft(N, M, seed=seed, binary_frac=0.3).astype(np.float64)
+    rank = rng.permutation(N)
+    for frac in (0.25, 0.5, 1.0):
+        b = O.contour_bands(U, rank, 0.5, frac)
+        iu, ii = (b & 1) > 0, (b & 2) > 0
+        au, ai = (b & 4) > 0, (b & 8) > 0
+        med = (b & 16) > 0
+        assert np.all(ii <= iu) and np.all(ai <= ai & iu) and np.all(iu <= au)
+        assert np.all(ai <= ii) and np.all(ii <= med) and np.all(med <= iu)
+        if frac == 1.0:
+            assert np.array_equal(iu, au) and np.array_equal(ii, ai)
+    if N == 1:
+        b = O.contour_bands(U, rank, 0.5)
+        assert np.array_equal(b, (U[0] > 0.5).astype(np.uint8) * 31)
+
+
+def test_bands_of_nested_disks_are_the_extreme_disks():
+    # PID orders nested disks centre-outward; the deepest half is a run of consecutive
+    # radii, whose union is its largest disk and whose intersection its smallest
+    radii = [3, 5, 7, 9, 11, 13, 15, 17, 19]
+    U = synth.nested_disks(radii, 48, 48).astype(np.float64)
+    depth = O.pid(U)[2]
+    rank = O.rank_by_depth(depth)
+    inner = np.nonzero(rank < 5)[0]
+    assert np.all(np.diff(inner) == 1)                 # a contiguous run of radii
+    b = O.contour_bands(U, rank, 0.5, 0.5)
+    assert np.array_equal((b & 1) > 0, U[inner.max()] > 0.5)
+    assert np.array_equal((b & 2) > 0, U[inner.min()] > 0.5)
+    assert np.array_equal((b & 4) > 0, U[-1] > 0.5)
+    assert np.array_equal((b & 8) > 0, U[0] > 0.5)
+    assert np.array_equal((b & 16) > 0, U[int(np.argmin(rank))] > 0.5)
