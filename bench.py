@@ -555,6 +555,30 @@ def main():
         t_ms = b0.elapsed_time(b1) / args.other_steps
         others[name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms}
 
+    # ---- contour boxplot bands of every ensemble from the step's ranks (Sec. 5.4) ----
+    bands = None
+    if rank == 0 and args.other_steps > 0:
+        bout = [torch.empty(M, dtype=torch.uint8, device=dev) for _ in range(E)]
+
+        def bands_step():
+            for e in range(E):
+                h.contour_bands(F[e], outs_main[e]["rank"], 0.5, 0.5,
+                                iso=(ISO_MU, ISO_SIGMA, 0), out=bout[e], stream=stream)
+        bands_step()
+        torch.cuda.synchronize()
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        reps = max(1, min(3, args.other_steps))
+        d0.record(stream)
+        for _ in range(reps):
+            bands_step()
+        d1.record(stream)
+        torch.cuda.synchronize()
+        b_ms = d0.elapsed_time(d1) / reps
+        bands = {"value": E * N * M / (b_ms * 1e-3), "unit": UNIT, "ms_per_step": b_ms,
+                 "read_gb_per_s": 4.0 * E * N * M / (b_ms * 1e-3) / 1e9,
+                 "calls_per_step": E, "tau": 0.5, "inner_fraction": 0.5}
+
     # ---- the same step as one call per ensemble (no batching, no graph) ----
     loop_ms = None
     if rank == 0 and args.other_steps > 0:
@@ -636,6 +660,8 @@ def main():
             "clocks": clocks,
             "other_paths": others,
         }
+        if bands is not None:
+            line["contour_bands"] = bands
         if loop_ms is not None:
             line["one_call_per_ensemble"] = {
                 "value": E * N * M / (loop_ms * 1e-3), "unit": UNIT, "ms_per_step": loop_ms,

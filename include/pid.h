@@ -123,7 +123,8 @@ typedef enum pid_kernel_kind {
   PID_KERNEL_GRAM = 1,      /* tensor-core Gram */
   PID_KERNEL_FINALIZE = 2,  /* FP64 reduction, depths, ranks */
   PID_KERNEL_ISO = 3,       /* isovalue map alone */
-  PID_KERNEL_KINDS = 4
+  PID_KERNEL_BANDS = 4,     /* contour boxplot bands */
+  PID_KERNEL_KINDS = 5
 } pid_kernel_kind;
 
 typedef struct pid_kernel_stats {
@@ -155,6 +156,26 @@ pid_status pid_autotune_enable(pid_handle h, int enable, int32_t* n_entries);
  */
 pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
                           const pid_iso* iso, float* U_out, int64_t ld_out, void* stream);
+
+/*
+ * pid_contour_bands — the bands of a contour boxplot (Sec. 5.4) from depths already
+ * computed. Every member is binarised, b_i(x) = [u_i(x) > tau], with u_i the soft mask
+ * itself (iso == NULL) or the isovalue map of the field (Sec. 3.5). For each cell x, the
+ * byte bands[x] collects:
+ *   bit 0 (1)   union of b_i over the inner population: the members whose rank is below
+ *               ceil(inner_fraction * N) (rank 0 = deepest, as the depth calls return it)
+ *   bit 1 (2)   intersection over the inner population
+ *   bit 2 (4)   union over all members        bit 3 (8)  intersection over all members
+ *   bit 4 (16)  b of the median member (rank 0)
+ * The band of a population is union AND NOT intersection. data: [N][ld] float32 (any N);
+ * rank: device int32 [N]; bands: device uint8 [M]. Requires 0 < tau < 1 and
+ * 0 < inner_fraction <= 1 (PID_ERR_INVALID_ARG otherwise). The binarisation is decided
+ * exactly: a field value is compared with the float nearest to the exact threshold F_tau
+ * (u(F_tau) = tau) on the correct side, so no rounding of u enters the decision.
+ */
+pid_status pid_contour_bands(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,
+                             const pid_iso* iso, const int32_t* rank, double tau,
+                             double inner_fraction, uint8_t* bands, void* stream);
 
 /*
  * pid_mean — PID-mean (Eq. 15-16) of soft masks U [N][ld] with cell measures w [M] (or NULL).

@@ -30,10 +30,12 @@ EXPORTS = [
     "pid_batch", "pid_profile_enable", "pid_profile_read", "pid_autotune_enable",
     "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
-    "pid_serve_stats_get", "pid_serve_stats_reset",
+    "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands",
 ]
-PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO = 0, 1, 2, 3
-KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3}
+PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
+BAND_INNER_UNION, BAND_INNER_INTERSECTION, BAND_ALL_UNION, BAND_ALL_INTERSECTION, BAND_MEDIAN = \
+    1, 2, 4, 8, 16
+KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3, "bands": 4}
 
 
 class PidError(RuntimeError):
@@ -99,6 +101,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_last_error": ([P], c_char_p),
         "pid_workspace_bytes": ([P], c_size_t),
         "pid_soft_masks": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, c_int64, P], c_int),
+        "pid_contour_bands": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, ctypes.c_double,
+                               ctypes.c_double, P, P], c_int),
         "pid_mean": ([P, P, c_int64, c_int64, c_int64, P, P, P, P, P, P], c_int),
         "pid_full": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_options), P, P, P, P, P, P, P],
                      c_int),
@@ -151,6 +155,11 @@ def pid_destroy(h):
 
 def pid_sync(h, stream=None):
     _check(h, load().pid_sync(h, stream))
+
+
+def pid_contour_bands(h, data, N, M, ld, iso, rank, tau, inner_fraction, bands, stream=None):
+    _check(h, load().pid_contour_bands(h, data, N, M, ld, None if iso is None else ctypes.byref(iso),
+                                       rank, float(tau), float(inner_fraction), bands, stream))
 
 
 def pid_soft_masks(h, F, N, M, ld, iso: pid_iso, U_out, ld_out, stream=None):
@@ -271,6 +280,24 @@ class Handle:
             o["mass"] = torch.empty(N, dtype=torch.float64, device=dev)
             o["mean_depth"] = torch.empty(N, dtype=torch.float64, device=dev)
         return o
+
+    def contour_bands(self, data, rank, tau, inner_fraction=0.5, iso=None, out=None, stream=None):
+        """Band flags per cell (uint8 [M], bits BAND_*) of the contour boxplot of the members
+        of `data` ([N][ld] soft masks, or fields with iso=(mu, sigma, superlevel)), ordered by
+        `rank` (int32 [N] on the device, 0 = deepest), binarised at u > tau."""
+        import torch
+        N, M, ld = _check_matrix(data, "data")
+        if rank.dtype != torch.int32 or not rank.is_cuda or rank.numel() != N:
+            raise ValueError("rank must be an int32 CUDA tensor with one entry per member")
+        if out is None:
+            out = torch.empty(M, dtype=torch.uint8, device=data.device)
+        iso_s = None
+        if iso is not None:
+            iso_s = pid_iso(PID_ISO_NORMAL, int(iso[2]) if len(iso) > 2 else 0, float(iso[0]),
+                            float(iso[1]))
+        pid_contour_bands(self.h, data.data_ptr(), N, M, ld, iso_s, rank.data_ptr(), tau,
+                          inner_fraction, out.data_ptr(), _stream(stream))
+        return out
 
     def soft_masks(self, F, mu, sigma, superlevel=False, out=None, stream=None):
         import torch

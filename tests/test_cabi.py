@@ -67,3 +67,9 @@ def test_serving_structs_and_host_checks(lib):
     bad = B.pid_serve_cfg(0, 0, 1, 1, 0, 0, 0)           # max_inflight < 1
     assert lib.pid_serve_start(ctypes.byref(out), ctypes.byref(bad)) == B.PID_ERR_INVALID_ARG
     assert lib.pid_serve_stop(None) == B.PID_OK
+
+
+def test_bands_host_checks(lib):
+    from paper_2512_15187_gb300 import binding as B
+    assert lib.pid_contour_bands(None, None, 4, 10, 10, None, None, 0.5, 0.5, None, None) == \
+        B.PID_ERR_INVALID_ARG
