@@ -158,6 +158,16 @@ pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, in
                           const pid_iso* iso, float* U_out, int64_t ld_out, void* stream);
 
 /*
+ * pid_selftest_wait_timeout — diagnostic of the bounded device waits, which every kernel
+ * uses instead of unbounded spins (the paper has no counterpart). One thread waits on a
+ * shared-memory mbarrier that nothing arrives at; after `seconds` (0 < seconds <= 2) the
+ * bounded wait gives up and the kernel sets the timeout bit of the handle's device error
+ * word, exactly as a stalled pipeline would. The next pid_sync returns PID_ERR_TIMEOUT and
+ * clears the word; the context stays usable (nothing faults or traps).
+ */
+pid_status pid_selftest_wait_timeout(pid_handle h, double seconds, void* stream);
+
+/*
  * pid_contour_bands — the bands of a contour boxplot (Sec. 5.4) from depths already
  * computed. Every member is binarised, b_i(x) = [u_i(x) > tau], with u_i the soft mask
  * itself (iso == NULL) or the isovalue map of the field (Sec. 3.5). For each cell x, the

@@ -31,6 +31,7 @@ EXPORTS = [
     "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
     "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands",
+    "pid_selftest_wait_timeout",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
 BAND_INNER_UNION, BAND_INNER_INTERSECTION, BAND_ALL_UNION, BAND_ALL_INTERSECTION, BAND_MEDIAN = \
@@ -101,6 +102,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_last_error": ([P], c_char_p),
         "pid_workspace_bytes": ([P], c_size_t),
         "pid_soft_masks": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, c_int64, P], c_int),
+        "pid_selftest_wait_timeout": ([P, ctypes.c_double, P], c_int),
         "pid_contour_bands": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, ctypes.c_double,
                                ctypes.c_double, P, P], c_int),
         "pid_mean": ([P, P, c_int64, c_int64, c_int64, P, P, P, P, P, P], c_int),

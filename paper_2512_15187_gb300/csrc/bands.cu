@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) bands_kernel(const __grid_constant__ Band
     const bool full = vec && x + 4 <= p.M;
     uint32_t iu = 0, ii = 15, au = 0, ai = 15, med = 0;
     bool any_inner = false;
-#pragma unroll 4
+#pragma unroll 8
     for (int64_t i = 0; i < p.N; ++i) {
       const float* row = p.data + i * p.ld + x;
       float4 v;
