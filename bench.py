@@ -397,6 +397,21 @@ def run_workloads(h, dev, stream):
         "batched_read_gb_per_s": read_bytes / (t_batch * 1e-3) / 1e9}
     del steps, extras
     torch.cuda.empty_cache()
+
+    # scalability study: PID-mean of 3D ellipsoid ensembles (80% normal, 20% outliers), one
+    # call each, over the ensemble size at 50^3 and over the resolution at 50 members
+    scal = {"unit": "ms per PID-mean call (ranks included)", "members_at_50cubed": {},
+            "resolution_at_50_members": {}}
+    for n in (100, 1000, 10000, 20000, 40000):
+        U = synth.ellipsoids_3d(n, 50, device=dev)
+        scal["members_at_50cubed"][str(n)] = timed(lambda: h.mean(U, stream=stream), 3)
+        del U
+    for r in (128, 256, 352, 512):
+        U = synth.ellipsoids_3d(50, r, device=dev)
+        scal["resolution_at_50_members"][f"{r}^3"] = timed(lambda: h.mean(U, stream=stream), 3)
+        del U
+    torch.cuda.empty_cache()
+    out["scalability_ellipsoids_3d"] = scal
     return out
 
 

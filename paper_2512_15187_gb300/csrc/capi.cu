@@ -195,14 +195,18 @@ pid_status check_iso(pid_handle h, const pid_iso* iso) {
   return PID_OK;
 }
 
-pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld) {
+pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld,
+                       int64_t max_n) {
   if (!h) return PID_ERR_INVALID_ARG;
   if (!data) return fail(h, PID_ERR_INVALID_ARG, "data pointer is NULL");
   if (N < 1 || M < 1) return fail(h, PID_ERR_INVALID_ARG, "N and M must be >= 1");
   if (ld < M) return fail(h, PID_ERR_INVALID_ARG, "ld must be >= M");
   if (M > (int64_t(1) << 31) - 4096) return fail(h, PID_ERR_UNSUPPORTED, "M must be < 2^31 - 4096");
   if (ld > (int64_t(1) << 37)) return fail(h, PID_ERR_UNSUPPORTED, "ld too large");
-  if (N > kMaxMembers) return fail(h, PID_ERR_UNSUPPORTED, "N above the supported maximum (512)");
+  if (N > max_n)
+    return fail(h, PID_ERR_UNSUPPORTED,
+                max_n == kMaxMembers ? "N above the supported maximum (512) of batches and serving"
+                                     : "N above the supported maximum (2^22)");
   return PID_OK;
 }
 
@@ -422,7 +426,7 @@ static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef
                        static_cast<int64_t>(pl.desc.N) * pl.desc.M, bytes, s);
 }
 
-static pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
+pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
   const int nb_stream = (2 * fd.N + 31) / 32;
   const int nb_gram = fd.kind == FIN_GRAM ? fin_gram_items(fd.N) : 0;
   fd.slices = std::max(1, std::min(nb_stream + nb_gram, 2 * h->sms));
@@ -439,6 +443,7 @@ static pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
 }
 
 pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s) {
+  if (in.N > kMaxMembers) return run_blocked(h, in, out, s);
   EnsPlan pl;
   pid_status st = plan_stream(h, in, &pl);
   if (st != PID_OK) return st;
@@ -674,7 +679,7 @@ static pid_status common_call(pid_handle h, const float* data, int64_t N, int64_
 pid_status pid_mean(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
                     const float* w, double* depth, double* in_in, double* in_out, int32_t* rank,
                     void* stream) {
-  pid_status st = check_shape(h, U, N, M, ld);
+  pid_status st = check_shape(h, U, N, M, ld, kMaxBlockedMembers);
   if (st != PID_OK) return st;
   EnsOutputs out{};
   out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
@@ -684,7 +689,7 @@ pid_status pid_mean(pid_handle h, const float* U, int64_t N, int64_t M, int64_t 
 pid_status pid_full(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
                     const float* w, const pid_options* opt, double* depth, double* in_in,
                     double* in_out, int32_t* rank, double* P, double* err_est, void* stream) {
-  pid_status st = check_shape(h, U, N, M, ld);
+  pid_status st = check_shape(h, U, N, M, ld, kMaxBlockedMembers);
   if (st != PID_OK) return st;
   if ((st = check_opt(h, opt)) != PID_OK) return st;
   pid_options o{PID_MODE_FULL_LINEAR, PID_FP32, 0, 0};
@@ -700,7 +705,7 @@ pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, i
                            const float* w, const pid_iso* iso, const pid_options* opt,
                            double* depth, double* in_in, double* in_out, int32_t* rank,
                            void* stream) {
-  pid_status st = check_shape(h, F, N, M, ld);
+  pid_status st = check_shape(h, F, N, M, ld, kMaxBlockedMembers);
   if (st != PID_OK) return st;
   if ((st = check_iso(h, iso)) != PID_OK) return st;
   if ((st = check_opt(h, opt)) != PID_OK) return st;

@@ -15,6 +15,7 @@
 namespace pidh {
 
 constexpr int64_t kMaxMembers = 512;   // largest N of the fused single-pass kernels
+constexpr int64_t kMaxBlockedMembers = int64_t(1) << 22;   // single calls, member-blocked path
 constexpr int kMaxTickets = 8192;      // ensembles per batch (one finalisation ticket each)
 
 struct BatchCache;  // batch.cu
@@ -133,7 +134,10 @@ pid_status cuda_fail(pid_handle h, cudaError_t e, const char* where);
 StreamCfg stream_cfg(int64_t N);
 void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t);
 pid_status check_iso(pid_handle h, const pid_iso* iso);
-pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld);
+pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld,
+                       int64_t max_n = kMaxMembers);
+pid_status launch_fin_one(pid_handle h, pidk::FinDesc fd, cudaStream_t s);
+pid_status run_blocked(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s);
 pid_status check_opt(pid_handle h, const pid_options* o);
 pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl);
 void stream_launch_geometry(const StreamCfg& cfg, int32_t stage_floats, int* depth, size_t* smem);

@@ -142,6 +142,39 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   if (!is_last) return;
   __threadfence();
 
+  // Phase 2 for ensembles larger than the CTA (member-blocked path, no Gram): the same
+  // per-member outputs over a strided loop; ranks come from a separate kernel.
+  if (N > kFinThreads) {
+    const double* S = d.sums;
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < N; j += kFinThreads) acc += __ldcg(S + j);
+    sred[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+      if (static_cast<int>(threadIdx.x) < o) sred[threadIdx.x] += sred[threadIdx.x + o];
+      __syncthreads();
+    }
+    const double mbar = sred[0] / N;
+    for (int j = threadIdx.x; j < N; j += kFinThreads) {
+      const double m = __ldcg(S + j), A = __ldcg(S + N + j) / N;
+      const double in_in = m > 0.0 ? A / m : 0.0;
+      const double mean_out = mbar > 0.0 ? A / mbar : 0.0;
+      if (d.mass) d.mass[j] = m;
+      if (d.mean_depth) d.mean_depth[j] = fmin(in_in, mean_out);
+      if (d.kind == FIN_LIN1) {
+        d.coef[j] = m > 0.0 ? static_cast<float>(1.0 / (static_cast<double>(N) * m)) : 0.0f;
+        continue;
+      }
+      const double in_out = d.kind == FIN_LIN2 ? __ldcg(S + 3 * N + j) : mean_out;
+      if (d.depth) d.depth[j] = fmin(in_in, in_out);
+      if (d.in_in) d.in_in[j] = in_in;
+      if (d.in_out) d.in_out[j] = in_out;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *d.ticket = 0u;
+    return;
+  }
+
   // Phase 2 (last CTA of this ensemble): per-member outputs and ranks.
   const int i = threadIdx.x;
   const double* S = d.sums;

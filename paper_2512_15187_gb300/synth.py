@@ -15,6 +15,8 @@ Workloads (sizes of the benchmark configurations):
                   unit disk with log-uniform lumped-area weights (non-Cartesian)
   plume_3d        smoke-plume-like 3D soft masks (sigmoid of a noise-displaced
                   cone, 5-octave fBm), generated on the device with torch
+  ellipsoids_3d   3D ellipsoid soft masks, 80% normal members and 20% outliers (the
+                  scalability study's ensembles), generated on the device with torch
 """
 from __future__ import annotations
 
@@ -227,4 +229,44 @@ def rbf_fields_2d_torch(N: int = 64, H: int = 512, W: int = 512, n_rbf: int = 32
         F = torch.bmm(gy, gx).view(n, H * W)
         F += 0.05 * torch.randn((n, H * W), generator=g, device=device)
         out[s:s + n] = F
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Scalability study: 3D ellipsoids with controlled contamination
+# ---------------------------------------------------------------------------
+
+def ellipsoids_3d(N: int, R: int, seed: int = DEFAULT_SEED + 5, outlier_frac: float = 0.2,
+                  device: str = "cuda", out=None, chunk: int = 64):
+    """Soft 3D ellipsoid masks on an R^3 grid over the unit cube, float32 [N, R^3].
+
+    Member i is an axis-aligned ellipsoid with centre c_i and semi-axes a_i, and soft mask
+    u = sigmoid((1 - s) / 0.05) with s the ellipsoid-normalised radius (s = 1 on the
+    surface). Normal members (the first 80%): c = 0.5 + N(0, 0.02) per axis, semi-axes
+    0.25 + N(0, 0.015). Outliers (the last 20%): c = 0.5 + N(0, 0.08), semi-axes drawn
+    from U[0.12, 0.38] independently per axis. These constants are this generator's own
+    choice (the paper does not print them).
+    """
+    import torch
+
+    if out is None:
+        out = torch.empty((N, R ** 3), dtype=torch.float32, device=device)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    n_out = int(round(outlier_frac * N))
+    n_norm = N - n_out
+    c = 0.5 + 0.02 * torch.randn((N, 3), generator=g, device=device)
+    a = 0.25 + 0.015 * torch.randn((N, 3), generator=g, device=device)
+    if n_out:
+        c[n_norm:] = 0.5 + 0.08 * torch.randn((n_out, 3), generator=g, device=device)
+        a[n_norm:] = 0.12 + 0.26 * torch.rand((n_out, 3), generator=g, device=device)
+    t = (torch.arange(R, dtype=torch.float32, device=device) + 0.5) / R
+    chunk = max(1, min(chunk, (1 << 27) // (R ** 3)))   # bounded temporaries
+    for s0 in range(0, N, chunk):
+        n = min(chunk, N - s0)
+        cz, cy, cx = (c[s0:s0 + n, k].view(n, 1, 1, 1) for k in range(3))
+        az, ay, ax = (a[s0:s0 + n, k].view(n, 1, 1, 1) for k in range(3))
+        s2 = (((t.view(1, R, 1, 1) - cz) / az) ** 2 + ((t.view(1, 1, R, 1) - cy) / ay) ** 2 +
+              ((t.view(1, 1, 1, R) - cx) / ax) ** 2)
+        out[s0:s0 + n] = torch.sigmoid((1.0 - torch.sqrt(s2)) / 0.05).view(n, -1)
     return out

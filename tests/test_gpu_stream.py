@@ -197,7 +197,7 @@ def test_invalid_arguments(H):
     with pytest.raises(B.PidError) as e:
         B.pid_mean(H.h, U.data_ptr(), 0, 100, 100, None, d.data_ptr(), None, None, None)
     assert e.value.status == B.PID_ERR_INVALID_ARG
-    big = torch.rand((513, 8), device="cuda")
+    big = torch.zeros(((1 << 22) + 1, 8), device="cuda")     # above the member limit
     with pytest.raises(B.PidError) as e:
         H.mean(big)
     assert e.value.status == B.PID_ERR_UNSUPPORTED
