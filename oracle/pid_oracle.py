@@ -21,6 +21,8 @@ Every function cites the passage it follows:
   cells accumulated block by block, for ensembles larger than host memory in float64)
   Sec. 5.4         contour boxplots: unions and intersections of the binarised members
                    of a depth-ordered population, and the median member
+  Sec. 3.5, Sec. 5 other mask models: a uniform isovalue distribution, the level-centred
+                   map of the weather example; Sec. 4.1 reliability-weighted mean contour
 
 Readings where the paper is silent (each also listed in the design notes):
   * Zero-mass reference mask: u subset_p v = 0 (Sec. 3.2), unlike eID's 1 (Eq. 1).
@@ -55,6 +57,9 @@ __all__ = [
     "pid_chunked",
     "pid_mean_chunked",
     "contour_bands",
+    "iso_soft_mask_uniform",
+    "level_soft_mask",
+    "pid_mean_weighted",
 ]
 
 
@@ -214,6 +219,42 @@ def iso_soft_mask(F, mu: float, sigma: float, superlevel: bool = False) -> np.nd
     if superlevel:
         z = -z
     return 0.5 * _erfc(z)
+
+
+def iso_soft_mask_uniform(F, mu: float, half_width: float, superlevel: bool = False) -> np.ndarray:
+    """Soft mask for an isovalue uniform on [mu - h, mu + h] (Sec. 3.5 with another
+    isovalue distribution): u(x) = P(F(x) < q) = clamp((mu + h - F) / (2 h), 0, 1), or
+    P(F(x) > q) = clamp((F - (mu - h)) / (2 h), 0, 1) for the super-level set."""
+    F = _f64(F)
+    if not half_width > 0:
+        raise ValueError("half_width must be > 0")
+    if superlevel:
+        return np.clip((F - (mu - half_width)) / (2.0 * half_width), 0.0, 1.0)
+    return np.clip((mu + half_width - F) / (2.0 * half_width), 0.0, 1.0)
+
+
+def level_soft_mask(F, level: float, half_width: float) -> np.ndarray:
+    """Level-centred soft mask (the weather example of Sec. 5): probability 1 at the level,
+    falling linearly to 0 at distance `half_width`: u = max(0, 1 - |F - level| / h)."""
+    F = _f64(F)
+    if not half_width > 0:
+        raise ValueError("half_width must be > 0")
+    return np.maximum(0.0, 1.0 - np.abs(F - level) / half_width)
+
+
+def pid_mean_weighted(U, member_weights, w=None):
+    """PID-mean against a reliability-weighted mean contour (Sec. 4.1):
+    u_bar = sum_j r_j u_j / sum_j r_j, then IN_in(i) = u_i subset_p u_bar and
+    IN_out(i) = u_bar subset_p u_i (Eq. 16). Returns (in_in, in_out, depth)."""
+    U = np.atleast_2d(_f64(U))
+    r = _f64(member_weights).reshape(-1)
+    if r.shape[0] != U.shape[0] or not np.all(r >= 0) or not r.sum() > 0:
+        raise ValueError("one non-negative member weight per member, not all zero")
+    ubar = (r[:, None] * U).sum(axis=0) / r.sum()
+    N = U.shape[0]
+    in_in = np.array([inclusion(U[i], ubar, w) for i in range(N)])
+    in_out = np.array([inclusion(ubar, U[i], w) for i in range(N)])
+    return in_in, in_out, np.minimum(in_in, in_out)
 
 
 def rank_by_depth(depth) -> np.ndarray:

@@ -376,3 +376,39 @@ def test_bands_of_nested_disks_are_the_extreme_disks():
     assert np.array_equal((b & 4) > 0, U[-1] > 0.5)
     assert np.array_equal((b & 8) > 0, U[0] > 0.5)
     assert np.array_equal((b & 16) > 0, U[int(np.argmin(rank))] > 0.5)
+
+
+# --- other mask models and the weighted mean contour ---------------------------------
+
+def test_uniform_isovalue_mask_closed_form():
+    # q ~ U[0.4, 0.6]: P(F < q) is 1 below 0.4, 0 above 0.6, and linear in between
+    F = np.array([0.0, 0.4, 0.45, 0.5, 0.55, 0.6, 1.0])
+    np.testing.assert_allclose(O.iso_soft_mask_uniform(F, 0.5, 0.1),
+                               [1.0, 1.0, 0.75, 0.5, 0.25, 0.0, 0.0], atol=1e-15)
+    np.testing.assert_allclose(O.iso_soft_mask_uniform(F, 0.5, 0.1, superlevel=True),
+                               [0.0, 0.0, 0.25, 0.5, 0.75, 1.0, 1.0], atol=1e-15)
+    # the mean of the uniform mask over a linear ramp equals the normal one's by symmetry
+    F = np.linspace(0, 1, 100001)
+    assert abs(O.iso_soft_mask_uniform(F, 0.5, 0.2).mean() - O.iso_soft_mask(F, 0.5, 0.1).mean()) < 1e-4
+
+
+def test_level_mask_closed_form():
+    F = np.array([0.2, 0.35, 0.5, 0.6, 0.7, 0.9])
+    np.testing.assert_allclose(O.level_soft_mask(F, 0.5, 0.2), [0.0, 0.25, 1.0, 0.5, 0.0, 0.0],
+                               atol=1e-15)
+
+
+def test_weighted_mean_contour_special_cases():
+    rng = np.random.default_rng(8)
+    U = synth.random_soft(6, 400, seed=8).astype(np.float64)
+    w = rng.uniform(0.5, 2, 400)
+    # equal reliabilities: plain PID-mean
+    np.testing.assert_allclose(np.array(O.pid_mean_weighted(U, np.full(6, 3.0), w)),
+                               np.array(O.pid_mean(U, w)), atol=1e-14)
+    # all reliability on member k: u_bar = u_k, the pairwise inclusions of Eq. 9
+    k = 2
+    r = np.zeros(6)
+    r[k] = 1.0
+    a, b, _ = O.pid_mean_weighted(U, r, w)
+    np.testing.assert_allclose(a, [O.inclusion(U[i], U[k], w) for i in range(6)], atol=1e-14)
+    np.testing.assert_allclose(b, [O.inclusion(U[k], U[i], w) for i in range(6)], atol=1e-14)
