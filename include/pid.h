@@ -75,7 +75,12 @@ typedef enum pid_precision {
 } pid_precision;
 
 typedef enum pid_iso_kind {
-  PID_ISO_NORMAL = 0        /* isovalue q ~ Normal(mu, sigma), Sec. 3.5 */
+  PID_ISO_NORMAL = 0,       /* isovalue q ~ Normal(mu, sigma), Sec. 3.5 */
+  PID_ISO_UNIFORM = 1,      /* isovalue q ~ Uniform[mu - sigma, mu + sigma] (sigma > 0):
+                               u = P(F < q) = clamp((mu + sigma - F) / (2 sigma), 0, 1) */
+  PID_ISO_LEVEL = 2         /* level-centred map of the weather example (Sec. 5): probability
+                               1 at the level mu, falling linearly to 0 at distance sigma:
+                               u = max(0, 1 - |F - mu| / sigma) (sigma > 0, superlevel 0) */
 } pid_iso_kind;
 
 /* Isovalue distribution for pid_soft_masks / pid_from_fields (Sec. 3.5). */
@@ -83,7 +88,8 @@ typedef struct pid_iso {
   int32_t kind;             /* pid_iso_kind */
   int32_t superlevel;       /* 0: inside = {F < q} (Eq. 2); 1: inside = {F > q} */
   double mu;                /* mean isovalue */
-  double sigma;             /* standard deviation, >= 0 (0 = hard threshold at mu) */
+  double sigma;             /* NORMAL: standard deviation, >= 0 (0 = hard threshold at mu);
+                               UNIFORM, LEVEL: half-width, > 0 */
 } pid_iso;
 
 typedef struct pid_options {
@@ -217,6 +223,23 @@ pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, i
                            const float* w, const pid_iso* iso, const pid_options* opt,
                            double* depth, double* in_in, double* in_out, int32_t* rank,
                            void* stream);
+
+/*
+ * pid_mean_weighted — PID-mean against a reliability-weighted mean contour (Sec. 4.1):
+ * u_bar = sum_j c_j u_j with c_j = r_j / sum_k r_k, IN_in(i) = u_i subset_p u_bar and
+ * IN_out(i) = u_bar subset_p u_i (the inclusions of Eq. 16), depth = min of the two.
+ * data: soft masks [N][ld] (iso = NULL) or scalar fields mapped through `iso`.
+ * member_weights: device float64 [N], r_j >= 0 and finite, not all zero; they are checked
+ * on the device (a violation sets the domain bit reported by pid_sync, and the outputs are
+ * zero). c_j is rounded to float32 once, and the mean contour's mass sum_j c_j m_j uses the
+ * same rounded c_j, so the two inclusions refer to one mean contour. Equal weights give
+ * pid_mean's results up to rounding. One streaming pass plus two small kernels; any
+ * N <= 2^22.
+ */
+pid_status pid_mean_weighted(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,
+                             const float* w, const pid_iso* iso, const double* member_weights,
+                             double* depth, double* in_in, double* in_out, int32_t* rank,
+                             void* stream);
 
 /*
  * One ensemble of a batch. `data` are soft masks (is_field = 0) or scalar fields mapped

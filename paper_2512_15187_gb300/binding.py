@@ -19,6 +19,8 @@ PID_ERR_TIMEOUT, PID_ERR_BUSY, PID_ERR_CANCELLED, PID_ERR_UNSUPPORTED = 5, 6, 7,
 PID_MODE_MEAN, PID_MODE_FULL, PID_MODE_FULL_LINEAR = 0, 1, 2
 PID_FP32, PID_BF16, PID_SPLIT_BF16, PID_FP8 = 0, 1, 2, 3
 PID_ISO_NORMAL = 0
+PID_ISO_UNIFORM = 1
+PID_ISO_LEVEL = 2
 
 MODES = {"mean": PID_MODE_MEAN, "full": PID_MODE_FULL, "gram": PID_MODE_FULL,
          "linear": PID_MODE_FULL_LINEAR, "full_linear": PID_MODE_FULL_LINEAR}
@@ -30,7 +32,7 @@ EXPORTS = [
     "pid_batch", "pid_profile_enable", "pid_profile_read", "pid_autotune_enable",
     "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
-    "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands",
+    "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands", "pid_mean_weighted",
     "pid_selftest_wait_timeout",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
@@ -47,6 +49,17 @@ class PidError(RuntimeError):
 
 class pid_iso(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("superlevel", c_int32), ("mu", c_double), ("sigma", c_double)]
+
+
+ISO_KINDS = {"normal": PID_ISO_NORMAL, "uniform": PID_ISO_UNIFORM, "level": PID_ISO_LEVEL}
+
+
+def make_iso(iso) -> "pid_iso":
+    """pid_iso from (mu, sigma[, superlevel[, kind]]); kind is "normal" (default), "uniform"
+    or "level" (or the PID_ISO_* value)."""
+    kind = iso[3] if len(iso) > 3 else "normal"
+    kind = ISO_KINDS[kind] if isinstance(kind, str) else int(kind)
+    return pid_iso(kind, int(iso[2]) if len(iso) > 2 else 0, float(iso[0]), float(iso[1]))
 
 
 class pid_options(ctypes.Structure):
@@ -110,6 +123,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                      c_int),
         "pid_from_fields": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_iso),
                              POINTER(pid_options), P, P, P, P, P], c_int),
+        "pid_mean_weighted": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_iso), P, P, P, P, P,
+                               P], c_int),
         "pid_batch": ([P, POINTER(pid_ensemble), c_int32, P], c_int),
         "pid_profile_enable": ([P, c_int], c_int),
         "pid_profile_read": ([P, c_int, POINTER(pid_kernel_stats)], c_int),
@@ -183,6 +198,13 @@ def pid_from_fields(h, F, N, M, ld, w, iso: pid_iso, opt: pid_options, depth, in
     _check(h, load().pid_from_fields(h, F, N, M, ld, w, ctypes.byref(iso),
                                      ctypes.byref(opt) if opt else None, depth, in_in, in_out,
                                      rank, stream))
+
+
+def pid_mean_weighted(h, data, N, M, ld, w, iso, member_weights, depth, in_in, in_out, rank,
+                      stream=None):
+    _check(h, load().pid_mean_weighted(h, data, N, M, ld, w,
+                                       None if iso is None else ctypes.byref(iso), member_weights,
+                                       depth, in_in, in_out, rank, stream))
 
 
 def pid_profile_enable(h, enable: bool):
@@ -293,20 +315,17 @@ class Handle:
             raise ValueError("rank must be an int32 CUDA tensor with one entry per member")
         if out is None:
             out = torch.empty(M, dtype=torch.uint8, device=data.device)
-        iso_s = None
-        if iso is not None:
-            iso_s = pid_iso(PID_ISO_NORMAL, int(iso[2]) if len(iso) > 2 else 0, float(iso[0]),
-                            float(iso[1]))
+        iso_s = None if iso is None else make_iso(iso)
         pid_contour_bands(self.h, data.data_ptr(), N, M, ld, iso_s, rank.data_ptr(), tau,
                           inner_fraction, out.data_ptr(), _stream(stream))
         return out
 
-    def soft_masks(self, F, mu, sigma, superlevel=False, out=None, stream=None):
+    def soft_masks(self, F, mu, sigma, superlevel=False, out=None, stream=None, kind="normal"):
         import torch
         N, M, ld = _check_matrix(F, "F")
         if out is None:
             out = torch.empty((N, M), dtype=torch.float32, device=F.device)
-        iso = pid_iso(PID_ISO_NORMAL, int(superlevel), float(mu), float(sigma))
+        iso = make_iso((mu, sigma, superlevel, kind))
         pid_soft_masks(self.h, F.data_ptr(), N, M, ld, iso, out.data_ptr(), out.stride(0),
                        _stream(stream))
         return out
@@ -317,6 +336,22 @@ class Handle:
         pid_mean(self.h, U.data_ptr(), N, M, ld, _ptr(w), o["depth"].data_ptr(),
                  o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
                  _stream(stream))
+        return o
+
+    def mean_weighted(self, data, member_weights, w=None, iso=None, stream=None):
+        """PID-mean against the weighted mean contour sum_j r_j u_j / sum_j r_j; data are soft
+        masks, or fields with iso=(mu, sigma[, superlevel[, kind]]); member_weights is a
+        float64 CUDA tensor [N]."""
+        import torch
+        N, M, ld = _check_matrix(data, "data")
+        r = member_weights
+        if r.dtype != torch.float64 or not r.is_cuda or r.numel() != N or not r.is_contiguous():
+            raise ValueError("member_weights must be a contiguous float64 CUDA tensor [N]")
+        o = self._outputs(N)
+        pid_mean_weighted(self.h, data.data_ptr(), N, M, ld, _ptr(w),
+                          None if iso is None else make_iso(iso), r.data_ptr(),
+                          o["depth"].data_ptr(), o["in_in"].data_ptr(), o["in_out"].data_ptr(),
+                          o["rank"].data_ptr(), _stream(stream))
         return o
 
     def full(self, U, w=None, mode="linear", precision="fp32", want_P=False, validate=False,
@@ -331,10 +366,10 @@ class Handle:
         return o
 
     def from_fields(self, F, mu, sigma, superlevel=False, w=None, mode="mean", precision="fp32",
-                    validate=False, stream=None):
+                    validate=False, stream=None, kind="normal"):
         N, M, ld = _check_matrix(F, "F")
         o = self._outputs(N)
-        iso = pid_iso(PID_ISO_NORMAL, int(superlevel), float(mu), float(sigma))
+        iso = make_iso((mu, sigma, superlevel, kind))
         opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
         pid_from_fields(self.h, F.data_ptr(), N, M, ld, _ptr(w), iso, opt, o["depth"].data_ptr(),
                         o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
@@ -364,8 +399,7 @@ class Handle:
             e.w = _ptr(it.get("w"))
             e.is_field = int(iso is not None)
             if iso is not None:
-                e.iso = pid_iso(PID_ISO_NORMAL, int(iso[2]) if len(iso) > 2 else 0, float(iso[0]),
-                                float(iso[1]))
+                e.iso = make_iso(iso)
             e.opt = pid_options(mode, prec, int(it.get("validate", False)), 0)
             for k in ("depth", "in_in", "in_out", "rank", "mass", "mean_depth", "P", "err_est"):
                 setattr(e, k, _ptr(o.get(k)))
@@ -425,8 +459,7 @@ class Server:
             w = None if w is None else np.ascontiguousarray(w, dtype=np.float32)
             wptr = None if w is None else w.ctypes.data
             keep = None
-        iso_s = pid_iso(PID_ISO_NORMAL, int(iso[2]) if iso and len(iso) > 2 else 0,
-                        float(iso[0]), float(iso[1])) if iso else pid_iso()
+        iso_s = make_iso(iso) if iso else pid_iso()
         self._chk(load().pid_serve_register(self.s, dptr, N, M, ld, wptr, int(iso is not None),
                                             ctypes.byref(iso_s), int(bool(copy)),
                                             ctypes.byref(ens)))

@@ -19,14 +19,19 @@ struct BandParams {
   uint8_t* out;          // [M]
   int64_t N, M, ld;
   int32_t n_inner;       // members with rank < n_inner form the inner population
-  int32_t cmp;           // 0: value > thr, 1: value < thr, 2: value > thr (field, super-level)
-  float thr;
+  int32_t cmp;           // 0: value > thr, 1: value < thr, 2: value > thr (field, super-level),
+                         // 3: thr < value < thr2 (field, level map)
+  float thr, thr2;
 };
 
 // Band bits of 4 cells as 4-bit masks, one bit per cell.
-__device__ __forceinline__ uint32_t bin4(float a, float b, float c, float d, int cmp, float t) {
+__device__ __forceinline__ uint32_t bin4(float a, float b, float c, float d, int cmp, float t,
+                                         float t2) {
   if (cmp == 1)
     return (a < t ? 1u : 0u) | (b < t ? 2u : 0u) | (c < t ? 4u : 0u) | (d < t ? 8u : 0u);
+  if (cmp == 3)
+    return (a > t && a < t2 ? 1u : 0u) | (b > t && b < t2 ? 2u : 0u) |
+           (c > t && c < t2 ? 4u : 0u) | (d > t && d < t2 ? 8u : 0u);
   return (a > t ? 1u : 0u) | (b > t ? 2u : 0u) | (c > t ? 4u : 0u) | (d > t ? 8u : 0u);
 }
 
@@ -52,7 +57,7 @@ __global__ void __launch_bounds__(256) bands_kernel(const __grid_constant__ Band
         v.z = x + 2 < p.M ? __ldg(row + 2) : 0.f;
         v.w = x + 3 < p.M ? __ldg(row + 3) : 0.f;
       }
-      const uint32_t b = bin4(v.x, v.y, v.z, v.w, p.cmp, p.thr);
+      const uint32_t b = bin4(v.x, v.y, v.z, v.w, p.cmp, p.thr, p.thr2);
       const int32_t r = __ldg(p.rank + i);
       au |= b;
       ai &= b;
@@ -139,6 +144,20 @@ extern "C" pid_status pid_contour_bands(pid_handle h, const float* data, int64_t
   if (!iso) {
     p.cmp = 0;
     p.thr = float_at_or_below(tau);
+  } else if (iso->kind == PID_ISO_UNIFORM) {
+    const double h = iso->sigma;
+    if (!iso->superlevel) {            // u = (mu + h - F) / 2h > tau <=> F < mu + h (1 - 2 tau)
+      p.cmp = 1;
+      p.thr = float_at_or_above(iso->mu + h * (1.0 - 2.0 * tau));
+    } else {                           // u = (F - mu + h) / 2h > tau <=> F > mu + h (2 tau - 1)
+      p.cmp = 2;
+      p.thr = float_at_or_below(iso->mu + h * (2.0 * tau - 1.0));
+    }
+  } else if (iso->kind == PID_ISO_LEVEL) {  // 1 - |F - mu| / h > tau <=> |F - mu| < h (1 - tau)
+    const double r = iso->sigma * (1.0 - tau);
+    p.cmp = 3;
+    p.thr = float_at_or_below(iso->mu - r);
+    p.thr2 = float_at_or_above(iso->mu + r);
   } else if (iso->sigma > 0.0) {
     const double z = normal_quantile(tau);
     if (!iso->superlevel) {            // u = Phi((mu - F) / sigma) > tau <=> F < mu - sigma z

@@ -230,8 +230,15 @@ pid_status run_blocked(pid_handle h, const EnsInput& in, const EnsOutputs& out, 
   fd.mass = out.mass;
   fd.mean_depth = out.mean_depth;
 
-  if ((st = blocked_pass(h, p, bytes, s)) != PID_OK) return st;
-  if (!linear) {
+  if (in.member_weights) {   // PID-mean against the weighted mean contour: one pass
+    if ((st = launch_member_coef_one(h, in.member_weights, N, coef, s)) != PID_OK) return st;
+    p.coef = coef;
+    if ((st = blocked_pass(h, p, bytes, s)) != PID_OK) return st;
+    fd.kind = FIN_WMEAN;
+    if ((st = launch_fin_one(h, fd, s)) != PID_OK) return st;
+  } else if ((st = blocked_pass(h, p, bytes, s)) != PID_OK) {
+    return st;
+  } else if (!linear) {
     fd.kind = FIN_MEAN;
     if ((st = launch_fin_one(h, fd, s)) != PID_OK) return st;
   } else {

@@ -163,6 +163,21 @@ static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
 void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t) {
   if (!iso) { *mode = ISO_NONE; *mu = 0.f; *inv = 0.f; *t = 0.f; return; }
+  if (iso->kind == PID_ISO_UNIFORM) {    // q ~ U[mu - h, mu + h]
+    const double h = iso->sigma;
+    *mode = iso->superlevel ? ISO_UNIFORM_ABOVE : ISO_UNIFORM_BELOW;
+    *mu = static_cast<float>(iso->superlevel ? iso->mu - h : iso->mu + h);
+    *inv = static_cast<float>(1.0 / (2.0 * h));
+    *t = 0.f;
+    return;
+  }
+  if (iso->kind == PID_ISO_LEVEL) {
+    *mode = ISO_LEVEL;
+    *mu = static_cast<float>(iso->mu);
+    *inv = static_cast<float>(1.0 / iso->sigma);
+    *t = 0.f;
+    return;
+  }
   *mu = static_cast<float>(iso->mu);
   if (iso->sigma > 0.0) {
     *mode = ISO_NORMAL;
@@ -187,11 +202,20 @@ void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t
 
 pid_status check_iso(pid_handle h, const pid_iso* iso) {
   if (!iso) return fail(h, PID_ERR_INVALID_ARG, "iso must not be NULL");
-  if (iso->kind != PID_ISO_NORMAL) return fail(h, PID_ERR_UNSUPPORTED, "unknown iso kind");
+  if (iso->kind != PID_ISO_NORMAL && iso->kind != PID_ISO_UNIFORM && iso->kind != PID_ISO_LEVEL)
+    return fail(h, PID_ERR_UNSUPPORTED, "unknown iso kind");
   if (!std::isfinite(iso->mu) || !std::isfinite(iso->sigma) || iso->sigma < 0.0)
     return fail(h, PID_ERR_INVALID_ARG, "iso needs finite mu and sigma >= 0");
   if (iso->superlevel != 0 && iso->superlevel != 1)
     return fail(h, PID_ERR_INVALID_ARG, "iso.superlevel must be 0 or 1");
+  if (iso->kind != PID_ISO_NORMAL && !(iso->sigma > 0.0))
+    return fail(h, PID_ERR_INVALID_ARG, "uniform and level maps need a half-width sigma > 0");
+  if (iso->kind != PID_ISO_NORMAL &&
+      !(std::fabs(iso->mu) + iso->sigma < 1e38 && 1.0 / (2.0 * iso->sigma) < 1e38))
+    return fail(h, PID_ERR_INVALID_ARG, "uniform and level maps need mu +- sigma and 1/(2 sigma) "
+                                        "inside the float range");
+  if (iso->kind == PID_ISO_LEVEL && iso->superlevel)
+    return fail(h, PID_ERR_INVALID_ARG, "the level map has no super-level form");
   return PID_OK;
 }
 
@@ -442,6 +466,14 @@ pid_status launch_fin_one(pid_handle h, FinDesc fd, cudaStream_t s) {
   return PID_OK;
 }
 
+pid_status launch_member_coef_one(pid_handle h, const double* r, int64_t N, float* coef,
+                                  cudaStream_t s) {
+  ProfScope ps(h, PID_KERNEL_FINALIZE, 8.0 * N + 4.0 * N, 0.0, s);
+  cudaError_t e = launch_member_coef(r, N, coef, h->err_word, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "member coefficient launch");
+  return PID_OK;
+}
+
 pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s) {
   if (in.N > kMaxMembers) return run_blocked(h, in, out, s);
   EnsPlan pl;
@@ -492,6 +524,12 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
     fd.n_gchunks = gp.n_gchunks;
     fd.P = out.P;
     fd.err_est = out.err_est;
+    return launch_fin_one(h, fd, s);
+  }
+  if (in.member_weights) {   // PID-mean against the weighted mean contour: one pass
+    if ((st = launch_member_coef_one(h, in.member_weights, in.N, coef, s)) != PID_OK) return st;
+    if ((st = launch_stream_one(h, pl, coef, s)) != PID_OK) return st;
+    fd.kind = FIN_WMEAN;
     return launch_fin_one(h, fd, s);
   }
   st = launch_stream_one(h, pl, nullptr, s);
@@ -666,8 +704,10 @@ pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, in
 
 static pid_status common_call(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,
                               const float* w, const pid_iso* iso, int mode, int prec, int validate,
-                              const EnsOutputs& out, void* stream) {
+                              const EnsOutputs& out, void* stream,
+                              const double* member_weights = nullptr) {
   EnsInput in;
+  in.member_weights = member_weights;
   in.data = data; in.N = N; in.M = M; in.ld = ld; in.w = w;
   in.is_field = iso != nullptr;
   if (iso) in.iso = *iso;
@@ -714,6 +754,20 @@ pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, i
   EnsOutputs out{};
   out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
   return common_call(h, F, N, M, ld, w, iso, o.mode, o.precision, o.validate, out, stream);
+}
+
+pid_status pid_mean_weighted(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,
+                             const float* w, const pid_iso* iso, const double* member_weights,
+                             double* depth, double* in_in, double* in_out, int32_t* rank,
+                             void* stream) {
+  pid_status st = check_shape(h, data, N, M, ld, kMaxBlockedMembers);
+  if (st != PID_OK) return st;
+  if (iso && (st = check_iso(h, iso)) != PID_OK) return st;
+  if (!member_weights) return fail(h, PID_ERR_INVALID_ARG, "member_weights must be non-NULL");
+  EnsOutputs out{};
+  out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
+  return common_call(h, data, N, M, ld, w, iso, PID_MODE_MEAN, PID_FP32, 0, out, stream,
+                     member_weights);
 }
 
 }  // extern "C"

@@ -83,6 +83,7 @@ struct EnsInput {
   int mode = PID_MODE_MEAN;
   int precision = PID_FP32;
   int validate = 0;
+  const double* member_weights = nullptr;  // weighted mean contour (PID_MODE_MEAN only)
 };
 
 struct EnsOutputs {
@@ -136,6 +137,8 @@ void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t
 pid_status check_iso(pid_handle h, const pid_iso* iso);
 pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld,
                        int64_t max_n = kMaxMembers);
+pid_status launch_member_coef_one(pid_handle h, const double* r, int64_t N, float* coef,
+                                  cudaStream_t s);
 pid_status launch_fin_one(pid_handle h, pidk::FinDesc fd, cudaStream_t s);
 pid_status run_blocked(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s);
 pid_status check_opt(pid_handle h, const pid_options* o);

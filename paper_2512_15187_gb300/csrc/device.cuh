@@ -263,11 +263,21 @@ __device__ __forceinline__ float2 iso_normal2(float2 f, float mu, float inv) {
   return make_float2(xs.x >= 0.f ? h.x : g.x, xs.y >= 0.f ? h.y : g.y);
 }
 
+// The piecewise-linear maps (modes 4-6): a uniform isovalue distribution (Sec. 3.5) and
+// the level-centred map of the weather example (Sec. 5).
+//   mode 4: u = clamp((mu - F) inv, 0, 1)   mode 5: u = clamp((F - mu) inv, 0, 1)
+//   mode 6: u = max(0, 1 - |F - mu| inv)
+__device__ __forceinline__ float iso_piecewise(float f, int32_t mode, float mu, float inv) {
+  if (mode == 6) return fmaxf(0.0f, fmaf(-fabsf(f - mu), inv, 1.0f));
+  const float v = mode == 4 ? (mu - f) * inv : (f - mu) * inv;
+  return fminf(fmaxf(v, 0.0f), 1.0f);
+}
+
 // Soft-mask value of one input element (Sec. 3.5); used by the standalone map.
 //   mode 1: u = P(F < q), q ~ Normal(mu, sigma): u = erfc(a)/2 with a = (F - mu) / (sigma
 //           sqrt 2), from xs = (F - mu) * inv, inv = +-sqrt(log2 e) / (sigma sqrt 2)
 //           (negated for the super-level set P(F > q)).
-//   mode 2/3: sigma = 0, the indicator of F < t or F > t.
+//   mode 2/3: sigma = 0, the indicator of F < t or F > t; modes 4-6: iso_piecewise.
 __device__ __forceinline__ float iso_value(float f, int32_t mode, float mu, float inv, float t) {
   if (mode == 1) {
     const float xs = (f - mu) * inv;
@@ -275,7 +285,8 @@ __device__ __forceinline__ float iso_value(float f, int32_t mode, float mu, floa
     return xs >= 0.f ? h : 1.0f - h;
   }
   if (mode == 2) return f < t ? 1.0f : 0.0f;
-  return f > t ? 1.0f : 0.0f;
+  if (mode == 3) return f > t ? 1.0f : 0.0f;
+  return iso_piecewise(f, mode, mu, inv);
 }
 
 }  // namespace pidk

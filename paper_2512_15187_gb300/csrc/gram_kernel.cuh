@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   int64_t ld = 0;
   uint32_t idesc = 0;
   float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f, scale = 1.0f;
+  int iso_md = 0;
   for (int u = u_begin; u < u_end && !aborted; ++u, ++kc) {
     if (u >= e_end) {
       dp = &gdesc(p, gram_find_ens(p, u));
@@ -358,7 +359,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       iso_mu = dp->iso_mu;
       iso_inv = dp->iso_inv;
       iso_t = dp->iso_t;
-      dir = (dp->iso_mode == ISO_STEP_ABOVE) ? -1.f : 1.f;
+      iso_md = dp->iso_mode;
+      dir = iso_pad_sign(iso_md);
       // Rows q, q+G, ... below N are this warp's members; rows past N read a padding value
       // that every isovalue kind maps to exactly 0 (and become zero operand rows, which only
       // feed accumulator rows that are never read).
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
           }
         }
       }
-      if constexpr (ISO != ISOK_NONE) iso_map_tile<ISO>(x, iso_mu, iso_inv, iso_t, dir);
+      if constexpr (ISO != ISOK_NONE) iso_map_tile<ISO>(x, iso_mu, iso_inv, iso_t, dir, iso_md);
       if (!full) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {

@@ -12,8 +12,16 @@ enum IsoMode : int32_t {
   ISO_NONE = 0,        // data are soft masks already
   ISO_NORMAL = 1,      // u = erfc((F - mu) * inv) / 2, inv = +-1 / (sigma sqrt 2)
   ISO_STEP_BELOW = 2,  // sigma = 0, sub-level:   u = 1[F < t]
-  ISO_STEP_ABOVE = 3   // sigma = 0, super-level: u = 1[F > t]
+  ISO_STEP_ABOVE = 3,  // sigma = 0, super-level: u = 1[F > t]
+  ISO_UNIFORM_BELOW = 4,  // u = clamp((mu - F) inv, 0, 1): q ~ U[mu - 1/inv, mu], P(F < q)
+  ISO_UNIFORM_ABOVE = 5,  // u = clamp((F - mu) inv, 0, 1): q ~ U[mu, mu + 1/inv], P(F > q)
+  ISO_LEVEL = 6           // u = max(0, 1 - |F - mu| inv)
 };
+
+// Padding rows read this sign of infinity so that the piecewise maps give exactly 0.
+inline constexpr float iso_pad_sign(int32_t mode) {
+  return (mode == ISO_STEP_ABOVE || mode == ISO_UNIFORM_ABOVE) ? -1.f : 1.f;
+}
 
 // Bits of the device error word.
 enum ErrBits : uint32_t { ERR_DOMAIN = 1u, ERR_TIMEOUT = 2u, ERR_INTERNAL = 4u };
@@ -96,7 +104,8 @@ enum FinKind : int32_t {
   FIN_MEAN = 0,   // PID-mean outputs from (m, A)
   FIN_LIN1 = 1,   // first pass of exact full PID: keep (m, A), emit coefficients 1/(N m_j)
   FIN_LIN2 = 2,   // second pass: B_i = IN_out(i); full-PID outputs
-  FIN_GRAM = 3    // full PID from the Gram partials plus (m, A)
+  FIN_GRAM = 3,   // full PID from the Gram partials plus (m, A)
+  FIN_WMEAN = 4   // PID-mean against the weighted mean contour sum_j c_j u_j (coef = c)
 };
 
 struct FinDesc {
@@ -107,7 +116,7 @@ struct FinDesc {
   int32_t slices;          // CTAs working on this ensemble
   int32_t pad0;
   double* sums;            // workspace [4N] FP64 m, A, (second-pass m), B; then FP32 G [N*N], C0 [N*N]
-  float* coef;             // FIN_LIN1 writes [N] coefficients here
+  float* coef;             // FIN_LIN1 writes [N] coefficients here; FIN_WMEAN reads c_j
   unsigned int* ticket;    // zero before the launch; the last CTA resets it
   double* depth;
   double* in_in;
@@ -140,13 +149,16 @@ struct IsoParams {
 constexpr int fin_gram_items(int N) { return (N * N + 1023) / 1024; }
 
 // Launchers (stream.cu).
-// Kernel family of an isovalue mode: 0 none, 1 normal, 2 step (either direction).
+// Kernel family of an isovalue mode: 0 none, 1 normal, 2 step (either direction) and the
+// piecewise-linear maps (uniform isovalue, level map), chosen at run time inside the kernel.
 inline int iso_kind(int32_t iso_mode) { return iso_mode == ISO_NONE ? 0 : (iso_mode == ISO_NORMAL ? 1 : 2); }
 
 cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, bool coef, int grid,
                           size_t smem, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
+cudaError_t launch_member_coef(const double* r, int64_t N, float* coef, uint32_t* err,
+                               cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
 size_t gram_smem_bytes(int G, bool wide, int prec, int dF, int dO, int stage_floats);
 cudaError_t launch_gram(const GramParams& p, int G, bool wide, int prec, int iso_kind, int grid,

@@ -146,17 +146,19 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   // per-member outputs over a strided loop; ranks come from a separate kernel.
   if (N > kFinThreads) {
     const double* S = d.sums;
+    const bool wm = d.kind == FIN_WMEAN;
     double acc = 0.0;
-    for (int j = threadIdx.x; j < N; j += kFinThreads) acc += __ldcg(S + j);
+    for (int j = threadIdx.x; j < N; j += kFinThreads)
+      acc += wm ? __ldcg(S + j) * static_cast<double>(__ldg(d.coef + j)) : __ldcg(S + j);
     sred[threadIdx.x] = acc;
     __syncthreads();
     for (int o = kFinThreads / 2; o > 0; o >>= 1) {
       if (static_cast<int>(threadIdx.x) < o) sred[threadIdx.x] += sred[threadIdx.x + o];
       __syncthreads();
     }
-    const double mbar = sred[0] / N;
+    const double mbar = wm ? sred[0] : sred[0] / N;
     for (int j = threadIdx.x; j < N; j += kFinThreads) {
-      const double m = __ldcg(S + j), A = __ldcg(S + N + j) / N;
+      const double m = __ldcg(S + j), A = wm ? __ldcg(S + N + j) : __ldcg(S + N + j) / N;
       const double in_in = m > 0.0 ? A / m : 0.0;
       const double mean_out = mbar > 0.0 ? A / mbar : 0.0;
       if (d.mass) d.mass[j] = m;
@@ -180,15 +182,18 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   const double* S = d.sums;
   double m = 0.0, A = 0.0;
   // The kernels sum A_i against the column sum N u_bar: the 1/N of Eq. 15 is applied here.
-  if (i < N) { m = __ldcg(S + i); A = __ldcg(S + N + i) / N; }
+  // Against a weighted mean contour sum_j c_j u_j (sum_j c_j = 1) A_i needs no scaling and
+  // the mean contour's mass is sum_j c_j m_j.
+  const bool wm = d.kind == FIN_WMEAN;
+  if (i < N) { m = __ldcg(S + i); A = wm ? __ldcg(S + N + i) : __ldcg(S + N + i) / N; }
   // m_bar = (1/N) sum_i m_i, a fixed-order tree over the thread index.
-  sred[i] = (i < N) ? m : 0.0;
+  sred[i] = (i < N) ? (wm ? m * static_cast<double>(__ldg(d.coef + i)) : m) : 0.0;
   __syncthreads();
   for (int o = kFinThreads / 2; o > 0; o >>= 1) {
     if (i < o) sred[i] += sred[i + o];
     __syncthreads();
   }
-  const double mbar = sred[0] / N;
+  const double mbar = wm ? sred[0] : sred[0] / N;
   __syncthreads();
 
   double depth = 0.0, in_in = 0.0, in_out = 0.0, err = 0.0;
@@ -198,7 +203,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     const double mean_depth = fmin(in_in_exact, mean_out);
     if (d.mass) d.mass[i] = m;
     if (d.mean_depth) d.mean_depth[i] = mean_depth;
-    if (d.kind == FIN_MEAN) {
+    if (d.kind == FIN_MEAN || wm) {
       in_in = in_in_exact; in_out = mean_out;
     } else if (d.kind == FIN_LIN1) {
       d.coef[i] = m > 0.0 ? static_cast<float>(1.0 / (static_cast<double>(N) * m)) : 0.0f;
@@ -319,6 +324,37 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
 
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s) {
   finalize_kernel<<<dim3(grid_x, grid_y), kFinThreads, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+// Coefficients of a weighted mean contour (Sec. 4.1): c_j = r_j / sum_k r_k from member
+// weights r_j >= 0, summed in FP64 in a fixed order (strided per thread, then a tree).
+// Weights that are negative, not finite, or all zero set the domain bit and give c = 0.
+__global__ void __launch_bounds__(kFinThreads, 1) member_coef_kernel(const double* r, int64_t N,
+                                                                     float* coef, uint32_t* err) {
+  __shared__ double sred[kFinThreads];
+  double acc = 0.0;
+  int bad = 0;
+  for (int64_t j = threadIdx.x; j < N; j += kFinThreads) {
+    const double v = r[j];
+    if (v >= 0.0 && v <= 1.7976931348623157e308) acc += v; else bad = 1;
+  }
+  sred[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = kFinThreads / 2; o > 0; o >>= 1) {
+    if (static_cast<int>(threadIdx.x) < o) sred[threadIdx.x] += sred[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double R = sred[0];
+  bad = __syncthreads_or(bad || !(R > 0.0 && R <= 1.7976931348623157e308));
+  if (bad && threadIdx.x == 0) atomicOr(err, ERR_DOMAIN);
+  for (int64_t j = threadIdx.x; j < N; j += kFinThreads)
+    coef[j] = bad ? 0.0f : static_cast<float>(r[j] / R);
+}
+
+cudaError_t launch_member_coef(const double* r, int64_t N, float* coef, uint32_t* err,
+                               cudaStream_t s) {
+  member_coef_kernel<<<1, kFinThreads, 0, s>>>(r, N, coef, err);
   return cudaGetLastError();
 }
 

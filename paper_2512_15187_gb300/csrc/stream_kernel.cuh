@@ -166,7 +166,7 @@ static_assert(sizeof(StreamProducer) <= kStreamProducerBytes, "producer cursor s
 // normal kind: pairs of neighbouring cells, or of neighbouring members when VEC = 1.
 template <int ISO, int MPW, int VEC>
 __device__ __forceinline__ void iso_map_tile(float (&x)[MPW][VEC], float mu, float inv, float t,
-                                             float dir) {
+                                             float dir, int mode) {
   if constexpr (ISO == ISOK_NORMAL && VEC % 2 == 0) {
 #pragma unroll
     for (int k = 0; k < MPW; ++k)
@@ -185,6 +185,20 @@ __device__ __forceinline__ void iso_map_tile(float (&x)[MPW][VEC], float mu, flo
         x[k][v] = u.x;
         x[k + 1][v] = u.y;
       }
+  } else if constexpr (ISO == ISOK_STEP) {
+    // the step maps (sigma = 0) or, for the other kinds, the piecewise-linear maps; the
+    // branch is uniform across the launch's ensemble
+    if (mode <= ISO_STEP_ABOVE) {
+#pragma unroll
+      for (int k = 0; k < MPW; ++k)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) x[k][v] = iso_map<ISO>(x[k][v], mu, inv, t, dir);
+    } else {
+#pragma unroll
+      for (int k = 0; k < MPW; ++k)
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) x[k][v] = iso_piecewise(x[k][v], mode, mu, inv);
+    }
   } else {
 #pragma unroll
     for (int k = 0; k < MPW; ++k)
@@ -321,6 +335,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   bool validate = false, has_w = false;
   float* u_out = nullptr;   // pass 1 of a field: soft masks stored for pass 2
   float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f, my_cf = 0.f;
+  int iso_md = 0;
   for (int u = u_begin; u < u_end && !aborted; ++u) {
     if (u >= e_end) {
       dp = &stream_desc(p, stream_find_ens(p, u));
@@ -335,7 +350,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       iso_mu = dp->iso_mu;
       iso_inv = dp->iso_inv;
       iso_t = dp->iso_t;
-      dir = (dp->iso_mode == ISO_STEP_ABOVE) ? -1.f : 1.f;
+      iso_md = dp->iso_mode;
+      dir = iso_pad_sign(iso_md);
       // Rows past N read this value, which every isovalue kind maps to exactly 0.
       pad = ISO == ISOK_NONE ? 0.f
                              : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
@@ -417,7 +433,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
             }
           }
         }
-        if constexpr (ISO != ISOK_NONE) iso_map_tile<ISO>(x, iso_mu, iso_inv, iso_t, dir);
+        if constexpr (ISO != ISOK_NONE) iso_map_tile<ISO>(x, iso_mu, iso_inv, iso_t, dir, iso_md);
         if constexpr (ISO != ISOK_NONE && !COEF) {
           // The soft masks of this tile, stored once so that pass 2 reads them instead of
           // repeating the isovalue map (rows are round_up(M, 4) floats, 16-byte aligned).
