@@ -242,6 +242,24 @@ pid_status pid_mean_weighted(pid_handle h, const float* data, int64_t N, int64_t
                              void* stream);
 
 /*
+ * pid_spacetime — 4D (space-time) PID: time is one more cell axis, so member i is the
+ * function u_i(x, t) over the cells (x, t) of T time steps, and every sum over cells in
+ * Eq. 6, 9, 14 and 15 runs over all T*M of them (the concatenation of the steps). steps:
+ * HOST array of T device pointers, step t holding the members' values [N][ld] at that time
+ * (soft masks, or fields mapped through `iso` when iso != NULL). w: cell measures [M],
+ * the same at every step (a uniform time step cancels in every inclusion ratio), or NULL.
+ * opt selects PID-mean, exact linear full PID or the tensor-core Gram as for pid_full
+ * (NULL = PID-mean). The steps stay where they are (no copy into one array): they become
+ * the descriptors of one persistent launch whose chunk partials are reduced by one
+ * finalisation. N <= 512 (the Gram modes: N <= 256), 1 <= T <= 65536; all steps share
+ * N, M and ld.
+ */
+pid_status pid_spacetime(pid_handle h, const float* const* steps, int32_t T, int64_t N,
+                         int64_t M, int64_t ld, const float* w, const pid_iso* iso,
+                         const pid_options* opt, double* depth, double* in_in, double* in_out,
+                         int32_t* rank, double* P, double* err_est, void* stream);
+
+/*
  * One ensemble of a batch. `data` are soft masks (is_field = 0) or scalar fields mapped
  * through `iso` (is_field = 1). Outputs as in pid_full; `mass` receives m_i and
  * `mean_depth` the PID-mean depth (both free by-products of every mode).

@@ -257,6 +257,16 @@ def pid_mean_weighted(U, member_weights, w=None):
     return in_in, in_out, np.minimum(in_in, in_out)
 
 
+def spacetime_cells(steps, w=None):
+    """4D PID (time as one more cell axis): the cells (x, t) of T time steps, each [N][M],
+    concatenated into one ensemble [N][T*M]; the cell measure w_x repeats at every step (a
+    uniform time step is a common factor of every sum and cancels in Eq. 9). Returns
+    (U, w) to pass to pid / pid_mean."""
+    steps = [np.atleast_2d(_f64(S)) for S in steps]
+    U = np.concatenate(steps, axis=1)
+    return U, (None if w is None else np.tile(_f64(w), len(steps)))
+
+
 def rank_by_depth(depth) -> np.ndarray:
     """Rank 0 = deepest member; higher rank = lower depth (Sec. 5.1).
 

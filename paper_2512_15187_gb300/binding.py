@@ -33,6 +33,7 @@ EXPORTS = [
     "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
     "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands", "pid_mean_weighted",
+    "pid_spacetime",
     "pid_selftest_wait_timeout",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
@@ -126,6 +127,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_mean_weighted": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_iso), P, P, P, P, P,
                                P], c_int),
         "pid_batch": ([P, POINTER(pid_ensemble), c_int32, P], c_int),
+        "pid_spacetime": ([P, P, c_int32, c_int64, c_int64, c_int64, P, POINTER(pid_iso),
+                           POINTER(pid_options), P, P, P, P, P, P, P], c_int),
         "pid_profile_enable": ([P, c_int], c_int),
         "pid_profile_read": ([P, c_int, POINTER(pid_kernel_stats)], c_int),
         "pid_autotune_enable": ([P, c_int, POINTER(c_int32)], c_int),
@@ -205,6 +208,15 @@ def pid_mean_weighted(h, data, N, M, ld, w, iso, member_weights, depth, in_in, i
     _check(h, load().pid_mean_weighted(h, data, N, M, ld, w,
                                        None if iso is None else ctypes.byref(iso), member_weights,
                                        depth, in_in, in_out, rank, stream))
+
+
+def pid_spacetime(h, steps, N, M, ld, w, iso, opt, depth, in_in, in_out, rank, P, err_est,
+                  stream=None):
+    arr = (c_void_p * len(steps))(*steps)
+    _check(h, load().pid_spacetime(h, arr, len(steps), N, M, ld, w,
+                                   None if iso is None else ctypes.byref(iso),
+                                   ctypes.byref(opt) if opt else None, depth, in_in, in_out,
+                                   rank, P, err_est, stream))
 
 
 def pid_profile_enable(h, enable: bool):
@@ -352,6 +364,25 @@ class Handle:
                           None if iso is None else make_iso(iso), r.data_ptr(),
                           o["depth"].data_ptr(), o["in_in"].data_ptr(), o["in_out"].data_ptr(),
                           o["rank"].data_ptr(), _stream(stream))
+        return o
+
+    def spacetime(self, steps, w=None, iso=None, mode="mean", precision="fp32", want_P=False,
+                  validate=False, stream=None):
+        """4D PID over the time steps `steps` (a list of [N][ld] CUDA tensors of one shape):
+        the cells (x, t) of all steps form one ensemble; the steps are not copied."""
+        if not steps:
+            raise ValueError("need at least one time step")
+        N, M, ld = _check_matrix(steps[0], "steps[0]")
+        for t, S in enumerate(steps):
+            if _check_matrix(S, f"steps[{t}]") != (N, M, ld):
+                raise ValueError("every time step needs the shape and row stride of steps[0]")
+        gram = MODES[mode] == PID_MODE_FULL and PRECISIONS[precision] != PID_FP32
+        o = self._outputs(N, want_P=want_P and gram)
+        opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
+        pid_spacetime(self.h, [S.data_ptr() for S in steps], N, M, ld, _ptr(w),
+                      None if iso is None else make_iso(iso), opt, o["depth"].data_ptr(),
+                      o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
+                      _ptr(o.get("P")), _ptr(o.get("err_est")), _stream(stream))
         return o
 
     def full(self, U, w=None, mode="linear", precision="fp32", want_P=False, validate=False,

@@ -105,8 +105,13 @@ static pid_status to_input(pid_handle h, const pid_ensemble& e, EnsInput* in) {
 // Lay out descriptors and workspace for the batch. Pointers are offsets from `base`.
 // store_u: for exact full PID of a field, pass 1 also writes the soft masks into the
 // workspace and pass 2 streams them (instead of repeating the isovalue map).
+// steps > 1: the `count` == `steps` records are the time steps of ONE space-time ensemble
+// (4D PID: the cells (x, t) of all steps concatenated). Step t writes its chunk partials
+// right after those of step t - 1, and one finalisation reduces all of them.
 static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, char* base,
-                             bool store_u, BatchPlan* bp) {
+                             bool store_u, BatchPlan* bp, int steps = 1) {
+  const bool st4 = steps > 1;
+  auto owner = [&](int e) { return st4 ? 0 : e; };
   std::vector<EnsInput> in(count);
   std::vector<EnsPlan> pl(count);
   std::vector<GramPlan> gp(count);
@@ -120,6 +125,15 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     is_lin[e] = in[e].mode == PID_MODE_FULL_LINEAR || (in[e].mode == PID_MODE_FULL && !is_gram[e]);
     if (is_gram[e] && (st = plan_gram(h, in[e], &gp[e])) != PID_OK) return st;
     stored[e] = store_u && is_lin[e] && in[e].is_field;
+  }
+  if (st4) {
+    for (int e = 1; e < count; ++e) {
+      if (in[e].N != in[0].N || in[e].M != in[0].M || in[e].w != in[0].w ||
+          in[e].is_field != in[0].is_field || in[e].mode != in[0].mode ||
+          in[e].precision != in[0].precision || pl[e].desc.n_chunks != pl[0].desc.n_chunks ||
+          (is_gram[e] && gp[e].n_gchunks != gp[0].n_gchunks))
+        return fail(h, PID_ERR_INVALID_ARG, "the time steps of a space-time ensemble differ");
+    }
   }
   // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
   std::map<ClassKey, std::vector<int>> pass1, pass2;
@@ -142,9 +156,13 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   for (auto& kv : pass2) n_s += static_cast<int>(kv.second.size());
   for (auto& kv : gram_cls) n_s += static_cast<int>(kv.second.size());
   (void)n_sdesc;
-  int n_lin = 0;
-  for (int e = 0; e < count; ++e) n_lin += is_lin[e];
-  const int n_f = count + n_lin;
+  int n_lin = 0, n_logical = 0;
+  for (int e = 0; e < count; ++e) {
+    if (owner(e) != e) continue;
+    n_lin += is_lin[e];
+    ++n_logical;
+  }
+  const int n_f = n_logical + n_lin;
   const size_t sdesc_bytes = align_up(static_cast<int64_t>(n_s) * sizeof(EnsDesc), 256);
   const size_t fdesc_bytes = align_up(static_cast<int64_t>(n_f) * sizeof(FinDesc), 256);
   bp->desc_bytes = sdesc_bytes + fdesc_bytes;
@@ -153,13 +171,23 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   std::vector<float*> coef(count), gpart(count, nullptr);
   std::vector<float*> scale(count, nullptr);
   for (int e = 0; e < count; ++e) {
-    const size_t pb = is_gram[e] ? std::max(pl[e].part_bytes, gp[e].part_bytes) : pl[e].part_bytes;
-    part[e] = reinterpret_cast<double*>(base + off); off += pb;
-    sums[e] = reinterpret_cast<double*>(base + off); off += pl[e].sums_bytes;
-    coef[e] = reinterpret_cast<float*>(base + off); off += pl[e].coef_bytes;
-    if (is_gram[e]) {
-      scale[e] = reinterpret_cast<float*>(base + off); off += 256;
-      gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes;
+    const int o = owner(e);
+    if (o == e) {
+      const size_t pb = is_gram[e] ? std::max(pl[e].part_bytes, gp[e].part_bytes) : pl[e].part_bytes;
+      part[e] = reinterpret_cast<double*>(base + off); off += pb * steps;
+      sums[e] = reinterpret_cast<double*>(base + off); off += pl[e].sums_bytes;
+      coef[e] = reinterpret_cast<float*>(base + off); off += pl[e].coef_bytes;
+      if (is_gram[e]) {
+        scale[e] = reinterpret_cast<float*>(base + off); off += 256;
+        gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes * steps;
+      }
+    } else {   // a later time step: its partials follow those of the steps before it
+      const int64_t n_ch = is_gram[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks;
+      part[e] = part[o] + static_cast<int64_t>(e) * n_ch * 2 * in[e].N;
+      sums[e] = sums[o];
+      coef[e] = coef[o];
+      scale[e] = scale[o];
+      if (is_gram[e]) gpart[e] = gpart[o] + static_cast<int64_t>(e) * n_ch * in[e].N * in[e].N;
     }
     pl[e].desc.part = part[e];
     if (stored[e]) {
@@ -178,7 +206,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     }
   }
   bp->work_bytes = off;
-  if (count > kMaxTickets) return fail(h, PID_ERR_UNSUPPORTED, "too many ensembles in one batch");
+  if (n_logical > kMaxTickets) return fail(h, PID_ERR_UNSUPPORTED, "too many ensembles in one batch");
 
   auto add_stream_class = [&](const ClassKey& k, const std::vector<int>& members, bool coef_pass) {
     Launch L;
@@ -213,7 +241,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     std::memset(&f, 0, sizeof(f));
     f.part = part[e];
     f.N = static_cast<int32_t>(in[e].N);
-    f.n_chunks = is_gram[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks;
+    f.n_chunks = steps * (is_gram[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks);
     f.kind = kind;
     f.sums = sums[e];
     f.coef = coef[e];
@@ -225,7 +253,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     if (kind != FIN_LIN2) { f.mass = o.mass; f.mean_depth = o.mean_depth; }
     if (kind == FIN_GRAM) {
       f.gpart = gpart[e];
-      f.n_gchunks = gp[e].n_gchunks;
+      f.n_gchunks = steps * gp[e].n_gchunks;
       f.P = o.P;
       f.err_est = o.err_est;
     }
@@ -252,7 +280,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       d.op_scale = nullptr;
       if (gp[e].prec == PID_FP8 && in[e].w) {
         d.op_scale = scale[e];
-        L.scales.push_back({in[e].w, in[e].M, scale[e]});
+        // once per ensemble (the time steps of a space-time ensemble share the scale)
+        if (owner(e) == e || e == kv.second[0]) L.scales.push_back({in[e].w, in[e].M, scale[e]});
       }
       units += gp[e].n_gchunks;
       L.bytes += gp[e].bytes;
@@ -272,6 +301,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.kind = Launch::FIN;
     L.first = static_cast<int>(bp->fdesc.size());
     for (int e = 0; e < count; ++e) {
+      if (owner(e) != e) continue;
       const int kind = is_gram[e] ? FIN_GRAM : (is_lin[e] ? FIN_LIN1 : FIN_MEAN);
       bp->fdesc.push_back(fin_for(e, kind));
       L.grid_x = std::max(L.grid_x, bp->fdesc.back().slices);
@@ -286,7 +316,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.kind = Launch::FIN;
     L.first = static_cast<int>(bp->fdesc.size());
     for (int e = 0; e < count; ++e) {
-      if (!is_lin[e]) continue;
+      if (!is_lin[e] || owner(e) != e) continue;
       bp->fdesc.push_back(fin_for(e, FIN_LIN2));
       L.grid_x = std::max(L.grid_x, bp->fdesc.back().slices);
     }
@@ -347,10 +377,10 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
 
 using namespace pidh;
 
-extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream) {
-  if (!h) return PID_ERR_INVALID_ARG;
-  if (count < 0 || (count > 0 && !ens)) return fail(h, PID_ERR_INVALID_ARG, "bad ensemble array");
-  if (count == 0) return PID_OK;
+namespace {
+
+pid_status run_batch(pid_handle h, const pid_ensemble* ens, int32_t count, int steps,
+                     void* stream) {
   DeviceGuard g(h->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (!h->batch) h->batch = new BatchCache();
@@ -362,9 +392,10 @@ extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t c
   const bool profiled = h->profiling;
   // Replay the cached graph when the batch is the one it was recorded for (same ensemble
   // records, same workspace): no planning, no tensor-map encoding, one graph launch.
-  std::vector<unsigned char> key(sizeof(pid_ensemble) * count + sizeof(void*));
+  std::vector<unsigned char> key(sizeof(pid_ensemble) * count + sizeof(void*) + sizeof(int));
   std::memcpy(key.data(), ens, sizeof(pid_ensemble) * count);
   std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
+  std::memcpy(key.data() + sizeof(pid_ensemble) * count + sizeof(void*), &steps, sizeof(int));
   if (c->use_graphs && !capturing && !profiled && c->exec && key == c->key) {
     cudaError_t e = cudaGraphLaunch(c->exec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch graph replay");
@@ -376,11 +407,11 @@ extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t c
   // handle's budget (or, without one, half of the free device memory).
   BatchPlan sizing;
   bool store_u = true;
-  pid_status st = plan_batch(h, ens, count, nullptr, store_u, &sizing);
+  pid_status st = plan_batch(h, ens, count, nullptr, store_u, &sizing, steps);
   if (st != PID_OK) return st;
   {
     BatchPlan lean;
-    if ((st = plan_batch(h, ens, count, nullptr, false, &lean)) != PID_OK) return st;
+    if ((st = plan_batch(h, ens, count, nullptr, false, &lean, steps)) != PID_OK) return st;
     const size_t extra = sizing.work_bytes - lean.work_bytes;
     size_t free_b = 0, total_b = 0;
     if (extra > 0) cudaMemGetInfo(&free_b, &total_b);
@@ -396,7 +427,7 @@ extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t c
   std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
   BatchPlan bp;
   char* base = static_cast<char*>(h->ws);
-  if ((st = plan_batch(h, ens, count, base, store_u, &bp)) != PID_OK) return st;
+  if ((st = plan_batch(h, ens, count, base, store_u, &bp, steps)) != PID_OK) return st;
   // Host image of the descriptors (pinned, so the upload is asynchronous and graph-safe).
   if (c->host_bytes < bp.desc_bytes) {
     if (c->exec) { cudaStreamSynchronize(s); }
@@ -448,4 +479,41 @@ extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t c
   e = cudaGraphLaunch(exec, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch graph launch");
   return PID_OK;
+}
+
+}  // namespace
+
+extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && !ens)) return fail(h, PID_ERR_INVALID_ARG, "bad ensemble array");
+  if (count == 0) return PID_OK;
+  return run_batch(h, ens, count, 1, stream);
+}
+
+extern "C" pid_status pid_spacetime(pid_handle h, const float* const* steps, int32_t T, int64_t N,
+                                    int64_t M, int64_t ld, const float* w, const pid_iso* iso,
+                                    const pid_options* opt, double* depth, double* in_in,
+                                    double* in_out, int32_t* rank, double* P, double* err_est,
+                                    void* stream) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  if (!steps || T < 1) return fail(h, PID_ERR_INVALID_ARG, "need T >= 1 time-step pointers");
+  if (T > kMaxSpacetimeSteps)
+    return fail(h, PID_ERR_UNSUPPORTED, "too many time steps (at most 65536)");
+  if (M > 0 && static_cast<int64_t>(T) * ((M + 4095) / 4096) > (int64_t(1) << 26))
+    return fail(h, PID_ERR_UNSUPPORTED, "T x M too large for one space-time ensemble");
+  pid_options o{PID_MODE_MEAN, PID_FP32, 0, 0};
+  if (opt) o = *opt;
+  std::vector<pid_ensemble> rec(T);
+  for (int32_t t = 0; t < T; ++t) {
+    pid_ensemble& e = rec[t];
+    std::memset(&e, 0, sizeof(e));
+    e.data = steps[t];
+    e.N = N; e.M = M; e.ld = ld; e.w = w;
+    e.is_field = iso != nullptr;
+    if (iso) e.iso = *iso;
+    e.opt = o;
+  }
+  rec[0].depth = depth; rec[0].in_in = in_in; rec[0].in_out = in_out; rec[0].rank = rank;
+  rec[0].P = P; rec[0].err_est = err_est;
+  return run_batch(h, rec.data(), T, T, stream);
 }

@@ -412,3 +412,36 @@ def test_weighted_mean_contour_special_cases():
     a, b, _ = O.pid_mean_weighted(U, r, w)
     np.testing.assert_allclose(a, [O.inclusion(U[i], U[k], w) for i in range(6)], atol=1e-14)
     np.testing.assert_allclose(b, [O.inclusion(U[k], U[i], w) for i in range(6)], atol=1e-14)
+
+
+# --- 4D space-time PID: time as one more cell axis -------------------------------------
+
+def test_spacetime_binary_members_are_eid_over_space_time_cells():
+    # binary members over 2 steps x 5 cells; the sets of (x, t) cells are built by hand
+    rng = np.random.default_rng(12)
+    steps = [(rng.uniform(size=(4, 5)) < 0.6).astype(np.float64) for _ in range(2)]
+    sets = [{(x, t) for t in range(2) for x in range(5) if steps[t][i, x] == 1.0}
+            for i in range(4)]
+    assert all(sets)
+    U, w = O.spacetime_cells(steps)
+    a, b, d = O.pid(U, w)
+    ea, eb, ed = O.eid(sets)
+    np.testing.assert_allclose(np.c_[a, b, d], np.c_[ea, eb, ed], atol=1e-14)
+
+
+def test_spacetime_invariants():
+    rng = np.random.default_rng(13)
+    S = [synth.random_soft(7, 300, seed=20 + t).astype(np.float64) for t in range(3)]
+    w = rng.uniform(0.5, 2.0, 300)
+    base = np.array(O.pid(*O.spacetime_cells(S, w)))
+    # one step: the plain ensemble
+    U1, w1 = O.spacetime_cells(S[:1], w)
+    np.testing.assert_allclose(np.array(O.pid(U1, w1)), np.array(O.pid(S[0], w)), atol=1e-14)
+    # the order of the time steps does not matter
+    np.testing.assert_allclose(np.array(O.pid(*O.spacetime_cells(S[::-1], w))), base, atol=1e-13)
+    # T identical steps: every sum scales by T, the depths of one step remain
+    np.testing.assert_allclose(np.array(O.pid_mean(*O.spacetime_cells([S[1]] * 4, w))),
+                               np.array(O.pid_mean(S[1], w)), atol=1e-13)
+    # a step whose members are all empty adds nothing
+    Z = np.zeros_like(S[0])
+    np.testing.assert_allclose(np.array(O.pid(*O.spacetime_cells(S + [Z], w))), base, atol=1e-13)
