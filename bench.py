@@ -570,7 +570,7 @@ def main():
         t_ms = b0.elapsed_time(b1) / args.other_steps
         others[name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms}
 
-    # ---- contour boxplot bands of every ensemble from the step's ranks (Sec. 5.4) ----
+    # ---- contour boxplot bands of every ensemble from the step's ranks (Sec. 6) ----
     bands = None
     if rank == 0 and args.other_steps > 0:
         bout = [torch.empty(M, dtype=torch.uint8, device=dev) for _ in range(E)]

@@ -78,7 +78,7 @@ typedef enum pid_iso_kind {
   PID_ISO_NORMAL = 0,       /* isovalue q ~ Normal(mu, sigma), Sec. 3.5 */
   PID_ISO_UNIFORM = 1,      /* isovalue q ~ Uniform[mu - sigma, mu + sigma] (sigma > 0):
                                u = P(F < q) = clamp((mu + sigma - F) / (2 sigma), 0, 1) */
-  PID_ISO_LEVEL = 2         /* level-centred map of the weather example (Sec. 5): probability
+  PID_ISO_LEVEL = 2         /* level-centred map of the weather example (Sec. 3.6): probability
                                1 at the level mu, falling linearly to 0 at distance sigma:
                                u = max(0, 1 - |F - mu| / sigma) (sigma > 0, superlevel 0) */
 } pid_iso_kind;
@@ -174,7 +174,7 @@ pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, in
 pid_status pid_selftest_wait_timeout(pid_handle h, double seconds, void* stream);
 
 /*
- * pid_contour_bands — the bands of a contour boxplot (Sec. 5.4) from depths already
+ * pid_contour_bands — the bands of a contour boxplot (Sec. 6) from depths already
  * computed. Every member is binarised, b_i(x) = [u_i(x) > tau], with u_i the soft mask
  * itself (iso == NULL) or the isovalue map of the field (Sec. 3.5). For each cell x, the
  * byte bands[x] collects:
@@ -242,7 +242,7 @@ pid_status pid_mean_weighted(pid_handle h, const float* data, int64_t N, int64_t
                              void* stream);
 
 /*
- * pid_spacetime — 4D (space-time) PID: time is one more cell axis, so member i is the
+ * pid_spacetime — 4D (space-time) PID (Sec. 6.3): time is one more cell axis, so member i is the
  * function u_i(x, t) over the cells (x, t) of T time steps, and every sum over cells in
  * Eq. 6, 9, 14 and 15 runs over all T*M of them (the concatenation of the steps). steps:
  * HOST array of T device pointers, step t holding the members' values [N][ld] at that time

@@ -19,10 +19,12 @@ Every function cites the passage it follows:
   Sec. 5.1         ranking: higher rank = lower depth
   (pid_chunked / pid_mean_chunked restate Eq. 6, 9, 10, 15, 16 with their sums over
   cells accumulated block by block, for ensembles larger than host memory in float64)
-  Sec. 5.4         contour boxplots: unions and intersections of the binarised members
+  Sec. 6           contour boxplots: unions and intersections of the binarised members
                    of a depth-ordered population, and the median member
-  Sec. 3.5, Sec. 5 other mask models: a uniform isovalue distribution, the level-centred
-                   map of the weather example; Sec. 4.1 reliability-weighted mean contour
+  Sec. 3.5, 3.6    other mask models: a uniform isovalue distribution, the level-centred
+                   map of the weather example
+  Sec. 4.1         the reliability-weighted mean contour
+  Sec. 6.3         4D (space-time) PID: time as one more cell axis
 
 Readings where the paper is silent (each also listed in the design notes):
   * Zero-mass reference mask: u subset_p v = 0 (Sec. 3.2), unlike eID's 1 (Eq. 1).
@@ -234,7 +236,7 @@ def iso_soft_mask_uniform(F, mu: float, half_width: float, superlevel: bool = Fa
 
 
 def level_soft_mask(F, level: float, half_width: float) -> np.ndarray:
-    """Level-centred soft mask (the weather example of Sec. 5): probability 1 at the level,
+    """Level-centred soft mask (the weather example of Sec. 3.6): probability 1 at the level,
     falling linearly to 0 at distance `half_width`: u = max(0, 1 - |F - level| / h)."""
     F = _f64(F)
     if not half_width > 0:
@@ -305,7 +307,7 @@ def eid(sets):
 
 
 # ---------------------------------------------------------------------------
-# Contour boxplot bands (Sec. 5.4): binarise each soft mask at a probability threshold,
+# Contour boxplot bands (Sec. 6): binarise each soft mask at a probability threshold,
 # then take the union and the intersection over the deepest fraction of the members and
 # over all members; the median member is the deepest one.
 # ---------------------------------------------------------------------------
@@ -316,7 +318,7 @@ BAND_MEDIAN = 16
 
 
 def contour_bands(U, rank, tau: float, inner_fraction: float = 0.5) -> np.ndarray:
-    """Per cell, a byte of band flags for the contour boxplot of Sec. 5.4.
+    """Per cell, a byte of band flags for the contour boxplot of Sec. 6.
 
     b_i(x) = [u_i(x) > tau]; the inner population is the ceil(inner_fraction N) members of
     lowest rank (rank 0 = deepest, Sec. 5.1), the outer population all N members.

@@ -1,4 +1,4 @@
-// Contour boxplot bands (Sec. 5.4): binarise every member at a probability threshold and
+// Contour boxplot bands (Sec. 6): binarise every member at a probability threshold and
 // collect, per cell, the unions and intersections over the deepest members and over all
 // members, and the median member. One HBM-bound pass over the ensemble: 4 B read per
 // member-cell, 1 B written per cell.

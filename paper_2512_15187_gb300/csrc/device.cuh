@@ -264,7 +264,7 @@ __device__ __forceinline__ float2 iso_normal2(float2 f, float mu, float inv) {
 }
 
 // The piecewise-linear maps (modes 4-6): a uniform isovalue distribution (Sec. 3.5) and
-// the level-centred map of the weather example (Sec. 5).
+// the level-centred map of the weather example (Sec. 3.6).
 //   mode 4: u = clamp((mu - F) inv, 0, 1)   mode 5: u = clamp((F - mu) inv, 0, 1)
 //   mode 6: u = max(0, 1 - |F - mu| inv)
 __device__ __forceinline__ float iso_piecewise(float f, int32_t mode, float mu, float inv) {

@@ -1,4 +1,4 @@
-"""GPU parity of the contour boxplot bands (pid_contour_bands, Sec. 5.4) with the FP64
+"""GPU parity of the contour boxplot bands (pid_contour_bands, Sec. 6) with the FP64
 oracle, bit for bit: soft masks and fields (normal isovalue, both level sets, sigma = 0),
 ragged and unaligned rows, any N, several thresholds and inner fractions, ranks from a
 permutation and from the library's own depths, and the 2D field workload at full size."""

@@ -1,6 +1,6 @@
 """GPU parity of the other mask models with the FP64 oracle: the isovalue uniform on
 [mu - h, mu + h] (Sec. 3.5 with another isovalue distribution, both level sets), the
-level-centred map of the weather example (Sec. 5), and PID-mean against a
+level-centred map of the weather example (Sec. 3.6), and PID-mean against a
 reliability-weighted mean contour (Sec. 4.1). Soft masks, every depth path (PID-mean,
 exact linear full PID, tensor-core Gram, the member-blocked path beyond 512 members,
 batches), contour bands bit for bit, and the host and device checks of the new inputs."""

@@ -333,7 +333,7 @@ def test_chunked_forms_do_not_depend_on_the_blocks(seed):
                                    atol=1e-13)
 
 
-# --- contour boxplot bands (Sec. 5.4) -------------------------------------------------
+# --- contour boxplot bands (Sec. 6) -------------------------------------------------
 
 def test_bands_hand_example():
     g = _load("hand_bands_3x6.json")
