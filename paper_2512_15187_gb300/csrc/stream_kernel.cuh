@@ -528,11 +528,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
             named_barrier(1 + grp, G * 32);
             lds_vec<VEC>(s, rb + G * T + lane * VEC);
           } else {
-#pragma unroll
             sum_partials<VEC, G>(s, rb + lane * VEC, T);
           }
         } else if constexpr (G == 2) {
-#pragma unroll
           sum_partials<VEC, G>(s, rb + lane * VEC, T);
         }
         // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
