@@ -242,6 +242,21 @@ pid_status pid_mean_weighted(pid_handle h, const float* data, int64_t N, int64_t
                              void* stream);
 
 /*
+ * pid_depth_from_matrix — PID (Eq. 10) from an inclusion matrix P[i][j] = u_i subset_p u_j
+ * (Eq. 9; row-major FP64 [N][ldp] on the device, as pid_full's Gram modes return it),
+ * optionally within groups of members. With labels (device int32 [N]; equal values = one
+ * group), member i is compared only with the members of its own group C(i), which gives the
+ * depth of i within its mode of a multimodal ensemble (Sec. 2.2):
+ *   IN_in(i) = (1/|C(i)|) sum_{j in C(i)} P[i][j],  IN_out(i) = (1/|C(i)|) sum_{j in C(i)} P[j][i],
+ *   depth = min, rank = position by depth within C(i) (0 = deepest; ties to the lower index).
+ * labels = NULL: one group, i.e. the results pid_full computes from the same P. Outputs as
+ * in pid_full (any may be NULL). 1 <= N <= 65536, ldp >= N. O(N^2) FP64 work, two kernels.
+ */
+pid_status pid_depth_from_matrix(pid_handle h, const double* P, int64_t N, int64_t ldp,
+                                 const int32_t* labels, double* depth, double* in_in,
+                                 double* in_out, int32_t* rank, void* stream);
+
+/*
  * pid_spacetime — 4D (space-time) PID (Sec. 6.3): time is one more cell axis, so member i is the
  * function u_i(x, t) over the cells (x, t) of T time steps, and every sum over cells in
  * Eq. 6, 9, 14 and 15 runs over all T*M of them (the concatenation of the steps). steps:

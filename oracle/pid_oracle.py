@@ -259,6 +259,26 @@ def pid_mean_weighted(U, member_weights, w=None):
     return in_in, in_out, np.minimum(in_in, in_out)
 
 
+def pid_grouped(U, labels, w=None):
+    """Full PID (Eq. 10) of each member within its group: member i is compared only with
+    the members j that share its label (the depth of i within its mode of a multimodal
+    ensemble, Sec. 2.2). Returns (in_in, in_out, depth, rank), rank within the group
+    (Sec. 5.1 ordering, ties to the lower member index)."""
+    U = np.atleast_2d(_f64(U))
+    labels = np.asarray(labels).reshape(-1)
+    N = U.shape[0]
+    if labels.shape[0] != N:
+        raise ValueError("one label per member")
+    in_in, in_out, depth = np.zeros(N), np.zeros(N), np.zeros(N)
+    rank = np.zeros(N, dtype=np.int64)
+    for g in np.unique(labels):
+        idx = np.nonzero(labels == g)[0]
+        a, b, d = pid(U[idx], w)
+        in_in[idx], in_out[idx], depth[idx] = a, b, d
+        rank[idx] = rank_by_depth(d)
+    return in_in, in_out, depth, rank
+
+
 def spacetime_cells(steps, w=None):
     """4D PID (time as one more cell axis): the cells (x, t) of T time steps, each [N][M],
     concatenated into one ensemble [N][T*M]; the cell measure w_x repeats at every step (a

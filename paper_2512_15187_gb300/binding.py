@@ -33,7 +33,7 @@ EXPORTS = [
     "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
     "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands", "pid_mean_weighted",
-    "pid_spacetime",
+    "pid_spacetime", "pid_depth_from_matrix",
     "pid_selftest_wait_timeout",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_mean_weighted": ([P, P, c_int64, c_int64, c_int64, P, POINTER(pid_iso), P, P, P, P, P,
                                P], c_int),
         "pid_batch": ([P, POINTER(pid_ensemble), c_int32, P], c_int),
+        "pid_depth_from_matrix": ([P, P, c_int64, c_int64, P, P, P, P, P, P], c_int),
         "pid_spacetime": ([P, P, c_int32, c_int64, c_int64, c_int64, P, POINTER(pid_iso),
                            POINTER(pid_options), P, P, P, P, P, P, P], c_int),
         "pid_profile_enable": ([P, c_int], c_int),
@@ -217,6 +218,11 @@ def pid_spacetime(h, steps, N, M, ld, w, iso, opt, depth, in_in, in_out, rank, P
                                    None if iso is None else ctypes.byref(iso),
                                    ctypes.byref(opt) if opt else None, depth, in_in, in_out,
                                    rank, P, err_est, stream))
+
+
+def pid_depth_from_matrix(h, P_, N, ldp, labels, depth, in_in, in_out, rank, stream=None):
+    _check(h, load().pid_depth_from_matrix(h, P_, N, ldp, labels, depth, in_in, in_out, rank,
+                                           stream))
 
 
 def pid_profile_enable(h, enable: bool):
@@ -383,6 +389,24 @@ class Handle:
                       None if iso is None else make_iso(iso), opt, o["depth"].data_ptr(),
                       o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
                       _ptr(o.get("P")), _ptr(o.get("err_est")), _stream(stream))
+        return o
+
+    def depth_from_matrix(self, P, labels=None, stream=None):
+        """Depths from an inclusion matrix P (float64 CUDA [N][ldp], P[i, j] = u_i subset_p
+        u_j), within the groups of `labels` (int32 CUDA [N]) or over all members."""
+        import torch
+        if P.dtype != torch.float64 or not P.is_cuda or P.dim() != 2 or P.stride(1) != 1:
+            raise ValueError("P must be a float64 CUDA matrix with unit column stride")
+        N = P.shape[0]
+        if P.shape[1] != N:
+            raise ValueError("P must be square")
+        if labels is not None and (labels.dtype != torch.int32 or not labels.is_cuda or
+                                   labels.numel() != N or not labels.is_contiguous()):
+            raise ValueError("labels must be a contiguous int32 CUDA tensor with one entry per member")
+        o = self._outputs(N)
+        pid_depth_from_matrix(self.h, P.data_ptr(), N, P.stride(0), _ptr(labels),
+                              o["depth"].data_ptr(), o["in_in"].data_ptr(),
+                              o["in_out"].data_ptr(), o["rank"].data_ptr(), _stream(stream))
         return o
 
     def full(self, U, w=None, mode="linear", precision="fp32", want_P=False, validate=False,

@@ -17,6 +17,7 @@ namespace pidh {
 constexpr int64_t kMaxMembers = 512;   // largest N of the fused single-pass kernels
 constexpr int64_t kMaxBlockedMembers = int64_t(1) << 22;   // single calls, member-blocked path
 constexpr int kMaxTickets = 8192;      // ensembles per batch (one finalisation ticket each)
+constexpr int64_t kMaxMatrixMembers = 65536;   // members of pid_depth_from_matrix
 constexpr int kMaxSpacetimeSteps = 65536;   // time steps of one space-time ensemble
 
 struct BatchCache;  // batch.cu

@@ -445,3 +445,48 @@ def test_spacetime_invariants():
     # a step whose members are all empty adds nothing
     Z = np.zeros_like(S[0])
     np.testing.assert_allclose(np.array(O.pid(*O.spacetime_cells(S + [Z], w))), base, atol=1e-13)
+
+
+# --- PID within groups of members (multimodal ensembles) -------------------------------
+
+def test_grouped_pid_special_cases():
+    U = synth.random_soft(9, 200, seed=31).astype(np.float64)
+    a, b, d = O.pid(U)
+    # one group: plain PID, ranks of Sec. 5.1
+    ga, gb, gd, gr = O.pid_grouped(U, np.zeros(9, dtype=int))
+    np.testing.assert_allclose(np.c_[ga, gb, gd], np.c_[a, b, d], atol=1e-15)
+    assert list(gr) == list(O.rank_by_depth(d))
+    # singletons: a member against itself only, u subset_p u = sum u^2 / sum u (Eq. 9)
+    sa, sb, sd, sr = O.pid_grouped(U, np.arange(9))
+    self_inc = (U * U).sum(axis=1) / U.sum(axis=1)
+    np.testing.assert_allclose(sd, self_inc, rtol=1e-14)
+    assert np.all(sr == 0)
+    B = (U > 0.5).astype(np.float64)       # binary members: fully included in themselves
+    assert np.all(O.pid_grouped(B, np.arange(9))[2] == 1.0)
+    # label values do not matter, only which members share one
+    lab = np.array([3, 3, 7, 7, 7, 3, -1, -1, 7])
+    ref = O.pid_grouped(U, lab)
+    for x, y in zip(ref, O.pid_grouped(U, np.where(lab == 3, 100, np.where(lab == 7, 5, 0)))):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_grouped_pid_of_two_disk_families_is_each_familys_order():
+    # two families of nested binary disks far apart; within a family the inclusion of disk
+    # i in disk j is |D_i & D_j| / |D_i| = min(|D_i|, |D_j|) / |D_i| from pixel counts, and
+    # the other family never enters
+    yy, xx = np.mgrid[0:64, 0:128]
+    masks, labels = [], []
+    for fam, cx in ((0, 32), (1, 96)):
+        for r in (6, 10, 14, 18, 22):
+            masks.append(((xx - cx) ** 2 + (yy - 32) ** 2 <= r * r).astype(np.float64).ravel())
+            labels.append(fam)
+    U = np.array(masks)
+    a, b, d, r = O.pid_grouped(U, np.array(labels))
+    for fam in (0, 1):
+        idx = np.arange(5) + 5 * fam
+        area = U[idx].sum(axis=1)
+        want_in = np.array([np.mean([min(ai, aj) / ai for aj in area]) for ai in area])
+        want_out = np.array([np.mean([min(ai, aj) / aj for aj in area]) for ai in area])
+        np.testing.assert_allclose(a[idx], want_in, rtol=1e-14)
+        np.testing.assert_allclose(b[idx], want_out, rtol=1e-14)
+        assert r[idx[2]] == 0 and sorted(r[idx]) == [0, 1, 2, 3, 4]
