@@ -71,7 +71,7 @@ typedef enum pid_precision {
   PID_FP32 = 0,
   PID_BF16 = 1,             /* u sqrt(w) rounded to bfloat16 */
   PID_SPLIT_BF16 = 2,       /* hi + lo bfloat16 pair; products hi*hi + hi*lo + lo*hi */
-  PID_FP8 = 3               /* E4M3 with a per-member power-of-two scale */
+  PID_FP8 = 3               /* E4M3 with one power-of-two scale per ensemble */
 } pid_precision;
 
 typedef enum pid_iso_kind {
@@ -257,11 +257,11 @@ pid_status pid_depth_from_matrix(pid_handle h, const double* P, int64_t N, int64
                                  double* in_out, int32_t* rank, void* stream);
 
 /*
- * pid_spacetime — 4D (space-time) PID (Sec. 6.3): time is one more cell axis, so member i is the
- * function u_i(x, t) over the cells (x, t) of T time steps, and every sum over cells in
- * Eq. 6, 9, 14 and 15 runs over all T*M of them (the concatenation of the steps). steps:
- * HOST array of T device pointers, step t holding the members' values [N][ld] at that time
- * (soft masks, or fields mapped through `iso` when iso != NULL). w: cell measures [M],
+ * pid_spacetime — 4D (space-time) PID (Sec. 6.3): time is one more cell axis, so member i
+ * is the function u_i(x, t) over the cells (x, t) of T time steps, and every sum over cells in
+ * Eq. 6, 9, 14 and 15 runs over all T*M of them (the concatenation of the steps).
+ * steps_host: HOST array of T device pointers, step t holding the members' values [N][ld]
+ * at that time (soft masks, or fields mapped through `iso` when iso != NULL). w: cell measures [M],
  * the same at every step (a uniform time step cancels in every inclusion ratio), or NULL.
  * opt selects PID-mean, exact linear full PID or the tensor-core Gram as for pid_full
  * (NULL = PID-mean). The steps stay where they are (no copy into one array): they become
@@ -269,7 +269,7 @@ pid_status pid_depth_from_matrix(pid_handle h, const double* P, int64_t N, int64
  * finalisation. N <= 512 (the Gram modes: N <= 256), 1 <= T <= 65536; all steps share
  * N, M and ld.
  */
-pid_status pid_spacetime(pid_handle h, const float* const* steps, int32_t T, int64_t N,
+pid_status pid_spacetime(pid_handle h, const float* const* steps_host, int32_t T, int64_t N,
                          int64_t M, int64_t ld, const float* w, const pid_iso* iso,
                          const pid_options* opt, double* depth, double* in_in, double* in_out,
                          int32_t* rank, double* P, double* err_est, void* stream);
@@ -299,7 +299,7 @@ typedef struct pid_ensemble {
 
 /*
  * pid_batch — many ensembles of uneven N and M in one persistent launch per kernel class,
- * recorded as one CUDA graph (fork/join over the classes) and replayed while the batch
+ * the class launches recorded in order as one CUDA graph and replayed while the batch
  * layout is unchanged. Results are bitwise identical to the single-ensemble calls.
  */
 pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
