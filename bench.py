@@ -70,18 +70,22 @@ from paper_2512_15187_gb300 import synth
 budget, max_steps, rows = {budget}, {max_steps}, {rows}
 pool = [synth.rbf_fields_2d(N={N}, H={H}, W={W}, n_rbf={K}, seed=synth.DEFAULT_SEED + 2 + 7919 * k)
         for k in range(2)]
-done, t_total, per = 0, 0.0, []
+done, t_total, per, ref = 0, 0.0, [], None
 while done < max_steps and t_total < budget:
     F = pool[done % len(pool)]
     band = (done // len(pool)) % ({H} // rows)
     F = np.ascontiguousarray(F.reshape({N}, {H}, {W})[:, band * rows:(band + 1) * rows].reshape({N}, -1))
     t0 = time.perf_counter()
     U = O.iso_soft_mask(F, {mu}, {sigma})
-    O.pid_mean(U)
-    O.pid(U)
+    mean = O.pid_mean(U)
+    full = O.pid(U)
     dt = time.perf_counter() - t0
+    if ref is None:   # the first sample's results, for the GPU paths to be checked against
+        ref = {{"mean": [list(map(float, v)) for v in mean],
+                "full": [list(map(float, v)) for v in full]}}
     per.append(dt); t_total += dt; done += 1
-print(json.dumps({{"steps": done, "seconds": t_total, "per_step": per, "cells": rows * {W}}}))
+print(json.dumps({{"steps": done, "seconds": t_total, "per_step": per, "cells": rows * {W},
+                  "ref": ref}}))
 """
 
 
@@ -97,6 +101,36 @@ def run_cpu_oracle(budget_s=12.0, max_steps=64, rows=GRID_H):
     if r.returncode != 0:
         raise RuntimeError("CPU oracle failed:\n" + r.stderr[-2000:])
     return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_parity(h, res, dev):
+    """Max abs error of every path's depths and inclusion fractions against the FP64
+    oracle's results (from the CPU leg) on the leg's first sample: the first ensemble of
+    the workload, generated on the host by the same seeded generator."""
+    import numpy as np
+    import torch
+
+    from paper_2512_15187_gb300 import synth
+    rows = res["cells"] // GRID_W
+    F = synth.rbf_fields_2d(N=N_MEMBERS, H=GRID_H, W=GRID_W, n_rbf=N_RBF,
+                            seed=synth.DEFAULT_SEED + 2)
+    F = np.ascontiguousarray(F.reshape(N_MEMBERS, GRID_H, GRID_W)[:, :rows].reshape(N_MEMBERS, -1))
+    Fd = torch.from_numpy(F).to(dev)
+    out = {"sample": f"{N_MEMBERS} members x {rows * GRID_W} cells (the oracle leg's first "
+                     f"sample); max abs error against the FP64 oracle",
+           "bars": {"fp32": 1e-6, "gram": 1e-3}}
+    for name, mode, prec, key in (("pid_mean_fp32", "mean", "fp32", "mean"),
+                                  ("full_exact_fp32", "linear", "fp32", "full"),
+                                  ("full_gram_bf16", "full", "bf16", "full"),
+                                  ("full_gram_split_bf16", "full", "split_bf16", "full"),
+                                  ("full_gram_fp8", "full", "fp8", "full")):
+        o = h.from_fields(Fd, ISO_MU, ISO_SIGMA, mode=mode, precision=prec)
+        h.sync()
+        errs = {}
+        for k, r in zip(("in_in", "in_out", "depth"), res["ref"][key]):
+            errs[k] = float(np.max(np.abs(o[k].cpu().numpy() - np.asarray(r))))
+        out[name] = errs
+    return out
 
 
 def cpu_baseline_record(res):
@@ -707,6 +741,8 @@ def main():
             line["workloads"] = workloads
         if cpu_res is not None:
             line["cpu_baseline"] = cpu_baseline_record(cpu_res)
+            if cpu_res.get("ref"):
+                line["parity"] = oracle_parity(h, cpu_res, dev)
         print(json.dumps(line), flush=True)
     h.close()
     if dist:
