@@ -497,13 +497,13 @@ extern "C" pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t c
   return run_batch(h, ens, count, 1, stream);
 }
 
-extern "C" pid_status pid_spacetime(pid_handle h, const float* const* steps, int32_t T, int64_t N,
+extern "C" pid_status pid_spacetime(pid_handle h, const float* const* steps_host, int32_t T, int64_t N,
                                     int64_t M, int64_t ld, const float* w, const pid_iso* iso,
                                     const pid_options* opt, double* depth, double* in_in,
                                     double* in_out, int32_t* rank, double* P, double* err_est,
                                     void* stream) {
   if (!h) return PID_ERR_INVALID_ARG;
-  if (!steps || T < 1) return fail(h, PID_ERR_INVALID_ARG, "need T >= 1 time-step pointers");
+  if (!steps_host || T < 1) return fail(h, PID_ERR_INVALID_ARG, "need T >= 1 time-step pointers");
   if (T > kMaxSpacetimeSteps)
     return fail(h, PID_ERR_UNSUPPORTED, "too many time steps (at most 65536)");
   if (M > 0 && static_cast<int64_t>(T) * ((M + 4095) / 4096) > (int64_t(1) << 26))
@@ -514,7 +514,7 @@ extern "C" pid_status pid_spacetime(pid_handle h, const float* const* steps, int
   for (int32_t t = 0; t < T; ++t) {
     pid_ensemble& e = rec[t];
     std::memset(&e, 0, sizeof(e));
-    e.data = steps[t];
+    e.data = steps_host[t];
     e.N = N; e.M = M; e.ld = ld; e.w = w;
     e.is_field = iso != nullptr;
     if (iso) e.iso = *iso;

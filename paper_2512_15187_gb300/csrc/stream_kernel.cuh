@@ -101,12 +101,10 @@ __device__ __forceinline__ void sts_vec(float* dst, const float (&src)[VEC]) {
   }
 }
 
-// Isovalue map kinds compiled into a kernel.
+// Isovalue map kinds compiled into a kernel: none, the Normal isovalue, and the step family
+// (sigma = 0 thresholds and the piecewise-linear maps, told apart at run time).
 enum IsoKind : int { ISOK_NONE = 0, ISOK_NORMAL = 1, ISOK_STEP = 2 };
 
-// Soft-mask value of one element for a compile-time isovalue kind (Sec. 3.5).
-//   NORMAL: u = erfc(xs) / 2, xs = (F - mu) * inv with inv = +-sqrt(log2 e) / (sigma sqrt 2)
-//   STEP:   u = 1[(F - t) * dir < 0], dir = +1 (F < t) or -1 (F > t)
 // s[v] = sum over r < G of part[r * stride + v], added in order r = 0, 1, ... (packed pairs
 // when VEC is even; the order, and so the bits, are those of a scalar loop).
 template <int VEC, int G>
@@ -137,6 +135,9 @@ __device__ __forceinline__ void sum_partials(float (&s)[VEC], const float* part,
   }
 }
 
+// Soft-mask value of one element for a compile-time isovalue kind (Sec. 3.5).
+//   NORMAL: u = erfc(xs) / 2, xs = (F - mu) * inv with inv = +-sqrt(log2 e) / (sigma sqrt 2)
+//   STEP:   u = 1[(F - t) * dir < 0], dir = +1 (F < t) or -1 (F > t)
 template <int ISO>
 __device__ __forceinline__ float iso_map(float f, float mu, float inv, float t, float dir) {
   if constexpr (ISO == ISOK_NORMAL) {
