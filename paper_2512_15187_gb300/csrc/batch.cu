@@ -53,9 +53,10 @@ static int64_t align_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 // One persistent launch per key. TMA-fed and directly loaded ensembles (rows not 16-byte
 // aligned) launch apart, so that one unaligned ensemble does not slow down its whole class.
 struct ClassKey {
-  int vec, G, coef, iso, tma;
+  int vec, G, coef, iso, tma, mpw;
   bool operator<(const ClassKey& o) const {
     if (tma != o.tma) return tma < o.tma;
+    if (mpw != o.mpw) return mpw < o.mpw;
     if (vec != o.vec) return vec < o.vec;
     if (G != o.G) return G < o.G;
     if (coef != o.coef) return coef < o.coef;
@@ -149,11 +150,11 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
           .push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
-      pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, pl[e].use_tma ? 1 : 0}].push_back(e);
+      pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, pl[e].use_tma ? 1 : 0, pl[e].cfg.mpw}].push_back(e);
       if (is_lin[e]) {
         // stored soft masks are 16-byte aligned rows, read through TMA in pass 2
         const int tma2 = stored[e] ? 1 : (pl[e].use_tma ? 1 : 0);
-        pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1, stored[e] ? 0 : ik, tma2}].push_back(e);
+        pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1, stored[e] ? 0 : ik, tma2, pl[e].cfg.mpw}].push_back(e);
       }
     }
   }

@@ -150,13 +150,20 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
 // a TMA stage moves sub x T cells of every member (sub = 1 keeps three stages in flight
 // for N up to 512).
 StreamCfg stream_cfg(int64_t N) {
-  if (N <= 8) return {4, 1, 128, 1};      // MPW <= 8
-  if (N <= 16) return {4, 2, 128, 1};     // MPW <= 8
-  if (N <= 32) return {4, 4, 128, 1};     // MPW <= 8
-  if (N <= 64) return {4, 8, 128, 1};     // MPW <= 8
-  if (N <= 128) return {4, 16, 128, 1};   // MPW <= 8
-  if (N <= 256) return {2, 16, 64, 1};    // MPW <= 16
-  return {1, 16, 32, 1};                  // MPW <= 32
+  // Every member slot of a class costs arithmetic whether or not a member fills it, so the
+  // classes above 64 members come in steps that keep the empty slots below about a fifth.
+  if (N <= 8) return {4, 1, 128, 1, 8};
+  if (N <= 16) return {4, 2, 128, 1, 8};
+  if (N <= 32) return {4, 4, 128, 1, 8};
+  if (N <= 64) return {4, 8, 128, 1, 8};
+  if (N <= 96) return {4, 16, 128, 1, 6};
+  if (N <= 128) return {4, 16, 128, 1, 8};
+  if (N <= 192) return {2, 16, 64, 1, 12};
+  if (N <= 256) return {2, 16, 64, 1, 16};
+  if (N <= 320) return {1, 16, 32, 1, 20};
+  if (N <= 384) return {1, 16, 32, 1, 24};
+  if (N <= 448) return {1, 16, 32, 1, 28};
+  return {1, 16, 32, 1, 32};
 }
 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -312,7 +319,8 @@ static std::string stream_tune_key(const StreamCfg& cfg, bool coef, const pidk::
   while ((int64_t(1) << (lg + 1)) <= cells) ++lg;
   const pidk::EnsDesc& d = sp.descs ? sp.one : sp.one;  // iso / weights flags come from `one`
   char buf[160];
-  std::snprintf(buf, sizeof(buf), "stream v%d g%d s%d c%d iso%d w%d tma%d n%d m%d", cfg.vec, cfg.G,
+  std::snprintf(buf, sizeof(buf), "stream v%d k%d g%d s%d c%d iso%d w%d tma%d n%d m%d", cfg.vec,
+                cfg.mpw, cfg.G,
                 cfg.sub, coef ? 1 : 0, d.iso_mode != 0, d.w != nullptr, sp.use_tma,
                 (max_n + 7) / 8 * 8, lg);
   return buf;
@@ -362,10 +370,10 @@ pid_status stream_launch(pid_handle h, StreamParams sp, const StreamCfg& cfg, bo
       t.xchg = c.first;
       t.depth = c.second;
       const size_t sm = stream_smem_bytes(cfg.vec, cfg.G, c.second, sp.stage_floats);
-      cudaError_t e = launch_stream(t, cfg.vec, cfg.G, ik, coef, grid, sm, s);  // warm-up
+      cudaError_t e = launch_stream(t, cfg.vec, cfg.mpw, cfg.G, ik, coef, grid, sm, s);  // warm-up
       if (e != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return cuda_fail(h, e, "tune"); }
       cudaEventRecord(e0, s);
-      for (int r = 0; r < 3; ++r) launch_stream(t, cfg.vec, cfg.G, ik, coef, grid, sm, s);
+      for (int r = 0; r < 3; ++r) launch_stream(t, cfg.vec, cfg.mpw, cfg.G, ik, coef, grid, sm, s);
       cudaEventRecord(e1, s);
       cudaEventSynchronize(e1);
       float ms = 0.f;
@@ -389,7 +397,7 @@ pid_status stream_launch(pid_handle h, StreamParams sp, const StreamCfg& cfg, bo
     smem = stream_smem_bytes(cfg.vec, cfg.G, sp.depth, sp.stage_floats);
   }
   ProfScope ps(h, PID_KERNEL_STREAM, bytes, 0.0, s);
-  cudaError_t e = launch_stream(sp, cfg.vec, cfg.G, ik, coef, grid, smem, s);
+  cudaError_t e = launch_stream(sp, cfg.vec, cfg.mpw, cfg.G, ik, coef, grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "stream kernel launch");
   return PID_OK;
 }

@@ -73,7 +73,8 @@ struct StreamCfg {
   int vec;  // cells per lane per register tile (4, 2, 1)
   int G;    // warps per group
   int T;    // cells per register tile (32 * vec)
-  int sub;  // register tiles per TMA stage (stage = sub * T cells = 128 for every class)
+  int sub;  // register tiles per TMA stage (1: a stage is one register tile)
+  int mpw;  // members per warp: the class holds G * mpw member rows
 };
 
 struct EnsInput {

@@ -153,8 +153,8 @@ constexpr int fin_gram_items(int N) { return (N * N + 1023) / 1024; }
 // piecewise-linear maps (uniform isovalue, level map), chosen at run time inside the kernel.
 inline int iso_kind(int32_t iso_mode) { return iso_mode == ISO_NONE ? 0 : (iso_mode == ISO_NORMAL ? 1 : 2); }
 
-cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, bool coef, int grid,
-                          size_t smem, cudaStream_t s);
+cudaError_t launch_stream(const StreamParams& p, int vec, int mpw, int G, int iso_kind, bool coef,
+                          int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s);
 cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 cudaError_t launch_member_coef(const double* r, int64_t N, float* coef, uint32_t* err,

@@ -119,7 +119,8 @@ extern "C" pid_status pid_mean_noalloc(const float* U, int64_t N, int64_t M, int
   const int n_groups = kStreamWarps / pl.cfg.G;
   int grid = (sp.total_units + n_groups - 1) / n_groups;
   grid = grid < 1 ? 1 : (grid > ds->sms ? ds->sms : grid);
-  if (launch_stream(sp, pl.cfg.vec, pl.cfg.G, iso_kind(sp.one.iso_mode), false, grid, smem, s) !=
+  if (launch_stream(sp, pl.cfg.vec, pl.cfg.mpw, pl.cfg.G, iso_kind(sp.one.iso_mode), false, grid,
+                    smem, s) !=
       cudaSuccess)
     return PID_ERR_CUDA;
 

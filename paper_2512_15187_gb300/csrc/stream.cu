@@ -23,26 +23,34 @@ PIDK_CLASS(4, 8, 1)
 PIDK_CLASS(4, 8, 2)
 PIDK_CLASS(4, 8, 4)
 PIDK_CLASS(4, 8, 8)
+PIDK_CLASS(4, 6, 16)
 PIDK_CLASS(4, 8, 16)
+PIDK_CLASS(2, 12, 16)
 PIDK_CLASS(2, 16, 16)
+PIDK_CLASS(1, 20, 16)
+PIDK_CLASS(1, 24, 16)
+PIDK_CLASS(1, 28, 16)
 PIDK_CLASS(1, 32, 16)
 #undef PIDK_CLASS
 
-cudaError_t launch_stream(const StreamParams& p, int vec, int G, int iso_kind, bool coef, int grid,
-                          size_t smem, cudaStream_t s) {
-  if (vec == 4) {
-    switch (G) {
-      case 1: return launch_stream_c4_8_1(p, iso_kind, coef, grid, smem, s);
-      case 2: return launch_stream_c4_8_2(p, iso_kind, coef, grid, smem, s);
-      case 4: return launch_stream_c4_8_4(p, iso_kind, coef, grid, smem, s);
-      case 8: return launch_stream_c4_8_8(p, iso_kind, coef, grid, smem, s);
-      case 16: return launch_stream_c4_8_16(p, iso_kind, coef, grid, smem, s);
-    }
-  } else if (vec == 2 && G == 16) {
-    return launch_stream_c2_16_16(p, iso_kind, coef, grid, smem, s);
-  } else if (vec == 1 && G == 16) {
-    return launch_stream_c1_32_16(p, iso_kind, coef, grid, smem, s);
-  }
+cudaError_t launch_stream(const StreamParams& p, int vec, int mpw, int G, int iso_kind, bool coef,
+                          int grid, size_t smem, cudaStream_t s) {
+#define PIDK_CASE(V, M, GG)                                                                   \
+  if (vec == V && mpw == M && G == GG)                                                       \
+    return launch_stream_c##V##_##M##_##GG(p, iso_kind, coef, grid, smem, s);
+  PIDK_CASE(4, 8, 1)
+  PIDK_CASE(4, 8, 2)
+  PIDK_CASE(4, 8, 4)
+  PIDK_CASE(4, 8, 8)
+  PIDK_CASE(4, 6, 16)
+  PIDK_CASE(4, 8, 16)
+  PIDK_CASE(2, 12, 16)
+  PIDK_CASE(2, 16, 16)
+  PIDK_CASE(1, 20, 16)
+  PIDK_CASE(1, 24, 16)
+  PIDK_CASE(1, 28, 16)
+  PIDK_CASE(1, 32, 16)
+#undef PIDK_CASE
   return cudaErrorInvalidValue;
 }
 
@@ -54,8 +62,13 @@ cudaError_t stream_kernels_init(int max_smem) {
   if (e == cudaSuccess) e = init_stream_c4_8_2(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_4(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_8(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_6_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c2_12_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c2_16_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c1_20_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c1_24_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c1_28_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c1_32_16(max_smem);
   return e;
 }
