@@ -151,10 +151,12 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
 // for N up to 512).
 StreamCfg stream_cfg(int64_t N) {
   // Every member slot of a class costs arithmetic whether or not a member fills it, so the
-  // classes above 64 members come in steps that keep the empty slots below about a fifth.
+  // classes above 16 members come in steps that keep the empty slots to about a fifth.
   if (N <= 8) return {4, 1, 128, 1, 8};
   if (N <= 16) return {4, 2, 128, 1, 8};
+  if (N <= 24) return {4, 4, 128, 1, 6};
   if (N <= 32) return {4, 4, 128, 1, 8};
+  if (N <= 48) return {4, 8, 128, 1, 6};
   if (N <= 64) return {4, 8, 128, 1, 8};
   if (N <= 96) return {4, 16, 128, 1, 6};
   if (N <= 128) return {4, 16, 128, 1, 8};

@@ -21,7 +21,9 @@ namespace pidk {
   cudaError_t init_stream_c##V##_##M##_##G(int);
 PIDK_CLASS(4, 8, 1)
 PIDK_CLASS(4, 8, 2)
+PIDK_CLASS(4, 6, 4)
 PIDK_CLASS(4, 8, 4)
+PIDK_CLASS(4, 6, 8)
 PIDK_CLASS(4, 8, 8)
 PIDK_CLASS(4, 6, 16)
 PIDK_CLASS(4, 8, 16)
@@ -40,7 +42,9 @@ cudaError_t launch_stream(const StreamParams& p, int vec, int mpw, int G, int is
     return launch_stream_c##V##_##M##_##GG(p, iso_kind, coef, grid, smem, s);
   PIDK_CASE(4, 8, 1)
   PIDK_CASE(4, 8, 2)
+  PIDK_CASE(4, 6, 4)
   PIDK_CASE(4, 8, 4)
+  PIDK_CASE(4, 6, 8)
   PIDK_CASE(4, 8, 8)
   PIDK_CASE(4, 6, 16)
   PIDK_CASE(4, 8, 16)
@@ -60,7 +64,9 @@ cudaError_t stream_kernels_init(int max_smem) {
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = init_stream_c4_8_1(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_2(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_6_4(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_4(max_smem);
+  if (e == cudaSuccess) e = init_stream_c4_6_8(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_8(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_6_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_16(max_smem);
