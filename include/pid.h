@@ -23,7 +23,10 @@
  *     pointers of torch CUDA tensors), except where a name ends in `_host`.
  *   - Ensemble data are row-major [N][ld] float32: member i, cell x at data[i*ld + x];
  *     ld >= M. Cell measures w are float32 [M], or NULL for unit measure (uniform grid,
- *     Eq. 12). Cell measures must be > 0 (Sec. 3.4).
+ *     Eq. 12). Cell measures must be > 0 (Sec. 3.4). Rows that start on 16-byte
+ *     boundaries (data and w 16-byte aligned, ld a multiple of 4) are staged by the tensor
+ *     memory accelerator; other rows are read with plain loads, about 2.5x slower for the
+ *     streaming passes, so pad ld to a multiple of 4 where the data allow it.
  *   - Outputs are float64 [N] (depths and inclusion fractions), int32 [N] (ranks:
  *     0 = deepest; ties go to the lower member index), float64 [N*N] (row-major inclusion
  *     matrix P[i*N + j] = u_i subset_p u_j). Any output pointer may be NULL to skip it.
