@@ -38,9 +38,12 @@ def _check(o, ref, tol=FP32_TOL, what=""):
     assert_rank_agrees_outside_ties(to_np(o["rank"]), d, tol)
 
 
+# every tile class (members <= 8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 320, 384, 448,
+# 512), filled and partly filled, with ragged cell counts
 SHAPES = [(1, 1), (1, 300), (2, 7), (3, 129), (7, 1000), (8, 4099), (9, 513), (16, 2000),
-          (17, 3001), (31, 777), (33, 5000), (64, 4097), (65, 2049), (128, 1025), (129, 999),
-          (200, 1500), (256, 640), (257, 333), (500, 450), (512, 257)]
+          (17, 3001), (24, 2500), (31, 777), (33, 5000), (48, 3000), (64, 4097), (65, 2049),
+          (96, 1000), (128, 1025), (129, 999), (192, 800), (200, 1500), (256, 640), (257, 333),
+          (350, 300), (384, 257), (420, 260), (448, 130), (500, 450), (512, 257)]
 
 
 @pytest.mark.parametrize("N,M", SHAPES)
@@ -55,7 +58,8 @@ def test_pid_mean_parity(H, N, M, weighted):
 
 
 @pytest.mark.parametrize("N,M", [(1, 50), (2, 7), (5, 1000), (20, 16384), (33, 5000), (64, 4097),
-                                 (129, 999), (257, 333), (500, 450)])
+                                 (90, 700), (129, 999), (257, 333), (350, 300), (420, 260),
+                                 (500, 450)])
 @pytest.mark.parametrize("weighted", [False, True])
 def test_full_linear_parity(H, N, M, weighted):
     U = synth.random_soft(N, M, seed=N * 31 + M, binary_frac=0.3)
