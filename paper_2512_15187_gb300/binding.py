@@ -266,9 +266,22 @@ def _stream(stream):
 
 
 def _check_matrix(x, name):
-    if x.dim() != 2 or x.dtype.__repr__() != "torch.float32" or not x.is_cuda or x.stride(1) != 1:
+    import torch
+    if x.dim() != 2 or x.dtype != torch.float32 or not x.is_cuda or x.stride(1) != 1:
         raise ValueError(f"{name} must be a 2-D float32 CUDA tensor with unit cell stride")
     return x.shape[0], x.shape[1], x.stride(0)
+
+
+def _weights(w, M, device):
+    """Device pointer of the cell measures w (float32 CUDA [M], contiguous), or None."""
+    import torch
+    if w is None:
+        return None
+    if (w.dtype != torch.float32 or not w.is_cuda or w.device != device or
+            w.numel() != M or (w.dim() == 1 and w.stride(0) != 1) or not w.is_contiguous()):
+        raise ValueError("w must be a contiguous float32 CUDA tensor of M cell measures on "
+                         "the data's device")
+    return w.data_ptr()
 
 
 class Handle:
@@ -351,7 +364,7 @@ class Handle:
     def mean(self, U, w=None, stream=None):
         N, M, ld = _check_matrix(U, "U")
         o = self._outputs(N)
-        pid_mean(self.h, U.data_ptr(), N, M, ld, _ptr(w), o["depth"].data_ptr(),
+        pid_mean(self.h, U.data_ptr(), N, M, ld, _weights(w, M, U.device), o["depth"].data_ptr(),
                  o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
                  _stream(stream))
         return o
@@ -366,7 +379,7 @@ class Handle:
         if r.dtype != torch.float64 or not r.is_cuda or r.numel() != N or not r.is_contiguous():
             raise ValueError("member_weights must be a contiguous float64 CUDA tensor [N]")
         o = self._outputs(N)
-        pid_mean_weighted(self.h, data.data_ptr(), N, M, ld, _ptr(w),
+        pid_mean_weighted(self.h, data.data_ptr(), N, M, ld, _weights(w, M, data.device),
                           None if iso is None else make_iso(iso), r.data_ptr(),
                           o["depth"].data_ptr(), o["in_in"].data_ptr(), o["in_out"].data_ptr(),
                           o["rank"].data_ptr(), _stream(stream))
@@ -385,7 +398,8 @@ class Handle:
         gram = MODES[mode] == PID_MODE_FULL and PRECISIONS[precision] != PID_FP32
         o = self._outputs(N, want_P=want_P and gram)
         opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
-        pid_spacetime(self.h, [S.data_ptr() for S in steps], N, M, ld, _ptr(w),
+        pid_spacetime(self.h, [S.data_ptr() for S in steps], N, M, ld,
+                      _weights(w, M, steps[0].device),
                       None if iso is None else make_iso(iso), opt, o["depth"].data_ptr(),
                       o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
                       _ptr(o.get("P")), _ptr(o.get("err_est")), _stream(stream))
@@ -415,7 +429,8 @@ class Handle:
         gram = MODES[mode] == PID_MODE_FULL and PRECISIONS[precision] != PID_FP32
         o = self._outputs(N, want_P=want_P and gram)
         opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
-        pid_full(self.h, U.data_ptr(), N, M, ld, _ptr(w), opt, o["depth"].data_ptr(),
+        pid_full(self.h, U.data_ptr(), N, M, ld, _weights(w, M, U.device), opt,
+                 o["depth"].data_ptr(),
                  o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
                  _ptr(o.get("P")), _ptr(o.get("err_est")), _stream(stream))
         return o
@@ -426,7 +441,8 @@ class Handle:
         o = self._outputs(N)
         iso = make_iso((mu, sigma, superlevel, kind))
         opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
-        pid_from_fields(self.h, F.data_ptr(), N, M, ld, _ptr(w), iso, opt, o["depth"].data_ptr(),
+        pid_from_fields(self.h, F.data_ptr(), N, M, ld, _weights(w, M, F.device), iso, opt,
+                        o["depth"].data_ptr(),
                         o["in_in"].data_ptr(), o["in_out"].data_ptr(), o["rank"].data_ptr(),
                         _stream(stream))
         return o
@@ -451,7 +467,7 @@ class Handle:
             iso = it.get("iso")
             e = pid_ensemble()
             e.data, e.N, e.M, e.ld = x.data_ptr(), N, M, ld
-            e.w = _ptr(it.get("w"))
+            e.w = _weights(it.get("w"), M, x.device)
             e.is_field = int(iso is not None)
             if iso is not None:
                 e.iso = make_iso(iso)
@@ -501,10 +517,11 @@ class Server:
         if copy is None:
             copy = not is_dev
         if is_dev:
-            N, M = data.shape
-            ld = data.stride(0)
+            if copy:
+                raise ValueError("copy=True takes host (numpy) data; device tensors are adopted")
+            N, M, ld = _check_matrix(data, "data")
             dptr = data.data_ptr()
-            wptr = None if w is None else w.data_ptr()
+            wptr = _weights(w, M, data.device)
             keep = (data, w)
         else:
             data = np.ascontiguousarray(data, dtype=np.float32)
