@@ -113,6 +113,7 @@ struct GramPlan {
   int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
   bool tma = true;         // rows 16-byte aligned: FP32 tiles staged by TMA
   int G = 16;              // warps per group (8: two groups per CTA for N <= 64)
+  int mpw = 8;             // members per warp of the narrow tile (6 for N <= 48, 64 < N <= 96)
   bool wide = false;       // 128 < N <= 256: 16 warps on 256 rows, two M = 128 row blocks
   int TS = 128;            // cells per FP32 stage (64 for the wide tile)
   int n_gchunks = 0;
@@ -160,8 +161,8 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
 
 // gram.cu
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
-void gram_geometry(pid_handle h, int G, bool wide, int prec, int32_t stage_floats, int* dF, int* dO,
-                   size_t* smem);
+void gram_geometry(pid_handle h, int G, int mpw, bool wide, int prec, int32_t stage_floats,
+                   int* dF, int* dO, size_t* smem);
 pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
                            float* gpart, float* scale, cudaStream_t s);
 // Gram launch over `count` device descriptors (part / gpart / op_scale already set).

@@ -24,6 +24,9 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   gp->prec = in.precision;
   gp->G = in.N <= 64 ? 8 : 16;        // two independent 8-warp groups when N <= 64
   gp->wide = in.N > kGramNarrowMaxN;   // two M = 128 row blocks, 64-cell FP32 stages
+  // 6 members per warp when they hold the ensemble (48 or 96 rows): the converters then
+  // skip the rows a tile of 8 per warp would leave empty
+  gp->mpw = (in.N <= 48 || (in.N > 64 && in.N <= 96)) ? 6 : 8;
   gp->TS = gp->wide ? 64 : 128;
   // Chunks (one FP32 partial Gram each) of 32 to 256 operand stages: every chunk costs a
   // TMEM drain, an N x N partial written and read back, and the MMA pipeline's ramp, so a
@@ -60,7 +63,8 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   gp->stage_floats = gp->tma ? static_cast<int32_t>(rup(in.N * gp->TS + gp->TS, 32)) : 32;
   gp->gpart_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * in.N * in.N * 4, 256);
   gp->part_bytes = rup(static_cast<int64_t>(gp->n_gchunks) * 2 * in.N * 8, 256);
-  gram_geometry(h, gp->G, gp->wide, gp->prec, gp->stage_floats, &gp->dF, &gp->dO, &gp->smem);
+  gram_geometry(h, gp->G, gp->mpw, gp->wide, gp->prec, gp->stage_floats, &gp->dF, &gp->dO,
+                &gp->smem);
   gp->flops = (in.precision == PID_SPLIT_BF16 ? 3.0 : 1.0) * 2.0 * static_cast<double>(in.N) *
               in.N * in.M;
   gp->bytes = 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0);
@@ -69,23 +73,23 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
 
 // Ring depths that fit the shared memory: at least two FP32 stages, then as many operand
 // stages as fit (at most four), then the FP32 ring deepened to at most six stages.
-void gram_geometry(pid_handle h, int G, bool wide, int prec, int32_t stage_floats, int* dF, int* dO,
-                   size_t* smem) {
+void gram_geometry(pid_handle h, int G, int mpw, bool wide, int prec, int32_t stage_floats,
+                   int* dF, int* dO, size_t* smem) {
   const size_t cap = static_cast<size_t>(h->max_smem > 0 ? h->max_smem : 232448);
   int f = 2, o = 4;
-  while (o > 1 && gram_smem_bytes(G, wide, prec, f, o, stage_floats) > cap) --o;
-  while (f > 1 && gram_smem_bytes(G, wide, prec, f, o, stage_floats) > cap) --f;
-  while (f < 6 && gram_smem_bytes(G, wide, prec, f + 1, o, stage_floats) <= cap) ++f;
+  while (o > 1 && gram_smem_bytes(G, mpw, wide, prec, f, o, stage_floats) > cap) --o;
+  while (f > 1 && gram_smem_bytes(G, mpw, wide, prec, f, o, stage_floats) > cap) --f;
+  while (f < 6 && gram_smem_bytes(G, mpw, wide, prec, f + 1, o, stage_floats) <= cap) ++f;
   *dF = f;
   *dO = o;
-  *smem = gram_smem_bytes(G, wide, prec, f, o, stage_floats);
+  *smem = gram_smem_bytes(G, mpw, wide, prec, f, o, stage_floats);
 }
 
-static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, bool wide, int prec,
-                              int iso_mode, int grid, size_t smem, double bytes, double flops,
-                              cudaStream_t s) {
+static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, int mpw, bool wide,
+                              int prec, int iso_mode, int grid, size_t smem, double bytes,
+                              double flops, cudaStream_t s) {
   ProfScope ps(h, PID_KERNEL_GRAM, bytes, flops, s);
-  cudaError_t e = launch_gram(gpar, G, wide, prec, iso_kind(iso_mode), grid, smem, s);
+  cudaError_t e = launch_gram(gpar, G, mpw, wide, prec, iso_kind(iso_mode), grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "Gram kernel launch");
   return PID_OK;
 }
@@ -116,8 +120,8 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   gpar.err = h->err_word;
   const int ng = kGramConvWarps / gp.G;
   const int grid = std::max(1, std::min(h->sms, (gp.n_gchunks + ng - 1) / ng));
-  return gram_launch(h, gpar, gp.G, gp.wide, gp.prec, gp.desc.iso_mode, grid, gp.smem, gp.bytes,
-                     gp.flops, s);
+  return gram_launch(h, gpar, gp.G, gp.mpw, gp.wide, gp.prec, gp.desc.iso_mode, grid, gp.smem,
+                     gp.bytes, gp.flops, s);
 }
 
 pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* descs, int count,
@@ -138,7 +142,8 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* de
   gpar.err = h->err_word;
   const int ng = kGramConvWarps / gp.G;
   const int grid = std::max(1, std::min(h->sms, (total_units + ng - 1) / ng));
-  return gram_launch(h, gpar, gp.G, gp.wide, gp.prec, iso_mode, grid, gp.smem, bytes, flops, s);
+  return gram_launch(h, gpar, gp.G, gp.mpw, gp.wide, gp.prec, iso_mode, grid, gp.smem, bytes,
+                     flops, s);
 }
 
 }  // namespace pidh

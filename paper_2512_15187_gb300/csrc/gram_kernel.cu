@@ -1,5 +1,6 @@
-// Instantiations of the tensor-core Gram kernel for N <= 128 (gram_kernel.cuh), the launch
-// dispatch over group size, precision and isovalue kind, and the FP8 operand scale.
+// Instantiations of the tensor-core Gram kernel for N <= 128 with 8 members per warp
+// (gram_kernel.cuh), the launch dispatch over tile, group size, precision and isovalue kind,
+// and the FP8 operand scale.
 #include "gram_kernel.cuh"
 
 namespace pidk {
@@ -7,11 +8,15 @@ namespace pidk {
 cudaError_t launch_gram_wide(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
                              cudaStream_t s);
 cudaError_t gram_wide_init(int max_smem);
+cudaError_t launch_gram_narrow6(const GramParams& p, int G, int prec, int iso_kind, int grid,
+                                size_t smem, cudaStream_t s);
+cudaError_t gram_narrow6_init(int max_smem);
 
-size_t gram_smem_bytes(int G, bool wide, int prec, int dF, int dO, int stage_floats) {
+size_t gram_smem_bytes(int G, int narrow_mpw, bool wide, int prec, int dF, int dO,
+                       int stage_floats) {
   const size_t NG = kGramConvWarps / G;
   const size_t T = wide ? GramShape<true>::T : GramShape<false>::T;
-  const size_t mpw = wide ? GramShape<true>::MPW : GramShape<false>::MPW;
+  const size_t mpw = wide ? GramShape<true>::MPW : static_cast<size_t>(narrow_mpw);
   const size_t plane = mpw * G * 128;
   const size_t op_stage = (prec == 2 ? 2 : 1) * (prec == 3 ? 1 : 2) * plane;
   const size_t rb = static_cast<size_t>(G) * T + T;
@@ -20,59 +25,20 @@ size_t gram_smem_bytes(int G, bool wide, int prec, int dF, int dO, int stage_flo
          16 + NG * sizeof(GramLeader);
 }
 
-template <int G, int ISO, int PREC>
-static cudaError_t gram_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
-  if (p.use_tma)
-    gram_kernel<G, ISO, PREC, true, false><<<grid, kGramThreads, smem, s>>>(p);
-  else
-    gram_kernel<G, ISO, PREC, false, false><<<grid, kGramThreads, smem, s>>>(p);
-  return cudaGetLastError();
-}
-
-template <int G>
-static cudaError_t launch_gram_g(const GramParams& p, int prec, int iso_kind, int grid,
-                                 size_t smem, cudaStream_t s) {
-#define PIDK_GRAM_CASE(ISO)                                                  \
-  if (iso_kind == ISO) {                                                     \
-    if (prec == 1) return gram_launch_t<G, ISO, 1>(p, grid, smem, s);        \
-    if (prec == 2) return gram_launch_t<G, ISO, 2>(p, grid, smem, s);        \
-    if (prec == 3) return gram_launch_t<G, ISO, 3>(p, grid, smem, s);        \
-  }
-  PIDK_GRAM_CASE(ISOK_NONE)
-  PIDK_GRAM_CASE(ISOK_NORMAL)
-  PIDK_GRAM_CASE(ISOK_STEP)
-#undef PIDK_GRAM_CASE
-  return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_gram(const GramParams& p, int G, bool wide, int prec, int iso_kind, int grid,
-                        size_t smem, cudaStream_t s) {
+cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec, int iso_kind,
+                        int grid, size_t smem, cudaStream_t s) {
   if (wide) return G == 16 ? launch_gram_wide(p, prec, iso_kind, grid, smem, s) : cudaErrorInvalidValue;
-  if (G == 8) return launch_gram_g<8>(p, prec, iso_kind, grid, smem, s);
-  if (G == 16) return launch_gram_g<16>(p, prec, iso_kind, grid, smem, s);
+  if (mpw == 6) return launch_gram_narrow6(p, G, prec, iso_kind, grid, smem, s);
+  if (mpw != 8) return cudaErrorInvalidValue;
+  if (G == 8) return gram_narrow_launch<8, 8>(p, prec, iso_kind, grid, smem, s);
+  if (G == 16) return gram_narrow_launch<16, 8>(p, prec, iso_kind, grid, smem, s);
   return cudaErrorInvalidValue;
-}
-
-template <int G>
-static cudaError_t gram_init_g(int max_smem) {
-  cudaError_t e = cudaSuccess;
-#define PIDK_GRAM_INIT(ISO, PREC)                                                            \
-  if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, true, false>,                         \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);         \
-  if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, false, false>,                        \
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
-  PIDK_GRAM_INIT(ISOK_NONE, 1) PIDK_GRAM_INIT(ISOK_NONE, 2) PIDK_GRAM_INIT(ISOK_NONE, 3)
-  PIDK_GRAM_INIT(ISOK_NORMAL, 1) PIDK_GRAM_INIT(ISOK_NORMAL, 2) PIDK_GRAM_INIT(ISOK_NORMAL, 3)
-  PIDK_GRAM_INIT(ISOK_STEP, 1) PIDK_GRAM_INIT(ISOK_STEP, 2) PIDK_GRAM_INIT(ISOK_STEP, 3)
-#undef PIDK_GRAM_INIT
-  return e;
 }
 
 cudaError_t gram_kernels_init(int max_smem) {
-  cudaError_t e = gram_init_g<8>(max_smem);
-  if (e == cudaSuccess) e = gram_init_g<16>(max_smem);
+  cudaError_t e = gram_narrow_init<8, 8>(max_smem);
+  if (e == cudaSuccess) e = gram_narrow_init<16, 8>(max_smem);
+  if (e == cudaSuccess) e = gram_narrow6_init(max_smem);
   return e == cudaSuccess ? gram_wide_init(max_smem) : e;
 }
 

@@ -53,11 +53,12 @@ struct GramLeader {
   uint32_t pend_idesc;
 };
 
-template <bool WIDE>
+// NMPW: members per warp of the narrow tile (8, or 6 for ensembles that fill 3/4 of it).
+template <bool WIDE, int NMPW = 8>
 struct GramShape {
   static constexpr int VEC = WIDE ? 2 : 4;             // cells per lane per register tile
   static constexpr int T = 32 * VEC;                   // cells per FP32 stage
-  static constexpr int MPW = WIDE ? 16 : 8;            // members per warp
+  static constexpr int MPW = WIDE ? 16 : NMPW;         // members per warp
   static constexpr int SPO = WIDE ? 2 : 1;             // FP32 stages per operand stage
   static constexpr int MB = WIDE ? 2 : 1;              // M = 128 row blocks
   static constexpr int NBUF = WIDE ? 1 : 2;            // accumulator buffers
@@ -97,9 +98,9 @@ __device__ __forceinline__ uint32_t sw128_offset(int i, int b) {
 // it to the stage's "operand free" mbarrier and, at a chunk's end, to the accumulator's
 // "ready" mbarrier; warps 0-3 drain the previous chunk's accumulator halfway through the
 // next chunk.
-template <int G, int ISO, int PREC, bool TMA, bool WIDE>
+template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = 8>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams p) {
-  using S = GramShape<WIDE>;
+  using S = GramShape<WIDE, NMPW>;
   constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, SPO = S::SPO, MB = S::MB, NBUF = S::NBUF;
   static_assert(!WIDE || G == 16, "the wide tile uses all 16 warps as one group");
   static_assert(SPO == 1 || SPO == 2, "FP32 stages per operand stage");
@@ -111,7 +112,10 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   constexpr uint32_t OP_STAGE = PLANES * KBLK * PLANE;
   constexpr uint32_t FMT = PREC == 3 ? 0u : 1u;      // E4M3 : BF16
   constexpr int RB = G * T + T;                      // exchange buffer floats
-  constexpr uint32_t BUFC = WIDE ? 512u : ROWS;      // TMEM columns per accumulator buffer
+  // TMEM columns per accumulator buffer: the group's rows rounded up to 64 or 128, so that
+  // buffers and groups start at the same columns for 6 and 8 members per warp
+  constexpr uint32_t BUFC = WIDE ? 512u : (ROWS <= 64 ? 64u : 128u);
+  static_assert(WIDE || NBUF * BUFC * NG <= S::TMEM_COLS, "accumulators fit the allocation");
   extern __shared__ __align__(1024) unsigned char smem_raw[];
 
   const int warp = threadIdx.x >> 5;
@@ -604,6 +608,50 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   __syncthreads();
   tc_fence_after();
   if (warp == 0) tmem_dealloc(*tmem_slot, S::TMEM_COLS);
+}
+
+// Host-side launch and opt-in helpers of the narrow tile for one members-per-warp count
+// (instantiated by gram_kernel.cu for 8 and gram_narrow6.cu for 6).
+template <int G, int ISO, int PREC, int NMPW>
+cudaError_t gram_narrow_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
+  if (p.use_tma)
+    gram_kernel<G, ISO, PREC, true, false, NMPW><<<grid, kGramThreads, smem, s>>>(p);
+  else
+    gram_kernel<G, ISO, PREC, false, false, NMPW><<<grid, kGramThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int G, int NMPW>
+cudaError_t gram_narrow_launch(const GramParams& p, int prec, int iso_kind, int grid,
+                               size_t smem, cudaStream_t s) {
+#define PIDK_GRAM_CASE(ISO)                                                         \
+  if (iso_kind == ISO) {                                                            \
+    if (prec == 1) return gram_narrow_launch_t<G, ISO, 1, NMPW>(p, grid, smem, s);  \
+    if (prec == 2) return gram_narrow_launch_t<G, ISO, 2, NMPW>(p, grid, smem, s);  \
+    if (prec == 3) return gram_narrow_launch_t<G, ISO, 3, NMPW>(p, grid, smem, s);  \
+  }
+  PIDK_GRAM_CASE(ISOK_NONE)
+  PIDK_GRAM_CASE(ISOK_NORMAL)
+  PIDK_GRAM_CASE(ISOK_STEP)
+#undef PIDK_GRAM_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <int G, int NMPW>
+cudaError_t gram_narrow_init(int max_smem) {
+  cudaError_t e = cudaSuccess;
+#define PIDK_GRAM_INIT(ISO, PREC)                                                            \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, true, false, NMPW>,                   \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);         \
+  if (e == cudaSuccess)                                                                      \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, false, false, NMPW>,                  \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  PIDK_GRAM_INIT(ISOK_NONE, 1) PIDK_GRAM_INIT(ISOK_NONE, 2) PIDK_GRAM_INIT(ISOK_NONE, 3)
+  PIDK_GRAM_INIT(ISOK_NORMAL, 1) PIDK_GRAM_INIT(ISOK_NORMAL, 2) PIDK_GRAM_INIT(ISOK_NORMAL, 3)
+  PIDK_GRAM_INIT(ISOK_STEP, 1) PIDK_GRAM_INIT(ISOK_STEP, 2) PIDK_GRAM_INIT(ISOK_STEP, 3)
+#undef PIDK_GRAM_INIT
+  return e;
 }
 
 }  // namespace pidk

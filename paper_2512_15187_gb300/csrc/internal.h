@@ -160,9 +160,10 @@ cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 cudaError_t launch_member_coef(const double* r, int64_t N, float* coef, uint32_t* err,
                                cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
-size_t gram_smem_bytes(int G, bool wide, int prec, int dF, int dO, int stage_floats);
-cudaError_t launch_gram(const GramParams& p, int G, bool wide, int prec, int iso_kind, int grid,
-                        size_t smem, cudaStream_t s);
+size_t gram_smem_bytes(int G, int narrow_mpw, bool wide, int prec, int dF, int dO,
+                       int stage_floats);
+cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec, int iso_kind,
+                        int grid, size_t smem, cudaStream_t s);
 cudaError_t gram_kernels_init(int max_smem);
 cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s);
 cudaError_t stream_kernels_init(int max_smem);
