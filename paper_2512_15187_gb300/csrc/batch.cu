@@ -141,13 +141,13 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   }
   // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
   std::map<ClassKey, std::vector<int>> pass1, pass2;
-  // ((((precision x 2 + TMA) x 2 + wide) x 32 + group size) x 16 + members per warp,
+  // ((((precision x 2 + TMA) x 2 + wide) x 32 + group size) x 32 + members per warp,
   //  isovalue kind)
   std::map<std::pair<int, int>, std::vector<int>> gram_cls;
   for (int e = 0; e < count; ++e) {
     if (is_gram[e]) {
       gram_cls[{(((gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 2 + (gp[e].wide ? 1 : 0)) * 32 +
-                 gp[e].G) * 16 + gp[e].mpw,
+                 gp[e].G) * 32 + gp[e].mpw,
                 iso_kind(gp[e].desc.iso_mode)}]
           .push_back(e);
     } else {

@@ -113,7 +113,8 @@ struct GramPlan {
   int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
   bool tma = true;         // rows 16-byte aligned: FP32 tiles staged by TMA
   int G = 16;              // warps per group (8: two groups per CTA for N <= 64)
-  int mpw = 8;             // members per warp of the narrow tile (6 for N <= 48, 64 < N <= 96)
+  int mpw = 8;             // members per warp: narrow 8 (6 for N <= 48, 64 < N <= 96),
+                           // wide 16 (12 for N <= 192)
   bool wide = false;       // 128 < N <= 256: 16 warps on 256 rows, two M = 128 row blocks
   int TS = 128;            // cells per FP32 stage (64 for the wide tile)
   int n_gchunks = 0;

@@ -8,16 +8,18 @@ namespace pidk {
 cudaError_t launch_gram_wide(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
                              cudaStream_t s);
 cudaError_t gram_wide_init(int max_smem);
+cudaError_t launch_gram_wide12(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
+                               cudaStream_t s);
+cudaError_t gram_wide12_init(int max_smem);
 cudaError_t launch_gram_narrow6(const GramParams& p, int G, int prec, int iso_kind, int grid,
                                 size_t smem, cudaStream_t s);
 cudaError_t gram_narrow6_init(int max_smem);
 
-size_t gram_smem_bytes(int G, int narrow_mpw, bool wide, int prec, int dF, int dO,
-                       int stage_floats) {
+// mpw: members per warp of the tile (6 or 8 narrow, 12 or 16 wide)
+size_t gram_smem_bytes(int G, int mpw, bool wide, int prec, int dF, int dO, int stage_floats) {
   const size_t NG = kGramConvWarps / G;
   const size_t T = wide ? GramShape<true>::T : GramShape<false>::T;
-  const size_t mpw = wide ? GramShape<true>::MPW : static_cast<size_t>(narrow_mpw);
-  const size_t plane = mpw * G * 128;
+  const size_t plane = static_cast<size_t>(mpw) * G * 128;
   const size_t op_stage = (prec == 2 ? 2 : 1) * (prec == 3 ? 1 : 2) * plane;
   const size_t rb = static_cast<size_t>(G) * T + T;
   return 1024 + NG * (dO * op_stage + static_cast<size_t>(dF) * stage_floats * 4 + 2 * rb * 4 +
@@ -27,18 +29,24 @@ size_t gram_smem_bytes(int G, int narrow_mpw, bool wide, int prec, int dF, int d
 
 cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec, int iso_kind,
                         int grid, size_t smem, cudaStream_t s) {
-  if (wide) return G == 16 ? launch_gram_wide(p, prec, iso_kind, grid, smem, s) : cudaErrorInvalidValue;
+  if (wide) {
+    if (G != 16) return cudaErrorInvalidValue;
+    if (mpw == 16) return launch_gram_wide(p, prec, iso_kind, grid, smem, s);
+    if (mpw == 12) return launch_gram_wide12(p, prec, iso_kind, grid, smem, s);
+    return cudaErrorInvalidValue;
+  }
   if (mpw == 6) return launch_gram_narrow6(p, G, prec, iso_kind, grid, smem, s);
   if (mpw != 8) return cudaErrorInvalidValue;
-  if (G == 8) return gram_narrow_launch<8, 8>(p, prec, iso_kind, grid, smem, s);
-  if (G == 16) return gram_narrow_launch<16, 8>(p, prec, iso_kind, grid, smem, s);
+  if (G == 8) return gram_tile_launch<8, 8>(p, prec, iso_kind, grid, smem, s);
+  if (G == 16) return gram_tile_launch<16, 8>(p, prec, iso_kind, grid, smem, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t gram_kernels_init(int max_smem) {
-  cudaError_t e = gram_narrow_init<8, 8>(max_smem);
-  if (e == cudaSuccess) e = gram_narrow_init<16, 8>(max_smem);
+  cudaError_t e = gram_tile_init<8, 8>(max_smem);
+  if (e == cudaSuccess) e = gram_tile_init<16, 8>(max_smem);
   if (e == cudaSuccess) e = gram_narrow6_init(max_smem);
+  if (e == cudaSuccess) e = gram_wide12_init(max_smem);
   return e == cudaSuccess ? gram_wide_init(max_smem) : e;
 }
 

@@ -53,12 +53,13 @@ struct GramLeader {
   uint32_t pend_idesc;
 };
 
-// NMPW: members per warp of the narrow tile (8, or 6 for ensembles that fill 3/4 of it).
-template <bool WIDE, int NMPW = 8>
+// NMPW: members per warp: 8 (narrow) or 16 (wide), or 6 / 12 for ensembles that fill at
+// most three quarters of those tiles.
+template <bool WIDE, int NMPW = (WIDE ? 16 : 8)>
 struct GramShape {
   static constexpr int VEC = WIDE ? 2 : 4;             // cells per lane per register tile
   static constexpr int T = 32 * VEC;                   // cells per FP32 stage
-  static constexpr int MPW = WIDE ? 16 : NMPW;         // members per warp
+  static constexpr int MPW = NMPW;                     // members per warp
   static constexpr int SPO = WIDE ? 2 : 1;             // FP32 stages per operand stage
   static constexpr int MB = WIDE ? 2 : 1;              // M = 128 row blocks
   static constexpr int NBUF = WIDE ? 1 : 2;            // accumulator buffers
@@ -98,7 +99,7 @@ __device__ __forceinline__ uint32_t sw128_offset(int i, int b) {
 // it to the stage's "operand free" mbarrier and, at a chunk's end, to the accumulator's
 // "ready" mbarrier; warps 0-3 drain the previous chunk's accumulator halfway through the
 // next chunk.
-template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = 8>
+template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = (WIDE ? 16 : 8)>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams p) {
   using S = GramShape<WIDE, NMPW>;
   constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, SPO = S::SPO, MB = S::MB, NBUF = S::NBUF;
@@ -610,25 +611,27 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   if (warp == 0) tmem_dealloc(*tmem_slot, S::TMEM_COLS);
 }
 
-// Host-side launch and opt-in helpers of the narrow tile for one members-per-warp count
-// (instantiated by gram_kernel.cu for 8 and gram_narrow6.cu for 6).
-template <int G, int ISO, int PREC, int NMPW>
-cudaError_t gram_narrow_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
+// Host-side launch and opt-in helpers of one tile (group size, members per warp, wide or
+// narrow): gram_kernel.cu instantiates the narrow tiles with 8 members per warp,
+// gram_narrow6.cu those with 6, gram_wide.cu the wide tile with 16 and gram_wide12.cu
+// with 12.
+template <int G, int ISO, int PREC, int NMPW, bool WIDE>
+cudaError_t gram_tile_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
   if (p.use_tma)
-    gram_kernel<G, ISO, PREC, true, false, NMPW><<<grid, kGramThreads, smem, s>>>(p);
+    gram_kernel<G, ISO, PREC, true, WIDE, NMPW><<<grid, kGramThreads, smem, s>>>(p);
   else
-    gram_kernel<G, ISO, PREC, false, false, NMPW><<<grid, kGramThreads, smem, s>>>(p);
+    gram_kernel<G, ISO, PREC, false, WIDE, NMPW><<<grid, kGramThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int G, int NMPW>
-cudaError_t gram_narrow_launch(const GramParams& p, int prec, int iso_kind, int grid,
-                               size_t smem, cudaStream_t s) {
-#define PIDK_GRAM_CASE(ISO)                                                         \
-  if (iso_kind == ISO) {                                                            \
-    if (prec == 1) return gram_narrow_launch_t<G, ISO, 1, NMPW>(p, grid, smem, s);  \
-    if (prec == 2) return gram_narrow_launch_t<G, ISO, 2, NMPW>(p, grid, smem, s);  \
-    if (prec == 3) return gram_narrow_launch_t<G, ISO, 3, NMPW>(p, grid, smem, s);  \
+template <int G, int NMPW, bool WIDE = false>
+cudaError_t gram_tile_launch(const GramParams& p, int prec, int iso_kind, int grid,
+                             size_t smem, cudaStream_t s) {
+#define PIDK_GRAM_CASE(ISO)                                                             \
+  if (iso_kind == ISO) {                                                                \
+    if (prec == 1) return gram_tile_launch_t<G, ISO, 1, NMPW, WIDE>(p, grid, smem, s);  \
+    if (prec == 2) return gram_tile_launch_t<G, ISO, 2, NMPW, WIDE>(p, grid, smem, s);  \
+    if (prec == 3) return gram_tile_launch_t<G, ISO, 3, NMPW, WIDE>(p, grid, smem, s);  \
   }
   PIDK_GRAM_CASE(ISOK_NONE)
   PIDK_GRAM_CASE(ISOK_NORMAL)
@@ -637,15 +640,15 @@ cudaError_t gram_narrow_launch(const GramParams& p, int prec, int iso_kind, int 
   return cudaErrorInvalidValue;
 }
 
-template <int G, int NMPW>
-cudaError_t gram_narrow_init(int max_smem) {
+template <int G, int NMPW, bool WIDE = false>
+cudaError_t gram_tile_init(int max_smem) {
   cudaError_t e = cudaSuccess;
 #define PIDK_GRAM_INIT(ISO, PREC)                                                            \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, true, false, NMPW>,                   \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, true, WIDE, NMPW>,                    \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);         \
   if (e == cudaSuccess)                                                                      \
-    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, false, false, NMPW>,                  \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISO, PREC, false, WIDE, NMPW>,                   \
                              cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
   PIDK_GRAM_INIT(ISOK_NONE, 1) PIDK_GRAM_INIT(ISOK_NONE, 2) PIDK_GRAM_INIT(ISOK_NONE, 3)
   PIDK_GRAM_INIT(ISOK_NORMAL, 1) PIDK_GRAM_INIT(ISOK_NORMAL, 2) PIDK_GRAM_INIT(ISOK_NORMAL, 3)

@@ -7,14 +7,14 @@ namespace pidk {
 
 cudaError_t launch_gram_narrow6(const GramParams& p, int G, int prec, int iso_kind, int grid,
                                 size_t smem, cudaStream_t s) {
-  if (G == 8) return gram_narrow_launch<8, 6>(p, prec, iso_kind, grid, smem, s);
-  if (G == 16) return gram_narrow_launch<16, 6>(p, prec, iso_kind, grid, smem, s);
+  if (G == 8) return gram_tile_launch<8, 6>(p, prec, iso_kind, grid, smem, s);
+  if (G == 16) return gram_tile_launch<16, 6>(p, prec, iso_kind, grid, smem, s);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t gram_narrow6_init(int max_smem) {
-  cudaError_t e = gram_narrow_init<8, 6>(max_smem);
-  return e == cudaSuccess ? gram_narrow_init<16, 6>(max_smem) : e;
+  cudaError_t e = gram_tile_init<8, 6>(max_smem);
+  return e == cudaSuccess ? gram_tile_init<16, 6>(max_smem) : e;
 }
 
 }  // namespace pidk

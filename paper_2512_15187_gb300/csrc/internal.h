@@ -160,8 +160,7 @@ cudaError_t launch_iso(const IsoParams& p, cudaStream_t s);
 cudaError_t launch_member_coef(const double* r, int64_t N, float* coef, uint32_t* err,
                                cudaStream_t s);
 size_t stream_smem_bytes(int vec, int G, int depth, int stage_floats);
-size_t gram_smem_bytes(int G, int narrow_mpw, bool wide, int prec, int dF, int dO,
-                       int stage_floats);
+size_t gram_smem_bytes(int G, int mpw, bool wide, int prec, int dF, int dO, int stage_floats);
 cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec, int iso_kind,
                         int grid, size_t smem, cudaStream_t s);
 cudaError_t gram_kernels_init(int max_smem);

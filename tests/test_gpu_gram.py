@@ -56,10 +56,12 @@ def test_gram_first_small_case(H):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-# every tile: 48 rows (N <= 48), 64, 96 (64 < N <= 96), 128, and the wide 256-row tile
+# every tile: 48 rows (N <= 48), 64, 96 (64 < N <= 96), 128, and the wide 192- and 256-row
+# tiles
 @pytest.mark.parametrize("N,M", [(1, 64), (2, 1000), (16, 4097), (33, 3000), (48, 5000),
                                  (49, 3001), (64, 65543), (65, 4100), (96, 6000), (100, 5000),
-                                 (128, 20000), (129, 777), (200, 20011), (256, 9000)])
+                                 (128, 20000), (129, 777), (192, 5003), (193, 2000),
+                                 (200, 20011), (256, 9000)])
 @pytest.mark.parametrize("weighted", [False, True])
 def test_gram_parity(H, prec, N, M, weighted):
     U = synth.random_soft(N, M, seed=N * 131 + M, binary_frac=0.2)
