@@ -165,6 +165,10 @@ pid_status pid_autotune_enable(pid_handle h, int enable, int32_t* n_entries);
  */
 pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
                           const pid_iso* iso, float* U_out, int64_t ld_out, void* stream);
+/* The same map with bfloat16 output: U_out holds the bit patterns of the float32 masks
+ * rounded to nearest even (2 bytes per element; the map itself runs in float32). */
+pid_status pid_soft_masks_bf16(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                               const pid_iso* iso, uint16_t* U_out, int64_t ld_out, void* stream);
 
 /*
  * pid_selftest_wait_timeout — diagnostic of the bounded device waits, which every kernel

@@ -33,7 +33,7 @@ EXPORTS = [
     "pid_mean_noalloc", "pid_serve_start", "pid_serve_stop", "pid_serve_register",
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
     "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands", "pid_mean_weighted",
-    "pid_spacetime", "pid_depth_from_matrix",
+    "pid_spacetime", "pid_depth_from_matrix", "pid_soft_masks_bf16",
     "pid_selftest_wait_timeout",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
@@ -116,6 +116,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_last_error": ([P], c_char_p),
         "pid_workspace_bytes": ([P], c_size_t),
         "pid_soft_masks": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, c_int64, P], c_int),
+        "pid_soft_masks_bf16": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, c_int64, P],
+                                c_int),
         "pid_selftest_wait_timeout": ([P, ctypes.c_double, P], c_int),
         "pid_contour_bands": ([P, P, c_int64, c_int64, c_int64, POINTER(pid_iso), P, ctypes.c_double,
                                ctypes.c_double, P, P], c_int),
@@ -351,14 +353,23 @@ class Handle:
                           inner_fraction, out.data_ptr(), _stream(stream))
         return out
 
-    def soft_masks(self, F, mu, sigma, superlevel=False, out=None, stream=None, kind="normal"):
+    def soft_masks(self, F, mu, sigma, superlevel=False, out=None, stream=None, kind="normal",
+                   dtype=None):
+        """Soft masks of the fields F; dtype torch.float32 (default) or torch.bfloat16."""
         import torch
         N, M, ld = _check_matrix(F, "F")
+        dtype = dtype if dtype is not None else (out.dtype if out is not None else torch.float32)
+        if dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError("soft masks are float32 or bfloat16")
         if out is None:
-            out = torch.empty((N, M), dtype=torch.float32, device=F.device)
+            out = torch.empty((N, M), dtype=dtype, device=F.device)
+        if out.dtype != dtype or not out.is_cuda or out.dim() != 2 or out.stride(1) != 1 or \
+                out.shape[0] != N or out.shape[1] < M:
+            raise ValueError("out must be an [N, >= M] CUDA tensor of the requested dtype")
         iso = make_iso((mu, sigma, superlevel, kind))
-        pid_soft_masks(self.h, F.data_ptr(), N, M, ld, iso, out.data_ptr(), out.stride(0),
-                       _stream(stream))
+        fn = load().pid_soft_masks_bf16 if dtype == torch.bfloat16 else load().pid_soft_masks
+        _check(self.h, fn(self.h, F.data_ptr(), N, M, ld, ctypes.byref(iso), out.data_ptr(),
+                          out.stride(0), _stream(stream)))
         return out
 
     def mean(self, U, w=None, stream=None):

@@ -695,8 +695,9 @@ pid_status pid_profile_read(pid_handle h, int kind, pid_kernel_stats* out) {
 
 size_t pid_workspace_bytes(pid_handle h) { return h ? h->ws_bytes : 0; }
 
-pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
-                          const pid_iso* iso, float* U_out, int64_t ld_out, void* stream) {
+static pid_status soft_masks_common(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                                    const pid_iso* iso, void* U_out, int64_t ld_out, bool bf16,
+                                    void* stream) {
   pid_status st = check_shape(h, F, N, M, ld);
   if (st == PID_ERR_UNSUPPORTED && N > kMaxMembers) st = PID_OK;  // elementwise: any N
   if (st != PID_OK) return st;
@@ -704,12 +705,24 @@ pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, in
   if (!U_out || ld_out < M) return fail(h, PID_ERR_INVALID_ARG, "U_out must be non-NULL with ld_out >= M");
   DeviceGuard g(h->device);
   IsoParams p;
+  std::memset(&p, 0, sizeof(p));
   p.F = F; p.U = U_out; p.N = N; p.M = M; p.ld = ld; p.ld_out = ld_out;
+  p.out_bf16 = bf16 ? 1 : 0;
   iso_fill(iso, &p.iso_mode, &p.iso_mu, &p.iso_inv, &p.iso_t);
-  ProfScope ps(h, PID_KERNEL_ISO, 8.0 * N * M, 0.0, static_cast<cudaStream_t>(stream));
+  ProfScope ps(h, PID_KERNEL_ISO, (bf16 ? 6.0 : 8.0) * N * M, 0.0, static_cast<cudaStream_t>(stream));
   cudaError_t e = launch_iso(p, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(h, e, "iso kernel launch");
   return PID_OK;
+}
+
+pid_status pid_soft_masks(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                          const pid_iso* iso, float* U_out, int64_t ld_out, void* stream) {
+  return soft_masks_common(h, F, N, M, ld, iso, U_out, ld_out, false, stream);
+}
+
+pid_status pid_soft_masks_bf16(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
+                               const pid_iso* iso, uint16_t* U_out, int64_t ld_out, void* stream) {
+  return soft_masks_common(h, F, N, M, ld, iso, U_out, ld_out, true, stream);
 }
 
 static pid_status common_call(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,

@@ -138,10 +138,11 @@ struct FinParams {
 
 struct IsoParams {
   const float* F;
-  float* U;
+  void* U;                 // float32 [N][ld_out], or bfloat16 bit patterns when out_bf16
   int64_t N, M, ld, ld_out;
   int32_t iso_mode;
   float iso_mu, iso_inv, iso_t;
+  int32_t out_bf16;
 };
 
 // Work items of the finalisation's Gram reduction: 32 warps each sum one 32-column block

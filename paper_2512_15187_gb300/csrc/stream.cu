@@ -4,6 +4,7 @@
 //                      inclusion fractions, depths and ranks of Eq. 10 / Eq. 16.
 //   * iso_kernel      — the isovalue map alone (pid_soft_masks, Sec. 3.5).
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -381,10 +382,32 @@ cudaError_t launch_member_coef(const double* r, int64_t N, float* coef, uint32_t
 // Isovalue map alone (pid_soft_masks)
 // ---------------------------------------------------------------------------------------
 
+// Stores VEC soft masks, as float32 or rounded to nearest-even bfloat16.
+template <bool BF16>
+__device__ __forceinline__ void iso_store4(void* base, int64_t off, const float4& u) {
+  if constexpr (BF16) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(u.x, u.y), b = __floats2bfloat162_rn(u.z, u.w);
+    uint2 v;
+    v.x = *reinterpret_cast<const uint32_t*>(&a);
+    v.y = *reinterpret_cast<const uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(static_cast<__nv_bfloat16*>(base) + off) = v;
+  } else {
+    *reinterpret_cast<float4*>(static_cast<float*>(base) + off) = u;
+  }
+}
+
+template <bool BF16>
+__device__ __forceinline__ void iso_store1(void* base, int64_t off, float u) {
+  if constexpr (BF16) static_cast<__nv_bfloat16*>(base)[off] = __float2bfloat16_rn(u);
+  else static_cast<float*>(base)[off] = u;
+}
+
+template <bool BF16>
 __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoParams p) {
+  // vector path: 16-byte aligned input rows, output rows aligned to 4 elements
   const bool vec = ((p.ld & 3) == 0) && ((p.ld_out & 3) == 0) &&
                    ((reinterpret_cast<uintptr_t>(p.F) & 15) == 0) &&
-                   ((reinterpret_cast<uintptr_t>(p.U) & 15) == 0);
+                   ((reinterpret_cast<uintptr_t>(p.U) & (BF16 ? 7 : 15)) == 0);
   const int64_t per_row = vec ? (p.M + 3) / 4 : p.M;
   const int64_t total = per_row * p.N;
   const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
@@ -392,7 +415,7 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
     const int64_t i = t / per_row;
     const int64_t j = t - i * per_row;
     const float* src = p.F + i * p.ld;
-    float* dst = p.U + i * p.ld_out;
+    const int64_t row = i * p.ld_out;
     if (vec) {
       const int64_t x = j * 4;
       if (x + 4 <= p.M) {
@@ -402,13 +425,15 @@ __global__ void __launch_bounds__(256) iso_kernel(const __grid_constant__ IsoPar
         u.y = iso_value(f.y, p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
         u.z = iso_value(f.z, p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
         u.w = iso_value(f.w, p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
-        *reinterpret_cast<float4*>(dst + x) = u;
+        iso_store4<BF16>(p.U, row + x, u);
       } else {
         for (int64_t xx = x; xx < p.M; ++xx)
-          dst[xx] = iso_value(__ldg(src + xx), p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
+          iso_store1<BF16>(p.U, row + xx,
+                           iso_value(__ldg(src + xx), p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t));
       }
     } else {
-      dst[j] = iso_value(__ldg(src + j), p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
+      iso_store1<BF16>(p.U, row + j,
+                       iso_value(__ldg(src + j), p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t));
     }
   }
 }
@@ -422,7 +447,10 @@ cudaError_t launch_iso(const IsoParams& p, cudaStream_t s) {
   const int64_t cap = static_cast<int64_t>(sms) * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  iso_kernel<<<static_cast<int>(blocks), 256, 0, s>>>(p);
+  if (p.out_bf16)
+    iso_kernel<true><<<static_cast<int>(blocks), 256, 0, s>>>(p);
+  else
+    iso_kernel<false><<<static_cast<int>(blocks), 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

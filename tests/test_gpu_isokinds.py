@@ -217,3 +217,30 @@ def test_invalid_member_weights_report_a_domain_error(H):
     assert_close(to_np(o["depth"]), O.pid_mean(to_np(U))[2], FP32_TOL, "after the error")
     with pytest.raises(ValueError):
         H.mean_weighted(U, torch.ones(19, dtype=torch.float64, device="cuda"))
+
+
+# --------------------------------------------------------------------------------------
+# bfloat16 output of the isovalue map
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kind,sup,sigma", [("normal", 0, 0.05), ("normal", 1, 0.05),
+                                            ("normal", 0, 0.0), ("uniform", 1, HW),
+                                            ("level", 0, HW)])
+@pytest.mark.parametrize("N,Hh,W", [(3, 17, 11), (12, 64, 80)])
+def test_soft_masks_bf16(H, kind, sup, sigma, N, Hh, W):
+    import torch
+    F = _fields(N, Hh, W, seed=11)
+    Fd = _dev(F)
+    a = H.soft_masks(Fd, MU, sigma, sup, kind=kind)
+    b = H.soft_masks(Fd, MU, sigma, sup, kind=kind, dtype=torch.bfloat16)
+    H.sync()
+    assert b.dtype == torch.bfloat16
+    # the float32 masks rounded to nearest even, element for element
+    assert torch.equal(b, a.to(torch.bfloat16))
+    if kind == "normal":
+        ref = O.iso_soft_mask(F, MU, sigma, bool(sup))
+    else:
+        ref = _masks(F, kind, sup)
+    # bfloat16 keeps 8 significant bits: half an ulp is at most 2^-9 of the value
+    err = np.abs(b.float().cpu().numpy() - ref)
+    assert np.all(err <= np.abs(ref) * 2.0 ** -9 + 1e-6)
