@@ -241,6 +241,6 @@ def test_soft_masks_bf16(H, kind, sup, sigma, N, Hh, W):
         ref = O.iso_soft_mask(F, MU, sigma, bool(sup))
     else:
         ref = _masks(F, kind, sup)
-    # bfloat16 keeps 8 significant bits: half an ulp is at most 2^-9 of the value
+    # bfloat16 keeps 8 significant bits (7 stored): half an ulp is at most 2^-8 of the value
     err = np.abs(b.float().cpu().numpy() - ref)
-    assert np.all(err <= np.abs(ref) * 2.0 ** -9 + 1e-6)
+    assert np.all(err <= np.abs(ref) * 2.0 ** -8 + 1e-6)
