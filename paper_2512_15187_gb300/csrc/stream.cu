@@ -121,6 +121,36 @@ __device__ void reduce_columns(const Src* src, int rows, int cols, int cb, doubl
   __syncthreads();
 }
 
+// acc + comp carries the running sum; comp holds the low-order part lost by acc (Kahan).
+__device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
+  const float y = v - comp;
+  const float t = acc + y;
+  comp = (t - acc) - y;
+  acc = t;
+}
+
+// Row r of an [N][N] FP32 matrix written by this kernel's grid (read through L2), dotted
+// with the shared vector v (v == nullptr: summed), by one warp: lane l takes the columns
+// l, l + 32, ... in order, then a fixed xor tree. A lane loads up to 8 columns before it
+// adds them, so the row costs one L2 round trip instead of one per column (kGramMaxN = 256
+// columns = 8 per lane).
+__device__ __forceinline__ float row_dot_warp(const float* row, const float* v, int N, int ln) {
+  static_assert(kGramMaxN <= 256, "at most 8 columns per lane");
+  float x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = ln + 32 * k;
+    x[k] = j < N ? __ldcg(row + j) : 0.f;
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int j = ln + 32 * k;
+    if (j < N) acc = v ? fmaf(x[k], v[j], acc) : acc + x[k];
+  }
+  return warp_sum(acc);
+}
+
 __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_constant__ FinParams p) {
   const FinDesc& d = fin_desc(p, blockIdx.y);
   if (static_cast<int>(blockIdx.x) >= d.slices) return;
@@ -147,11 +177,22 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
       const int col = (cb - nb_stream) * 1024 + static_cast<int>(threadIdx.x);
       const int NN = N * N;
       if (col < NN) {
-        double acc = 0.0;
-#pragma unroll 4
-        for (int r = 0; r < d.n_gchunks; ++r)
-          acc += static_cast<double>(__ldcs(d.gpart + static_cast<size_t>(r) * NN + col));
-        reinterpret_cast<float*>(d.sums + 4 * N)[col] = static_cast<float>(acc);
+        // Compensated (Kahan) FP32 sum in chunk order: close to an FP64 sum, at the FP32
+        // rate (GB300 issues FP64 adds at a small fraction of it, and this sum has
+        // n_gchunks * N^2 terms per ensemble). 8 chunks' values are loaded before they are
+        // added, so the loop is not one memory round trip per chunk.
+        float acc = 0.f, comp = 0.f;
+        const float* src = d.gpart + col;
+        int r = 0;
+        for (; r + 8 <= d.n_gchunks; r += 8) {
+          float v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = __ldcs(src + static_cast<size_t>(r + k) * NN);
+#pragma unroll
+          for (int k = 0; k < 8; ++k) kahan_add(acc, comp, v[k]);
+        }
+        for (; r < d.n_gchunks; ++r) kahan_add(acc, comp, __ldcs(src + static_cast<size_t>(r) * NN));
+        reinterpret_cast<float*>(d.sums + 4 * N)[col] = acc;
       }
     }
   }
@@ -257,14 +298,23 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     // Raw sums: row r of the stored array is G'_{., r}, which equals row r of G' up to
     // the rounding of the tensor-core sums.
     for (int r = wi; r < N; r += kFinThreads / 32) {
-      float acc = 0.f;
-      for (int j = ln; j < N; j += 32) acc += __ldcg(Cg + r * N + j);
-      acc = warp_sum(acc);
+      const float acc = row_dot_warp(Cg + r * N, nullptr, N, ln);
       if (ln == 0) sdn[r] = acc;
     }
-    for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
-      const int r = k / N, c = k - r * N;
-      C0[k] = 0.5f * (__ldcg(Cg + r + c * N) + __ldcg(Cg + k));
+    // C0 = (G' + G'^T) / 2, one warp per row, each lane's 8 columns loaded together
+    for (int r = wi; r < N; r += kFinThreads / 32) {
+      float a[8], b[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = ln + 32 * k;
+        a[k] = c < N ? __ldcg(Cg + r + c * N) : 0.f;
+        b[k] = c < N ? __ldcg(Cg + r * N + c) : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = ln + 32 * k;
+        if (c < N) C0[r * N + c] = 0.5f * (a[k] + b[k]);
+      }
     }
     __syncthreads();
     if (i < N) {
@@ -278,9 +328,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     // more than 2^-22 relative (at most 24 sweeps).
     for (int it = 0; it < 24; ++it) {
       for (int r = wi; r < N; r += kFinThreads / 32) {
-        float acc = 0.f;
-        for (int j = ln; j < N; j += 32) acc = fmaf(__ldcg(C0 + r * N + j), sd[j], acc);
-        acc = warp_sum(acc);
+        const float acc = row_dot_warp(C0 + r * N, sd, N, ln);
         if (ln == 0) sdn[r] = (sd[r] > 0.f && acc > 0.f) ? sqrtf(sd[r] * sdm[r] / acc) : 0.f;
       }
       __syncthreads();
@@ -295,9 +343,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     if (i < N) sdm[i] = m > 0.0 ? static_cast<float>(sd[i] / m) : 0.f;
     __syncthreads();
     for (int r = wi; r < N; r += kFinThreads / 32) {
-      float acc = 0.f;
-      for (int j = ln; j < N; j += 32) acc = fmaf(__ldcg(C0 + r * N + j), sdm[j], acc);
-      acc = warp_sum(acc);
+      const float acc = row_dot_warp(C0 + r * N, sdm, N, ln);
       if (ln == 0) sdn[r] = sd[r] * acc;
     }
     __syncthreads();
@@ -330,11 +376,22 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     if (i == 0 && d.err_est) d.err_est[0] = sred[0];
     if (d.P) {
       const float* C0 = reinterpret_cast<const float*>(S + 4 * N) + N * N;   // symmetrised above
-      for (int k = threadIdx.x; k < N * N; k += kFinThreads) {
-        const int r = k / N, cc = k - r * N;   // P[r][cc] = C_{r,cc} / m_r
+      // P[r][cc] = C_{r,cc} / m_r: one warp per row, one FP64 division per row
+      const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
+      for (int r = wi; r < N; r += kFinThreads / 32) {
         const double mr = __ldcg(S + r);
-        const double c = static_cast<double>(sd[r] * sd[cc] * __ldcg(C0 + k));
-        d.P[k] = mr > 0.0 ? c / mr : 0.0;
+        const double inv = mr > 0.0 ? 1.0 / mr : 0.0;
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int cc = ln + 32 * k;
+          x[k] = cc < N ? __ldcg(C0 + r * N + cc) : 0.f;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int cc = ln + 32 * k;
+          if (cc < N) d.P[static_cast<size_t>(r) * N + cc] = static_cast<double>(sd[r] * sd[cc] * x[k]) * inv;
+        }
       }
     }
   }
