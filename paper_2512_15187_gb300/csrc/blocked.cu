@@ -138,24 +138,29 @@ __global__ void __launch_bounds__(256) accum_kernel(const __grid_constant__ Bloc
 }
 
 // rank[i] = #{j : d_j > d_i or (d_j == d_i and j < i)}; depths staged through shared memory.
+// rank[i] += number of members j in this block's slice of [0, N) (blockIdx.y of gridDim.y
+// equal slices) that are deeper than i, or as deep with a lower index. The slices run as
+// separate blocks for occupancy; the counts are integers, so adding them with atomics
+// gives the same ranks in any order. rank must be zero before the launch.
 __global__ void __launch_bounds__(256) rank_kernel(const double* depth, int64_t N, int32_t* rank) {
-  __shared__ double tile[2048];
+  __shared__ unsigned long long tile[2048];   // order keys of the depths
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const double di = i < N ? depth[i] : 0.0;
+  const unsigned long long di = order_key(i < N ? depth[i] : 0.0);
+  const int64_t lo = N * blockIdx.y / gridDim.y, hi = N * (blockIdx.y + 1) / gridDim.y;
   int64_t r = 0;
-  for (int64_t j0 = 0; j0 < N; j0 += 2048) {
-    const int64_t n = N - j0 < 2048 ? N - j0 : 2048;
+  for (int64_t j0 = lo; j0 < hi; j0 += 2048) {
+    const int64_t n = hi - j0 < 2048 ? hi - j0 : 2048;
     __syncthreads();
-    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) tile[k] = depth[j0 + k];
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) tile[k] = order_key(depth[j0 + k]);
     __syncthreads();
     if (i < N) {
       for (int64_t k = 0; k < n; ++k) {
-        const double dj = tile[k];
+        const unsigned long long dj = tile[k];
         r += (dj > di) || (dj == di && j0 + k < i);
       }
     }
   }
-  if (i < N) rank[i] = static_cast<int32_t>(r);
+  if (i < N && r > 0) atomicAdd(rank + i, static_cast<int32_t>(r));
 }
 
 }  // namespace pidk
@@ -254,8 +259,12 @@ pid_status run_blocked(pid_handle h, const EnsInput& in, const EnsOutputs& out, 
     if ((st = launch_fin_one(h, f2, s)) != PID_OK) return st;
   }
   if (big && out.rank) {
-    rank_kernel<<<static_cast<unsigned>((N + 255) / 256), 256, 0, s>>>(fd.depth, N, out.rank);
-    const cudaError_t e = cudaGetLastError();
+    const unsigned slices = static_cast<unsigned>(N / 4096 < 1 ? 1 : (N / 4096 > 16 ? 16 : N / 4096));
+    cudaError_t e = cudaMemsetAsync(out.rank, 0, static_cast<size_t>(N) * sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "rank reset");
+    rank_kernel<<<dim3(static_cast<unsigned>((N + 255) / 256), slices), 256, 0, s>>>(fd.depth, N,
+                                                                                    out.rank);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(h, e, "rank kernel launch");
   }
   return PID_OK;

@@ -187,6 +187,15 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Order-preserving integer key of a double: for non-NaN a, b, a < b <=> key(a) < key(b) and
+// a == b <=> key(a) == key(b) (-0 is folded into +0). GB300 issues FP64 compares at a small
+// fraction of the integer rate, so the O(N^2) rank counts compare keys.
+__device__ __forceinline__ unsigned long long order_key(double d) {
+  const long long b = __double_as_longlong(d + 0.0);
+  return b >= 0 ? static_cast<unsigned long long>(b) | 0x8000000000000000ull
+                : ~static_cast<unsigned long long>(b);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

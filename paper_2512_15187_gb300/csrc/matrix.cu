@@ -79,17 +79,17 @@ matrix_depth_kernel(const __grid_constant__ MatrixParams p) {
 __global__ void __launch_bounds__(kMatThreads) group_rank_kernel(const double* depth,
                                                                  const int32_t* labels, int64_t N,
                                                                  int32_t* rank) {
-  __shared__ double td[kMatThreads];
+  __shared__ unsigned long long td[kMatThreads];   // order keys of the depths
   __shared__ int32_t tl[kMatThreads];
   const int64_t i = static_cast<int64_t>(blockIdx.x) * kMatThreads + threadIdx.x;
-  const double di = i < N ? depth[i] : 0.0;
+  const unsigned long long di = order_key(i < N ? depth[i] : 0.0);
   const int32_t li = (i < N && labels) ? labels[i] : 0;
   int64_t r = 0;
   for (int64_t j0 = 0; j0 < N; j0 += kMatThreads) {
     const int64_t n = N - j0 < kMatThreads ? N - j0 : kMatThreads;
     __syncthreads();
     if (threadIdx.x < n) {
-      td[threadIdx.x] = depth[j0 + threadIdx.x];
+      td[threadIdx.x] = order_key(depth[j0 + threadIdx.x]);
       tl[threadIdx.x] = labels ? labels[j0 + threadIdx.x] : 0;
     }
     __syncthreads();

@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   const FinDesc& d = fin_desc(p, blockIdx.y);
   if (static_cast<int>(blockIdx.x) >= d.slices) return;
   __shared__ double scratch[32][33];
-  __shared__ double sdepth[1024];
+  __shared__ unsigned long long skey[1024];   // order keys of the depths (ranks)
   __shared__ double sred[1024];
   __shared__ float sd[kGramMaxN], sdn[kGramMaxN];   // Gram calibration scales
   __shared__ float sdm[kGramMaxN];                  // d_j / m_j (0 for zero mass)
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
       depth = fmin(in_in, in_out);
     }
   }
-  sdepth[i] = (i < N) ? depth : 0.0;
+  skey[i] = order_key((i < N) ? depth : 0.0);
   sred[i] = err;
   __syncthreads();
   if (i < N) {
@@ -360,10 +360,11 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     if (d.in_in) d.in_in[i] = in_in;
     if (d.in_out) d.in_out[i] = in_out;
     if (d.rank) {
+      const unsigned long long ki = skey[i];
       int r = 0;
       for (int j = 0; j < N; ++j) {
-        const double dj = sdepth[j];
-        r += (dj > depth) || (dj == depth && j < i);
+        const unsigned long long kj = skey[j];
+        r += (kj > ki) || (kj == ki && j < i);
       }
       d.rank[i] = r;
     }
