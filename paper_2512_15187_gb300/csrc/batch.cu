@@ -160,12 +160,10 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       }
     }
   }
-  const int n_sdesc = static_cast<int>(count + pass2.size() * 0);
   int n_s = 0;
   for (auto& kv : pass1) n_s += static_cast<int>(kv.second.size());
   for (auto& kv : pass2) n_s += static_cast<int>(kv.second.size());
   for (auto& kv : gram_cls) n_s += static_cast<int>(kv.second.size());
-  (void)n_sdesc;
   int n_lin = 0, n_logical = 0;
   for (int e = 0; e < count; ++e) {
     if (owner(e) != e) continue;
@@ -218,7 +216,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   bp->work_bytes = off;
   if (n_logical > kMaxTickets) return fail(h, PID_ERR_UNSUPPORTED, "too many ensembles in one batch");
 
-  auto add_stream_class = [&](const ClassKey& k, const std::vector<int>& members, bool coef_pass) {
+  auto add_stream_class = [&](const std::vector<int>& members, bool coef_pass) {
     Launch L;
     L.kind = Launch::STREAM;
     L.first = static_cast<int>(bp->sdesc.size());
@@ -244,7 +242,6 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     }
     L.total_units = units;
     bp->launches.push_back(L);
-    (void)k;
   };
   auto fin_for = [&](int e, int kind) {
     FinDesc f;
@@ -305,7 +302,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.total_units = units;
     bp->launches.push_back(L);
   }
-  for (auto& kv : pass1) add_stream_class(kv.first, kv.second, false);
+  for (auto& kv : pass1) add_stream_class(kv.second, false);
   {
     Launch L;
     L.kind = Launch::FIN;
@@ -321,7 +318,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   }
   // Phase 2: exact full PID, second streaming pass and its finalisation.
   if (n_lin) {
-    for (auto& kv : pass2) add_stream_class(kv.first, kv.second, true);
+    for (auto& kv : pass2) add_stream_class(kv.second, true);
     Launch L;
     L.kind = Launch::FIN;
     L.first = static_cast<int>(bp->fdesc.size());

@@ -319,7 +319,7 @@ static std::string stream_tune_key(const StreamCfg& cfg, bool coef, const pidk::
                                    int32_t max_n, int64_t cells) {
   int lg = 0;
   while ((int64_t(1) << (lg + 1)) <= cells) ++lg;
-  const pidk::EnsDesc& d = sp.descs ? sp.one : sp.one;  // iso / weights flags come from `one`
+  const pidk::EnsDesc& d = sp.one;   // iso and weight flags: those of the class's first ensemble
   char buf[160];
   std::snprintf(buf, sizeof(buf), "stream v%d k%d g%d s%d c%d iso%d w%d tma%d n%d m%d", cfg.vec,
                 cfg.mpw, cfg.G,
