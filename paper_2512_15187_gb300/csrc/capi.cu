@@ -3,6 +3,7 @@
 // finalisation) and gram.cu (tensor-core Gram for full PID).
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -60,8 +61,15 @@ static cudaEvent_t pool_event(pid_handle h) {
   return e;
 }
 
+// NVTX range names of the kernel kinds (pid_kernel_kind order): every launch the library
+// makes is bracketed by a host range, so external profilers attribute kernels to the calls.
+static const char* const kNvtxNames[PID_KERNEL_KINDS] = {
+    "pid: streaming pass", "pid: tensor-core Gram", "pid: finalisation", "pid: isovalue map",
+    "pid: contour bands"};
+
 ProfScope::ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStream_t s)
     : h_(h), s_(s) {
+  nvtxRangePushA(kind >= 0 && kind < PID_KERNEL_KINDS ? kNvtxNames[kind] : "pid");
   if (!h_ || !h_->profiling) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s_, &cs);
@@ -74,6 +82,7 @@ ProfScope::ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStr
 
 ProfScope::~ProfScope() {
   if (idx_ >= 0) cudaEventRecord(h_->prof_pending[idx_].stop, s_);
+  nvtxRangePop();
 }
 
 static void prof_drain(pid_handle h) {
