@@ -73,3 +73,23 @@ def test_bands_host_checks(lib):
     from paper_2512_15187_gb300 import binding as B
     assert lib.pid_contour_bands(None, None, 4, 10, 10, None, None, 0.5, 0.5, None, None) == \
         B.PID_ERR_INVALID_ARG
+
+
+def test_binding_rejects_tensors_a_kernel_cannot_read():
+    # host tensors, wrong dtypes and wrong lengths fail in the binding, before any call
+    import torch
+
+    from paper_2512_15187_gb300 import binding as B
+    with pytest.raises(ValueError):
+        B._check_matrix(torch.zeros(2, 3), "data")                      # host memory
+    with pytest.raises(ValueError):
+        B._check_matrix(torch.zeros(2, 3, dtype=torch.float64), "data")
+    dev = torch.device("cuda", 0)
+    assert B._weights(None, 3, dev) is None
+    with pytest.raises(ValueError):
+        B._weights(torch.ones(3), 3, dev)                                # host memory
+    iso = B.make_iso((0.5, 0.1, 1, "uniform"))
+    assert (iso.kind, iso.superlevel, iso.mu, iso.sigma) == (B.PID_ISO_UNIFORM, 1, 0.5, 0.1)
+    assert B.make_iso((0.5, 0.05)).kind == B.PID_ISO_NORMAL
+    with pytest.raises(KeyError):
+        B.make_iso((0.5, 0.1, 0, "triangle"))
