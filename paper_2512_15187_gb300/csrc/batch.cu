@@ -5,7 +5,9 @@
 // class runs as one persistent launch of the streaming kernel over the flat list of all its
 // (ensemble, chunk) units; one finalisation launch then serves every ensemble. The exact
 // full PID adds a second streaming launch per class and a second finalisation. Full PID on
-// tensor cores runs one Gram launch per class instead of the first streaming pass.
+// tensor cores runs one Gram launch per class instead of the first streaming pass; above 256
+// members the Gram is row-block-tiled (operands staged in HBM, one launch pair per ensemble)
+// and the ensemble's exact PID-mean sums come from the first streaming pass of its class.
 //
 // The whole sequence (descriptor upload + launches) is recorded once into a CUDA graph and
 // replayed while the caller submits the same batch layout (same pointers and shapes).
@@ -65,7 +67,7 @@ struct ClassKey {
 };
 
 struct Launch {
-  enum Kind { STREAM, GRAM, FIN } kind;
+  enum Kind { STREAM, GRAM, FIN, TILED } kind;
   int first, count;        // descriptor range (stream/gram: EnsDesc index; fin: FinDesc index)
   StreamCfg cfg;
   bool coef = false;
@@ -80,6 +82,12 @@ struct Launch {
   int iso_mode = 0;
   struct Scale { const float* w; int64_t M; float* out; };
   std::vector<Scale> scales;  // FP8 operand scales to compute before the Gram launch
+  // TILED launches (one ensemble or time step): operand staging + tiled Gram
+  EnsInput in;
+  TiledPlan tp;
+  void* op = nullptr;
+  float* gpart = nullptr;
+  float* scale = nullptr;
 };
 
 struct BatchPlan {
@@ -119,7 +127,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   std::vector<EnsInput> in(count);
   std::vector<EnsPlan> pl(count);
   std::vector<GramPlan> gp(count);
-  std::vector<int> is_gram(count, 0), is_lin(count, 0), stored(count, 0);
+  std::vector<TiledPlan> tp(count);
+  std::vector<int> is_gram(count, 0), is_lin(count, 0), stored(count, 0), tiled(count, 0);
   std::vector<EnsPlan> pl2(count);   // pass 2 over the stored soft masks
   for (int e = 0; e < count; ++e) {
     pid_status st = to_input(h, ens[e], &in[e]);
@@ -127,7 +136,12 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     if ((st = plan_stream(h, in[e], &pl[e])) != PID_OK) return st;
     is_gram[e] = in[e].mode == PID_MODE_FULL && in[e].precision != PID_FP32;
     is_lin[e] = in[e].mode == PID_MODE_FULL_LINEAR || (in[e].mode == PID_MODE_FULL && !is_gram[e]);
-    if (is_gram[e] && (st = plan_gram(h, in[e], &gp[e])) != PID_OK) return st;
+    tiled[e] = is_gram[e] && in[e].N > kGramMaxN;
+    if (tiled[e]) {
+      if ((st = plan_gram_tiled(h, in[e], &tp[e])) != PID_OK) return st;
+    } else if (is_gram[e] && (st = plan_gram(h, in[e], &gp[e])) != PID_OK) {
+      return st;
+    }
     stored[e] = store_u && is_lin[e] && in[e].is_field;
   }
   if (st4) {
@@ -135,7 +149,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       if (in[e].N != in[0].N || in[e].M != in[0].M || in[e].w != in[0].w ||
           in[e].is_field != in[0].is_field || in[e].mode != in[0].mode ||
           in[e].precision != in[0].precision || pl[e].desc.n_chunks != pl[0].desc.n_chunks ||
-          (is_gram[e] && gp[e].n_gchunks != gp[0].n_gchunks))
+          (is_gram[e] && gp[e].n_gchunks != gp[0].n_gchunks) ||
+          (tiled[e] && tp[e].n_gchunks != tp[0].n_gchunks))
         return fail(h, PID_ERR_INVALID_ARG, "the time steps of a space-time ensemble differ");
     }
   }
@@ -145,7 +160,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   //  isovalue kind)
   std::map<std::pair<int, int>, std::vector<int>> gram_cls;
   for (int e = 0; e < count; ++e) {
-    if (is_gram[e]) {
+    if (is_gram[e] && !tiled[e]) {
       gram_cls[{(((gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 2 + (gp[e].wide ? 1 : 0)) * 32 +
                  gp[e].G) * 32 + gp[e].mpw,
                 iso_kind(gp[e].desc.iso_mode)}]
@@ -178,24 +193,33 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   std::vector<double*> part(count), sums(count);
   std::vector<float*> coef(count), gpart(count, nullptr);
   std::vector<float*> scale(count, nullptr);
+  // Operand planes of the tiled Gram: one buffer, reused by the tiled launches in turn.
+  size_t op_bytes = 0;
+  for (int e = 0; e < count; ++e)
+    if (tiled[e]) op_bytes = std::max(op_bytes, tp[e].op_bytes);
+  void* op_buf = nullptr;
+  if (op_bytes) { op_buf = base + off; off += align_up(static_cast<int64_t>(op_bytes), 1024); }
+  // chunks of an ensemble's (m, A) partials and of its Gram partials
+  auto part_chunks = [&](int e) { return is_gram[e] && !tiled[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks; };
+  auto gram_chunks = [&](int e) { return tiled[e] ? tp[e].n_gchunks : gp[e].n_gchunks; };
   for (int e = 0; e < count; ++e) {
     const int o = owner(e);
     if (o == e) {
-      const size_t pb = is_gram[e] ? std::max(pl[e].part_bytes, gp[e].part_bytes) : pl[e].part_bytes;
+      const size_t pb = is_gram[e] && !tiled[e] ? std::max(pl[e].part_bytes, gp[e].part_bytes) : pl[e].part_bytes;
       part[e] = reinterpret_cast<double*>(base + off); off += pb * steps;
       sums[e] = reinterpret_cast<double*>(base + off); off += pl[e].sums_bytes;
       coef[e] = reinterpret_cast<float*>(base + off); off += pl[e].coef_bytes;
       if (is_gram[e]) {
         scale[e] = reinterpret_cast<float*>(base + off); off += 256;
-        gpart[e] = reinterpret_cast<float*>(base + off); off += gp[e].gpart_bytes * steps;
+        gpart[e] = reinterpret_cast<float*>(base + off);
+        off += (tiled[e] ? tp[e].gpart_bytes : gp[e].gpart_bytes) * steps;
       }
     } else {   // a later time step: its partials follow those of the steps before it
-      const int64_t n_ch = is_gram[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks;
-      part[e] = part[o] + static_cast<int64_t>(e) * n_ch * 2 * in[e].N;
+      part[e] = part[o] + static_cast<int64_t>(e) * part_chunks(e) * 2 * in[e].N;
       sums[e] = sums[o];
       coef[e] = coef[o];
       scale[e] = scale[o];
-      if (is_gram[e]) gpart[e] = gpart[o] + static_cast<int64_t>(e) * n_ch * in[e].N * in[e].N;
+      if (is_gram[e]) gpart[e] = gpart[o] + static_cast<int64_t>(e) * gram_chunks(e) * in[e].N * in[e].N;
     }
     pl[e].desc.part = part[e];
     if (stored[e]) {
@@ -248,7 +272,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     std::memset(&f, 0, sizeof(f));
     f.part = part[e];
     f.N = static_cast<int32_t>(in[e].N);
-    f.n_chunks = steps * (is_gram[e] ? gp[e].n_gchunks : pl[e].desc.n_chunks);
+    f.n_chunks = steps * part_chunks(e);
     f.kind = kind;
     f.sums = sums[e];
     f.coef = coef[e];
@@ -260,7 +284,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     if (kind != FIN_LIN2) { f.mass = o.mass; f.mean_depth = o.mean_depth; }
     if (kind == FIN_GRAM) {
       f.gpart = gpart[e];
-      f.n_gchunks = steps * gp[e].n_gchunks;
+      f.n_gchunks = steps * gram_chunks(e);
       f.P = o.P;
       f.err_est = o.err_est;
     }
@@ -303,6 +327,19 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     bp->launches.push_back(L);
   }
   for (auto& kv : pass1) add_stream_class(kv.second, false);
+  for (int e = 0; e < count; ++e) {
+    if (!tiled[e]) continue;
+    Launch L;
+    L.kind = Launch::TILED;
+    L.first = e;
+    L.count = 1;
+    L.in = in[e];
+    L.tp = tp[e];
+    L.op = op_buf;
+    L.gpart = gpart[e];
+    L.scale = scale[e];   // the steps of a space-time ensemble share w, hence the scale
+    bp->launches.push_back(L);
+  }
   {
     Launch L;
     L.kind = Launch::FIN;
@@ -365,6 +402,9 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       }
       pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units,
                                         L.cells, L.iso_mode, L.bytes, L.flops, s);
+      if (st != PID_OK) return st;
+    } else if (L.kind == Launch::TILED) {
+      pid_status st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, s);
       if (st != PID_OK) return st;
     } else {
       FinParams fp;

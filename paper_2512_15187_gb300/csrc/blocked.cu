@@ -186,7 +186,7 @@ static pid_status blocked_pass(pid_handle h, const BlockedParams& p, double byte
 pid_status run_blocked(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s) {
   if (in.mode == PID_MODE_FULL && in.precision != PID_FP32)
     return fail(h, PID_ERR_UNSUPPORTED,
-                "the tensor-core Gram takes N <= 256 in this build; use PID_MODE_FULL_LINEAR");
+                "the tensor-core Gram takes N <= 512; use PID_MODE_FULL_LINEAR");
   if (in.validate)
     return fail(h, PID_ERR_UNSUPPORTED, "validation is not available for N > 512");
   const bool linear = in.mode != PID_MODE_MEAN;

@@ -137,6 +137,23 @@ bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Operand plane [outer rows][inner elements] of 2-byte (BF16) or 1-byte (E4M3) elements,
+// read in boxes of 128 bytes x 128 rows in the 128-byte swizzle layout of the tensor cores;
+// elements past the extents read as zero.
+bool encode_2d_sw128(CUtensorMap* m, const void* base, int elem_bytes, uint64_t inner,
+                     uint64_t outer, uint64_t row_bytes) {
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn || (elem_bytes != 1 && elem_bytes != 2)) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {static_cast<cuuint32_t>(128 / elem_bytes), 128};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+            const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
   EncodeTiledFn fn = get_encode_fn();
   if (!fn) return false;
@@ -493,6 +510,50 @@ pid_status launch_member_coef_one(pid_handle h, const double* r, int64_t N, floa
   return PID_OK;
 }
 
+// Full PID on the tensor cores for 256 < N <= 512: the streaming pass gives the exact
+// PID-mean sums (m_i, N A_i) that calibrate the Gram, the operand rows are staged in HBM,
+// the tiled kernel forms the chunk partial Grams, and the finalisation does the rest.
+static pid_status run_gram_tiled(pid_handle h, const EnsInput& in, EnsPlan& pl,
+                                 const EnsOutputs& out, cudaStream_t s) {
+  TiledPlan tp;
+  pid_status st = plan_gram_tiled(h, in, &tp);
+  if (st != PID_OK) return st;
+  const size_t off_sums = pl.part_bytes;
+  const size_t off_coef = off_sums + pl.sums_bytes;
+  const size_t off_scale = off_coef + pl.coef_bytes;
+  const size_t off_gpart = off_scale + 256;
+  const size_t off_op = off_gpart + tp.gpart_bytes;
+  st = ensure_workspace(h, off_op + tp.op_bytes, s);
+  if (st != PID_OK) return st;
+  char* ws = static_cast<char*>(h->ws);
+  double* part = reinterpret_cast<double*>(ws);
+  float* gpart = reinterpret_cast<float*>(ws + off_gpart);
+  pl.desc.part = part;
+  if ((st = launch_stream_one(h, pl, nullptr, s)) != PID_OK) return st;
+  st = launch_gram_tiled_one(h, in, tp, ws + off_op, gpart, reinterpret_cast<float*>(ws + off_scale), s);
+  if (st != PID_OK) return st;
+  FinDesc fd;
+  std::memset(&fd, 0, sizeof(fd));
+  fd.kind = FIN_GRAM;
+  fd.part = part;
+  fd.N = pl.desc.N;
+  fd.n_chunks = pl.desc.n_chunks;
+  fd.gpart = gpart;
+  fd.n_gchunks = tp.n_gchunks;
+  fd.sums = reinterpret_cast<double*>(ws + off_sums);
+  fd.coef = reinterpret_cast<float*>(ws + off_coef);
+  fd.ticket = h->tickets;
+  fd.depth = out.depth;
+  fd.in_in = out.in_in;
+  fd.in_out = out.in_out;
+  fd.rank = out.rank;
+  fd.mass = out.mass;
+  fd.mean_depth = out.mean_depth;
+  fd.P = out.P;
+  fd.err_est = out.err_est;
+  return launch_fin_one(h, fd, s);
+}
+
 pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, cudaStream_t s) {
   if (in.N > kMaxMembers) return run_blocked(h, in, out, s);
   EnsPlan pl;
@@ -500,6 +561,7 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
   if (st != PID_OK) return st;
   const bool gram = in.mode == PID_MODE_FULL && in.precision != PID_FP32;
   const bool linear = in.mode == PID_MODE_FULL_LINEAR || (in.mode == PID_MODE_FULL && !gram);
+  if (gram && in.N > kGramMaxN) return run_gram_tiled(h, in, pl, out, s);
   GramPlan gp;
   size_t part_bytes = pl.part_bytes, gram_bytes = 0;
   if (gram) {

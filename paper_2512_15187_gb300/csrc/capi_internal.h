@@ -127,6 +127,24 @@ struct GramPlan {
   double bytes = 0, flops = 0;
 };
 
+// Row-block-tiled Gram for 256 < N <= 512 (gram.cu, kernels in gram_tiled.cu): the
+// operand rows are staged in HBM and each CTA computes one tile of one cell chunk.
+struct TiledPlan {
+  int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
+  int R = 0;               // 128-row blocks
+  int tiles = 0;           // tiles per chunk (upper block triangle, column blocks in pairs)
+  int64_t ldo = 0;         // operand row stride in elements (a multiple of 64)
+  int elem_bytes = 2;      // 2 (BF16) or 1 (E4M3)
+  int planes = 1;          // 2 for split BF16
+  int64_t chunk_cells = 0;
+  int n_gchunks = 0;
+  int stages = 2;
+  size_t smem = 0;
+  size_t op_bytes = 0;     // operand planes
+  size_t gpart_bytes = 0;  // [n_gchunks][N][N] float32
+  double op_rw_bytes = 0, gemm_bytes = 0, flops = 0;
+};
+
 class DeviceGuard {
  public:
   explicit DeviceGuard(int dev);
@@ -159,6 +177,8 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
 bool encode_2d(CUtensorMap* m, const void* base, uint64_t inner, uint64_t outer, uint64_t row_bytes,
                uint32_t box_inner, uint32_t box_outer);
 bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
+bool encode_2d_sw128(CUtensorMap* m, const void* base, int elem_bytes, uint64_t inner,
+                     uint64_t outer, uint64_t row_bytes);
 
 // gram.cu
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
@@ -171,6 +191,12 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDe
                              int count, int total_units, int64_t total_work, int iso_mode,
                              double bytes, double flops,
                              cudaStream_t s);
+
+pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp);
+// Operand staging and the tiled Gram launch; `op` holds tp.op_bytes, `gpart` tp.gpart_bytes,
+// `scale` one float (E4M3 of a weighted ensemble).
+pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
+                                 float* gpart, float* scale, cudaStream_t s);
 
 // batch.cu
 void destroy_batch_cache(pid_handle h);

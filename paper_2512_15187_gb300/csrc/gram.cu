@@ -17,8 +17,7 @@ static int64_t rup(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   *gp = GramPlan{};
   if (in.N > kGramMaxN)
-    return fail(h, PID_ERR_UNSUPPORTED,
-                "the tensor-core Gram takes N <= 256 in this build; use PID_MODE_FULL_LINEAR");
+    return fail(h, PID_ERR_UNSUPPORTED, "the fused tensor-core Gram takes N <= 256");
   const uintptr_t a = reinterpret_cast<uintptr_t>(in.data);
   gp->tma = in.ld % 4 == 0 && a % 16 == 0 && (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
   gp->prec = in.precision;
@@ -145,6 +144,104 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* de
   const int grid = std::max(1, std::min(h->sms, (total_units + ng - 1) / ng));
   return gram_launch(h, gpar, gp.G, gp.mpw, gp.wide, gp.prec, iso_mode, grid, gp.smem, bytes,
                      flops, s);
+}
+
+// ---------------------------------------------------------------------------------------
+// Row-block-tiled Gram (256 < N <= 512)
+// ---------------------------------------------------------------------------------------
+
+pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
+  *tp = TiledPlan{};
+  if (in.N > kGramTiledMaxN)
+    return fail(h, PID_ERR_UNSUPPORTED,
+                "the tensor-core Gram takes N <= 512; use PID_MODE_FULL_LINEAR");
+  tp->prec = in.precision;
+  tp->R = static_cast<int>((in.N + 127) / 128);
+  tp->tiles = 0;
+  for (int r = 0; r < tp->R; ++r) tp->tiles += (tp->R - r + 1) / 2;
+  tp->elem_bytes = in.precision == PID_FP8 ? 1 : 2;
+  tp->planes = in.precision == PID_SPLIT_BF16 ? 2 : 1;
+  tp->ldo = rup(in.M, 64);
+  // Chunks: about two waves of CTAs over the SMs; every chunk adds an N x N FP32 partial
+  // (written by the tiles, read by the finalisation), so chunks stay at 4096 cells or more.
+  const int64_t target = std::max<int64_t>(1, 2 * static_cast<int64_t>(h->sms) / tp->tiles);
+  int64_t chunk = rup((in.M + target - 1) / target, 256);
+  chunk = std::min<int64_t>(std::max<int64_t>(chunk, 4096), 65536);
+  tp->chunk_cells = chunk;
+  tp->n_gchunks = static_cast<int>((in.M + chunk - 1) / chunk);
+  const size_t cap = static_cast<size_t>(h->max_smem > 0 ? h->max_smem : 232448);
+  tp->stages = 6;
+  while (tp->stages > 2 && gram_tiled_smem_bytes(tp->prec, tp->stages) > cap) --tp->stages;
+  tp->smem = gram_tiled_smem_bytes(tp->prec, tp->stages);
+  if (tp->smem > cap) return fail(h, PID_ERR_UNSUPPORTED, "tiled Gram stages do not fit shared memory");
+  const int64_t plane = rup(static_cast<int64_t>(in.N) * tp->ldo * tp->elem_bytes, 1024);
+  tp->op_bytes = static_cast<size_t>(tp->planes * plane);
+  tp->gpart_bytes = rup(static_cast<int64_t>(tp->n_gchunks) * in.N * in.N * 4, 256);
+  const double nm = static_cast<double>(in.N) * in.M;
+  tp->op_rw_bytes = 4.0 * nm + (in.w ? 4.0 * in.M : 0.0) + nm * tp->elem_bytes * tp->planes;
+  tp->gemm_bytes = nm * tp->elem_bytes * tp->planes;
+  // useful products: the upper block triangle of 128-row blocks, as issued
+  double blocks = 0;
+  for (int r = 0; r < tp->R; ++r) blocks += tp->R - r;
+  tp->flops = (in.precision == PID_SPLIT_BF16 ? 3.0 : 1.0) * 2.0 * blocks * 128.0 * 128.0 * in.M;
+  return PID_OK;
+}
+
+pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
+                                 float* gpart, float* scale, cudaStream_t s) {
+  const float* op_scale = nullptr;
+  if (tp.prec == PID_FP8 && in.w) {
+    cudaError_t e = launch_fp8_scale(in.w, in.M, scale, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
+    op_scale = scale;
+  }
+  const int64_t plane = rup(static_cast<int64_t>(in.N) * tp.ldo * tp.elem_bytes, 1024);
+  char* hi = static_cast<char*>(op);
+  char* lo = tp.planes == 2 ? hi + plane : nullptr;
+
+  OperandParams op_p;
+  std::memset(&op_p, 0, sizeof(op_p));
+  op_p.F = in.data;
+  op_p.w = in.w;
+  op_p.hi = hi;
+  op_p.lo = lo;
+  op_p.op_scale = op_scale;
+  op_p.ld = in.ld;
+  op_p.ldo = tp.ldo;
+  op_p.N = static_cast<int32_t>(in.N);
+  op_p.M = static_cast<int32_t>(in.M);
+  iso_fill(in.is_field ? &in.iso : nullptr, &op_p.iso_mode, &op_p.iso_mu, &op_p.iso_inv, &op_p.iso_t);
+  op_p.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
+                (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
+  {
+    ProfScope ps(h, PID_KERNEL_GRAM, tp.op_rw_bytes, 0.0, s);
+    cudaError_t e = launch_gram_operands(op_p, tp.prec, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "Gram operand launch");
+  }
+
+  TiledParams tpar;
+  std::memset(&tpar, 0, sizeof(tpar));
+  const uint64_t row_bytes = static_cast<uint64_t>(tp.ldo) * tp.elem_bytes;
+  if (!encode_2d_sw128(&tpar.op_hi, hi, tp.elem_bytes, static_cast<uint64_t>(in.M),
+                       static_cast<uint64_t>(in.N), row_bytes) ||
+      (lo && !encode_2d_sw128(&tpar.op_lo, lo, tp.elem_bytes, static_cast<uint64_t>(in.M),
+                              static_cast<uint64_t>(in.N), row_bytes)))
+    return fail(h, PID_ERR_CUDA, "tensor map encoding failed");
+  if (!lo) tpar.op_lo = tpar.op_hi;
+  tpar.gpart = gpart;
+  tpar.op_scale = op_scale;
+  tpar.N = static_cast<int32_t>(in.N);
+  tpar.M = static_cast<int32_t>(in.M);
+  tpar.R = tp.R;
+  tpar.chunk_cells = static_cast<int32_t>(tp.chunk_cells);
+  tpar.n_chunks = tp.n_gchunks;
+  tpar.tiles_per_chunk = tp.tiles;
+  tpar.stages = tp.stages;
+  tpar.err = h->err_word;
+  ProfScope ps(h, PID_KERNEL_GRAM, tp.gemm_bytes, tp.flops, s);
+  cudaError_t e = launch_gram_tiled(tpar, tp.prec, tp.n_gchunks * tp.tiles, tp.smem, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "tiled Gram launch");
+  return PID_OK;
 }
 
 }  // namespace pidh

@@ -47,6 +47,7 @@ cudaError_t gram_kernels_init(int max_smem) {
   if (e == cudaSuccess) e = gram_tile_init<16, 8>(max_smem);
   if (e == cudaSuccess) e = gram_narrow6_init(max_smem);
   if (e == cudaSuccess) e = gram_wide12_init(max_smem);
+  if (e == cudaSuccess) e = gram_tiled_init(max_smem);
   return e == cudaSuccess ? gram_wide_init(max_smem) : e;
 }
 

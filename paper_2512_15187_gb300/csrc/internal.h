@@ -82,6 +82,7 @@ constexpr int kGramEpiWarps = 4;      // converter warps 0..3, one per TMEM lane
 constexpr int kGramThreads = kGramConvWarps * 32;
 constexpr int kGramMaxN = 256;        // two M = 128 tensor-core row blocks (the wide tile)
 constexpr int kGramNarrowMaxN = 128;  // one M = 128 row block
+constexpr int kGramTiledMaxN = 512;   // row-block-tiled Gram over operands staged in HBM
 
 struct GramParams {
   EnsDesc one;
@@ -95,6 +96,35 @@ struct GramParams {
   int32_t TS;            // cells per FP32 stage: 128, or 64 for the wide tile (N > 128)
   int32_t xchg;
   int32_t use_tma;       // 0: converters read FP32 directly (rows not 16-byte aligned)
+  uint32_t* err;
+};
+
+// Row-block-tiled Gram (256 < N <= 512): operand rows staged in HBM, then one CTA per
+// (cell chunk, 128-row block, column tile).
+struct OperandParams {
+  const float* F;          // [N][ld] soft masks, or fields mapped by iso_mode
+  const float* w;          // [M] cell measures or nullptr
+  void* hi;                // [N][ldo] BF16 bit patterns, or E4M3 bytes
+  void* lo;                // split BF16: [N][ldo] low parts; else nullptr
+  const float* op_scale;   // E4M3: device scalar multiplying every operand (nullptr = 256)
+  int64_t ld, ldo;         // ldo: a multiple of 64 elements
+  int32_t N, M;
+  int32_t iso_mode;
+  float iso_mu, iso_inv, iso_t;
+  int32_t vec_ok;          // rows and weights 16-byte aligned: 4-cell vector loads
+  int32_t pad;
+};
+
+struct TiledParams {
+  CUtensorMap op_hi;       // [N][ldo] operands; box {128 bytes of cells, 128 rows}, 128-byte swizzle
+  CUtensorMap op_lo;       // split BF16: the low parts
+  float* gpart;            // [n_chunks][N][N] FP32 partial Grams (G_ij at j*N + i)
+  const float* op_scale;   // E4M3 scale (nullptr = 256)
+  int32_t N, M, R;         // members, cells, 128-row blocks
+  int32_t chunk_cells;     // multiple of 128
+  int32_t n_chunks, tiles_per_chunk;
+  int32_t stages;          // operand stages in the ring
+  int32_t pad;
   uint32_t* err;
 };
 
@@ -166,6 +196,11 @@ cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec
                         int grid, size_t smem, cudaStream_t s);
 cudaError_t gram_kernels_init(int max_smem);
 cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s);
+// Row-block-tiled Gram (gram_tiled.cu).
+cudaError_t launch_gram_operands(const OperandParams& p, int prec, cudaStream_t s);
+cudaError_t launch_gram_tiled(const TiledParams& p, int prec, int grid, size_t smem, cudaStream_t s);
+cudaError_t gram_tiled_init(int max_smem);
+size_t gram_tiled_smem_bytes(int prec, int stages);
 cudaError_t stream_kernels_init(int max_smem);
 
 }  // namespace pidk

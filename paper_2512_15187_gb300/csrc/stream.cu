@@ -131,22 +131,22 @@ __device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
 
 // Row r of an [N][N] FP32 matrix written by this kernel's grid (read through L2), dotted
 // with the shared vector v (v == nullptr: summed), by one warp: lane l takes the columns
-// l, l + 32, ... in order, then a fixed xor tree. A lane loads up to 8 columns before it
-// adds them, so the row costs one L2 round trip instead of one per column (kGramMaxN = 256
-// columns = 8 per lane).
+// l, l + 32, ... in order, then a fixed xor tree. A lane loads 8 columns (a 256-column
+// block) before it adds them, so a block costs one L2 round trip instead of one per column.
 __device__ __forceinline__ float row_dot_warp(const float* row, const float* v, int N, int ln) {
-  static_assert(kGramMaxN <= 256, "at most 8 columns per lane");
-  float x[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int j = ln + 32 * k;
-    x[k] = j < N ? __ldcg(row + j) : 0.f;
-  }
   float acc = 0.f;
+  for (int b = 0; b < N; b += 256) {
+    float x[8];
 #pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int j = ln + 32 * k;
-    if (j < N) acc = v ? fmaf(x[k], v[j], acc) : acc + x[k];
+    for (int k = 0; k < 8; ++k) {
+      const int j = b + ln + 32 * k;
+      x[k] = j < N ? __ldcg(row + j) : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int j = b + ln + 32 * k;
+      if (j < N) acc = v ? fmaf(x[k], v[j], acc) : acc + x[k];
+    }
   }
   return warp_sum(acc);
 }
@@ -157,8 +157,8 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   __shared__ double scratch[32][33];
   __shared__ unsigned long long skey[1024];   // order keys of the depths (ranks)
   __shared__ double sred[1024];
-  __shared__ float sd[kGramMaxN], sdn[kGramMaxN];   // Gram calibration scales
-  __shared__ float sdm[kGramMaxN];                  // d_j / m_j (0 for zero mass)
+  __shared__ float sd[kGramTiledMaxN], sdn[kGramTiledMaxN];   // Gram calibration scales
+  __shared__ float sdm[kGramTiledMaxN];                       // d_j / m_j (0 for zero mass)
   __shared__ int is_last;
 
   const int N = d.N;
@@ -301,19 +301,22 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
       const float acc = row_dot_warp(Cg + r * N, nullptr, N, ln);
       if (ln == 0) sdn[r] = acc;
     }
-    // C0 = (G' + G'^T) / 2, one warp per row, each lane's 8 columns loaded together
+    // C0 = (G' + G'^T) / 2, one warp per row, each lane's 8 columns of a 256-column block
+    // loaded together
     for (int r = wi; r < N; r += kFinThreads / 32) {
-      float a[8], b[8];
+      for (int c0 = 0; c0 < N; c0 += 256) {
+        float a[8], b[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int c = ln + 32 * k;
-        a[k] = c < N ? __ldcg(Cg + r + c * N) : 0.f;
-        b[k] = c < N ? __ldcg(Cg + r * N + c) : 0.f;
-      }
+        for (int k = 0; k < 8; ++k) {
+          const int c = c0 + ln + 32 * k;
+          a[k] = c < N ? __ldcg(Cg + r + c * N) : 0.f;
+          b[k] = c < N ? __ldcg(Cg + r * N + c) : 0.f;
+        }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int c = ln + 32 * k;
-        if (c < N) C0[r * N + c] = 0.5f * (a[k] + b[k]);
+        for (int k = 0; k < 8; ++k) {
+          const int c = c0 + ln + 32 * k;
+          if (c < N) C0[r * N + c] = 0.5f * (a[k] + b[k]);
+        }
       }
     }
     __syncthreads();
@@ -382,16 +385,18 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
       for (int r = wi; r < N; r += kFinThreads / 32) {
         const double mr = __ldcg(S + r);
         const double inv = mr > 0.0 ? 1.0 / mr : 0.0;
-        float x[8];
+        for (int c0 = 0; c0 < N; c0 += 256) {
+          float x[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int cc = ln + 32 * k;
-          x[k] = cc < N ? __ldcg(C0 + r * N + cc) : 0.f;
-        }
+          for (int k = 0; k < 8; ++k) {
+            const int cc = c0 + ln + 32 * k;
+            x[k] = cc < N ? __ldcg(C0 + r * N + cc) : 0.f;
+          }
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-          const int cc = ln + 32 * k;
-          if (cc < N) d.P[static_cast<size_t>(r) * N + cc] = static_cast<double>(sd[r] * sd[cc] * x[k]) * inv;
+          for (int k = 0; k < 8; ++k) {
+            const int cc = c0 + ln + 32 * k;
+            if (cc < N) d.P[static_cast<size_t>(r) * N + cc] = static_cast<double>(sd[r] * sd[cc] * x[k]) * inv;
+          }
         }
       }
     }

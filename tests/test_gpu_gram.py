@@ -134,7 +134,7 @@ def test_gram_in_batch_with_exact_mean(H):
 def test_gram_rejects_too_many_members(H):
     import torch
     from paper_2512_15187_gb300 import binding as B
-    U = torch.rand((257, 256), device="cuda")
+    U = torch.rand((513, 256), device="cuda")
     with pytest.raises(B.PidError) as e:
         H.full(U, mode="full", precision="bf16")
     assert e.value.status == B.PID_ERR_UNSUPPORTED

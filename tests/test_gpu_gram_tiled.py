@@ -1,0 +1,159 @@
+"""GPU parity of the row-block-tiled tensor-core Gram (256 < N <= 512 members) vs the FP64
+oracle: single calls, fields, unaligned rows, batches and space-time ensembles.
+
+Bar: as for the fused Gram (1e-3 absolute on depths, fractions and P; the same ranking
+outside ties; IN_in exact to the FP32 bar; binary masks exact).
+"""
+import numpy as np
+import pytest
+
+from oracle import pid_oracle as O
+from paper_2512_15187_gb300 import synth
+from tests.helpers import (FP32_TOL, GRAM_TOL, assert_close, assert_rank_agrees_outside_ties,
+                           assert_rank_valid, to_np)
+
+pytestmark = pytest.mark.gpu
+PRECS = ["bf16", "split_bf16", "fp8"]
+FP8_SMALL_M_TOL = 1e-2
+FP8_P_TOL = 5e-3
+
+
+@pytest.fixture(scope="module")
+def H():
+    from paper_2512_15187_gb300 import binding, build
+    build.build()
+    h = binding.Handle(0)
+    yield h
+    h.close()
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _tols(prec, M):
+    tol = GRAM_TOL if (prec != "fp8" or M >= 4096) else FP8_SMALL_M_TOL
+    return tol, (max(tol, FP8_P_TOL) if prec == "fp8" else tol)
+
+
+def _check(o, U, w, tol, what, p_tol=None):
+    a, b, d = O.pid(U, w)
+    assert_close(to_np(o["in_in"]), a, FP32_TOL, what + " in_in")
+    assert_close(to_np(o["in_out"]), b, tol, what + " in_out")
+    assert_close(to_np(o["depth"]), d, tol, what + " depth")
+    assert_rank_valid(to_np(o["rank"]), to_np(o["depth"]))
+    assert_rank_agrees_outside_ties(to_np(o["rank"]), d, tol)
+    if "P" in o:
+        P = to_np(o["P"])
+        assert_close(P, O.inclusion_matrix(U, w), p_tol or tol, what + " P")
+        assert 0.0 <= float(to_np(o["err_est"])[0]) <= 10 * tol
+        assert_close(P.mean(axis=1), a, 1e-6, what + " P row means")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+# three and four 128-row blocks, full and ragged; cell counts below one K-block, ragged
+# against the 64- and 128-cell K-blocks, and over several chunks
+@pytest.mark.parametrize("N,M", [(257, 100), (300, 4097), (384, 20011), (385, 3000),
+                                 (448, 9001), (500, 33000), (512, 5000)])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_tiled_gram_parity(H, prec, N, M, weighted):
+    U = synth.random_soft(N, M, seed=N * 17 + M, binary_frac=0.2)
+    w = np.random.default_rng(M + 1).uniform(0.2, 5, M).astype(np.float32) if weighted else None
+    o = H.full(_dev(U), None if w is None else _dev(w), mode="full", precision=prec, want_P=True)
+    H.sync()
+    tol, p_tol = _tols(prec, M)
+    _check(o, U, w, tol, f"tiled {prec} N={N} M={M} w={weighted}", p_tol)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiled_gram_binary_masks_are_exact(H, prec):
+    # {0,1} operands are exact in BF16 and E4M3 and every Gram entry is an integer count
+    # below 2^24, so the tensor cores add nothing; what remains is the FP32 arithmetic of the
+    # finalisation, whose 320-term row sums round at a few 1e-8 each: the FP32 bar applies.
+    rng = np.random.default_rng(11)
+    Ub = (rng.uniform(size=(320, 3000)) < rng.uniform(0.05, 0.9, (320, 1))).astype(np.float32)
+    Ub[5] = 0.0   # one empty member: zero mass, inclusions 0 by convention
+    o = H.full(_dev(Ub), mode="full", precision=prec, want_P=True)
+    H.sync()
+    a, b, d = O.pid(Ub)
+    for k, r in zip(("in_in", "in_out", "depth"), (a, b, d)):
+        assert_close(to_np(o[k]), r, FP32_TOL, f"{prec} binary {k}")
+    assert_close(to_np(o["P"]), O.inclusion_matrix(Ub), FP32_TOL, f"{prec} binary P")
+    assert float(to_np(o["err_est"])[0]) <= 1e-6
+
+
+def test_tiled_split_bf16_is_much_tighter(H):
+    U = synth.random_soft(400, 1 << 15, seed=4)
+    ref = O.pid(U)[2]
+    o = H.full(_dev(U), mode="full", precision="split_bf16")
+    H.sync()
+    assert float(np.max(np.abs(to_np(o["depth"]) - ref))) <= 2e-5
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("superlevel", [False, True])
+def test_tiled_gram_from_fields(H, prec, superlevel):
+    F = synth.rbf_fields_2d(N=300, H=96, W=80, n_rbf=8)
+    F = (F - np.median(F, axis=1, keepdims=True)).astype(np.float32)
+    w = np.random.default_rng(3).uniform(0.5, 2, F.shape[1]).astype(np.float32)
+    o = H.from_fields(_dev(F), 0.01, 0.05, superlevel=superlevel, w=_dev(w), mode="full",
+                      precision=prec)
+    H.sync()
+    _check(o, O.iso_soft_mask(F, 0.01, 0.05, superlevel), w, GRAM_TOL, f"tiled fields {prec}")
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tiled_gram_unaligned_rows(H, prec):
+    import torch
+    N, M, ld = 270, 5001, 5003   # rows not 16-byte aligned: scalar loads in both passes
+    U = synth.random_soft(N, M, seed=8)
+    buf = torch.zeros((N, ld), dtype=torch.float32, device="cuda")
+    buf[:, :M] = _dev(U)
+    o = H.full(buf[:, :M], mode="full", precision=prec, want_P=True)
+    H.sync()
+    tol, p_tol = _tols(prec, M)
+    _check(o, U, None, tol, f"tiled unaligned {prec}", p_tol)
+
+
+def test_tiled_gram_in_batch(H):
+    rng = np.random.default_rng(21)
+    items, refs = [], []
+    for k, (N, prec) in enumerate([(300, "bf16"), (100, "fp8"), (512, "split_bf16"), (64, "fp32"),
+                                    (400, "fp8"), (257, "bf16")]):
+        M = int(rng.integers(3000, 12000))
+        U = synth.random_soft(N, M, seed=700 + k)
+        w = rng.uniform(0.5, 3, M).astype(np.float32) if k % 2 else None
+        mode = "linear" if prec == "fp32" else "full"
+        items.append(dict(data=_dev(U), w=None if w is None else _dev(w), mode=mode,
+                          precision=prec, want_P=mode == "full"))
+        refs.append((U, w, prec, mode))
+    outs = H.batch(items)
+    H.sync()
+    for o, (U, w, prec, mode) in zip(outs, refs):
+        if mode == "linear":
+            assert_close(to_np(o["depth"]), O.pid(U, w)[2], FP32_TOL, "batch linear")
+            continue
+        tol, p_tol = _tols(prec, U.shape[1])
+        _check(o, U, w, tol, f"batch tiled {prec} N={U.shape[0]}", p_tol)
+        assert_close(to_np(o["mean_depth"]), O.pid_mean(U, w)[2], FP32_TOL, "exact PID-mean by-product")
+    # single calls give the same depths (the same kernels, the same arithmetic order)
+    for o, (U, w, prec, mode) in zip(outs, refs):
+        if mode != "full":
+            continue
+        s = H.full(_dev(U), None if w is None else _dev(w), mode="full", precision=prec)
+        H.sync()
+        np.testing.assert_array_equal(to_np(s["depth"]), to_np(o["depth"]))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp8"])
+def test_tiled_gram_spacetime(H, prec):
+    # 4D PID: the cells of all time steps form one ensemble (Sec. 6)
+    T, N, M = 3, 290, 4000
+    steps = [synth.random_soft(N, M, seed=50 + t) for t in range(T)]
+    w = np.random.default_rng(9).uniform(0.5, 2, M).astype(np.float32)
+    o = H.spacetime([_dev(X) for X in steps], w=_dev(w), mode="full", precision=prec, want_P=True)
+    H.sync()
+    U = np.concatenate(steps, axis=1)
+    tol, p_tol = _tols(prec, T * M)
+    _check(o, U, np.tile(w, T), tol, f"spacetime tiled {prec}", p_tol)

@@ -131,7 +131,7 @@ def test_host_checks(H):
     with pytest.raises(B.PidError):
         H.spacetime([torch.rand((513, 64), device="cuda")] * 2)       # N beyond one tile
     with pytest.raises(B.PidError):
-        H.spacetime([torch.rand((300, 64), device="cuda")] * 2, mode="full", precision="bf16")
+        H.spacetime([torch.rand((513, 64), device="cuda")] * 2, mode="full", precision="bf16")
     o = H.spacetime([a, a], mode="mean")                               # still usable
     H.sync()
     assert_close(to_np(o["depth"]), O.pid_mean(to_np(a))[2], FP32_TOL, "after errors")
