@@ -401,6 +401,22 @@ def run_workloads(h, dev, stream):
     out["noncartesian_128x1M_weighted"] = {"unit": "member-cells/s per call", **thr}
     del Ud, wd, Un, wn
 
+    # full PID of 300 and 512 members on 2^20 cells (above 256 members the Gram modes run
+    # the row-block-tiled Gram), one call per path, beside the exact linear path
+    gt = torch.Generator(device=dev)
+    gt.manual_seed(6)
+    tiled = {"unit": "member-cells/s per call"}
+    for N in (300, 512):
+        X = torch.rand((N, 1 << 20), generator=gt, device=dev)
+        paths = [("full_exact_fp32", lambda: h.full(X, mode="linear", stream=stream))]
+        paths += [(f"full_gram_{p}", lambda p=p: h.full(X, mode="full", precision=p, stream=stream))
+                  for p in ("bf16", "split_bf16", "fp8")]
+        for name, fn in paths:
+            tiled[f"N{N}_{name}"] = N * (1 << 20) / (timed(fn, 5) * 1e-3)
+        del X
+    out["gram_tiled_300_512_members_x1M"] = tiled
+    torch.cuda.empty_cache()
+
     # 3D plume: 2 time steps of 200 x 256^3 plus 48 uneven ensembles (N in [10, 500],
     # M log-uniform in [64^2, 128^3]); PID-mean, and the E4M3 / split-BF16 Gram for the
     # plume steps, exact full PID for the extras

@@ -216,6 +216,10 @@ pid_status pid_mean(pid_handle h, const float* U, int64_t N, int64_t M, int64_t 
  * from the identity IN_in(i) = u_i subset_p u_bar (Eq. 17). opt->mode =
  * PID_MODE_FULL_LINEAR computes the same depths exactly in O(NM); P and err_est are then
  * not written. opt may be NULL (FULL_LINEAR, no validation).
+ * The Gram modes take N <= 512 (PID_ERR_UNSUPPORTED above; FULL_LINEAR takes any N). Up to
+ * 256 members one fused pass converts the operands on chip; from 257 to 512 the operand
+ * rows are first staged in the handle's workspace (N * round_up(M, 64) * 2 bytes for BF16,
+ * twice that for split BF16, half for E4M3) and the Gram runs over 128-row blocks.
  */
 pid_status pid_full(pid_handle h, const float* U, int64_t N, int64_t M, int64_t ld,
                     const float* w, const pid_options* opt, double* depth, double* in_in,
@@ -273,7 +277,7 @@ pid_status pid_depth_from_matrix(pid_handle h, const double* P, int64_t N, int64
  * opt selects PID-mean, exact linear full PID or the tensor-core Gram as for pid_full
  * (NULL = PID-mean). The steps stay where they are (no copy into one array): they become
  * the descriptors of one persistent launch whose chunk partials are reduced by one
- * finalisation. N <= 512 (the Gram modes: N <= 256), 1 <= T <= 65536; all steps share
+ * finalisation. N <= 512, 1 <= T <= 65536; all steps share
  * N, M and ld.
  */
 pid_status pid_spacetime(pid_handle h, const float* const* steps_host, int32_t T, int64_t N,

@@ -29,6 +29,7 @@
 
 #include "device.cuh"
 #include "internal.h"
+#include "stream_kernel.cuh"
 
 namespace pidk {
 
@@ -44,17 +45,19 @@ __host__ __device__ constexpr uint32_t tiled_stage_bytes(int prec) { return (pre
 
 }  // namespace
 
-template <int PREC>
+// ISO: the isovalue map family (none, normal, step or piecewise), applied with the
+// streaming kernel's own tile map, so the staged masks are bitwise those of its pass.
+template <int PREC, int ISO>
 __global__ void __launch_bounds__(kOperandThreads) gram_operand_kernel(const __grid_constant__ OperandParams p) {
   const int i = blockIdx.y;
   const int64_t x0 = (static_cast<int64_t>(blockIdx.x) * kOperandThreads + threadIdx.x) * 4;
   if (x0 >= p.M) return;
   const float* row = p.F + static_cast<int64_t>(i) * p.ld;
   const bool full = x0 + 4 <= p.M;
-  float f[4], w[4];
+  float x[1][4], w[4] = {1.f, 1.f, 1.f, 1.f};
   if (p.vec_ok && full) {
     const float4 a = __ldcs(reinterpret_cast<const float4*>(row + x0));
-    f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+    x[0][0] = a.x; x[0][1] = a.y; x[0][2] = a.z; x[0][3] = a.w;
     if (p.w) {
       const float4 b = __ldg(reinterpret_cast<const float4*>(p.w + x0));
       w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
@@ -62,22 +65,31 @@ __global__ void __launch_bounds__(kOperandThreads) gram_operand_kernel(const __g
   } else {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      f[v] = x0 + v < p.M ? __ldcs(row + x0 + v) : 0.f;
+      x[0][v] = x0 + v < p.M ? __ldcs(row + x0 + v) : 0.f;
       if (p.w) w[v] = x0 + v < p.M ? __ldg(p.w + x0 + v) : 0.f;
     }
   }
+  if constexpr (ISO != ISOK_NONE)
+    iso_map_tile<ISO>(x, p.iso_mu, p.iso_inv, p.iso_t, iso_pad_sign(p.iso_mode), p.iso_mode);
   float t[4];
 #pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const float u = p.iso_mode == ISO_NONE ? f[v] : iso_value(f[v], p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
-    t[v] = x0 + v < p.M ? (p.w ? u * sqrtf(w[v]) : u) : 0.f;
+  for (int v = 0; v < 4; v += 2) {
+    float2 u = make_float2(x[0][v], x[0][v + 1]);
+    if (p.w) u = f2_mul(u, make_float2(sqrtf(w[v]), sqrtf(w[v + 1])));
+    t[v] = u.x;
+    t[v + 1] = u.y;
+  }
+  if (!full) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+      if (x0 + v >= p.M) t[v] = 0.f;
   }
   // ldo is a multiple of 64 elements and x0 of 4: the 4 operands of a thread never cross
   // the end of the row's storage.
   if constexpr (PREC == 3) {
     const float sc = p.op_scale ? *p.op_scale : 256.0f;
-    const uint32_t lo2 = __nv_cvt_float2_to_fp8x2(make_float2(t[0] * sc, t[1] * sc), __NV_SATFINITE, __NV_E4M3);
-    const uint32_t hi2 = __nv_cvt_float2_to_fp8x2(make_float2(t[2] * sc, t[3] * sc), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t lo2 = __nv_cvt_float2_to_fp8x2(f2_mul(make_float2(t[0], t[1]), f2(sc)), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi2 = __nv_cvt_float2_to_fp8x2(f2_mul(make_float2(t[2], t[3]), f2(sc)), __NV_SATFINITE, __NV_E4M3);
     uint8_t* dst = static_cast<uint8_t*>(p.hi) + static_cast<int64_t>(i) * p.ldo + x0;
     *reinterpret_cast<uint32_t*>(dst) = (lo2 & 0xffffu) | (hi2 << 16);
   } else {
@@ -265,12 +277,20 @@ size_t gram_tiled_smem_bytes(int prec, int stages) {
 
 int gram_tiled_threads() { return kTiledThreads; }
 
+template <int PREC>
+static void operand_launch(const OperandParams& p, dim3 grid, cudaStream_t s) {
+  const int kind = iso_kind(p.iso_mode);
+  if (kind == ISOK_NONE) gram_operand_kernel<PREC, ISOK_NONE><<<grid, kOperandThreads, 0, s>>>(p);
+  else if (kind == ISOK_NORMAL) gram_operand_kernel<PREC, ISOK_NORMAL><<<grid, kOperandThreads, 0, s>>>(p);
+  else gram_operand_kernel<PREC, ISOK_STEP><<<grid, kOperandThreads, 0, s>>>(p);
+}
+
 cudaError_t launch_gram_operands(const OperandParams& p, int prec, cudaStream_t s) {
   const dim3 grid(static_cast<unsigned>((p.M + 4 * kOperandThreads - 1) / (4 * kOperandThreads)),
                   static_cast<unsigned>(p.N));
-  if (prec == 1) gram_operand_kernel<1><<<grid, kOperandThreads, 0, s>>>(p);
-  else if (prec == 2) gram_operand_kernel<2><<<grid, kOperandThreads, 0, s>>>(p);
-  else if (prec == 3) gram_operand_kernel<3><<<grid, kOperandThreads, 0, s>>>(p);
+  if (prec == 1) operand_launch<1>(p, grid, s);
+  else if (prec == 2) operand_launch<2>(p, grid, s);
+  else if (prec == 3) operand_launch<3>(p, grid, s);
   else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
