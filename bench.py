@@ -417,18 +417,25 @@ def run_workloads(h, dev, stream):
     out["gram_tiled_300_512_members_x1M"] = tiled
     torch.cuda.empty_cache()
 
-    # 3D plume: 2 time steps of 200 x 256^3 plus 48 uneven ensembles (N in [10, 500],
-    # M log-uniform in [64^2, 128^3]); PID-mean, and the E4M3 / split-BF16 Gram for the
-    # plume steps, exact full PID for the extras
-    steps = [synth.plume_3d(200, 256, t=t) for t in (0, 8)]
+    # 3D plume: the 16 time steps of 200 x 256^3 (13.4 GB each, 215 GB together, resident
+    # at once) plus 48 uneven ensembles (N in [10, 500], M log-uniform in [64^2, 128^3]);
+    # PID-mean, and the E4M3 / split-BF16 Gram for the plume steps, exact full PID for the
+    # extras. The steps held are bounded by the free device memory (recorded).
     rng = np.random.default_rng(4)
     g = torch.Generator(device=dev)
     g.manual_seed(4)
-    extras = []
+    shapes = []
     for _ in range(48):
         N = int(rng.integers(10, 501))
         M = int(round(math.exp(rng.uniform(math.log(64 ** 2), math.log(128 ** 3)))))
-        extras.append(torch.rand((N, M), generator=g, device=dev))
+        shapes.append((N, M))
+    extra_bytes = sum(4 * N * M for N, M in shapes)
+    step_bytes = 4 * 200 * 256 ** 3
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info(dev)
+    n_steps = int(max(1, min(16, (free - extra_bytes - (6 << 30)) // step_bytes)))
+    steps = [synth.plume_3d(200, 256, t=t, T=16) for t in range(n_steps)]
+    extras = [torch.rand(sh, generator=g, device=dev) for sh in shapes]
     items = [dict(data=U, mode="mean") for U in steps]
     items += [dict(data=U, mode="full", precision=p) for U in steps for p in ("fp8", "split_bf16")]
     items += [dict(data=X, mode=m) for X in extras for m in ("mean", "linear")]
@@ -447,13 +454,14 @@ def run_workloads(h, dev, stream):
     o_items = h.batch(items, stream=stream)
     t_batch = timed(lambda: h.batch(items, stream=stream, outs=o_items), 3)
     t_loop = timed(loop, 3)
-    out["plume_2x200x256cubed_plus_48_uneven"] = {
+    out["plume_3d_200x256cubed_steps_plus_48_uneven"] = {
+        "time_steps": n_steps, "resident_gb": (n_steps * step_bytes + extra_bytes) / 1e9,
         "items": len(items), "member_cells_per_call": member_cells,
         "batched_ms": t_batch, "one_call_per_ensemble_ms": t_loop,
         "batched_speedup": t_loop / t_batch,
         "batched_member_cells_per_s": member_cells / (t_batch * 1e-3),
         "batched_read_gb_per_s": read_bytes / (t_batch * 1e-3) / 1e9}
-    del steps, extras
+    del steps, extras, items, o_items, loop   # the item list and the loop hold the 215 GB
     torch.cuda.empty_cache()
 
     # scalability study: PID-mean of 3D ellipsoid ensembles (80% normal, 20% outliers), one
