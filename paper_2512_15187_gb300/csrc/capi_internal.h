@@ -132,7 +132,9 @@ struct GramPlan {
 struct TiledPlan {
   int prec = 0;            // PID_BF16, PID_SPLIT_BF16 or PID_FP8
   int R = 0;               // 128-row blocks
-  int tiles = 0;           // tiles per chunk (upper block triangle, column blocks in pairs)
+  int tiles = 0;           // tiles per chunk (gram_tiles)
+  pidk::TileDesc tile[pidk::kMaxTiles];
+  int slots = 0;           // 128-row blocks per stage and plane
   int64_t ldo = 0;         // operand row stride in elements (a multiple of 64)
   int elem_bytes = 2;      // 2 (BF16) or 1 (E4M3)
   int planes = 1;          // 2 for split BF16

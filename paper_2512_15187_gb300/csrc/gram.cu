@@ -157,8 +157,12 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
                 "the tensor-core Gram takes N <= 512; use PID_MODE_FULL_LINEAR");
   tp->prec = in.precision;
   tp->R = static_cast<int>((in.N + 127) / 128);
-  tp->tiles = 0;
-  for (int r = 0; r < tp->R; ++r) tp->tiles += (tp->R - r + 1) / 2;
+  // BF16 and E4M3: whole rows of the block triangle per tile (up to 4 blocks per stage);
+  // split BF16 carries two planes per block, so its tiles take at most two column blocks
+  tp->tiles = gram_tiles(tp->R, in.precision != PID_SPLIT_BF16, tp->tile);
+  tp->slots = 0;
+  for (int t = 0; t < tp->tiles; ++t)
+    tp->slots = std::max(tp->slots, tp->tile[t].nlb + (tp->tile[t].xa >= 0 ? 1 : 0));
   tp->elem_bytes = in.precision == PID_FP8 ? 1 : 2;
   tp->planes = in.precision == PID_SPLIT_BF16 ? 2 : 1;
   tp->ldo = rup(in.M, 64);
@@ -171,8 +175,8 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
   tp->n_gchunks = static_cast<int>((in.M + chunk - 1) / chunk);
   const size_t cap = static_cast<size_t>(h->max_smem > 0 ? h->max_smem : 232448);
   tp->stages = 6;
-  while (tp->stages > 2 && gram_tiled_smem_bytes(tp->prec, tp->stages) > cap) --tp->stages;
-  tp->smem = gram_tiled_smem_bytes(tp->prec, tp->stages);
+  while (tp->stages > 2 && gram_tiled_smem_bytes(tp->prec, tp->slots, tp->stages) > cap) --tp->stages;
+  tp->smem = gram_tiled_smem_bytes(tp->prec, tp->slots, tp->stages);
   if (tp->smem > cap) return fail(h, PID_ERR_UNSUPPORTED, "tiled Gram stages do not fit shared memory");
   const int64_t plane = rup(static_cast<int64_t>(in.N) * tp->ldo * tp->elem_bytes, 1024);
   tp->op_bytes = static_cast<size_t>(tp->planes * plane);
@@ -237,6 +241,8 @@ pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPl
   tpar.n_chunks = tp.n_gchunks;
   tpar.tiles_per_chunk = tp.tiles;
   tpar.stages = tp.stages;
+  tpar.slots = tp.slots;
+  for (int t = 0; t < tp.tiles; ++t) tpar.tiles[t] = tp.tile[t];
   tpar.err = h->err_word;
   ProfScope ps(h, PID_KERNEL_GRAM, tp.gemm_bytes, tp.flops, s);
   cudaError_t e = launch_gram_tiled(tpar, tp.prec, tp.n_gchunks * tp.tiles, tp.smem, s);

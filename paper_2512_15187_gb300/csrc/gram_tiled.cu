@@ -10,12 +10,16 @@
 //   * gram_operand_kernel maps each input element once (isovalue map of Sec. 3.5, times
 //     sqrt w) and stores the operand rows in HBM as BF16, as a BF16 hi + lo pair, or as
 //     E4M3 times the ensemble's power-of-two scale: [N][ldo] planes, cells contiguous;
-//   * gram_tiled_kernel computes one tile of one cell chunk per CTA: row block r (128
-//     members) against one or two column blocks c >= r (the upper block triangle; the
-//     finalisation symmetrises). The tensor memory accelerator loads each 128-byte K-block
-//     of the operand rows in the 128-byte swizzle layout the tensor cores read (rows past
-//     N and cells past M are zero-filled by the copy), one thread issues tcgen05.mma into
-//     a 128 x 256 FP32 accumulator, and four warps drain it into the chunk's partial Gram,
+//   * gram_tiled_kernel computes one tile of one cell chunk per CTA, from a table of the
+//     upper block triangle's products (row block r of 128 members against column blocks
+//     c >= r; the finalisation symmetrises). BF16 and E4M3 tiles take whole block rows,
+//     the two shortest rows after the first paired, so every tile but one carries the
+//     same work and each block is loaded by few CTAs of its chunk; split BF16, with two
+//     planes per block, takes at most two column blocks per tile. The tensor memory
+//     accelerator loads each 128-byte K-block of the operand rows in the 128-byte swizzle
+//     layout the tensor cores read (rows past N and cells past M are zero-filled by the
+//     copy), one thread issues tcgen05.mma into a 128 x 512 FP32 accumulator (at most 256
+//     columns per instruction), and four warps drain it into the chunk's partial Gram,
 //     writing both G_ij and its mirror G_ji for the off-diagonal blocks.
 //
 // The exact PID-mean sums (m_i, A_i) that calibrate the Gram come from the streaming
@@ -38,10 +42,7 @@ namespace {
 constexpr int kOperandThreads = 256;          // 4 cells per thread: 1024 cells per CTA row
 constexpr int kTiledThreads = 128;            // 4 warps: one per tensor-memory lane quarter
 constexpr uint32_t kBlockBytes = 128 * 128;   // one 128-row block of a 128-byte K-block
-constexpr uint32_t kTiledTmemCols = 256;      // 128 x 256 FP32 accumulator
-
-// Operand bytes per stage and plane: the row block and up to two column blocks.
-__host__ __device__ constexpr uint32_t tiled_stage_bytes(int prec) { return (prec == 2 ? 2u : 1u) * 3u * kBlockBytes; }
+constexpr uint32_t kTiledTmemCols = 512;      // 128 x 512 FP32 accumulator (all of it)
 
 }  // namespace
 
@@ -111,19 +112,19 @@ __global__ void __launch_bounds__(kOperandThreads) gram_operand_kernel(const __g
   }
 }
 
-// One CTA per (cell chunk, row block r, column tile): the tiles of a chunk run r = 0..R-1,
-// each over the column blocks r, r+1, ... in pairs, so a chunk has
-// tiles_per_chunk = sum_r ceil((R - r) / 2) of them (4 for R = 3, 6 for R = 4).
+// One CTA per (cell chunk, tile): the tile table (gram_tiles) lists, for every tile of a
+// chunk, the 128-row blocks to load and the row-block x column-blocks products to form.
 template <int PREC>
 __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __grid_constant__ TiledParams p) {
   constexpr int PLANES = PREC == 2 ? 2 : 1;
   constexpr uint32_t FMT = PREC == 3 ? 0u : 1u;   // E4M3 : BF16
   constexpr int KB = PREC == 3 ? 128 : 64;        // cells per 128-byte K-block
-  constexpr uint32_t STAGE = tiled_stage_bytes(PREC);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
   unsigned char* smem = smem_raw + ((1024u - (raw & 1023u)) & 1023u);
   const int S = p.stages;
+  const uint32_t PLANE = static_cast<uint32_t>(p.slots) * kBlockBytes;   // one plane of a stage
+  const uint32_t STAGE = PLANES * PLANE;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + static_cast<size_t>(S) * STAGE);
   uint64_t* empty = full + S;
   uint64_t* accF = empty + S;
@@ -132,17 +133,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
   int* issued = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int c = static_cast<int>(blockIdx.x) / p.tiles_per_chunk;
-  int t = static_cast<int>(blockIdx.x) - c * p.tiles_per_chunk;
-  int r = 0;
-  for (; r < p.R - 1; ++r) {
-    const int nt = (p.R - r + 1) / 2;
-    if (t < nt) break;
-    t -= nt;
-  }
-  const int cb0 = r + 2 * t;                   // first column block of the tile
-  const int nb = min(2, p.R - cb0);            // column blocks: 1 or 2
-  const bool a_in_b = cb0 == r;                // the row block is the first column block
-  const uint32_t width = static_cast<uint32_t>(nb) * 128u;
+  const TileDesc& td = p.tiles[static_cast<int>(blockIdx.x) - c * p.tiles_per_chunk];
+  const int lb0 = td.lb0, nlb = td.nlb, xa = td.xa, nseg = td.nseg;
+  // stage slot of row block b: the loaded range first, then the extra row block
+  auto slot_of = [&](int b) { return (b >= lb0 && b < lb0 + nlb) ? b - lb0 : nlb; };
   const int N = p.N;
   const int cell0 = c * p.chunk_cells;
   const int cells = min(p.chunk_cells, p.M - cell0);
@@ -166,9 +160,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
   const uint32_t tmem = *tmem_slot;
   bool ok = true;
 
-  // Stage layout, per plane (hi, then lo): [row block][column block 0][column block 1].
+  // Stage layout, per plane (hi, then lo): [slot 0] .. [slot nlb - 1] [extra row block].
   if (warp == 0 && lane == 0) {
-    const uint32_t bytes = static_cast<uint32_t>(PLANES * ((a_in_b ? 0 : 1) + nb)) * kBlockBytes;
+    const uint32_t bytes = static_cast<uint32_t>(PLANES * (nlb + (xa >= 0 ? 1 : 0))) * kBlockBytes;
     int kb = 0;
     for (; kb < nkb; ++kb) {
       const int slot = kb % S;
@@ -182,15 +176,16 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
 #pragma unroll
       for (int pl = 0; pl < PLANES; ++pl) {
         const CUtensorMap* map = pl ? &p.op_lo : &p.op_hi;
-        unsigned char* base = st + pl * 3 * kBlockBytes;
-        if (!a_in_b) tma_load_2d(base, map, &full[slot], x, 128 * r);
-        for (int b = 0; b < nb; ++b)
-          tma_load_2d(base + (1 + b) * kBlockBytes, map, &full[slot], x, 128 * (cb0 + b));
+        unsigned char* base = st + pl * PLANE;
+        for (int b = 0; b < nlb; ++b)
+          tma_load_2d(base + b * kBlockBytes, map, &full[slot], x, 128 * (lb0 + b));
+        if (xa >= 0) tma_load_2d(base + nlb * kBlockBytes, map, &full[slot], x, 128 * xa);
       }
     }
     *issued = kb;
   } else if (warp == 1 && lane == 0) {
-    const uint32_t idesc = umma_idesc(FMT, 128, width);
+    const uint32_t id256 = umma_idesc(FMT, 128, 256), id128 = umma_idesc(FMT, 128, 128);
+    const uint64_t lo_off = PLANE >> 4;   // hi plane -> lo plane (descriptor units)
     for (int kb = 0; kb < nkb; ++kb) {
       const int slot = kb % S;
       if (!mbar_wait_bounded(&full[slot], static_cast<uint32_t>((kb / S) & 1), kWaitTimeoutNs)) {
@@ -199,20 +194,28 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
       }
       tc_fence_after();
       const uint32_t st = smem_u32(smem) + static_cast<uint32_t>(slot) * STAGE;
-      const uint64_t bh = umma_desc_sw128(st + kBlockBytes);
-      const uint64_t ah = a_in_b ? bh : umma_desc_sw128(st);
-      constexpr uint64_t lo_off = (3 * kBlockBytes) >> 4;   // hi plane -> lo plane
+      for (int sg = 0; sg < nseg; ++sg) {
+        const uint64_t ah = umma_desc_sw128(st + static_cast<uint32_t>(slot_of(td.ra[sg])) * kBlockBytes);
+        const int width = 128 * td.nb[sg];
+        // one MMA covers at most 256 columns: B rows n0 .. n0 + 255 start n0 x 128 bytes in
+        for (int n0 = 0; n0 < width; n0 += 256) {
+          const uint64_t bh = umma_desc_sw128(st + static_cast<uint32_t>(slot_of(td.cb[sg])) * kBlockBytes +
+                                              static_cast<uint32_t>(n0) * 128u);
+          const uint32_t idesc = width - n0 >= 256 ? id256 : id128;
+          const uint32_t d = tmem + static_cast<uint32_t>(td.col[sg] + n0);
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {   // 4 x 32 bytes along K in the 128-byte row
-        const uint64_t k16 = static_cast<uint64_t>((ks * 32) >> 4);
-        const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
-        if constexpr (PREC == 3) {
-          umma_f8(tmem, ah + k16, bh + k16, idesc, acc);
-        } else {
-          umma_f16(tmem, ah + k16, bh + k16, idesc, acc);
-          if constexpr (PREC == 2) {
-            umma_f16(tmem, ah + k16, bh + lo_off + k16, idesc, 1u);
-            umma_f16(tmem, ah + lo_off + k16, bh + k16, idesc, 1u);
+          for (int ks = 0; ks < 4; ++ks) {   // 4 x 32 bytes along K in the 128-byte row
+            const uint64_t k16 = static_cast<uint64_t>((ks * 32) >> 4);
+            const uint32_t acc = (kb == 0 && ks == 0) ? 0u : 1u;
+            if constexpr (PREC == 3) {
+              umma_f8(d, ah + k16, bh + k16, idesc, acc);
+            } else {
+              umma_f16(d, ah + k16, bh + k16, idesc, acc);
+              if constexpr (PREC == 2) {
+                umma_f16(d, ah + k16, bh + lo_off + k16, idesc, 1u);
+                umma_f16(d, ah + lo_off + k16, bh + k16, idesc, 1u);
+              }
+            }
           }
         }
       }
@@ -222,32 +225,36 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
   }
   __syncwarp();
 
-  // Drain: warp w holds accumulator rows 32 w .. 32 w + 31 (member 128 r + 32 w + lane).
+  // Drain: warp w holds accumulator rows 32 w .. 32 w + 31 of every segment (member
+  // 128 ra + 32 w + lane).
   if (!mbar_wait_bounded(accF, 0u, kWaitTimeoutNs)) ok = false;
   __syncwarp();
   tc_fence_after();
   {
-    const int i = 128 * r + 32 * warp + lane;
     float* gp = p.gpart + static_cast<size_t>(c) * N * N;
     float unscale = 1.0f;
     if constexpr (PREC == 3) {
       const float sc = p.op_scale ? *p.op_scale : 256.0f;
       unscale = 1.0f / (sc * sc);
     }
-    for (uint32_t j0 = 0; j0 < width; j0 += 32) {
-      const int jb = 128 * cb0 + static_cast<int>(j0);   // first member of these columns
-      if (jb >= N) break;                                 // the same for the whole warp
-      float v[32];
-      tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + j0, v);
-      const bool mirror = !(a_in_b && j0 < 128);          // off the diagonal block
-      if (i < N) {
+    for (int sg = 0; sg < nseg; ++sg) {
+      const int ra = td.ra[sg], cb = td.cb[sg], width = 128 * td.nb[sg];
+      const int i = 128 * ra + 32 * warp + lane;
+      for (int j0 = 0; j0 < width; j0 += 32) {
+        const int jb = 128 * cb + j0;                 // first member of these columns
+        if (jb >= N) break;                           // the same for the whole warp
+        float v[32];
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(td.col[sg] + j0), v);
+        const bool mirror = jb / 128 != ra;           // off the diagonal block
+        if (i < N) {
 #pragma unroll
-        for (int jj = 0; jj < 32; ++jj) {
-          const int j = jb + jj;
-          if (j < N) {
-            const float g = v[jj] * unscale;
-            gp[static_cast<size_t>(j) * N + i] = g;
-            if (mirror) gp[static_cast<size_t>(i) * N + j] = g;
+          for (int jj = 0; jj < 32; ++jj) {
+            const int j = jb + jj;
+            if (j < N) {
+              const float g = v[jj] * unscale;
+              gp[static_cast<size_t>(j) * N + i] = g;
+              if (mirror) gp[static_cast<size_t>(i) * N + j] = g;
+            }
           }
         }
       }
@@ -271,8 +278,55 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
   if (warp == 0) tmem_dealloc(tmem, kTiledTmemCols);
 }
 
-size_t gram_tiled_smem_bytes(int prec, int stages) {
-  return 1024 + static_cast<size_t>(stages) * tiled_stage_bytes(prec) + (2 * stages + 2) * 8 + 16;
+int gram_tiles(int R, bool wide, TileDesc* out) {
+  int n = 0;
+  auto add = [&](int lb0, int nlb, int xa, int nseg, const int* ra, const int* cb, const int* nb) {
+    TileDesc t{};
+    t.lb0 = static_cast<int8_t>(lb0);
+    t.nlb = static_cast<int8_t>(nlb);
+    t.xa = static_cast<int8_t>(xa);
+    t.nseg = static_cast<int8_t>(nseg);
+    int col = 0;
+    for (int s = 0; s < nseg; ++s) {
+      t.ra[s] = static_cast<int8_t>(ra[s]);
+      t.cb[s] = static_cast<int8_t>(cb[s]);
+      t.nb[s] = static_cast<int8_t>(nb[s]);
+      t.col[s] = static_cast<int16_t>(col);
+      col += 128 * nb[s];
+    }
+    out[n++] = t;
+  };
+  if (wide && (R == 3 || R == 4)) {
+    // whole rows of the upper block triangle, the two shortest rows after the first paired:
+    // R = 3: {0: 0-2}, {1: 1-2, 2: 2}; R = 4: {0: 0-3}, {1: 1-3, 3: 3}, {2: 2-3}
+    {
+      const int ra[1] = {0}, cb[1] = {0}, nb[1] = {R};
+      add(0, R, -1, 1, ra, cb, nb);
+    }
+    {
+      const int ra[2] = {1, R - 1}, cb[2] = {1, R - 1}, nb[2] = {R - 1, 1};
+      add(1, R - 1, -1, 2, ra, cb, nb);
+    }
+    if (R == 4) {
+      const int ra[1] = {2}, cb[1] = {2}, nb[1] = {2};
+      add(2, 2, -1, 1, ra, cb, nb);
+    }
+    return n;
+  }
+  // row block r against the column blocks r, r+1, ... in pairs; the row block is loaded
+  // apart unless it is the pair's first block
+  for (int r = 0; r < R; ++r) {
+    for (int c0 = r; c0 < R; c0 += 2) {
+      const int ra[1] = {r}, cb[1] = {c0}, nb[1] = {c0 + 1 < R ? 2 : 1};
+      add(c0, nb[0], c0 == r ? -1 : r, 1, ra, cb, nb);
+    }
+  }
+  return n;
+}
+
+size_t gram_tiled_smem_bytes(int prec, int slots, int stages) {
+  return 1024 + static_cast<size_t>(stages) * (prec == 2 ? 2u : 1u) * slots * kBlockBytes +
+         (2 * stages + 2) * 8 + 16;
 }
 
 int gram_tiled_threads() { return kTiledThreads; }

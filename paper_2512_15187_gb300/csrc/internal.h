@@ -115,6 +115,16 @@ struct OperandParams {
   int32_t pad;
 };
 
+// One tile of a cell chunk: the 128-row blocks lb0 .. lb0 + nlb - 1 are loaded per K-block
+// (plus block xa when xa >= 0), and each segment multiplies row block ra[s] against the nb[s]
+// column blocks from cb[s] on, into accumulator columns from col[s] on (at most 512 in all).
+struct TileDesc {
+  int8_t lb0, nlb, xa, nseg;
+  int8_t ra[2], cb[2], nb[2];
+  int16_t col[2];
+};
+constexpr int kMaxTiles = 8;
+
 struct TiledParams {
   CUtensorMap op_hi;       // [N][ldo] operands; box {128 bytes of cells, 128 rows}, 128-byte swizzle
   CUtensorMap op_lo;       // split BF16: the low parts
@@ -124,7 +134,8 @@ struct TiledParams {
   int32_t chunk_cells;     // multiple of 128
   int32_t n_chunks, tiles_per_chunk;
   int32_t stages;          // operand stages in the ring
-  int32_t pad;
+  int32_t slots;           // 128-row blocks per stage and plane
+  TileDesc tiles[kMaxTiles];
   uint32_t* err;
 };
 
@@ -200,7 +211,10 @@ cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t
 cudaError_t launch_gram_operands(const OperandParams& p, int prec, cudaStream_t s);
 cudaError_t launch_gram_tiled(const TiledParams& p, int prec, int grid, size_t smem, cudaStream_t s);
 cudaError_t gram_tiled_init(int max_smem);
-size_t gram_tiled_smem_bytes(int prec, int stages);
+size_t gram_tiled_smem_bytes(int prec, int slots, int stages);
+// The tiles of one cell chunk for R row blocks: whole rows of the upper block triangle
+// (short rows paired) when `wide`, else at most two column blocks per tile.
+int gram_tiles(int R, bool wide, TileDesc* out);
 cudaError_t stream_kernels_init(int max_smem);
 
 }  // namespace pidk
