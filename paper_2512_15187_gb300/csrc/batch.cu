@@ -404,7 +404,7 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
                                         L.cells, L.iso_mode, L.bytes, L.flops, s);
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::TILED) {
-      pid_status st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, s);
+      pid_status st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, true, s);
       if (st != PID_OK) return st;
     } else {
       FinParams fp;

@@ -529,8 +529,16 @@ static pid_status run_gram_tiled(pid_handle h, const EnsInput& in, EnsPlan& pl,
   double* part = reinterpret_cast<double*>(ws);
   float* gpart = reinterpret_cast<float*>(ws + off_gpart);
   pl.desc.part = part;
+  // BF16 operands come straight from the streaming pass (its one-cell-per-lane classes,
+  // which every N > 256 uses); split BF16 and E4M3 are staged by their own kernel.
+  const bool fused = tp.prec == PID_BF16 && pl.cfg.vec == 1;
+  if (fused) {
+    pl.desc.op_out = reinterpret_cast<uint16_t*>(ws + off_op);
+    pl.desc.op_ld = tp.ldo;
+  }
   if ((st = launch_stream_one(h, pl, nullptr, s)) != PID_OK) return st;
-  st = launch_gram_tiled_one(h, in, tp, ws + off_op, gpart, reinterpret_cast<float*>(ws + off_scale), s);
+  st = launch_gram_tiled_one(h, in, tp, ws + off_op, gpart, reinterpret_cast<float*>(ws + off_scale),
+                             !fused, s);
   if (st != PID_OK) return st;
   FinDesc fd;
   std::memset(&fd, 0, sizeof(fd));

@@ -195,10 +195,11 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDe
                              cudaStream_t s);
 
 pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp);
-// Operand staging and the tiled Gram launch; `op` holds tp.op_bytes, `gpart` tp.gpart_bytes,
-// `scale` one float (E4M3 of a weighted ensemble).
+// Operand staging (unless the streaming pass already wrote the BF16 operands) and the
+// tiled Gram launch; `op` holds tp.op_bytes, `gpart` tp.gpart_bytes, `scale` one float
+// (E4M3 of a weighted ensemble).
 pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
-                                 float* gpart, float* scale, cudaStream_t s);
+                                 float* gpart, float* scale, bool stage_operands, cudaStream_t s);
 
 // batch.cu
 void destroy_batch_cache(pid_handle h);

@@ -192,7 +192,7 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
 }
 
 pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
-                                 float* gpart, float* scale, cudaStream_t s) {
+                                 float* gpart, float* scale, bool stage_operands, cudaStream_t s) {
   const float* op_scale = nullptr;
   if (tp.prec == PID_FP8 && in.w) {
     cudaError_t e = launch_fp8_scale(in.w, in.M, scale, s);
@@ -217,7 +217,7 @@ pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPl
   iso_fill(in.is_field ? &in.iso : nullptr, &op_p.iso_mode, &op_p.iso_mu, &op_p.iso_inv, &op_p.iso_t);
   op_p.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
                 (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
-  {
+  if (stage_operands) {
     ProfScope ps(h, PID_KERNEL_GRAM, tp.op_rw_bytes, 0.0, s);
     cudaError_t e = launch_gram_operands(op_p, tp.prec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "Gram operand launch");

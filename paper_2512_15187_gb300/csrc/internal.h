@@ -58,6 +58,9 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   int64_t work_begin;   // member-cells of the launch's earlier ensembles (0 for the first)
   float* u_out;         // streaming pass 1 of a field: also store the soft masks here,
                         // [N][round_up(M, 4)] float32, for pass 2 to read (nullptr = no)
+  uint16_t* op_out;     // first streaming pass: also store u sqrt(w) as BF16 tensor-core
+                        // operands of the row-block-tiled Gram, [N][op_ld] (nullptr = no)
+  int64_t op_ld;        // a multiple of 64
 };
 
 struct StreamParams {

@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.cuh"
@@ -451,6 +452,44 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 #pragma unroll
                   for (int v = 0; v < VEC; ++v)
                     if (xl + v < M) __stcs(dst + v, x[k][v]);
+                }
+              }
+            }
+          }
+        }
+        if constexpr (!COEF && VEC == 1) {
+          // BF16 operands u sqrt(w) of the row-block-tiled Gram (N > 256: the one-cell-per-lane
+          // classes), written from the masks this pass maps anyway (cells past M are never
+          // read: the tile kernel's copies zero-fill them).
+          // read through the descriptor here, so the pointer holds no register in the loop
+          uint16_t* const op_out = dp->op_out;
+          if (op_out != nullptr) {
+            const int64_t op_ld = dp->op_ld;
+            float sw[VEC];
+#pragma unroll
+            for (int v = 0; v < VEC; ++v) sw[v] = has_w ? sqrtf(wv[v]) : 1.f;
+#pragma unroll
+            for (int k = 0; k < MPW; ++k) {
+              const int i = q + k * G;
+              if (i < N) {
+                uint16_t* dst = op_out + static_cast<int64_t>(i) * op_ld + xl;
+                uint16_t b[VEC];
+#pragma unroll
+                for (int v = 0; v < VEC; ++v)
+                  b[v] = __bfloat16_as_ushort(__float2bfloat16_rn(x[k][v] * sw[v]));
+                if (xl + VEC <= M) {
+                  if constexpr (VEC == 4) {
+                    *reinterpret_cast<uint2*>(dst) = make_uint2(b[0] | (static_cast<uint32_t>(b[1]) << 16),
+                                                                b[2] | (static_cast<uint32_t>(b[3]) << 16));
+                  } else if constexpr (VEC == 2) {
+                    *reinterpret_cast<uint32_t*>(dst) = b[0] | (static_cast<uint32_t>(b[1]) << 16);
+                  } else {
+                    dst[0] = b[0];
+                  }
+                } else {
+#pragma unroll
+                  for (int v = 0; v < VEC; ++v)
+                    if (xl + v < M) dst[v] = b[v];
                 }
               }
             }
