@@ -312,6 +312,9 @@ typedef struct pid_ensemble {
  * pid_batch — many ensembles of uneven N and M in one persistent launch per kernel class,
  * the class launches recorded in order as one CUDA graph and replayed while the batch
  * layout is unchanged. Results are bitwise identical to the single-ensemble calls.
+ * Gram-mode ensembles of 257 to 512 members run the row-block-tiled Gram after their
+ * class's streaming launch, one operand-staging and one tile launch each; they share one
+ * operand buffer in the workspace, sized for the largest of them.
  */
 pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
 
