@@ -86,6 +86,7 @@ struct Launch {
   EnsInput in;
   TiledPlan tp;
   void* op = nullptr;
+  bool stage = true;       // stage the operands (else the streaming pass wrote them)
   float* gpart = nullptr;
   float* scale = nullptr;
 };
@@ -116,7 +117,9 @@ static pid_status to_input(pid_handle h, const pid_ensemble& e, EnsInput* in) {
 
 // Lay out descriptors and workspace for the batch. Pointers are offsets from `base`.
 // store_u: for exact full PID of a field, pass 1 also writes the soft masks into the
-// workspace and pass 2 streams them (instead of repeating the isovalue map).
+// workspace and pass 2 streams them (instead of repeating the isovalue map); and the
+// streaming pass of a BF16 tiled-Gram ensemble writes its operands into a buffer of its own
+// (instead of a staging pass into one shared buffer).
 // steps > 1: the `count` == `steps` records are the time steps of ONE space-time ensemble
 // (4D PID: the cells (x, t) of all steps concatenated). Step t writes its chunk partials
 // right after those of step t - 1, and one finalisation reduces all of them.
@@ -193,10 +196,23 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   std::vector<double*> part(count), sums(count);
   std::vector<float*> coef(count), gpart(count, nullptr);
   std::vector<float*> scale(count, nullptr);
-  // Operand planes of the tiled Gram: one buffer, reused by the tiled launches in turn.
+  // Operand planes of the tiled Gram: written by the streaming pass into one buffer per
+  // ensemble (BF16, store_u), else staged into one buffer reused by the launches in turn.
+  std::vector<int> fused(count, 0);
+  std::vector<void*> op_own(count, nullptr);
   size_t op_bytes = 0;
-  for (int e = 0; e < count; ++e)
-    if (tiled[e]) op_bytes = std::max(op_bytes, tp[e].op_bytes);
+  for (int e = 0; e < count; ++e) {
+    if (!tiled[e]) continue;
+    fused[e] = store_u && tp[e].prec == PID_BF16 && pl[e].cfg.vec == 1;
+    if (fused[e]) {
+      op_own[e] = base + off;
+      off += align_up(static_cast<int64_t>(tp[e].op_bytes), 1024);
+      pl[e].desc.op_out = static_cast<uint16_t*>(op_own[e]);
+      pl[e].desc.op_ld = tp[e].ldo;
+    } else {
+      op_bytes = std::max(op_bytes, tp[e].op_bytes);
+    }
+  }
   void* op_buf = nullptr;
   if (op_bytes) { op_buf = base + off; off += align_up(static_cast<int64_t>(op_bytes), 1024); }
   // chunks of an ensemble's (m, A) partials and of its Gram partials
@@ -252,7 +268,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     for (int e : members) {
       const EnsPlan& p = (coef_pass && stored[e]) ? pl2[e] : pl[e];
       EnsDesc d = p.desc;
-      if (coef_pass) d.u_out = nullptr;
+      if (coef_pass) { d.u_out = nullptr; d.op_out = nullptr; }
       d.unit_begin = units;
       d.work_begin = L.cells;
       d.coef = coef_pass ? coef[e] : nullptr;
@@ -335,7 +351,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.count = 1;
     L.in = in[e];
     L.tp = tp[e];
-    L.op = op_buf;
+    L.op = fused[e] ? op_own[e] : op_buf;
+    L.stage = !fused[e];
     L.gpart = gpart[e];
     L.scale = scale[e];   // the steps of a space-time ensemble share w, hence the scale
     bp->launches.push_back(L);
@@ -404,7 +421,7 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
                                         L.cells, L.iso_mode, L.bytes, L.flops, s);
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::TILED) {
-      pid_status st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, true, s);
+      pid_status st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, L.stage, s);
       if (st != PID_OK) return st;
     } else {
       FinParams fp;
