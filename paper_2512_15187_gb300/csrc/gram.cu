@@ -158,8 +158,9 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
   tp->prec = in.precision;
   tp->R = static_cast<int>((in.N + 127) / 128);
   // BF16 and E4M3: whole rows of the block triangle per tile (up to 4 blocks per stage);
-  // split BF16 carries two planes per block, so its tiles take at most two column blocks
-  tp->tiles = gram_tiles(tp->R, in.precision != PID_SPLIT_BF16, tp->tile);
+  // split BF16 carries two planes per block: whole rows for 3 row blocks (two stages of
+  // 96 KB), else tiles of at most two column blocks
+  tp->tiles = gram_tiles(tp->R, in.precision != PID_SPLIT_BF16 || tp->R == 3, tp->tile);
   tp->slots = 0;
   for (int t = 0; t < tp->tiles; ++t)
     tp->slots = std::max(tp->slots, tp->tile[t].nlb + (tp->tile[t].xa >= 0 ? 1 : 0));

@@ -15,7 +15,8 @@
 //     c >= r; the finalisation symmetrises). BF16 and E4M3 tiles take whole block rows,
 //     the two shortest rows after the first paired, so every tile but one carries the
 //     same work and each block is loaded by few CTAs of its chunk; split BF16, with two
-//     planes per block, takes at most two column blocks per tile. The tensor memory
+//     planes per block, does so for three row blocks and otherwise takes at most two
+//     column blocks per tile. The tensor memory
 //     accelerator loads each 128-byte K-block of the operand rows in the 128-byte swizzle
 //     layout the tensor cores read (rows past N and cells past M are zero-filled by the
 //     copy), one thread issues tcgen05.mma into a 128 x 512 FP32 accumulator (at most 256
@@ -328,8 +329,6 @@ size_t gram_tiled_smem_bytes(int prec, int slots, int stages) {
   return 1024 + static_cast<size_t>(stages) * (prec == 2 ? 2u : 1u) * slots * kBlockBytes +
          (2 * stages + 2) * 8 + 16;
 }
-
-int gram_tiled_threads() { return kTiledThreads; }
 
 template <int PREC>
 static void operand_launch(const OperandParams& p, dim3 grid, cudaStream_t s) {

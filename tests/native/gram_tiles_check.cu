@@ -51,11 +51,14 @@ int main() {
         std::printf("R=%d wide=%d: %zu of %d blocks covered\n", R, wide, seen.size(), R * (R + 1) / 2);
         ++bad;
       }
-      // the ring must hold at least two stages in the 227 KB of shared memory of a CTA
-      const int prec = wide ? 1 : 2;
-      if (gram_tiled_smem_bytes(prec, slots, 2) > 232448) {
-        std::printf("R=%d wide=%d: two stages of %d slots do not fit\n", R, wide, slots);
-        ++bad;
+      // the ring must hold at least two stages in the 227 KB of shared memory of a CTA, for
+      // every precision that uses the table (split BF16 takes the wide one for R = 3 only)
+      for (int prec = 1; prec <= 3; ++prec) {
+        const bool uses = wide ? (prec != 2 || R == 3) : (prec == 2 && R != 3);
+        if (uses && gram_tiled_smem_bytes(prec, slots, 2) > 232448) {
+          std::printf("R=%d wide=%d prec=%d: two stages of %d slots do not fit\n", R, wide, prec, slots);
+          ++bad;
+        }
       }
     }
   }
