@@ -1,16 +1,23 @@
 #!/usr/bin/env python
 """Throughput benchmark of the PID hot path on GB300.
 
-Workload: fuzzy isocontours. Each ensemble is N = 64 scalar fields on a 512 x 512 grid
-(sum of 32 Gaussian bumps + noise), mapped to soft masks by an isovalue ~ Normal(0.5, 0.05).
-One step runs the whole hot path over a batch of E ensembles through one pid_batch call:
-isovalue map (fused) -> masses and mean contour -> PID-mean -> full PID -> FP64
-finalisation and ranking. The metric counts member x cell pairs processed per second.
+Headline workload: the large 3D batch. 16 time steps of an ensemble of N = 200 smoke-plume
+soft masks on a 256^3 grid (215 GB, resident together) plus 48 uneven ensembles (N in
+[10, 500], M log-uniform in [64^2, 128^3]). One step is ONE pid_batch call (recorded once,
+replayed as a CUDA graph) over 144 items: for every time step PID-mean in FP32 and full PID
+on the tensor cores with E4M3 (per-member scales) and with split-BF16 operands; for every
+uneven ensemble PID-mean and exact full PID. The metric counts the member x cell pairs of
+every item per second.
+
+Beside it (secondary records): the 2D fields workload (256 ensembles of 64 x 512^2 fields
+through the isovalue map), the other paths on it, contour bands, the small and
+non-Cartesian workloads, the tiled Gram at 300 and 512 members, the scalability study and
+the serving loop.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-With --impl reference the FP64 CPU oracle is timed on the host cores on a bounded sample
-of the same workload. Under torchrun (N > 1) every rank processes its own batch (replicas,
+With --impl reference the FP64 CPU oracle is timed on the host cores on bounded samples of
+the headline workload. Under torchrun (N > 1) every rank processes its own batch (replicas,
 weak scaling); rank 0 prints one JSON line.
 """
 from __future__ import annotations
@@ -18,11 +25,13 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -30,122 +39,109 @@ sys.path.insert(0, ROOT)
 
 METRIC = "member·cells/s for PID-mean & full PID (HBM / tensor roofline %); served p50/p99 ms"
 UNIT = "member·cells/s"
+# headline: the 3D plume batch
+C4_T, C4_N, C4_R, C4_EXTRAS = 16, 200, 256, 48
+C4_PLANES = 4                      # host samples: slabs of 4 z-planes (262144 cells)
+WORKLOAD = ("3D plume batch: 16 time steps x 200 members x 256^3 FP32 soft masks + 48 uneven "
+            "ensembles (N in [10, 500], M in [64^2, 128^3]), one graph-replayed pid_batch")
+# secondary: fuzzy isocontours of 2D fields
 N_MEMBERS, GRID_H, GRID_W, N_RBF = 64, 512, 512, 32
 ISO_MU, ISO_SIGMA = 0.5, 0.05
-WORKLOAD = "fuzzy isocontours: 64 members x 512x512 FP32 fields, isovalue ~ Normal(0.5, 0.05)"
+WORKLOAD_2D = "fuzzy isocontours: 64 members x 512x512 FP32 fields, isovalue ~ Normal(0.5, 0.05)"
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--ensembles", type=int, default=256, help="ensembles per step (per GPU)")
-    ap.add_argument("--mode", default="linear", choices=["linear", "full", "mean"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "split_bf16", "fp8"])
+    ap.add_argument("--time-steps", type=int, default=C4_T,
+                    help="time steps of the 3D plume held and processed per step (at most 16)")
+    ap.add_argument("--ensembles", type=int, default=256,
+                    help="2D fields record: ensembles per step (per GPU)")
     ap.add_argument("--other-steps", type=int, default=10,
                     help="steps timed for each alternative path reported beside the headline")
-    ap.add_argument("--e2e-ensembles", type=int, default=16)
+    ap.add_argument("--e2e-steps", type=int, default=6, help="time steps streamed in the e2e record")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the 2D fields record and its other paths")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="seconds of Poisson arrivals per serving scenario (0 = skip serving)")
     ap.add_argument("--no-workloads", action="store_true",
-                    help="skip the other benchmark workloads (ellipses, non-Cartesian, 3D plume batch)")
+                    help="skip the other benchmark workloads (ellipses, non-Cartesian, tiled, scalability)")
     ap.add_argument("--source-hash", action="store_true",
                     help="print the kernel-source stamp that ncu summaries carry, and exit")
     return ap.parse_args()
 
 
 # ---------------------------------------------------------------------------------------
-# CPU oracle leg (runs in a child process with one BLAS/OpenMP thread)
+# CPU oracle leg: bounded samples of the headline workload, in a child process with a
+# chosen number of BLAS/OpenMP threads (started before, or apart from, any CUDA work)
 # ---------------------------------------------------------------------------------------
 
 CPU_SNIPPET = r"""
-import json, sys, time
+import json, os, sys, time
 sys.path.insert(0, {root!r})
 import numpy as np
+import torch
+torch.set_num_threads(os.cpu_count() or 1)   # input generation only (not timed)
 from oracle import pid_oracle as O
 from paper_2512_15187_gb300 import synth
-budget, max_steps, rows = {budget}, {max_steps}, {rows}
-pool = [synth.rbf_fields_2d(N={N}, H={H}, W={W}, n_rbf={K}, seed=synth.DEFAULT_SEED + 2 + 7919 * k)
-        for k in range(2)]
-done, t_total, per, ref = 0, 0.0, [], None
+budget, max_steps = {budget}, {max_steps}
+done, t_total, per = 0, 0.0, []
 while done < max_steps and t_total < budget:
-    F = pool[done % len(pool)]
-    band = (done // len(pool)) % ({H} // rows)
-    F = np.ascontiguousarray(F.reshape({N}, {H}, {W})[:, band * rows:(band + 1) * rows].reshape({N}, -1))
+    t = done % {T}
+    z0 = {R} // 4 + ({planes} * (done // {T})) % ({R} // 4)
+    U = synth.plume_3d_slab({N}, {R}, z0, {planes}, t=t, T={T}).numpy()
     t0 = time.perf_counter()
-    U = O.iso_soft_mask(F, {mu}, {sigma})
     mean = O.pid_mean(U)
     full = O.pid(U)
     dt = time.perf_counter() - t0
-    if ref is None:   # the first sample's results, for the GPU paths to be checked against
-        ref = {{"mean": [list(map(float, v)) for v in mean],
-                "full": [list(map(float, v)) for v in full]}}
     per.append(dt); t_total += dt; done += 1
-print(json.dumps({{"steps": done, "seconds": t_total, "per_step": per, "cells": rows * {W},
-                  "ref": ref}}))
+print(json.dumps({{"steps": done, "seconds": t_total, "per_step": per,
+                  "cells": {planes} * {R} * {R}, "members": {N}}}))
 """
 
 
-def run_cpu_oracle(budget_s=12.0, max_steps=64, rows=GRID_H, threads=1):
-    """Time the FP64 oracle on `rows`-row bands of the workload's ensembles with `threads`
-    BLAS/OpenMP threads (its pairwise sums are one matrix product per ensemble)."""
+def run_cpu_oracle(budget_s=12.0, max_steps=64, threads=1):
+    """Time the FP64 oracle (PID-mean, then full PID by its O(N^2 M) pairwise sums) on host
+    samples of the plume workload: 200 members on a slab of 4 z-planes of the 256^3 grid
+    (262144 cells), a different time step and slab per sample."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = CPU_SNIPPET.format(root=ROOT, budget=budget_s, max_steps=max_steps, rows=rows,
-                              N=N_MEMBERS, H=GRID_H, W=GRID_W, K=N_RBF, mu=ISO_MU, sigma=ISO_SIGMA)
+    code = CPU_SNIPPET.format(root=ROOT, budget=budget_s, max_steps=max_steps, N=C4_N, R=C4_R,
+                              T=C4_T, planes=C4_PLANES)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError("CPU oracle failed:\n" + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    res["threads"] = threads
+    return res
 
 
-def oracle_parity(h, res, dev):
-    """Max abs error of every path's depths and inclusion fractions against the FP64
-    oracle's results (from the CPU leg) on the leg's first sample: the first ensemble of
-    the workload, generated on the host by the same seeded generator."""
-    import numpy as np
-    import torch
-
-    from paper_2512_15187_gb300 import synth
-    rows = res["cells"] // GRID_W
-    F = synth.rbf_fields_2d(N=N_MEMBERS, H=GRID_H, W=GRID_W, n_rbf=N_RBF,
-                            seed=synth.DEFAULT_SEED + 2)
-    F = np.ascontiguousarray(F.reshape(N_MEMBERS, GRID_H, GRID_W)[:, :rows].reshape(N_MEMBERS, -1))
-    Fd = torch.from_numpy(F).to(dev)
-    out = {"sample": f"{N_MEMBERS} members x {rows * GRID_W} cells (the oracle leg's first "
-                     f"sample); max abs error against the FP64 oracle",
-           "bars": {"fp32": 1e-6, "gram": 1e-3}}
-    for name, mode, prec, key in (("pid_mean_fp32", "mean", "fp32", "mean"),
-                                  ("full_exact_fp32", "linear", "fp32", "full"),
-                                  ("full_gram_bf16", "full", "bf16", "full"),
-                                  ("full_gram_split_bf16", "full", "split_bf16", "full"),
-                                  ("full_gram_fp8", "full", "fp8", "full")):
-        o = h.from_fields(Fd, ISO_MU, ISO_SIGMA, mode=mode, precision=prec)
-        h.sync()
-        errs = {}
-        for k, r in zip(("in_in", "in_out", "depth"), res["ref"][key]):
-            errs[k] = float(np.max(np.abs(o[k].cpu().numpy() - np.asarray(r))))
-        out[name] = errs
-    return out
+def cpu_value(res, skip=0):
+    """member·cells/s of the oracle: each sample is two items (PID-mean and full PID) of
+    N x cells member·cells each."""
+    t = res["per_step"][skip:]
+    return 2.0 * len(t) * res["members"] * res["cells"] / sum(t), sum(t), len(t)
 
 
-def cpu_baseline_record(res):
-    mc = res["steps"] * N_MEMBERS * res["cells"]
-    rec = {"value": mc / res["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": f"{res['steps']} ensemble(s) of the workload, {res['cells']} cells each "
-                     f"(64 members): FP64 isovalue map + PID-mean + full PID by O(N^2 M) pairs, "
-                     f"{res['seconds']:.1f} s of one thread"}
-    allc = res.get("all_cores")
+def cpu_baseline_record(res, allc=None):
+    v, sec, n = cpu_value(res)
+    rec = {"value": v, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+           "sample": f"{n} host sample(s) of the plume workload: {res['members']} members x "
+                     f"{res['cells']} cells (4 z-planes of a 256^3 time step), FP64 PID-mean + "
+                     f"full PID by O(N^2 M) pairs, each counted as one item; {sec:.1f} s of "
+                     f"{res['threads']} thread(s)"}
     if allc:
-        rec["all_cores"] = {"value": allc["steps"] * N_MEMBERS * allc["cells"] / allc["seconds"],
-                            "unit": UNIT, "cores": allc["threads"],
-                            "sample": f"{allc['steps']} ensemble(s), the same sample with "
-                                      f"{allc['threads']} BLAS/OpenMP threads"}
+        va, seca, na = cpu_value(allc)
+        rec["all_cores"] = {"value": va, "unit": UNIT, "cores": allc["threads"],
+                            "sample": f"{na} sample(s), the same recipe with {allc['threads']} "
+                                      f"BLAS/OpenMP threads"}
     return rec
 
 
@@ -233,15 +229,15 @@ def kernel_sources_sha16():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel, workload_tag):
-    """DRAM bytes per launch from the committed ncu summary profiles/<kernel>_*<tag>*.md, if
-    it was taken from the current sources (else None)."""
+def ncu_traffic(prefix):
+    """DRAM bytes per full launch from the committed ncu summary profiles/<prefix>*.md, if
+    it was taken from the current kernel sources (else None)."""
     prof_dir = os.path.join(ROOT, "profiles")
     if not os.path.isdir(prof_dir):
         return None
     sha = kernel_sources_sha16()
     for name in sorted(os.listdir(prof_dir)):
-        if not (name.endswith(".md") and name.startswith(kernel) and workload_tag in name):
+        if not (name.endswith(".md") and name.startswith(prefix)):
             continue
         txt = open(os.path.join(prof_dir, name)).read()
         m1 = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
@@ -249,6 +245,72 @@ def ncu_traffic(kernel, workload_tag):
         if m1 and m2 and m1.group(1) == sha:
             return float(m2.group(1))
     return None
+
+
+# kernel kinds of the library's profiler -> kernel names and committed ncu summary prefixes
+KIND_KERNEL = {"stream": "stream_kernel", "gram": "gram_kernel (BF16 operands)",
+               "gram_split": "gram_kernel (split-BF16 operands)",
+               "gram_fp8": "gram_kernel (E4M3 operands)", "finalize": "finalize_kernel",
+               "iso": "iso_kernel", "bands": "bands_kernel", "operands": "gram_operand_kernel",
+               "scale": "member_max_kernel + member_scale_kernel"}
+
+
+def tensor_peak(kind, peaks, sustained):
+    """Dense tensor peak for the kind's operand type: measured BF16 (burst or sustained);
+    E4M3 at twice that, the nominal FP8 : BF16 ratio of the part."""
+    base = peaks["bf16_tflops_sustained"] if sustained and peaks.get("bf16_tflops_sustained") \
+        else peaks["bf16_tflops"]
+    return base * (2.0 if kind == "gram_fp8" else 1.0)
+
+
+def kernel_table(prof, peaks, sustained):
+    """Per kernel kind over the timed region: launches, time per launch, share of the
+    library's kernel time, and the fractions of the HBM and tensor rooflines reached on
+    algorithmic bytes and useful flops."""
+    total = sum(v["total_ms"] for v in prof.values() if v["launches"])
+    rows = {}
+    for k, v in prof.items():
+        if not v["launches"]:
+            continue
+        t = v["total_ms"] * 1e-3
+        r = {"kernel": KIND_KERNEL.get(k, k), "launches": v["launches"],
+             "ms_per_launch": v["total_ms"] / v["launches"], "share": v["total_ms"] / total,
+             "algorithmic_gb_per_launch": v["bytes"] / v["launches"] / 1e9,
+             "hbm_frac": v["bytes"] / t / 1e9 / peaks["hbm_gbs"]}
+        if v["flops"] > 0:
+            r["useful_tflop_per_launch"] = v["flops"] / v["launches"] / 1e12
+            r["tensor_frac"] = v["flops"] / t / 1e12 / tensor_peak(k, peaks, sustained)
+        rows[k] = r
+    return rows
+
+
+def roofline_record(kind, st, peaks, sustained, traffic):
+    """The contract's roofline object for one kernel kind: the roofline that binds is the one
+    with the longer ideal time (bytes / HBM peak against useful flops / tensor peak)."""
+    t = st["total_ms"] * 1e-3
+    hbm = st["bytes"] / t / 1e9
+    rec = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": hbm / peaks["hbm_gbs"], "traffic": traffic}
+    if st["flops"] > 0:
+        tp = tensor_peak(kind, peaks, sustained)
+        tens = st["flops"] / t / 1e12
+        rec["hbm_frac"] = hbm / peaks["hbm_gbs"]
+        rec["tensor_frac"] = tens / tp
+        rec["tensor_achieved_tflops"] = tens
+        rec["tensor_peak_tflops"] = tp
+        if st["flops"] / (tp * 1e12) >= st["bytes"] / (peaks["hbm_gbs"] * 1e9):
+            rec.update({"bound": "tensor", "achieved": tens, "peak": tp, "unit": "TFLOP/s",
+                        "frac": tens / tp})
+    rec["peak_source"] = ("measured" if peaks["source"] == "measured" else "fallback") + \
+        (" (tensor: sustained BF16" + (" x 2, the nominal E4M3 ratio)" if kind == "gram_fp8" else ")")
+         if st["flops"] > 0 and sustained else "")
+    rec["kernel"] = KIND_KERNEL.get(kind, kind)
+    rec["launches"] = st["launches"]
+    rec["ms_per_launch"] = st["total_ms"] / st["launches"]
+    rec["algorithmic_bytes_per_launch"] = st["bytes"] / st["launches"]
+    if st["flops"] > 0:
+        rec["useful_flops_per_launch"] = st["flops"] / st["launches"]
+    return rec
 
 
 # ---------------------------------------------------------------------------------------

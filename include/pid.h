@@ -74,8 +74,24 @@ typedef enum pid_precision {
   PID_FP32 = 0,
   PID_BF16 = 1,             /* u sqrt(w) rounded to bfloat16 */
   PID_SPLIT_BF16 = 2,       /* hi + lo bfloat16 pair; products hi*hi + hi*lo + lo*hi */
-  PID_FP8 = 3               /* E4M3 with one power-of-two scale per ensemble */
+  PID_FP8 = 3               /* E4M3 with a power-of-two scale per member (see below) */
 } pid_precision;
+
+/*
+ * E4M3 operands (PID_FP8). Member i's operands are u_i sqrt(w) s_i, with s_i the largest
+ * power of two such that max_x u_i(x) sqrt(w_x) s_i <= 448, the largest finite E4M3 value;
+ * the tensor-core Gram is unscaled exactly, G_ij = G'_ij / (s_i s_j), as it leaves tensor
+ * memory. Because u subset_p v is unchanged by scaling u (Eq. 9), every member keeps E4M3's
+ * 3-bit relative precision however small its values are. The scales take one extra read of
+ * the ensemble (PID_KERNEL_SCALE) before the Gram. E4M3 rounding (up to 2^-4 of a value per
+ * element) averages over cells: depths and IN_out stay within 1e-3 of the exact values from
+ * 4096 cells on, but one inclusion P_ij is not averaged over members. So a PID_FP8 request
+ * with fewer than 4096 cells (per time step, times the steps of a space-time ensemble) or
+ * with P requested computes its Gram from BF16 operands instead; pid_gram_operands tells
+ * which operands a request uses.
+ */
+pid_status pid_gram_operands(int32_t precision, int64_t cells, int32_t want_matrix,
+                             int32_t* operands);
 
 typedef enum pid_iso_kind {
   PID_ISO_NORMAL = 0,       /* isovalue q ~ Normal(mu, sigma), Sec. 3.5 */
@@ -129,11 +145,15 @@ size_t pid_workspace_bytes(pid_handle h);
  */
 typedef enum pid_kernel_kind {
   PID_KERNEL_STREAM = 0,    /* PID-mean / exact full-PID streaming pass */
-  PID_KERNEL_GRAM = 1,      /* tensor-core Gram */
+  PID_KERNEL_GRAM = 1,      /* tensor-core Gram, BF16 operands */
   PID_KERNEL_FINALIZE = 2,  /* FP64 reduction, depths, ranks */
   PID_KERNEL_ISO = 3,       /* isovalue map alone */
   PID_KERNEL_BANDS = 4,     /* contour boxplot bands */
-  PID_KERNEL_KINDS = 5
+  PID_KERNEL_GRAM_SPLIT = 5,  /* tensor-core Gram, split BF16 operands */
+  PID_KERNEL_GRAM_FP8 = 6,  /* tensor-core Gram, E4M3 operands */
+  PID_KERNEL_OPERANDS = 7,  /* operand staging of the row-block-tiled Gram (N > 256) */
+  PID_KERNEL_SCALE = 8,     /* per-member E4M3 operand scales (one read of the ensemble) */
+  PID_KERNEL_KINDS = 9
 } pid_kernel_kind;
 
 typedef struct pid_kernel_stats {
@@ -351,8 +371,19 @@ typedef struct pid_serve_stats {
 typedef struct pid_server_s* pid_server;
 
 pid_status pid_serve_start(pid_server* out, const pid_serve_cfg* cfg);
-/* Stop the scheduler: waiting requests complete with PID_ERR_CANCELLED, steps in flight
- * finish. Frees everything the server owns. */
+/* Shut the server down in two steps.
+ * pid_serve_cancel: the server takes no more requests (submit and register return
+ *   PID_ERR_CANCELLED), queued requests complete with PID_ERR_CANCELLED, steps in flight
+ *   finish, and every thread blocked in pid_serve_wait returns that request's status
+ *   (PID_OK or PID_ERR_CANCELLED). Returns once the scheduler has exited. The handle stays
+ *   valid: waits, stats and further cancels still work. Any thread may call it, any number
+ *   of times.
+ * pid_serve_stop: cancels (if not yet cancelled), waits until no thread is inside a
+ *   pid_serve_* call on this server, then frees everything the server owns. The handle is
+ *   invalid once it returns. Calls already inside the server when it is entered (a blocked
+ *   wait, say) are safe; no new call may START once pid_serve_stop has been entered: join
+ *   or quiesce other threads first (cancel, join, stop). */
+pid_status pid_serve_cancel(pid_server s);
 pid_status pid_serve_stop(pid_server s);
 /* Register an ensemble [N][ld] float32 (soft masks, or fields with `iso`), cell measures w
  * [M] (or NULL). copy = 1: data (and w) are HOST pointers copied into device memory the
@@ -378,10 +409,10 @@ pid_status pid_serve_stats_get(pid_server s, pid_serve_stats* out);
 pid_status pid_serve_stats_reset(pid_server s);
 
 /*
- * pid_mean_noalloc — PID-mean (the same result as pid_mean) for callers that cannot
- * allocate device memory: code recording a CUDA graph, real-time loops in which a
- * cudaMalloc would synchronise the device, and host applications whose own allocator owns
- * all device memory. The paper has no counterpart; this is an interface convenience.
+ * pid_mean_noalloc — PID-mean (bitwise the result of pid_mean) for callers that cannot
+ * allocate device memory: real-time loops in which a cudaMalloc would synchronise the
+ * device, and host applications whose own allocator owns all device memory. The paper has
+ * no counterpart; this is an interface convenience.
  *
  * No handle is needed and nothing is allocated: the scratch (per-chunk partial sums, FP64
  * totals, a finalisation ticket and an error word) lives in one fixed 4 MiB array inside
@@ -396,7 +427,17 @@ pid_status pid_serve_stats_reset(pid_server s);
  * The first call on a device (with that device current) performs a one-time set-up: it
  * looks up the device address of the scratch array and opts the kernels in to their shared
  * memory; make that first call before any stream capture. Later calls only enqueue work
- * on `stream` and can be captured.
+ * on `stream`.
+ *
+ * The launch always takes the default column-sum exchange and ring depth of the streaming
+ * kernel (no autotuning); every such choice sums in the same fixed order, so the outputs
+ * equal pid_mean's bit for bit, tuned or not.
+ *
+ * There is no handle, so pid_last_error has no text for this call: the status alone says
+ * what went wrong. PID_ERR_INVALID_ARG: N, M or ld out of range (N >= 1, M >= 1, ld >= M),
+ * a null U, or no output. PID_ERR_UNSUPPORTED: N > 512, or the problem needs more scratch
+ * than the fixed array holds (see Limits). PID_ERR_CUDA: the one-time set-up or a launch
+ * failed.
  *
  * Every call on a device shares the one scratch array, which keeps the previous call's
  * contents; each call clears the parts that must start at zero. Calls whose work overlaps

@@ -26,7 +26,7 @@ Every function cites the passage it follows:
   Sec. 4.1         the reliability-weighted mean contour
   Sec. 6.3         4D (space-time) PID: time as one more cell axis
 
-Readings where the paper is silent (each also listed in the design notes):
+Readings where the paper is silent (Sec. 3.2, Sec. 3.5, Sec. 5.1 leave these open):
   * Zero-mass reference mask: u subset_p v = 0 (Sec. 3.2), unlike eID's 1 (Eq. 1).
   * The sums over j in Eq. 10 / Eq. 14 include j = i and are normalised by 1/N.
   * Isovalue distribution q ~ Normal(mu, sigma): u(x) = P(F(x) < q) =

@@ -34,12 +34,14 @@ EXPORTS = [
     "pid_serve_update", "pid_serve_unregister", "pid_serve_submit", "pid_serve_wait",
     "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands", "pid_mean_weighted",
     "pid_spacetime", "pid_depth_from_matrix", "pid_soft_masks_bf16",
-    "pid_selftest_wait_timeout",
+    "pid_selftest_wait_timeout", "pid_gram_operands", "pid_serve_cancel",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
+PID_KERNEL_GRAM_SPLIT, PID_KERNEL_GRAM_FP8, PID_KERNEL_OPERANDS, PID_KERNEL_SCALE = 5, 6, 7, 8
 BAND_INNER_UNION, BAND_INNER_INTERSECTION, BAND_ALL_UNION, BAND_ALL_INTERSECTION, BAND_MEDIAN = \
     1, 2, 4, 8, 16
-KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3, "bands": 4}
+KERNEL_KINDS = {"stream": 0, "gram": 1, "finalize": 2, "iso": 3, "bands": 4, "gram_split": 5,
+                "gram_fp8": 6, "operands": 7, "scale": 8}
 
 
 class PidError(RuntimeError):
@@ -138,6 +140,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_mean_noalloc": ([P, c_int64, c_int64, c_int64, P, P, P, P, P, P, P], c_int),
         "pid_serve_start": ([POINTER(c_void_p), POINTER(pid_serve_cfg)], c_int),
         "pid_serve_stop": ([P], c_int),
+        "pid_serve_cancel": ([P], c_int),
+        "pid_gram_operands": ([c_int32, c_int64, c_int32, POINTER(c_int32)], c_int),
         "pid_serve_register": ([P, P, c_int64, c_int64, c_int64, P, c_int32, POINTER(pid_iso),
                                 c_int32, POINTER(c_int64)], c_int),
         "pid_serve_update": ([P, c_int64, P], c_int),
@@ -243,11 +247,32 @@ def pid_autotune_enable(h, enable: bool) -> int:
     return int(n.value)
 
 
+_NOALLOC_STATUS = {
+    PID_ERR_INVALID_ARG: "N, M or ld out of range (N >= 1, M >= 1, ld >= M), a null U, or no output",
+    PID_ERR_UNSUPPORTED: "N above 512, or more per-chunk partials than the fixed 4 MiB scratch holds",
+    PID_ERR_CUDA: "the one-time device set-up or a kernel launch failed",
+}
+
+
 def pid_mean_noalloc(U, N, M, ld, w, depth, in_in, in_out, rank, device_status=None,
                      stream=None):
-    """PID-mean through the allocation-free entry point (no handle; fixed internal scratch)."""
-    _check(None, load().pid_mean_noalloc(U, N, M, ld, w, depth, in_in, in_out, rank,
-                                         device_status, stream))
+    """PID-mean through the allocation-free entry point (no handle; fixed internal scratch).
+    It reports status codes only (there is no handle for pid_last_error): the error text
+    says what each code means for this call."""
+    st = load().pid_mean_noalloc(U, N, M, ld, w, depth, in_in, in_out, rank, device_status,
+                                 stream)
+    if st != PID_OK:
+        raise PidError(st, "pid_mean_noalloc: " + _NOALLOC_STATUS.get(
+            st, load().pid_status_string(st).decode()))
+
+
+def pid_gram_operands(precision, cells: int, want_matrix: bool) -> int:
+    """The operand precision (PID_BF16, PID_SPLIT_BF16 or PID_FP8) a Gram request runs with."""
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    out = c_int32(-1)
+    _check(None, load().pid_gram_operands(prec, int(cells), int(bool(want_matrix)),
+                                          ctypes.byref(out)))
+    return int(out.value)
 
 
 def pid_batch(h, ensembles, stream=None):
@@ -325,13 +350,14 @@ class Handle:
     def workspace_bytes(self) -> int:
         return int(load().pid_workspace_bytes(self.h))
 
-    def _outputs(self, N, want_P=False, extras=False):
+    def _outputs(self, N, want_P=False, extras=False, want_err=False):
         import torch
         dev = torch.device("cuda", self.device)
         o = {k: torch.empty(N, dtype=torch.float64, device=dev) for k in ("depth", "in_in", "in_out")}
         o["rank"] = torch.empty(N, dtype=torch.int32, device=dev)
         if want_P:
             o["P"] = torch.empty((N, N), dtype=torch.float64, device=dev)
+        if want_P or want_err:
             o["err_est"] = torch.empty(1, dtype=torch.float64, device=dev)
         if extras:
             o["mass"] = torch.empty(N, dtype=torch.float64, device=dev)
@@ -435,10 +461,12 @@ class Handle:
         return o
 
     def full(self, U, w=None, mode="linear", precision="fp32", want_P=False, validate=False,
-             stream=None):
+             stream=None, want_err=False):
+        """Full PID; want_P returns the inclusion matrix P, want_err (or want_P) the Gram's
+        raw error estimate err_est (Gram modes only)."""
         N, M, ld = _check_matrix(U, "U")
         gram = MODES[mode] == PID_MODE_FULL and PRECISIONS[precision] != PID_FP32
-        o = self._outputs(N, want_P=want_P and gram)
+        o = self._outputs(N, want_P=want_P and gram, want_err=want_err and gram)
         opt = pid_options(MODES[mode], PRECISIONS[precision], int(validate), 0)
         pid_full(self.h, U.data_ptr(), N, M, ld, _weights(w, M, U.device), opt,
                  o["depth"].data_ptr(),
@@ -508,6 +536,12 @@ class Server:
     def _chk(self, st):
         if st != PID_OK:
             raise PidError(st, load().pid_status_string(st).decode())
+
+    def cancel(self):
+        """Stop taking requests: queued ones end cancelled, running steps finish, and waits
+        return. The server stays valid (waits and stats still work) until stop()."""
+        if self.s:
+            self._chk(load().pid_serve_cancel(self.s))
 
     def stop(self):
         if self.s:

@@ -80,8 +80,8 @@ struct Launch {
   double bytes = 0, flops = 0;
   GramPlan gp;             // GRAM launches
   int iso_mode = 0;
-  struct Scale { const float* w; int64_t M; float* out; };
-  std::vector<Scale> scales;  // FP8 operand scales to compute before the Gram launch
+  struct Scale { EnsInput in; float* out; };
+  std::vector<Scale> scales;  // E4M3 member scales to compute before the Gram launch
   // TILED launches (one ensemble or time step): operand staging + tiled Gram
   EnsInput in;
   TiledPlan tp;
@@ -136,6 +136,11 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   for (int e = 0; e < count; ++e) {
     pid_status st = to_input(h, ens[e], &in[e]);
     if (st != PID_OK) return st;
+    // E4M3 requests below its cell floor, or asking for P, take BF16 operands (the Gram of
+    // a space-time ensemble sums over the cells of all its steps)
+    if (in[e].mode == PID_MODE_FULL)
+      in[e].precision = gram_operand_precision(in[e].precision, in[e].M * steps,
+                                               ens[owner(e)].P != nullptr);
     if ((st = plan_stream(h, in[e], &pl[e])) != PID_OK) return st;
     is_gram[e] = in[e].mode == PID_MODE_FULL && in[e].precision != PID_FP32;
     is_lin[e] = in[e].mode == PID_MODE_FULL_LINEAR || (in[e].mode == PID_MODE_FULL && !is_gram[e]);
@@ -226,7 +231,6 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       sums[e] = reinterpret_cast<double*>(base + off); off += pl[e].sums_bytes;
       coef[e] = reinterpret_cast<float*>(base + off); off += pl[e].coef_bytes;
       if (is_gram[e]) {
-        scale[e] = reinterpret_cast<float*>(base + off); off += 256;
         gpart[e] = reinterpret_cast<float*>(base + off);
         off += (tiled[e] ? tp[e].gpart_bytes : gp[e].gpart_bytes) * steps;
       }
@@ -234,8 +238,13 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       part[e] = part[o] + static_cast<int64_t>(e) * part_chunks(e) * 2 * in[e].N;
       sums[e] = sums[o];
       coef[e] = coef[o];
-      scale[e] = scale[o];
       if (is_gram[e]) gpart[e] = gpart[o] + static_cast<int64_t>(e) * gram_chunks(e) * in[e].N * in[e].N;
+    }
+    // E4M3 member scales: every ensemble (and every time step) has its own, undone before
+    // its partial Grams are summed
+    if (is_gram[e] && in[e].precision == PID_FP8) {
+      scale[e] = reinterpret_cast<float*>(base + off);
+      off += kScaleBytes;
     }
     pl[e].desc.part = part[e];
     if (stored[e]) {
@@ -325,10 +334,9 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       d.part = part[e];
       d.gpart = gpart[e];
       d.op_scale = nullptr;
-      if (gp[e].prec == PID_FP8 && in[e].w) {
+      if (gp[e].prec == PID_FP8) {
         d.op_scale = scale[e];
-        // once per ensemble (the time steps of a space-time ensemble share the scale)
-        if (owner(e) == e || e == kv.second[0]) L.scales.push_back({in[e].w, in[e].M, scale[e]});
+        L.scales.push_back({in[e], scale[e]});
       }
       units += gp[e].n_gchunks;
       L.bytes += gp[e].bytes;
@@ -354,7 +362,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.op = fused[e] ? op_own[e] : op_buf;
     L.stage = !fused[e];
     L.gpart = gpart[e];
-    L.scale = scale[e];   // the steps of a space-time ensemble share w, hence the scale
+    L.scale = scale[e];
     bp->launches.push_back(L);
   }
   {
@@ -414,8 +422,8 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::GRAM) {
       for (const auto& sc : L.scales) {
-        e = launch_fp8_scale(sc.w, sc.M, sc.out, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
+        const pid_status st = launch_member_scales_one(h, sc.in, sc.out, s);
+        if (st != PID_OK) return st;
       }
       pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units,
                                         L.cells, L.iso_mode, L.bytes, L.flops, s);

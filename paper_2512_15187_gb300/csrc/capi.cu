@@ -521,7 +521,7 @@ static pid_status run_gram_tiled(pid_handle h, const EnsInput& in, EnsPlan& pl,
   const size_t off_sums = pl.part_bytes;
   const size_t off_coef = off_sums + pl.sums_bytes;
   const size_t off_scale = off_coef + pl.coef_bytes;
-  const size_t off_gpart = off_scale + 256;
+  const size_t off_gpart = off_scale + kScaleBytes;
   const size_t off_op = off_gpart + tp.gpart_bytes;
   st = ensure_workspace(h, off_op + tp.op_bytes, s);
   if (st != PID_OK) return st;
@@ -575,7 +575,7 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
   if (gram) {
     if ((st = plan_gram(h, in, &gp)) != PID_OK) return st;
     part_bytes = std::max(part_bytes, gp.part_bytes);
-    gram_bytes = gp.gpart_bytes + 256;  // partial Grams + the FP8 operand scale
+    gram_bytes = gp.gpart_bytes + kScaleBytes;  // partial Grams + the E4M3 member scales
   }
   const size_t need = part_bytes + pl.sums_bytes + pl.coef_bytes + gram_bytes;
   st = ensure_workspace(h, need, s);
@@ -603,7 +603,7 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
   fd.mean_depth = out.mean_depth;
 
   if (gram) {
-    float* gpart = reinterpret_cast<float*>(gbase + 256);
+    float* gpart = reinterpret_cast<float*>(gbase + kScaleBytes);
     float* scale = reinterpret_cast<float*>(gbase);
     st = launch_gram_one(h, in, gp, part, gpart, scale, s);
     if (st != PID_OK) return st;
@@ -649,6 +649,14 @@ using namespace pidh;
 // =======================================================================================
 
 extern "C" {
+
+pid_status pid_gram_operands(int32_t precision, int64_t cells, int32_t want_matrix,
+                             int32_t* operands) {
+  if (!operands || precision < PID_FP32 || precision > PID_FP8 || cells < 0)
+    return PID_ERR_INVALID_ARG;
+  *operands = gram_operand_precision(precision, cells, want_matrix != 0);
+  return PID_OK;
+}
 
 const char* pid_status_string(pid_status s) {
   switch (s) {
@@ -840,7 +848,8 @@ pid_status pid_full(pid_handle h, const float* U, int64_t N, int64_t M, int64_t 
   EnsOutputs out{};
   out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
   out.P = P; out.err_est = err_est;
-  return common_call(h, U, N, M, ld, w, nullptr, o.mode, o.precision, o.validate, out, stream);
+  const int prec = o.mode == PID_MODE_FULL ? gram_operand_precision(o.precision, M, P != nullptr) : o.precision;
+  return common_call(h, U, N, M, ld, w, nullptr, o.mode, prec, o.validate, out, stream);
 }
 
 pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, int64_t ld,
@@ -855,7 +864,8 @@ pid_status pid_from_fields(pid_handle h, const float* F, int64_t N, int64_t M, i
   if (opt) o = *opt;
   EnsOutputs out{};
   out.depth = depth; out.in_in = in_in; out.in_out = in_out; out.rank = rank;
-  return common_call(h, F, N, M, ld, w, iso, o.mode, o.precision, o.validate, out, stream);
+  const int prec = o.mode == PID_MODE_FULL ? gram_operand_precision(o.precision, M, false) : o.precision;
+  return common_call(h, F, N, M, ld, w, iso, o.mode, prec, o.validate, out, stream);
 }
 
 pid_status pid_mean_weighted(pid_handle h, const float* data, int64_t N, int64_t M, int64_t ld,

@@ -182,7 +182,20 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box);
 bool encode_2d_sw128(CUtensorMap* m, const void* base, int elem_bytes, uint64_t inner,
                      uint64_t outer, uint64_t row_bytes);
 
+// E4M3 operands carry 3 mantissa bits: per-element rounding up to 2^-4 of the value, noise
+// that averages over the cells of a member (~0.04 / sqrt(cells)). Depths and IN_out meet the
+// 1e-3 bar from kFp8MinCells cells on; single inclusions P_ij are not averaged over
+// members. A PID_FP8 request with fewer cells, or one that asks for P, therefore computes
+// the Gram from BF16 operands.
+constexpr int64_t kFp8MinCells = 4096;
+inline int gram_operand_precision(int prec, int64_t cells, bool want_matrix) {
+  return (prec == PID_FP8 && (want_matrix || cells < kFp8MinCells)) ? PID_BF16 : prec;
+}
+
 // gram.cu
+// Per-member E4M3 operand scales of one ensemble into `region` (pidk::kScaleBytes of
+// workspace: [2N] scales and inverses, then [N] reduction keys).
+pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* region, cudaStream_t s);
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
 void gram_geometry(pid_handle h, int G, int mpw, bool wide, int prec, int32_t stage_floats,
                    int* dF, int* dO, size_t* smem);
@@ -196,8 +209,8 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDe
 
 pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp);
 // Operand staging (unless the streaming pass already wrote the BF16 operands) and the
-// tiled Gram launch; `op` holds tp.op_bytes, `gpart` tp.gpart_bytes, `scale` one float
-// (E4M3 of a weighted ensemble).
+// tiled Gram launch; `op` holds tp.op_bytes, `gpart` tp.gpart_bytes, `scale`
+// pidk::kScaleBytes (E4M3 member scales).
 pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
                                  float* gpart, float* scale, bool stage_operands, cudaStream_t s);
 

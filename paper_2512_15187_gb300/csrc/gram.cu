@@ -85,10 +85,33 @@ void gram_geometry(pid_handle h, int G, int mpw, bool wide, int prec, int32_t st
   *smem = gram_smem_bytes(G, mpw, wide, prec, f, o, stage_floats);
 }
 
+pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* region, cudaStream_t s) {
+  ScaleParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.data = in.data;
+  sp.w = in.w;
+  sp.ld = in.ld;
+  sp.N = static_cast<int32_t>(in.N);
+  sp.M = static_cast<int32_t>(in.M);
+  iso_fill(in.is_field ? &in.iso : nullptr, &sp.iso_mode, &sp.iso_mu, &sp.iso_inv, &sp.iso_t);
+  sp.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
+              (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
+  sp.scale = region;
+  sp.maxkey = reinterpret_cast<unsigned int*>(region + 2 * kGramTiledMaxN);
+  ProfScope ps(h, PID_KERNEL_SCALE, 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0), 0.0, s);
+  const cudaError_t e = launch_member_scales(sp, h->sms, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "E4M3 member scale launch");
+  return PID_OK;
+}
+
+static int gram_kind(int prec) {
+  return prec == PID_SPLIT_BF16 ? PID_KERNEL_GRAM_SPLIT : (prec == PID_FP8 ? PID_KERNEL_GRAM_FP8 : PID_KERNEL_GRAM);
+}
+
 static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, int mpw, bool wide,
                               int prec, int iso_mode, int grid, size_t smem, double bytes,
                               double flops, cudaStream_t s) {
-  ProfScope ps(h, PID_KERNEL_GRAM, bytes, flops, s);
+  ProfScope ps(h, gram_kind(prec), bytes, flops, s);
   cudaError_t e = launch_gram(gpar, G, mpw, wide, prec, iso_kind(iso_mode), grid, smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "Gram kernel launch");
   return PID_OK;
@@ -102,9 +125,9 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   gpar.one.part = part;
   gpar.one.gpart = gpart;
   gpar.one.op_scale = nullptr;
-  if (gp.prec == PID_FP8 && in.w) {
-    cudaError_t e = launch_fp8_scale(in.w, in.M, scale, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
+  if (gp.prec == PID_FP8) {
+    const pid_status st = launch_member_scales_one(h, in, scale, s);
+    if (st != PID_OK) return st;
     gpar.one.op_scale = scale;
   }
   gpar.n_ens = 1;
@@ -195,9 +218,9 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
 pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
                                  float* gpart, float* scale, bool stage_operands, cudaStream_t s) {
   const float* op_scale = nullptr;
-  if (tp.prec == PID_FP8 && in.w) {
-    cudaError_t e = launch_fp8_scale(in.w, in.M, scale, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "FP8 scale launch");
+  if (tp.prec == PID_FP8) {
+    const pid_status st = launch_member_scales_one(h, in, scale, s);
+    if (st != PID_OK) return st;
     op_scale = scale;
   }
   const int64_t plane = rup(static_cast<int64_t>(in.N) * tp.ldo * tp.elem_bytes, 1024);
@@ -219,7 +242,7 @@ pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPl
   op_p.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
                 (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
   if (stage_operands) {
-    ProfScope ps(h, PID_KERNEL_GRAM, tp.op_rw_bytes, 0.0, s);
+    ProfScope ps(h, PID_KERNEL_OPERANDS, tp.op_rw_bytes, 0.0, s);
     cudaError_t e = launch_gram_operands(op_p, tp.prec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "Gram operand launch");
   }
@@ -245,7 +268,7 @@ pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPl
   tpar.slots = tp.slots;
   for (int t = 0; t < tp.tiles; ++t) tpar.tiles[t] = tp.tile[t];
   tpar.err = h->err_word;
-  ProfScope ps(h, PID_KERNEL_GRAM, tp.gemm_bytes, tp.flops, s);
+  ProfScope ps(h, gram_kind(tp.prec), tp.gemm_bytes, tp.flops, s);
   cudaError_t e = launch_gram_tiled(tpar, tp.prec, tp.n_gchunks * tp.tiles, tp.smem, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "tiled Gram launch");
   return PID_OK;

@@ -1,6 +1,8 @@
 // Instantiations of the tensor-core Gram kernel for N <= 128 with 8 members per warp
 // (gram_kernel.cuh), the launch dispatch over tile, group size, precision and isovalue kind,
-// and the FP8 operand scale.
+// and the per-member E4M3 operand scales.
+#include <algorithm>
+
 #include "gram_kernel.cuh"
 
 namespace pidk {
@@ -24,7 +26,7 @@ size_t gram_smem_bytes(int G, int mpw, bool wide, int prec, int dF, int dO, int 
   const size_t rb = static_cast<size_t>(G) * T + T;
   return 1024 + NG * (dO * op_stage + static_cast<size_t>(dF) * stage_floats * 4 + 2 * rb * 4 +
                       (static_cast<size_t>(dF) + dO + 5) * 8 + 8) + 16 +
-         16 + NG * sizeof(GramLeader);
+         16 + NG * sizeof(GramLeader) + kGramConvWarps * kGramMaxMpw * sizeof(float);
 }
 
 cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec, int iso_kind,
@@ -51,27 +53,156 @@ cudaError_t gram_kernels_init(int max_smem) {
   return e == cudaSuccess ? gram_wide_init(max_smem) : e;
 }
 
-// Power-of-two E4M3 operand scale for weighted ensembles: the largest operand is
-// u sqrt(w) <= sqrt(max w), mapped at or below 448 (the largest finite E4M3 value).
-__global__ void fp8_scale_kernel(const float* w, int64_t M, float* out) {
-  __shared__ unsigned int smax;
-  if (threadIdx.x == 0) smax = 0u;
-  __syncthreads();
-  unsigned int local = 0u;
-  for (int64_t x = threadIdx.x; x < M; x += blockDim.x) local = max(local, __float_as_uint(w[x]));
-  atomicMax(&smax, local);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const float r = sqrtf(__uint_as_float(smax));
-    float s = 1.0f;
-    // largest power of two with r * s <= 448
-    if (r > 0.f && isfinite(r)) s = exp2f(floorf(log2f(448.0f / r)));
-    *out = s;
+// ---- Per-member E4M3 operand scales ----
+//
+// The inclusion u_i subset_p u_j = G_ij / m_i does not change when u_i is multiplied by a
+// positive constant (Eq. 9: the scale cancels between the sums of the ratio), so each
+// member's operands may carry a power-of-two scale s_i of their own, undone exactly when
+// the Gram partials leave the tensor memory (G_ij = G'_ij / (s_i s_j)). Choosing s_i as the
+// largest power of two with max_x u_i(x) sqrt(w_x) s_i <= 448 (the largest finite E4M3
+// value) puts every member's largest operand in the top binade of E4M3, so a member whose
+// values are all small keeps E4M3's full relative precision instead of falling into its
+// subnormal range.
+//
+// One pass finds the per-member maxima. Soft masks, and weighted fields (mapped element by
+// element), reduce the operand u sqrt(w) itself. For unweighted fields it is enough to find
+// the field value that the map sends highest, since every isovalue map is monotone in a
+// simple function of F (its "proxy"), and to map that one value.
+
+namespace {
+
+// Order-preserving unsigned key of a float (keys compare as the floats do; 0 is below the
+// key of every float, so a zeroed key array is the identity of the maximum).
+__device__ __forceinline__ unsigned int fkey(float v) {
+  const unsigned int b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned int k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Proxy of a field value: the soft mask of each isovalue mode is a non-decreasing function
+// of it (Normal: u = erfc(xs)/2 decreases in xs = (F - mu) inv, whose sign carries the
+// direction; sub-level step and uniform maps decrease in F; super-level ones increase;
+// the level map decreases in |F - mu|).
+__device__ __forceinline__ float iso_proxy(float f, int32_t mode, float mu, float inv) {
+  switch (mode) {
+    case ISO_NORMAL: return -((f - mu) * inv);
+    case ISO_STEP_BELOW:
+    case ISO_UNIFORM_BELOW: return -f;
+    case ISO_LEVEL: return -fabsf(f - mu);
+    default: return f;   // ISO_STEP_ABOVE, ISO_UNIFORM_ABOVE
   }
 }
 
-cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s) {
-  fp8_scale_kernel<<<1, 1024, 0, s>>>(w, M, out);
+// The soft mask of the field value whose proxy is p, with the arithmetic of iso_value
+// (the negations are exact, so the value equals the map of that field value).
+__device__ __forceinline__ float iso_from_proxy(float p, int32_t mode, float mu, float inv, float t) {
+  switch (mode) {
+    case ISO_NORMAL: {
+      const float xs = -p;
+      const float h = half_erfc_scaled(fabsf(xs));
+      return xs >= 0.f ? h : 1.0f - h;
+    }
+    case ISO_STEP_BELOW: return iso_value(-p, mode, mu, inv, t);
+    case ISO_UNIFORM_BELOW: return iso_value(-p, mode, mu, inv, t);
+    case ISO_LEVEL: return fmaxf(0.0f, fmaf(p, inv, 1.0f));
+    default: return iso_value(p, mode, mu, inv, t);
+  }
+}
+
+constexpr int kScaleThreads = 256;
+
+// PROXY: unweighted fields (reduce the proxy of F); otherwise reduce u sqrt(w), mapping
+// fields element by element. One CTA per (member, segment of seg_cells cells).
+template <bool PROXY>
+__global__ void __launch_bounds__(kScaleThreads) member_max_kernel(const __grid_constant__ ScaleParams p) {
+  const int i = blockIdx.y;
+  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * p.seg_cells;
+  const int64_t c1 = min(static_cast<int64_t>(p.M), c0 + p.seg_cells);
+  const float* row = p.data + static_cast<int64_t>(i) * p.ld;
+  const bool field = p.iso_mode != ISO_NONE;
+  float best = PROXY ? -__int_as_float(0x7f800000) : 0.0f;
+  for (int64_t x = c0 + 4 * static_cast<int64_t>(threadIdx.x); x < c1; x += 4 * kScaleThreads) {
+    float f[4], w[4] = {1.f, 1.f, 1.f, 1.f};
+    int n = 4;
+    if (p.vec_ok && x + 4 <= c1) {
+      const float4 a = __ldcs(reinterpret_cast<const float4*>(row + x));
+      f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+      if (!PROXY && p.w) {
+        const float4 b = __ldg(reinterpret_cast<const float4*>(p.w + x));
+        w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
+      }
+    } else {
+      n = static_cast<int>(c1 - x < 4 ? c1 - x : 4);
+      for (int v = 0; v < n; ++v) {
+        f[v] = __ldcs(row + x + v);
+        if (!PROXY && p.w) w[v] = __ldg(p.w + x + v);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      if (v >= n) break;
+      float val;
+      if constexpr (PROXY) {
+        val = iso_proxy(f[v], p.iso_mode, p.iso_mu, p.iso_inv);
+      } else {
+        const float u = field ? iso_value(f[v], p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t) : f[v];
+        val = p.w ? u * sqrtf(w[v]) : u;
+      }
+      best = fmaxf(best, val);
+    }
+  }
+  // block maximum, then one atomic per CTA
+  __shared__ float red[kScaleThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = red[0];
+    for (int k = 1; k < kScaleThreads / 32; ++k) b = fmaxf(b, red[k]);
+    atomicMax(p.maxkey + i, fkey(b));
+  }
+}
+
+// s_i from the maximum: the largest k with v 2^k <= 448 = 1.75 * 2^8, i.e. k = 8 - e when
+// the significand of v (in [1, 2)) is at most 1.75, else 7 - e; k is kept within [-63, 63]
+// so that every product of two inverse scales is a normal FP32 power of two. A member with
+// no positive value (all zeros) takes s_i = 1.
+__global__ void member_scale_kernel(const __grid_constant__ ScaleParams p, bool proxy) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= p.N) return;
+  float v = fkey_inv(p.maxkey[i]);
+  if (proxy) v = iso_from_proxy(v, p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
+  int k = 0;
+  if (v > 0.f && v < __int_as_float(0x7f800000)) {
+    const unsigned int b = __float_as_uint(v);
+    const int e = static_cast<int>((b >> 23) & 0xffu) - 127;   // -127: subnormal v
+    k = ((b & 0x7fffffu) <= 0x600000u ? 8 : 7) - e;
+    k = max(-63, min(63, k));
+  }
+  p.scale[i] = __uint_as_float(static_cast<unsigned int>(127 + k) << 23);
+  p.scale[p.N + i] = __uint_as_float(static_cast<unsigned int>(127 - k) << 23);
+}
+
+}  // namespace
+
+cudaError_t launch_member_scales(const ScaleParams& p, int sms, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(p.maxkey, 0, static_cast<size_t>(p.N) * sizeof(unsigned int), s);
+  if (e != cudaSuccess) return e;
+  ScaleParams q = p;
+  // about four CTAs per SM over all members, segments of at least 4096 cells
+  const int64_t want = std::max<int64_t>(1, (4LL * sms + p.N - 1) / p.N);
+  const int64_t segs = std::max<int64_t>(1, std::min<int64_t>(want, (p.M + 4095) / 4096));
+  q.seg_cells = static_cast<int32_t>(((p.M + segs - 1) / segs + 1023) / 1024 * 1024);
+  const dim3 grid(static_cast<unsigned>((p.M + q.seg_cells - 1) / q.seg_cells), static_cast<unsigned>(p.N));
+  const bool proxy = p.iso_mode != ISO_NONE && p.w == nullptr;
+  if (proxy) member_max_kernel<true><<<grid, kScaleThreads, 0, s>>>(q);
+  else member_max_kernel<false><<<grid, kScaleThreads, 0, s>>>(q);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  member_scale_kernel<<<(p.N + 255) / 256, 256, 0, s>>>(q, proxy);
   return cudaGetLastError();
 }
 

@@ -8,7 +8,7 @@
 //     isovalue map (Sec. 3.5), run the exact PID-mean arithmetic of the streaming kernel
 //     (mean contour, m_i, A_i) and write u sqrt(w) as tensor-core operands into a shared-
 //     memory ring in the K-major 128-byte-swizzle layout: BF16, a hi + lo BF16 pair, or
-//     E4M3 times a power-of-two scale;
+//     E4M3 times a power-of-two scale per member (see member_max_kernel);
 //   * one thread issues tcgen05.mma with A = B = that operand tile (G = U' U'^T), M = 128
 //     rows, N = N rounded up to 16, accumulating in FP32 in tensor memory (double-buffered
 //     per cell chunk); split BF16 issues hi.hi + hi.lo + lo.hi;
@@ -105,6 +105,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, SPO = S::SPO, MB = S::MB, NBUF = S::NBUF;
   static_assert(!WIDE || G == 16, "the wide tile uses all 16 warps as one group");
   static_assert(SPO == 1 || SPO == 2, "FP32 stages per operand stage");
+  static_assert(MPW <= kGramMaxMpw, "member scale slots per warp");
   constexpr int NG = kGramConvWarps / G;             // independent groups per CTA
   constexpr int ROWS = MPW * G;                      // operand rows a group writes (>= N)
   constexpr uint32_t PLANE = ROWS * 128;             // one K-block: [ROWS][128 bytes]
@@ -139,6 +140,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags_all + 2 * NG);
   GramLeader* lead_all = reinterpret_cast<GramLeader*>(
       (reinterpret_cast<uintptr_t>(tmem_slot + 1) + 15) & ~static_cast<uintptr_t>(15));
+  // E4M3: the per-member operand scales of each warp's members (written and read by that
+  // warp alone)
+  float* wsc = reinterpret_cast<float*>(lead_all + NG) + warp * kGramMaxMpw;
 
   unsigned char* op_ring = smem + static_cast<size_t>(grp) * dO * OP_STAGE;
   float* f_ring = f_all + static_cast<size_t>(grp) * dF * SF;
@@ -286,7 +290,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 
   // ---- accumulator drain of the group's kc-th unit (warps 0-3, one TMEM lane quarter each)
   // into that unit's partial Gram gp [N][N] ----
-  auto drain = [&](float* gp, int N, float unscale, long kc) -> bool {
+  // E4M3 operands carry the per-member scales osc[0..N) (nullptr: 256 for every member),
+  // undone here exactly: G_ij = G'_ij / (s_i s_j), the inverses osc[N + i] being powers of two.
+  auto drain = [&](float* gp, int N, const float* osc, long kc) -> bool {
     const int nmma = (N + 15) & ~15;
     const int b = static_cast<int>(kc % NBUF);
     if (!mbar_wait_bounded(&accF[b], static_cast<uint32_t>((kc / NBUF) & 1), kWaitTimeoutNs))
@@ -300,9 +306,23 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         float v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * q) << 16) + b * BUFC + mb * 256 + j0, v);
         if (row < N) {
+          if constexpr (PREC == 3) {
+            if (osc != nullptr) {
+              const float ir = osc[N + row];
 #pragma unroll
-          for (int jj = 0; jj < 32; ++jj)
-            if (j0 + jj < N) gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj] * unscale;
+              for (int jj = 0; jj < 32; ++jj)
+                if (j0 + jj < N)
+                  gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj] * (ir * osc[N + j0 + jj]);
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 32; ++jj)
+                if (j0 + jj < N) gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj] * (1.0f / 65536.0f);
+            }
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 32; ++jj)
+              if (j0 + jj < N) gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj];
+          }
         }
       }
     }
@@ -332,7 +352,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   long o_round = 0;
   float* prev_gp = nullptr;          // partial Gram of the previous unit, still to drain
   int prev_N = 0;
-  float prev_unscale = 1.0f;
+  const float* prev_osc = nullptr;   // its E4M3 member scales
   long prev_kc = -1;
   bool aborted = false;
   uint32_t bad = 0;
@@ -345,7 +365,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   const float* wptr = nullptr;
   int64_t ld = 0;
   uint32_t idesc = 0;
-  float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f, scale = 1.0f;
+  float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f;
+  const float* osc = nullptr;   // E4M3 member scales of the current ensemble
   int iso_md = 0;
   for (int u = u_begin; u < u_end && !aborted; ++u, ++kc) {
     if (u >= e_end) {
@@ -372,7 +393,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       pad = ISO == ISOK_NONE ? 0.f
                              : (ISO == ISOK_NORMAL ? copysignf(__int_as_float(0x7f800000), iso_inv)
                                                    : dir * __int_as_float(0x7f800000));
-      if constexpr (PREC == 3) scale = dp->op_scale ? *dp->op_scale : 256.0f;
+      if constexpr (PREC == 3) {
+        osc = dp->op_scale;
+        if (lane < MPW) {
+          const int i = q + lane * G;
+          wsc[lane] = osc == nullptr ? 256.0f : (i < N ? osc[i] : 1.0f);
+        }
+        __syncwarp();
+      }
     }
     const EnsDesc& d = *dp;
     const int c = u - e_begin;
@@ -521,7 +549,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
           float2 t = make_float2(x[m][v], x[m][v + 1]);
           if (has_w) t = f2_mul(t, make_float2(sw[v], sw[v + 1]));
           if constexpr (PREC == 3) {
-            t = f2_mul(t, f2(scale));
+            t = f2_mul(t, f2(wsc[m]));
             h[v / 2] = __nv_cvt_float2_to_fp8x2(t, __NV_SATFINITE, __NV_E4M3);
           } else {
             const __nv_bfloat162 hb = __floats2bfloat162_rn(t.x, t.y);
@@ -561,14 +589,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       // last products have long landed; a single buffer must be drained before the next
       // chunk's first MMA, which is issued after the barrier of its second operand stage.
       if (q < kGramEpiWarps && prev_gp != nullptr && st == (NBUF == 2 ? n_st / 2 : 0)) {
-        if (!drain(prev_gp, prev_N, prev_unscale, prev_kc)) cflag[(kt + 1) & 1] = 1;
+        if (!drain(prev_gp, prev_N, prev_osc, prev_kc)) cflag[(kt + 1) & 1] = 1;
         prev_gp = nullptr;
       }
     }
     if (aborted) break;
     prev_gp = d.gpart + static_cast<size_t>(c) * N * N;
     prev_N = N;
-    prev_unscale = PREC == 3 ? 1.0f / (scale * scale) : 1.0f;
+    prev_osc = osc;
     prev_kc = kc;
 #pragma unroll
     for (int m = 0; m < MPW; ++m) {
@@ -588,7 +616,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     if (cflag[kt & 1]) aborted = true;
     if (!aborted && leader && !issue_pending()) aborted = true;
     if (!aborted && q < kGramEpiWarps && prev_gp != nullptr &&
-        !drain(prev_gp, prev_N, prev_unscale, prev_kc))
+        !drain(prev_gp, prev_N, prev_osc, prev_kc))
       aborted = true;
   }
   if (bad) atomicOr(p.err, bad);

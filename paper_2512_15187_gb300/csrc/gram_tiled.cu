@@ -9,7 +9,7 @@
 //
 //   * gram_operand_kernel maps each input element once (isovalue map of Sec. 3.5, times
 //     sqrt w) and stores the operand rows in HBM as BF16, as a BF16 hi + lo pair, or as
-//     E4M3 times the ensemble's power-of-two scale: [N][ldo] planes, cells contiguous;
+//     E4M3 times the member's power-of-two scale: [N][ldo] planes, cells contiguous;
 //   * gram_tiled_kernel computes one tile of one cell chunk per CTA, from a table of the
 //     upper block triangle's products (row block r of 128 members against column blocks
 //     c >= r; the finalisation symmetrises). BF16 and E4M3 tiles take whole block rows,
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kOperandThreads) gram_operand_kernel(const __g
   // ldo is a multiple of 64 elements and x0 of 4: the 4 operands of a thread never cross
   // the end of the row's storage.
   if constexpr (PREC == 3) {
-    const float sc = p.op_scale ? *p.op_scale : 256.0f;
+    const float sc = p.op_scale ? p.op_scale[i] : 256.0f;   // member i's power-of-two scale
     const uint32_t lo2 = __nv_cvt_float2_to_fp8x2(f2_mul(make_float2(t[0], t[1]), f2(sc)), __NV_SATFINITE, __NV_E4M3);
     const uint32_t hi2 = __nv_cvt_float2_to_fp8x2(f2_mul(make_float2(t[2], t[3]), f2(sc)), __NV_SATFINITE, __NV_E4M3);
     uint8_t* dst = static_cast<uint8_t*>(p.hi) + static_cast<int64_t>(i) * p.ldo + x0;
@@ -233,11 +233,9 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
   tc_fence_after();
   {
     float* gp = p.gpart + static_cast<size_t>(c) * N * N;
-    float unscale = 1.0f;
-    if constexpr (PREC == 3) {
-      const float sc = p.op_scale ? *p.op_scale : 256.0f;
-      unscale = 1.0f / (sc * sc);
-    }
+    // E4M3: G_ij = G'_ij / (s_i s_j) with the members' power-of-two scales (inverses at
+    // op_scale[N + i]); the product of two inverses is exact
+    const float* inv = PREC == 3 && p.op_scale ? p.op_scale + N : nullptr;
     for (int sg = 0; sg < nseg; ++sg) {
       const int ra = td.ra[sg], cb = td.cb[sg], width = 128 * td.nb[sg];
       const int i = 128 * ra + 32 * warp + lane;
@@ -248,11 +246,12 @@ __global__ void __launch_bounds__(kTiledThreads, 1) gram_tiled_kernel(const __gr
         tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(td.col[sg] + j0), v);
         const bool mirror = jb / 128 != ra;           // off the diagonal block
         if (i < N) {
+          const float ir = PREC != 3 ? 1.0f : (inv ? inv[i] : 1.0f / 65536.0f);
 #pragma unroll
           for (int jj = 0; jj < 32; ++jj) {
             const int j = jb + jj;
             if (j < N) {
-              const float g = v[jj] * unscale;
+              const float g = PREC != 3 ? v[jj] : v[jj] * (inv ? ir * inv[j] : ir);
               gp[static_cast<size_t>(j) * N + i] = g;
               if (mirror) gp[static_cast<size_t>(i) * N + j] = g;
             }

@@ -54,7 +54,7 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   int32_t validate;
   int32_t pad0;
   float* gpart;         // Gram launches: [n_chunks][N][N] float32 partial Gram (G_ij at j*N + i)
-  const float* op_scale;  // Gram FP8: device scalar multiplying every operand (nullptr = 256)
+  const float* op_scale;  // Gram E4M3: [2N] per-member scales s_i, then 1/s_i (nullptr = 256)
   int64_t work_begin;   // member-cells of the launch's earlier ensembles (0 for the first)
   float* u_out;         // streaming pass 1 of a field: also store the soft masks here,
                         // [N][round_up(M, 4)] float32, for pass 2 to read (nullptr = no)
@@ -86,6 +86,7 @@ constexpr int kGramThreads = kGramConvWarps * 32;
 constexpr int kGramMaxN = 256;        // two M = 128 tensor-core row blocks (the wide tile)
 constexpr int kGramNarrowMaxN = 128;  // one M = 128 row block
 constexpr int kGramTiledMaxN = 512;   // row-block-tiled Gram over operands staged in HBM
+constexpr int kGramMaxMpw = 16;       // members per converter warp (the 256-row wide tile)
 
 struct GramParams {
   EnsDesc one;
@@ -109,7 +110,7 @@ struct OperandParams {
   const float* w;          // [M] cell measures or nullptr
   void* hi;                // [N][ldo] BF16 bit patterns, or E4M3 bytes
   void* lo;                // split BF16: [N][ldo] low parts; else nullptr
-  const float* op_scale;   // E4M3: device scalar multiplying every operand (nullptr = 256)
+  const float* op_scale;   // E4M3: [2N] per-member scales s_i, then 1/s_i (nullptr = 256)
   int64_t ld, ldo;         // ldo: a multiple of 64 elements
   int32_t N, M;
   int32_t iso_mode;
@@ -132,7 +133,7 @@ struct TiledParams {
   CUtensorMap op_hi;       // [N][ldo] operands; box {128 bytes of cells, 128 rows}, 128-byte swizzle
   CUtensorMap op_lo;       // split BF16: the low parts
   float* gpart;            // [n_chunks][N][N] FP32 partial Grams (G_ij at j*N + i)
-  const float* op_scale;   // E4M3 scale (nullptr = 256)
+  const float* op_scale;   // E4M3: [2N] per-member scales s_i, then 1/s_i (nullptr = 256)
   int32_t N, M, R;         // members, cells, 128-row blocks
   int32_t chunk_cells;     // multiple of 128
   int32_t n_chunks, tiles_per_chunk;
@@ -209,7 +210,24 @@ size_t gram_smem_bytes(int G, int mpw, bool wide, int prec, int dF, int dO, int 
 cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec, int iso_kind,
                         int grid, size_t smem, cudaStream_t s);
 cudaError_t gram_kernels_init(int max_smem);
-cudaError_t launch_fp8_scale(const float* w, int64_t M, float* out, cudaStream_t s);
+// Per-member E4M3 operand scales (gram_kernel.cu): s_i is the largest power of two with
+// max_x u_i(x) sqrt(w_x) s_i <= 448, the largest finite E4M3 value.
+struct ScaleParams {
+  const float* data;       // [N][ld] soft masks, or fields mapped by iso_mode
+  const float* w;          // [M] cell measures or nullptr
+  int64_t ld;
+  int32_t N, M;
+  int32_t iso_mode;
+  float iso_mu, iso_inv, iso_t;
+  int32_t vec_ok;          // rows and weights 16-byte aligned: 4-cell vector loads
+  int32_t seg_cells;       // cells per CTA (a multiple of 1024)
+  unsigned int* maxkey;    // [N] order-preserving keys of the per-member maxima (workspace)
+  float* scale;            // [2N] out: s_i, then 1/s_i
+};
+// Zero the keys, reduce the per-member maxima and write the scales (three launches).
+cudaError_t launch_member_scales(const ScaleParams& p, int sms, cudaStream_t s);
+// Workspace of one ensemble's scales: [2N] floats and [N] keys, for N <= 512.
+constexpr size_t kScaleBytes = 8192;
 // Row-block-tiled Gram (gram_tiled.cu).
 cudaError_t launch_gram_operands(const OperandParams& p, int prec, cudaStream_t s);
 cudaError_t launch_gram_tiled(const TiledParams& p, int prec, int grid, size_t smem, cudaStream_t s);

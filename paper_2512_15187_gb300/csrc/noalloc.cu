@@ -1,9 +1,8 @@
 // pid_mean_noalloc: PID-mean without any device allocation.
 //
-// Some callers cannot allocate device memory when they need a depth: code recording a CUDA
-// graph (an allocation during stream capture is an error), real-time loops where a
-// cudaMalloc would synchronise the device, and host applications that hand out all device
-// memory through their own allocator. The regular entry points allocate workspace through
+// Some callers cannot allocate device memory when they need a depth: real-time loops where
+// a cudaMalloc would synchronise the device, and host applications that hand out all
+// device memory through their own allocator. The regular entry points allocate workspace through
 // a handle; this one keeps its scratch (the per-chunk partial sums, the FP64 totals, the
 // finalisation ticket and the device error word) in a fixed array compiled into the
 // library, and otherwise runs the same streaming and finalisation kernels as pid_mean.

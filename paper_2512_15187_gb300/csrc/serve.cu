@@ -76,7 +76,9 @@ size_t out_block_bytes(int64_t N) {  // depth, in_in, in_out, mean_depth (f64) +
 struct pid_server_s {
   pid_serve_cfg cfg{};
   std::mutex mu;
-  std::condition_variable cv_sched, cv_done;
+  std::condition_variable cv_sched, cv_done, cv_idle;
+  int active = 0;              // threads inside a pid_serve_* call (counted under mu)
+  std::once_flag join_once;    // the scheduler is joined by the first pid_serve_cancel
   std::deque<std::shared_ptr<Request>> queue;
   std::unordered_map<uint64_t, std::shared_ptr<Request>> reqs;
   std::map<int64_t, std::unique_ptr<Ensemble>> ens;
@@ -94,6 +96,18 @@ struct pid_server_s {
 };
 
 namespace {
+
+// Counts the calling thread as inside the server for the scope's lifetime; s->mu must be
+// held when the scope begins and when it ends (declare it after the lock).
+class CallScope {
+ public:
+  explicit CallScope(pid_server s) : s_(s) { ++s_->active; }
+  ~CallScope() {
+    if (--s_->active == 0) s_->cv_idle.notify_all();
+  }
+ private:
+  pid_server s_;
+};
 
 void finish(pid_server s, const std::shared_ptr<Request>& r, pid_status st) {
   r->status = st;
@@ -299,14 +313,30 @@ pid_status pid_serve_start(pid_server* out, const pid_serve_cfg* cfg) {
   return PID_OK;
 }
 
-pid_status pid_serve_stop(pid_server s) {
-  if (!s) return PID_OK;
+pid_status pid_serve_cancel(pid_server s) {
+  if (!s) return PID_ERR_INVALID_ARG;
   {
     std::lock_guard<std::mutex> lk(s->mu);
     s->stopping = true;
   }
   s->cv_sched.notify_all();
-  if (s->sched.joinable()) s->sched.join();
+  // The scheduler cancels the queue, lets the running steps finish and exits; every
+  // request is then done and every waiter has been woken.
+  std::call_once(s->join_once, [s] {
+    if (s->sched.joinable()) s->sched.join();
+  });
+  return PID_OK;
+}
+
+pid_status pid_serve_stop(pid_server s) {
+  if (!s) return PID_OK;
+  pid_serve_cancel(s);
+  {
+    // threads still inside a call (a wait that has just been woken) leave before the
+    // server is freed
+    std::unique_lock<std::mutex> lk(s->mu);
+    s->cv_idle.wait(lk, [s] { return s->active == 0; });
+  }
   DeviceGuard g(s->cfg.device);
   for (Slot& sl : s->slots) {
     if (sl.stream) cudaStreamSynchronize(sl.stream);
@@ -342,6 +372,7 @@ pid_status pid_serve_register(pid_server s, const float* data, int64_t N, int64_
   e->bytes = static_cast<size_t>(N) * ld * 4 + (w ? static_cast<size_t>(M) * 4 : 0);
   DeviceGuard g(s->cfg.device);
   std::lock_guard<std::mutex> lk(s->mu);
+  CallScope cs(s);
   if (s->stopping) return PID_ERR_CANCELLED;
   const size_t reserve = static_cast<size_t>(s->cfg.max_inflight) * s->cfg.workspace_reserve_bytes;
   if (s->cfg.hbm_budget_bytes && s->resident + e->bytes + reserve > s->cfg.hbm_budget_bytes)
@@ -384,6 +415,7 @@ pid_status pid_serve_update(pid_server s, int64_t ensemble_id, const float* data
   if (!s || !data_host) return PID_ERR_INVALID_ARG;
   DeviceGuard g(s->cfg.device);
   std::unique_lock<std::mutex> lk(s->mu);
+  CallScope cs(s);
   Ensemble* e = find_ens(s, ensemble_id);
   if (!e || !e->owned) return PID_ERR_INVALID_ARG;
   s->cv_done.wait(lk, [&] { return e->inflight == 0; });
@@ -399,6 +431,7 @@ pid_status pid_serve_unregister(pid_server s, int64_t ensemble_id) {
   if (!s) return PID_ERR_INVALID_ARG;
   DeviceGuard g(s->cfg.device);
   std::unique_lock<std::mutex> lk(s->mu);
+  CallScope cs(s);
   Ensemble* e = find_ens(s, ensemble_id);
   if (!e) return PID_ERR_INVALID_ARG;
   s->cv_done.wait(lk, [&] { return e->inflight == 0; });
@@ -421,6 +454,7 @@ pid_status pid_serve_submit(pid_server s, int64_t ensemble_id, const pid_options
   r->opt = opt ? *opt : pid_options{PID_MODE_MEAN, PID_FP32, 0, 0};
   {
     std::lock_guard<std::mutex> lk(s->mu);
+    CallScope cs(s);
     if (s->stopping) return PID_ERR_CANCELLED;
     if (!find_ens(s, ensemble_id)) return PID_ERR_INVALID_ARG;
     if (static_cast<int32_t>(s->queue.size()) >= s->cfg.max_queue) return PID_ERR_BUSY;
@@ -441,6 +475,7 @@ pid_status pid_serve_wait(pid_server s, uint64_t ticket, int64_t timeout_ms, dou
                           double* mean_depth_host) {
   if (!s) return PID_ERR_INVALID_ARG;
   std::unique_lock<std::mutex> lk(s->mu);
+  CallScope cs(s);
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return PID_ERR_INVALID_ARG;
   std::shared_ptr<Request> r = it->second;
@@ -449,7 +484,7 @@ pid_status pid_serve_wait(pid_server s, uint64_t ticket, int64_t timeout_ms, dou
   } else if (!s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; })) {
     return PID_ERR_TIMEOUT;
   }
-  s->reqs.erase(it);
+  s->reqs.erase(r->ticket);   // `it` may be stale: other tickets were erased while we waited
   if (r->status == PID_OK) {
     const size_t n = r->depth.size();
     if (depth_host) std::memcpy(depth_host, r->depth.data(), n * 8);
@@ -464,6 +499,7 @@ pid_status pid_serve_wait(pid_server s, uint64_t ticket, int64_t timeout_ms, dou
 pid_status pid_serve_stats_get(pid_server s, pid_serve_stats* out) {
   if (!s || !out) return PID_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
+  CallScope cs(s);
   std::memset(out, 0, sizeof(*out));
   out->submitted = s->submitted;
   out->completed = s->completed;
@@ -493,6 +529,7 @@ pid_status pid_serve_stats_get(pid_server s, pid_serve_stats* out) {
 pid_status pid_serve_stats_reset(pid_server s) {
   if (!s) return PID_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(s->mu);
+  CallScope cs(s);
   s->submitted = s->completed = s->failed = s->steps = s->batched = 0;
   s->member_cells = 0;
   s->lat_ms.clear();

@@ -5,6 +5,8 @@
     python -m paper_2512_15187_gb300.profile_case mean          # PID-mean of soft masks
     python -m paper_2512_15187_gb300.profile_case linear        # exact full PID, O(N M)
     python -m paper_2512_15187_gb300.profile_case gram --precision bf16 --ensembles 4
+    python -m paper_2512_15187_gb300.profile_case plume --side 128   # one 3D plume step:
+        # PID-mean, E4M3 Gram and split-BF16 Gram of 200 members on side^3 cells, one batch
 
 Each case builds its inputs on the device (seeded), makes one call (planning, tuning and
 graph capture), then `--repeat` timed calls, and prints the best call time (CUDA events,
@@ -19,7 +21,8 @@ import argparse
 
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fields", "fields-full", "mean", "linear", "gram"])
+    ap.add_argument("case", choices=["fields", "fields-full", "mean", "linear", "gram", "plume"])
+    ap.add_argument("--side", type=int, default=128, help="plume: cells per axis")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--cells", type=int, default=1 << 20)
     ap.add_argument("--ensembles", type=int, default=1,
@@ -37,11 +40,19 @@ def main(argv=None) -> None:
     from . import binding, build, synth
     build.build()
     N, M, E = a.members, a.cells, a.ensembles
+    if a.case == "plume":
+        N, M, E = 200, a.side ** 3, 1
     if 4.0 * N * M * E > a.max_gb * 1e9:
         raise SystemExit(f"input above --max-gb {a.max_gb}")
     h = binding.Handle(0)
     if a.no_autotune:
         h.autotune(False)
+    if a.case == "plume":
+        U = synth.plume_3d(N, a.side, t=8, T=16)
+        items = [dict(data=U, mode="mean"), dict(data=U, mode="full", precision="fp8"),
+                 dict(data=U, mode="full", precision="split_bf16")]
+        _run(h, items, a, f"plume N={N} M={M} (mean, fp8, split_bf16)")
+        return
     X = torch.empty((E, N, M), device="cuda")
     side = int(round(M ** 0.5))
     for e in range(E):
@@ -56,6 +67,11 @@ def main(argv=None) -> None:
     prec = a.precision if mode == "full" else "fp32"
     items = [dict(data=X[e], iso=(0.5, 0.05, 0) if is_field else None, mode=mode, precision=prec)
              for e in range(E)]
+    _run(h, items, a, f"{a.case} {mode} {prec} N={N} M={M} E={E}")
+
+
+def _run(h, items, a, label) -> None:
+    import torch
     outs = h.batch(items)          # first call: plans, tunes and records the graph
     h.sync()
     h.profile(True)
@@ -71,8 +87,7 @@ def main(argv=None) -> None:
     h.sync()
     prof = h.profile_read()
     h.profile(False)
-    print("ok", a.case, mode, prec, f"N={N} M={M} E={E}", float(outs[0]["depth"].sum()),
-          f"call best {min(ms):.3f} ms")
+    print("ok", label, float(outs[0]["depth"].sum()), f"call best {min(ms):.3f} ms")
     for kind, st in prof.items():
         if st["launches"]:
             per = st["total_ms"] / st["launches"]

@@ -14,7 +14,8 @@ Workloads (sizes of the benchmark configurations):
   radial_disk     N = 128 perturbed radial masks on 2^20 scattered points in the
                   unit disk with log-uniform lumped-area weights (non-Cartesian)
   plume_3d        smoke-plume-like 3D soft masks (sigmoid of a noise-displaced
-                  cone, 5-octave fBm), generated on the device with torch
+                  cone, 5-octave fBm), generated on the device with torch;
+                  plume_3d_slab gives a slab of z-planes of the same recipe
   ellipsoids_3d   3D ellipsoid soft masks, 80% normal members and 20% outliers (the
                   scalability study's ensembles), generated on the device with torch
 """
@@ -197,6 +198,50 @@ def plume_3d(N: int, R: int, t: int = 0, T: int = 16, seed: int = DEFAULT_SEED +
             lat = torch.rand((1, 1, L, L, L), generator=g, device=device) * 2.0 - 1.0
             noise += amp * Fnn.interpolate(lat, size=(R, R, R), mode="trilinear",
                                           align_corners=True)[0, 0]
+            amp *= 0.5
+        out[i] = torch.sigmoid((base + 0.08 * noise) / 0.02).reshape(-1)
+    return out
+
+
+def plume_3d_slab(N: int, R: int, z0: int, nz: int, t: int = 0, T: int = 16,
+                  seed: int = DEFAULT_SEED + 4, device: str = "cpu", octaves: int = 5):
+    """Planes z0 .. z0 + nz - 1 of plume_3d(N, R, t, T, seed) on `device`: [N, nz * R^2].
+
+    The same recipe restricted to a slab of the volume, for samples that a host can afford
+    (the whole 256^3 volume of 200 members takes minutes on host cores). Trilinear
+    interpolation with aligned corners is separable, so each octave's lattice is
+    interpolated along z at the slab's planes first, then bilinearly in (y, x). On a given
+    device the lattices are the draws of plume_3d, so the slab matches the corresponding
+    planes of the full volume up to rounding; on the host the generator's stream differs from
+    the GPU's, so a host slab is another member of the same ensemble distribution.
+    """
+    import torch
+    import torch.nn.functional as Fnn
+
+    zs = torch.arange(z0, z0 + nz, dtype=torch.float32, device=device)
+    z = (zs / (R - 1)).view(nz, 1, 1)
+    yy = torch.linspace(-0.5, 0.5, R, device=device).view(1, R, 1)
+    xx = torch.linspace(-0.5, 0.5, R, device=device).view(1, 1, R)
+    rho = torch.sqrt(yy ** 2 + xx ** 2)
+    h = 0.3 + 0.65 * t / max(T - 1, 1)
+    cone = (0.04 + 0.25 * z) * torch.clamp((h - z) / 0.08, 0.0, 1.0)
+    base = cone - rho  # [nz, R, R]
+    out = torch.empty((N, nz * R * R), dtype=torch.float32, device=device)
+    for i in range(N):
+        g = torch.Generator(device=device)
+        g.manual_seed((int(seed) * 1_000_003 + t * 10_007 + i) & 0x7FFFFFFFFFFFFFFF)
+        noise = torch.zeros((nz, R, R), device=device)
+        amp = 1.0
+        for o in range(octaves):
+            L = 4 * (2 ** o) + 1
+            lat = torch.rand((L, L, L), generator=g, device=device) * 2.0 - 1.0
+            # along z: lattice coordinate of each slab plane, linear weights
+            pz = zs * (L - 1) / (R - 1)
+            k0 = torch.clamp(pz.floor().long(), 0, L - 2)
+            fz = (pz - k0.to(pz.dtype)).view(nz, 1, 1)
+            planes = lat[k0] * (1.0 - fz) + lat[k0 + 1] * fz          # [nz, L, L]
+            noise += amp * Fnn.interpolate(planes.unsqueeze(1), size=(R, R), mode="bilinear",
+                                           align_corners=True)[:, 0]
             amp *= 0.5
         out[i] = torch.sigmoid((base + 0.08 * noise) / 0.02).reshape(-1)
     return out

@@ -69,7 +69,7 @@ def test_ellipses_20x128x128(H):
     _check(outs[0], ref_mean, FP32_TOL, "ellipses mean")
     _check(outs[1], ref_full, FP32_TOL, "ellipses linear")
     for o, p in zip(outs[2:5], PRECS):
-        _check(o, ref_full, GRAM_TOL, f"ellipses {p}", P, 5e-3 if p == "fp8" else GRAM_TOL)
+        _check(o, ref_full, GRAM_TOL, f"ellipses {p}", P, GRAM_TOL)
     sets = [set(np.nonzero(r)[0].tolist()) for r in Ub]
     ref_eid = O.eid(sets)
     for o in outs[5:]:

@@ -6,6 +6,7 @@ steps, and admission (HBM budget, queue length) and shutdown must answer with th
 documented status codes.
 """
 import threading
+import time
 
 import numpy as np
 import pytest
@@ -142,27 +143,66 @@ def test_admission_budget_and_queue(B):
     srv.stop()
 
 
-def test_stop_cancels_waiting_requests(B):
+def test_cancel_releases_waiters_before_the_server_is_freed(B):
+    """Waiters blocked on their tickets get PID_OK or PID_ERR_CANCELLED from the cancel, are
+    joined, and only then is the server freed: no wait runs on freed memory."""
     from paper_2512_15187_gb300.binding import PID_ERR_CANCELLED, PID_OK, load
-    import ctypes
     big = synth.random_soft(128, 1 << 21, seed=3)
     srv = B.Server(max_inflight=1, max_batch=1, max_queue=64)
     i = srv.register(big)
     tickets = [srv.submit(i, "linear") for _ in range(20)]
-    # stop from another thread while most requests wait; waiters see CANCELLED or OK
     handle = srv.s
-    statuses = []
+    statuses = {}
 
-    def waiter():
-        for t in tickets:
-            statuses.append(load().pid_serve_wait(handle, t, 60000, None, None, None, None, None))
+    def waiter(ts):
+        for t in ts:
+            statuses[t] = load().pid_serve_wait(handle, t, -1, None, None, None, None, None)
 
-    th = threading.Thread(target=waiter)
-    th.start()
-    load().pid_serve_stop(handle)
-    th.join()
+    threads = [threading.Thread(target=waiter, args=(tickets[k::4],)) for k in range(4)]
+    for th in threads:
+        th.start()
+    srv.cancel()                       # returns once every request is done
+    for th in threads:
+        th.join()
+    assert sorted(statuses) == sorted(tickets)
+    assert all(s in (PID_OK, PID_ERR_CANCELLED) for s in statuses.values()), statuses
+    assert any(s == PID_ERR_CANCELLED for s in statuses.values())
+    # after the cancel the server refuses new work but stays valid until stop
+    with pytest.raises(B.PidError) as e:
+        srv.submit(i, "mean")
+    assert e.value.status == PID_ERR_CANCELLED
+    assert srv.stats()["submitted"] == 20
+    srv.stop()
+
+
+def test_stop_waits_for_blocked_waiters(B):
+    """pid_serve_stop entered while threads are still blocked in pid_serve_wait: they return
+    (OK or CANCELLED) before the server is freed, and stop returns after them."""
+    from paper_2512_15187_gb300.binding import PID_ERR_CANCELLED, PID_OK, load
+    big = synth.random_soft(128, 1 << 21, seed=4)
+    srv = B.Server(max_inflight=1, max_batch=1, max_queue=64)
+    i = srv.register(big)
+    tickets = [srv.submit(i, "linear") for _ in range(12)]
+    handle = srv.s
+    statuses = {}
+    entered = threading.Barrier(4)
+
+    def waiter(t):
+        entered.wait()
+        statuses[t] = load().pid_serve_wait(handle, t, -1, None, None, None, None, None)
+
+    # three threads wait on the last tickets (still queued when stop begins)
+    threads = [threading.Thread(target=waiter, args=(t,)) for t in tickets[-3:]]
+    for th in threads:
+        th.start()
+    entered.wait()
+    time.sleep(0.05)                   # let them block inside the wait
+    assert load().pid_serve_stop(handle) == PID_OK
     srv.s = None
-    assert all(s in (PID_OK, PID_ERR_CANCELLED, 1) for s in statuses)
+    for th in threads:
+        th.join()
+    assert sorted(statuses) == sorted(tickets[-3:])
+    assert all(s in (PID_OK, PID_ERR_CANCELLED) for s in statuses.values()), statuses
 
 
 def test_time_step_update_of_resident_ensemble(B):

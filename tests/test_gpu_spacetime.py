@@ -62,8 +62,7 @@ def test_spacetime_gram_and_inclusion_matrix(H, T, N, precision):
     for k, r in zip(("in_in", "in_out", "depth"), ref):
         assert_close(to_np(o[k]), r, GRAM_TOL, f"gram T={T} {precision} {k}")
     assert_rank_agrees_outside_ties(to_np(o["rank"]), ref[2], GRAM_TOL)
-    p_tol = 5e-3 if precision == "fp8" else GRAM_TOL
-    assert_close(to_np(o["P"]), O.inclusion_matrix(U, wt), p_tol, "P")
+    assert_close(to_np(o["P"]), O.inclusion_matrix(U, wt), GRAM_TOL, "P")
 
 
 @pytest.mark.parametrize("iso", [(0.5, 0.05, 0), (0.5, 0.0, 1), (0.5, 0.1, 0, "level"),

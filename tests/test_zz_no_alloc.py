@@ -1,14 +1,13 @@
 """pid_mean_noalloc: PID-mean for callers that cannot allocate device memory.
 
-Code that records a CUDA graph, real-time loops in which a cudaMalloc would synchronise the
-device, and host applications whose own allocator owns all device memory cannot let the
-library allocate workspace. pid_mean_noalloc keeps its scratch in a fixed array inside the
-library instead; it must return what pid_mean returns, call after call.
+Real-time loops in which a cudaMalloc would synchronise the device, and host applications
+whose own allocator owns all device memory, cannot let the library allocate workspace.
+pid_mean_noalloc keeps its scratch in a fixed array inside the library instead; it must
+return bit for bit what pid_mean returns, call after call (the scratch keeps the previous
+call's partial sums, so a leak of them into the next call would show as a changed bit).
 """
-import numpy as np
 import pytest
 
-from tests.helpers import FP32_TOL, assert_close, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -43,9 +42,15 @@ def test_noalloc_matches_pid_mean_on_two_calls(N, M, weighted):
     h.sync()
     for _ in range(2):   # the shared scratch keeps the previous call's contents
         got = _noalloc(U, w)
-        for k in ("in_in", "in_out", "depth"):
-            assert_close(to_np(got[k]), to_np(ref[k]), FP32_TOL, f"noalloc {k}")
-        assert np.array_equal(to_np(got["rank"]), to_np(ref["rank"]))
+        for k in ("in_in", "in_out", "depth", "rank"):
+            assert torch.equal(got[k], ref[k]), f"noalloc {k} differs from pid_mean"
+    # a smaller problem after a larger one: fewer chunks, stale partials left behind
+    U2 = U[: max(1, N // 3), : M // 2]
+    ref2 = h.mean(U2, None if w is None else w[: M // 2].contiguous())
+    h.sync()
+    got2 = _noalloc(U2, None if w is None else w[: M // 2].contiguous())
+    for k in ("in_in", "in_out", "depth", "rank"):
+        assert torch.equal(got2[k], ref2[k]), f"noalloc {k} differs after a larger call"
     h.close()
 
 
@@ -54,8 +59,11 @@ def test_noalloc_rejects_problems_beyond_its_scratch():
     from paper_2512_15187_gb300 import binding as B, build
     build.build()
     N, M = 512, 4_400_000          # needs more than the 4 MiB of per-chunk partials
-    U = torch.empty((N, M), dtype=torch.float32, device="cuda")  # never read: rejected first
+    # the size check rejects the call before any kernel could read U: a small real buffer
+    # stands in for the 9 GB a problem of this size would occupy
+    U = torch.empty(16, dtype=torch.float32, device="cuda")
     d = torch.empty(N, dtype=torch.float64, device="cuda")
     with pytest.raises(B.PidError) as e:
         B.pid_mean_noalloc(U.data_ptr(), N, M, M, None, d.data_ptr(), None, None, None, None, None)
     assert e.value.status == B.PID_ERR_UNSUPPORTED
+    assert "scratch" in str(e.value)
