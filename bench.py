@@ -400,8 +400,8 @@ def run_serving(device, seconds, rate_hz, budget_bytes=150 << 30, n_ens=24, seed
 
 # ---------------------------------------------------------------------------------------
 # The other workloads, reported beside the headline: 2D ellipses (latency), non-Cartesian
-# weighted points (throughput), and a 3D plume batch with uneven extras in one pid_batch
-# call against the same work as one call per ensemble.
+# weighted points (throughput), the tiled Gram beyond 256 members, and the scalability
+# study.
 # ---------------------------------------------------------------------------------------
 
 def run_workloads(h, dev, stream):
@@ -479,53 +479,6 @@ def run_workloads(h, dev, stream):
     out["gram_tiled_300_512_members_x1M"] = tiled
     torch.cuda.empty_cache()
 
-    # 3D plume: the 16 time steps of 200 x 256^3 (13.4 GB each, 215 GB together, resident
-    # at once) plus 48 uneven ensembles (N in [10, 500], M log-uniform in [64^2, 128^3]);
-    # PID-mean, and the E4M3 / split-BF16 Gram for the plume steps, exact full PID for the
-    # extras. The steps held are bounded by the free device memory (recorded).
-    rng = np.random.default_rng(4)
-    g = torch.Generator(device=dev)
-    g.manual_seed(4)
-    shapes = []
-    for _ in range(48):
-        N = int(rng.integers(10, 501))
-        M = int(round(math.exp(rng.uniform(math.log(64 ** 2), math.log(128 ** 3)))))
-        shapes.append((N, M))
-    extra_bytes = sum(4 * N * M for N, M in shapes)
-    step_bytes = 4 * 200 * 256 ** 3
-    torch.cuda.empty_cache()
-    free, _ = torch.cuda.mem_get_info(dev)
-    n_steps = int(max(1, min(16, (free - extra_bytes - (6 << 30)) // step_bytes)))
-    steps = [synth.plume_3d(200, 256, t=t, T=16) for t in range(n_steps)]
-    extras = [torch.rand(sh, generator=g, device=dev) for sh in shapes]
-    items = [dict(data=U, mode="mean") for U in steps]
-    items += [dict(data=U, mode="full", precision=p) for U in steps for p in ("fp8", "split_bf16")]
-    items += [dict(data=X, mode=m) for X in extras for m in ("mean", "linear")]
-    passes = {"mean": 1, "full": 1, "linear": 2}
-    member_cells = sum(it["data"].shape[0] * it["data"].shape[1] for it in items)
-    read_bytes = sum(4.0 * it["data"].numel() * passes[it["mode"]] for it in items)
-
-    def loop():
-        for it in items:
-            if it["mode"] == "mean":
-                h.mean(it["data"], stream=stream)
-            else:
-                h.full(it["data"], mode=it["mode"], precision=it.get("precision", "fp32"),
-                       stream=stream)
-
-    o_items = h.batch(items, stream=stream)
-    t_batch = timed(lambda: h.batch(items, stream=stream, outs=o_items), 3)
-    t_loop = timed(loop, 3)
-    out["plume_3d_200x256cubed_steps_plus_48_uneven"] = {
-        "time_steps": n_steps, "resident_gb": (n_steps * step_bytes + extra_bytes) / 1e9,
-        "items": len(items), "member_cells_per_call": member_cells,
-        "batched_ms": t_batch, "one_call_per_ensemble_ms": t_loop,
-        "batched_speedup": t_loop / t_batch,
-        "batched_member_cells_per_s": member_cells / (t_batch * 1e-3),
-        "batched_read_gb_per_s": read_bytes / (t_batch * 1e-3) / 1e9}
-    del steps, extras, items, o_items, loop   # the item list and the loop hold the 215 GB
-    torch.cuda.empty_cache()
-
     # scalability study: PID-mean of 3D ellipsoid ensembles (80% normal, 20% outliers), one
     # call each, over the ensemble size at 50^3 and over the resolution at 50 members
     scal = {"unit": "ms per PID-mean call (ranks included)", "members_at_50cubed": {},
@@ -544,27 +497,264 @@ def run_workloads(h, dev, stream):
 
 
 def run_reference(args, rank):
-    """The oracle as it stands on the host cores: each step is one ensemble of the workload
-    restricted to a 128-row band of the grid (64 x 65536 member x cells)."""
+    """The oracle as it stands on the host cores, on the headline workload's metric: each step
+    is one host sample of the plume (200 members on 4 z-planes of a 256^3 time step), FP64
+    PID-mean and full PID, one thread. Rank 0 only."""
     if rank != 0:
         return
-    rows = 128
-    res = run_cpu_oracle(budget_s=1e9, max_steps=args.warmup + args.steps, rows=rows)
-    t = res["per_step"][args.warmup:]
-    sec = sum(t)
-    value = len(t) * N_MEMBERS * res["cells"] / sec
+    res = run_cpu_oracle(budget_s=1e9, max_steps=args.warmup + args.steps)
+    value, sec, n = cpu_value(res, skip=args.warmup)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * sec / len(t), "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * sec / n, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_cells_per_step": res["cells"],
-                       "path": ["isovalue map", "pid_mean", "full_pid (O(N^2 M) pairs)"],
+            "config": {"workload": WORKLOAD, "sample_members": res["members"],
+                       "sample_cells_per_step": res["cells"],
+                       "path": ["pid_mean", "full_pid (O(N^2 M) pairs)"],
                        "parallelism": "host, one thread (rank 0 only)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"one ensemble per step, {rows} of {GRID_H} grid rows"},
+                             "sample": f"one host sample per step: {res['members']} members x "
+                                       f"{res['cells']} cells (4 z-planes of a 256^3 plume "
+                                       f"time step), PID-mean + full PID counted as two items"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+# Headline: the 3D plume batch
+# ---------------------------------------------------------------------------------------
+
+def c4_shapes(rank=0):
+    """(N, M) of the 48 uneven ensembles: N ~ U{10..500}, M log-uniform in [64^2, 128^3]."""
+    import numpy as np
+    rng = np.random.default_rng(4 + 1009 * rank)
+    shapes = []
+    for _ in range(C4_EXTRAS):
+        N = int(rng.integers(10, 501))
+        M = int(round(math.exp(rng.uniform(math.log(64 ** 2), math.log(128 ** 3)))))
+        shapes.append((N, M))
+    return shapes
+
+
+def c4_inputs(dev, n_steps, shapes, rank=0):
+    """The plume time steps [200, 256^3] and the uneven soft-mask ensembles, on the device."""
+    import torch
+
+    from paper_2512_15187_gb300 import synth
+    g = torch.Generator(device=dev)
+    g.manual_seed(4 + 1009 * rank)
+    steps = [synth.plume_3d(C4_N, C4_R, t=t, T=C4_T, seed=synth.DEFAULT_SEED + 4 + 7 * rank)
+             for t in range(n_steps)]
+    extras = [torch.rand(sh, generator=g, device=dev) for sh in shapes]
+    return steps, extras
+
+
+def c4_items(steps, extras):
+    """Per time step PID-mean, E4M3 Gram and split-BF16 Gram; per extra PID-mean and exact
+    full PID. Items of a time step are consecutive: [mean, fp8, split_bf16]."""
+    items = []
+    for U in steps:
+        items += [dict(data=U, mode="mean"), dict(data=U, mode="full", precision="fp8"),
+                  dict(data=U, mode="full", precision="split_bf16")]
+    items += [dict(data=X, mode=m) for X in extras for m in ("mean", "linear")]
+    return items
+
+
+def c4_parity(h, U, outs3):
+    """Max abs error of one time step's three results (PID-mean, E4M3 and split-BF16 full PID,
+    from the timed batch) against the FP64 oracle, whose sums over the 16.8M cells are
+    accumulated in blocks copied from the device (the step does not fit the host as float64)."""
+    import numpy as np
+
+    from oracle import pid_oracle as O
+
+    def blocks(block=1 << 20):
+        for x0 in range(0, U.shape[1], block):
+            yield U[:, x0:x0 + block].cpu().numpy(), None
+
+    t0 = time.perf_counter()
+    ref_mean = O.pid_mean_chunked(blocks())
+    ref_full = O.pid_chunked(blocks())
+    out = {"sample": f"time step 0 of the timed batch, {U.shape[0]} members x {U.shape[1]} cells, "
+                     f"every member; block-accumulated FP64 oracle "
+                     f"({time.perf_counter() - t0:.0f} s on the host)",
+           "bars": {"fp32": 1e-6, "gram": 1e-3}}
+    for name, o, ref in (("pid_mean_fp32", outs3[0], ref_mean),
+                         ("full_gram_e4m3", outs3[1], ref_full),
+                         ("full_gram_split_bf16", outs3[2], ref_full)):
+        out[name] = {k: float(np.max(np.abs(o[k].cpu().numpy() - np.asarray(r))))
+                     for k, r in zip(("in_in", "in_out", "depth"), ref)}
+        r = o["rank"].cpu().numpy()
+        d = np.asarray(ref[2])
+        diff = d[:, None] - d[None, :]
+        bar = 1e-6 if name == "pid_mean_fp32" else 1e-3
+        firm = np.abs(diff) > 2 * bar
+        out[name]["rank_pairs_against_oracle_outside_ties"] = int(
+            (firm & (np.sign(diff) != -np.sign(r[:, None] - r[None, :]))).sum())
+    return out
+
+
+def c4_e2e(binding, dev, stream, step_src, n_iters, rank):
+    """End to end through the public API: every iteration copies one time step (13.4 GB) from
+    pinned host memory into one of two device buffers, runs its three items (PID-mean, E4M3
+    and split-BF16 full PID) as one pid_batch and reads the depths back to pinned host
+    memory. The copy of step k overlaps the compute of step k - 1 (two buffers, two handles,
+    a copy stream); the timed region is the device time of n_iters iterations."""
+    import torch
+    host = torch.empty(step_src.shape, dtype=torch.float32, pin_memory=True)
+    host.copy_(step_src)
+    bufs = [torch.empty(step_src.shape, dtype=torch.float32, device=dev) for _ in range(2)]
+    hs = [binding.Handle(dev.index) for _ in range(2)]
+    its = [[dict(data=b, mode="mean"), dict(data=b, mode="full", precision="fp8"),
+            dict(data=b, mode="full", precision="split_bf16")] for b in bufs]
+    outs = [hs[k].batch(its[k], stream=stream) for k in range(2)]
+    copy_stream = torch.cuda.Stream(device=dev)
+    landed = [torch.cuda.Event() for _ in range(2)]
+    consumed = [torch.cuda.Event() for _ in range(2)]
+    for k in range(2):
+        consumed[k].record(stream)
+    N = step_src.shape[0]
+    res_host = torch.empty((2, 3, N), dtype=torch.float64, pin_memory=True)
+
+    def iteration(k):
+        b = k % 2
+        copy_stream.wait_event(consumed[b])      # the batch two iterations back read it
+        with torch.cuda.stream(copy_stream):
+            bufs[b].copy_(host, non_blocking=True)
+        landed[b].record(copy_stream)
+        stream.wait_event(landed[b])
+        hs[b].batch(its[b], stream=stream, outs=outs[b])
+        consumed[b].record(stream)
+        res_host[b].copy_(torch.stack([o["depth"] for o in outs[b]]), non_blocking=True)
+
+    for k in range(2):
+        iteration(k)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for k in range(n_iters):
+        iteration(k)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / n_iters
+    for hh in hs:
+        hh.close()
+    del bufs, host
+    return ms, 3 * N * step_src.shape[1], 4 * step_src.numel(), 3 * N * 8
+
+
+# ---------------------------------------------------------------------------------------
+# Secondary record: 2D fields through the isovalue map (256 ensembles of 64 x 512^2)
+# ---------------------------------------------------------------------------------------
+
+def fields_2d_record(h, dev, stream, args, rank, peaks):
+    import numpy as np
+    import torch
+
+    from oracle import pid_oracle as O
+    from paper_2512_15187_gb300 import synth
+    E, N, M = args.ensembles, N_MEMBERS, GRID_H * GRID_W
+    F = torch.empty((E, N, M), dtype=torch.float32, device=dev)
+    for e in range(E):
+        synth.rbf_fields_2d_torch(N, GRID_H, GRID_W, N_RBF,
+                                  seed=synth.DEFAULT_SEED + 2 + 7919 * (e + 100003 * rank),
+                                  device=dev, out=F[e])
+    rec = {"workload": WORKLOAD_2D, "ensembles_per_step": E,
+           "l2": f"inputs larger than L2 ({E * N * M * 4 / 1e9:.1f} GB per step)", "paths": {}}
+    for name, mode, prec in (("iso_pid_mean_exact_full_fp32", "linear", "fp32"),
+                             ("pid_mean_fp32", "mean", "fp32"),
+                             ("full_pid_gram_bf16", "full", "bf16"),
+                             ("full_pid_gram_split_bf16", "full", "split_bf16"),
+                             ("full_pid_gram_fp8", "full", "fp8")):
+        its = [dict(data=F[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=mode, precision=prec)
+               for e in range(E)]
+        h.autotune(True)
+        o_its = h.batch(its, stream=stream)
+        h.sync()
+        h.autotune(False)
+        h.profile(True)                  # records the profiled graph once, untimed
+        h.batch(its, stream=stream, outs=o_its)
+        h.sync()
+        h.profile(True)                  # reset the counters
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.other_steps):
+            h.batch(its, stream=stream, outs=o_its)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        prof = h.profile_read()
+        h.profile(False)
+        t_ms = b0.elapsed_time(b1) / args.other_steps
+        kt = kernel_table(prof, peaks, sustained=False)
+        dom = max(kt, key=lambda k: kt[k]["share"])
+        traffic = ncu_traffic("stream_kernel_fields_exact_64x512x512") if mode == "linear" else None
+        rec["paths"][name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms,
+                              "roofline": roofline_record(dom, {**prof[dom]}, peaks, False, traffic),
+                              "kernels": kt}
+    # contour boxplot bands of every ensemble from the exact full-PID ranks (Sec. 6)
+    o_lin = h.batch([dict(data=F[e], iso=(ISO_MU, ISO_SIGMA, 0), mode="linear") for e in range(E)],
+                    stream=stream)
+    bout = [torch.empty(M, dtype=torch.uint8, device=dev) for _ in range(E)]
+
+    def bands_step():
+        for e in range(E):
+            h.contour_bands(F[e], o_lin[e]["rank"], 0.5, 0.5, iso=(ISO_MU, ISO_SIGMA, 0),
+                            out=bout[e], stream=stream)
+    bands_step()
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(3):
+        bands_step()
+    d1.record(stream)
+    torch.cuda.synchronize()
+    b_ms = d0.elapsed_time(d1) / 3
+    rec["contour_bands"] = {"value": E * N * M / (b_ms * 1e-3), "unit": UNIT, "ms_per_step": b_ms,
+                            "read_gb_per_s": 4.0 * E * N * M / (b_ms * 1e-3) / 1e9,
+                            "calls_per_step": E, "tau": 0.5, "inner_fraction": 0.5}
+    # the exact step as one call per ensemble (no batching, no graph)
+    def loop_step():
+        for e in range(E):
+            h.from_fields(F[e], ISO_MU, ISO_SIGMA, mode="linear", stream=stream)
+    loop_step()
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(2):
+        loop_step()
+    c1.record(stream)
+    torch.cuda.synchronize()
+    loop_ms = c0.elapsed_time(c1) / 2
+    rec["one_call_per_ensemble_exact"] = {
+        "ms_per_step": loop_ms,
+        "batched_speedup": loop_ms / rec["paths"]["iso_pid_mean_exact_full_fp32"]["ms_per_step"]}
+    # parity on one band of the first ensemble against the FP64 oracle
+    rows = 128
+    Fh = synth.rbf_fields_2d(N=N, H=GRID_H, W=GRID_W, n_rbf=N_RBF, seed=synth.DEFAULT_SEED + 2)
+    Fh = np.ascontiguousarray(Fh.reshape(N, GRID_H, GRID_W)[:, :rows].reshape(N, -1))
+    U = O.iso_soft_mask(Fh, ISO_MU, ISO_SIGMA)
+    refs = {"mean": O.pid_mean(U), "full": O.pid(U)}
+    Fd = torch.from_numpy(Fh).to(dev)
+    par = {"sample": f"{N} members x {rows * GRID_W} cells of the workload's first ensemble; "
+                     f"max abs error against the FP64 oracle", "bars": {"fp32": 1e-6, "gram": 1e-3}}
+    for name, mode, prec, key in (("pid_mean_fp32", "mean", "fp32", "mean"),
+                                  ("full_exact_fp32", "linear", "fp32", "full"),
+                                  ("full_gram_bf16", "full", "bf16", "full"),
+                                  ("full_gram_split_bf16", "full", "split_bf16", "full"),
+                                  ("full_gram_fp8", "full", "fp8", "full")):
+        o = h.from_fields(Fd, ISO_MU, ISO_SIGMA, mode=mode, precision=prec)
+        h.sync()
+        par[name] = {k: float(np.max(np.abs(o[k].cpu().numpy() - np.asarray(r))))
+                     for k, r in zip(("in_in", "in_out", "depth"), refs[key])}
+    rec["parity"] = par
+    del F, o_lin, bout
+    torch.cuda.empty_cache()
+    return rec
 
 
 # ---------------------------------------------------------------------------------------
@@ -583,14 +773,13 @@ def main():
         run_reference(args, rank)
         return
 
-    cpu_res = None
+    # the oracle on the host, in child processes started before any CUDA work
+    cpu_res = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_res = run_cpu_oracle(budget_s=12.0, max_steps=16, rows=GRID_H)  # before any CUDA work
+        cpu_res = run_cpu_oracle(budget_s=15.0, max_steps=12, threads=1)
         cores = os.cpu_count() or 1
-        if cores > 1:   # the same oracle with every host core, as context
-            cpu_res["all_cores"] = run_cpu_oracle(budget_s=12.0, max_steps=16, rows=GRID_H,
-                                                  threads=cores)
-            cpu_res["all_cores"]["threads"] = cores
+        if cores > 1:
+            cpu_all = run_cpu_oracle(budget_s=8.0, max_steps=12, threads=cores)
 
     import torch
     torch.cuda.set_device(local_rank)
@@ -599,38 +788,43 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
-    from paper_2512_15187_gb300 import binding, build, synth
+    from paper_2512_15187_gb300 import binding, build
     build.build()
     h = binding.Handle(local_rank)
-    E, N, M = args.ensembles, N_MEMBERS, GRID_H * GRID_W
     dev = torch.device("cuda", local_rank)
-
-    # ---- inputs resident in HBM: E ensembles of fields, generated on the device ----
-    F = torch.empty((E, N, M), dtype=torch.float32, device=dev)
-    for e in range(E):
-        synth.rbf_fields_2d_torch(N, GRID_H, GRID_W, N_RBF,
-                                  seed=synth.DEFAULT_SEED + 2 + 7919 * (e + 100003 * rank),
-                                  device=dev, out=F[e])
-    items = [dict(data=F[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=args.mode, precision=args.precision)
-             for e in range(E)]
     stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
 
-    outs_main = h.batch(items, stream=stream)     # outputs written in place by every step
+    # ---- headline inputs, resident in HBM: the plume steps and the uneven ensembles ----
+    step_bytes = 4 * C4_N * C4_R ** 3
+    shapes = c4_shapes(rank)
+    extra_bytes = sum(4 * N * M for N, M in shapes)
+    free, _ = torch.cuda.mem_get_info(dev)
+    # the steps held: all 16 when they fit beside the extras and 8 GB of workspace (recorded)
+    n_steps = int(max(1, min(args.time_steps, (free - extra_bytes - (8 << 30)) // step_bytes)))
+    steps, extras = c4_inputs(dev, n_steps, shapes, rank)
+    items = c4_items(steps, extras)
+    member_cells = sum(it["data"].shape[0] * it["data"].shape[1] for it in items)
+    resident_gb = (sum(4.0 * U.numel() for U in steps) + sum(4.0 * X.numel() for X in extras)) / 1e9
 
-    def step():
-        return h.batch(items, stream=stream, outs=outs_main)
-
-    h.autotune(True)          # first warm-up step times the launch candidates
-    for _ in range(args.warmup):
-        step()
+    h.autotune(True)                                 # the first call times the candidates
+    outs = h.batch(items, stream=stream)
     h.sync()
     h.autotune(False)
+    # The timed steps replay the batch's CUDA graph with the library's timing nodes armed
+    # (two event records around every kernel), so each kernel's device time is measured in
+    # the timed region itself; profiling is switched on before the warm-up, so that the
+    # profiled graph is recorded there.
+    h.profile(True)
+    for _ in range(max(3, args.warmup)):
+        h.batch(items, stream=stream, outs=outs)
+    h.sync()
 
     # ---- timed region ----
     uuid = str(torch.cuda.get_device_properties(dev).uuid)
     sampler = ClockSampler(uuid if uuid.startswith("GPU-") else "GPU-" + uuid)
     sampler.start()
-    h.profile(True)
+    h.profile(True)                                  # reset the counters (same graph)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
@@ -638,7 +832,7 @@ def main():
     t1 = torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        step()
+        h.batch(items, stream=stream, outs=outs)
     t1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -649,103 +843,55 @@ def main():
     clocks = sampler.stop()
     h.sync()
     ms = max_over_ranks(ms, dist, dev)
-    total_mc = world * args.steps * E * N * M
-    value = total_mc / (ms * 1e-3)
-
-    # ---- roofline of the dominant kernel (launched by the library on `stream`) ----
-    peaks = measured_peaks()
-    kinds = {k: v for k, v in prof.items() if v["launches"] > 0}
-    dom = max(kinds, key=lambda k: kinds[k]["total_ms"])
-    st = kinds[dom]
-    per_launch_ms = st["total_ms"] / st["launches"]
-    if dom == "gram" and st["flops"] > 0 and args.precision != "fp32":
-        achieved = st["flops"] / (st["total_ms"] * 1e-3) / 1e12
-        peak = peaks["bf16_tflops"] * (2.0 if args.precision == "fp8" else 1.0)
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s"}
-    else:
-        achieved = st["bytes"] / (st["total_ms"] * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["peak_source"] = peaks["source"]
-    roof["kernel"] = {"stream": "stream_kernel", "gram": "gram_kernel", "finalize": "finalize_kernel",
-                      "iso": "iso_kernel"}[dom]
-    roof["launches"] = st["launches"]
-    roof["ms_per_launch"] = per_launch_ms
-    roof["algorithmic_bytes_per_launch"] = st["bytes"] / st["launches"]
-    traffic = ncu_traffic(roof["kernel"], f"{N}x{GRID_H}x{GRID_W}") if dom in ("stream", "gram") \
-        else None
-    roof["traffic"] = traffic
+    value = world * args.steps * member_cells / (ms * 1e-3)
     gpu_launches = sum(v["launches"] for v in prof.values())
 
-    # ---- the other paths on the same batch (reported beside the headline) ----
-    others = {}
-    for name, mode, prec in (("pid_mean_fp32", "mean", "fp32"),
-                             ("full_pid_exact_fp32", "linear", "fp32"),
-                             ("full_pid_gram_bf16", "full", "bf16"),
-                             ("full_pid_gram_split_bf16", "full", "split_bf16"),
-                             ("full_pid_gram_fp8", "full", "fp8")):
-        if args.other_steps <= 0 or (mode == args.mode and prec == args.precision):
-            continue
-        its = [dict(data=F[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=mode, precision=prec)
-               for e in range(E)]
-        h.autotune(True)
-        o_its = h.batch(its, stream=stream)
-        h.batch(its, stream=stream, outs=o_its)
-        h.sync()
-        h.autotune(False)
-        b0 = torch.cuda.Event(enable_timing=True)
-        b1 = torch.cuda.Event(enable_timing=True)
-        b0.record(stream)
-        for _ in range(args.other_steps):
-            h.batch(its, stream=stream, outs=o_its)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        t_ms = b0.elapsed_time(b1) / args.other_steps
-        others[name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms}
+    # ---- roofline of the dominant kernel (a long step: sustained tensor peak) ----
+    kt = kernel_table(prof, peaks, sustained=True)
+    dom = max(kt, key=lambda k: kt[k]["share"])
+    prefix = {"gram_split": "gram_kernel_split_bf16_plume", "gram_fp8": "gram_kernel_e4m3_plume",
+              "stream": "stream_kernel_plume"}.get(dom, dom)
+    roof = roofline_record(dom, prof[dom], peaks, True, ncu_traffic(prefix))
 
-    # ---- contour boxplot bands of every ensemble from the step's ranks (Sec. 6) ----
-    bands = None
-    if rank == 0 and args.other_steps > 0:
-        bout = [torch.empty(M, dtype=torch.uint8, device=dev) for _ in range(E)]
-
-        def bands_step():
-            for e in range(E):
-                h.contour_bands(F[e], outs_main[e]["rank"], 0.5, 0.5,
-                                iso=(ISO_MU, ISO_SIGMA, 0), out=bout[e], stream=stream)
-        bands_step()
-        torch.cuda.synchronize()
-        d0 = torch.cuda.Event(enable_timing=True)
-        d1 = torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(3, args.other_steps))
-        d0.record(stream)
-        for _ in range(reps):
-            bands_step()
-        d1.record(stream)
-        torch.cuda.synchronize()
-        b_ms = d0.elapsed_time(d1) / reps
-        bands = {"value": E * N * M / (b_ms * 1e-3), "unit": UNIT, "ms_per_step": b_ms,
-                 "read_gb_per_s": 4.0 * E * N * M / (b_ms * 1e-3) / 1e9,
-                 "calls_per_step": E, "tau": 0.5, "inner_fraction": 0.5}
-
-    # ---- the same step as one call per ensemble (no batching, no graph) ----
+    # ---- the same batch as one call per item ----
     loop_ms = None
-    if rank == 0 and args.other_steps > 0:
-        def loop_step():
-            for e in range(E):
-                h.from_fields(F[e], ISO_MU, ISO_SIGMA, mode=args.mode, precision=args.precision,
-                              stream=stream)
-        loop_step()
+    if rank == 0:
+        def loop():
+            for it in items:
+                if it["mode"] == "mean":
+                    h.mean(it["data"], stream=stream)
+                else:
+                    h.full(it["data"], mode=it["mode"], precision=it.get("precision", "fp32"),
+                           stream=stream)
+        loop()
         torch.cuda.synchronize()
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        reps = max(1, min(3, args.other_steps))
-        c0.record(stream)
-        for _ in range(reps):
-            loop_step()
-        c1.record(stream)
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        for _ in range(2):
+            loop()
+        l1.record(stream)
         torch.cuda.synchronize()
-        loop_ms = c0.elapsed_time(c1) / reps
+        loop_ms = l0.elapsed_time(l1) / 2
+        del loop          # the closure holds the items, hence the 240 GB
 
+    # ---- parity of time step 0 against the FP64 oracle ----
+    parity = None
+    if rank == 0 and not args.no_parity:
+        parity = c4_parity(h, steps[0], outs[0:3])
+
+    # ---- end to end: one time step per iteration from pinned host memory ----
+    step0 = steps[0].cpu()
+    del items, outs, steps, extras
+    torch.cuda.empty_cache()
+    e2e_ms, e2e_mc, h2d, d2h = c4_e2e(binding, dev, stream, step0, max(3, args.e2e_steps), rank)
+    del step0
+    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+
+    # ---- secondary records ----
+    secondary = None
+    if rank == 0 and not args.no_secondary and args.other_steps > 0:
+        secondary = fields_2d_record(h, dev, stream, args, rank, peaks)
     serving = None
     if rank == 0 and args.serve_seconds > 0:
         serving = run_serving(local_rank, args.serve_seconds, 200.0)
@@ -753,95 +899,49 @@ def main():
     if rank == 0 and not args.no_workloads:
         workloads = run_workloads(h, dev, stream)
 
-    # ---- end to end: pinned host inputs -> device -> results back, every step ----
-    Ee = min(args.e2e_ensembles, E)
-    host = torch.empty((Ee, N, M), dtype=torch.float32, pin_memory=True)
-    for e in range(Ee):
-        host[e].copy_(synth.rbf_fields_2d_torch(N, GRID_H, GRID_W, N_RBF,
-                                                seed=synth.DEFAULT_SEED + 2 + 7919 * (e + 100003 * rank),
-                                                device=dev).cpu())
-    dbuf = torch.empty((Ee, N, M), dtype=torch.float32, device=dev)
-    items_e = [dict(data=dbuf[e], iso=(ISO_MU, ISO_SIGMA, 0), mode=args.mode,
-                    precision=args.precision) for e in range(Ee)]
-    res_host = torch.empty((Ee, N), dtype=torch.float64, pin_memory=True)
-
-    # The host link (about 210 GB/s pinned host-to-device on this machine) dominates: the
-    # step's inputs are copied in S slices on a copy stream and each slice's batch starts
-    # as soon as its slice has landed, so the compute hides behind the remaining copies.
-    # Each slice has its own handle, so that every slice replays its own recorded graph.
-    S = 4 if Ee % 4 == 0 else 1
-    per = Ee // S
-    hs = [h] + [binding.Handle(local_rank) for _ in range(S - 1)]
-    copy_stream = torch.cuda.Stream(device=dev)
-    sub_items = [items_e[k * per:(k + 1) * per] for k in range(S)]
-    sub_outs = [hs[k].batch(sub_items[k], stream=stream) for k in range(S)]
-    landed = [torch.cuda.Event() for _ in range(S)]
-    consumed = [torch.cuda.Event() for _ in range(S)]
-    for k in range(S):
-        consumed[k].record(stream)
-
-    def e2e_step():
-        for k in range(S):
-            copy_stream.wait_event(consumed[k])    # the previous step's slice k was read
-            with torch.cuda.stream(copy_stream):
-                dbuf[k * per:(k + 1) * per].copy_(host[k * per:(k + 1) * per], non_blocking=True)
-            landed[k].record(copy_stream)
-        for k in range(S):
-            stream.wait_event(landed[k])
-            hs[k].batch(sub_items[k], stream=stream, outs=sub_outs[k])
-            consumed[k].record(stream)
-        res_host.copy_(torch.stack([o["depth"] for so in sub_outs for o in so]), non_blocking=True)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    k_e2e = max(3, min(args.steps, 20))
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(k_e2e):
-        e2e_step()
-    a1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = a0.elapsed_time(a1) / k_e2e
-    e2e_ms = max_over_ranks(e2e_ms, dist, dev)
-    e2e_value = world * Ee * N * M / (e2e_ms * 1e-3)
-
     if rank == 0:
-        modes = {"linear": ["isovalue map", "pid_mean_fp32", "full_pid_exact_fp32"],
-                 "full": ["isovalue map", "pid_mean_fp32",
-                          f"full_pid_gram_{args.precision} (calibrated to exact row sums)"],
-                 "mean": ["isovalue map", "pid_mean_fp32"]}[args.mode]
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "members": N, "grid": f"{GRID_H}x{GRID_W}",
-                       "ensembles_per_step": E, "path": modes,
-                       "l2": f"inputs larger than L2 ({E * N * M * 4 / 1e9:.1f} GB per step per GPU)",
+            "dtype": "f32 inputs; tensor cores on e4m3 and split-bf16 operands; f64 finalisation",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "time_steps": n_steps, "members": C4_N,
+                       "grid": f"{C4_R}^3", "uneven_ensembles": C4_EXTRAS,
+                       "items_per_step": 3 * n_steps + 2 * C4_EXTRAS,
+                       "member_cells_per_step": member_cells,
+                       "counting": "every (ensemble, mode) item counts its N x M member-cells",
+                       "path": ["per time step: pid_mean_fp32, full_pid_gram_e4m3 (per-member "
+                                "scales), full_pid_gram_split_bf16",
+                                "per uneven ensemble: pid_mean_fp32, full_pid_exact_fp32",
+                                "fp64 finalisation and ranking"],
+                       "resident_gb": resident_gb,
+                       "l2": f"inputs larger than L2 ({resident_gb:.0f} GB resident per GPU)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": Ee * N * M * 4,
-                    "d2h_bytes_per_step": Ee * N * 8, "ensembles_per_step": Ee},
+            "kernels": kt,
+            "e2e": {"value": world * e2e_mc / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_ms,
+                    "step": "one plume time step (200 x 256^3) copied in from pinned host memory, "
+                            "its PID-mean, E4M3 and split-BF16 full PID, depths read back; "
+                            "copies overlap the previous step's compute"},
             "gpu_launches": gpu_launches,
             "clocks": clocks,
-            "other_paths": others,
         }
-        if bands is not None:
-            line["contour_bands"] = bands
         if loop_ms is not None:
-            line["one_call_per_ensemble"] = {
-                "value": E * N * M / (loop_ms * 1e-3), "unit": UNIT, "ms_per_step": loop_ms,
-                "batched_speedup": loop_ms / (ms / args.steps)}
+            line["one_call_per_item"] = {"ms_per_step": loop_ms,
+                                         "batched_speedup": loop_ms / (ms / args.steps)}
+        if cpu_res is not None:
+            line["cpu_baseline"] = cpu_baseline_record(cpu_res, cpu_all)
+        if parity is not None:
+            line["parity"] = parity
+        if secondary is not None:
+            line["fields_2d"] = secondary
         if serving is not None:
             line["serving"] = serving
         if workloads is not None:
             line["workloads"] = workloads
-        if cpu_res is not None:
-            line["cpu_baseline"] = cpu_baseline_record(cpu_res)
-            if cpu_res.get("ref"):
-                line["parity"] = oracle_parity(h, cpu_res, dev)
         print(json.dumps(line), flush=True)
     h.close()
     if dist:

@@ -33,7 +33,53 @@ struct BatchCache {
   size_t host_bytes = 0;
   bool use_graphs = true;
   int64_t replays = 0;
+  // A graph recorded with profiling on brackets every kernel with two event-record nodes;
+  // each replay sets fresh events on them, so every replay's launches are timed.
+  struct ProfNodes { cudaGraphNode_t start, stop; int kind; double bytes, flops; };
+  std::vector<ProfNodes> prof;
 };
+
+// Fresh events on the graph's timing nodes, queued for the profiler, before a replay.
+static pid_status arm_graph_profiling(pid_handle h, BatchCache* c) {
+  for (const auto& pn : c->prof) {
+    ProfRecord r{pn.kind, prof_event(h), prof_event(h), pn.bytes, pn.flops};
+    if (cudaGraphExecEventRecordNodeSetEvent(c->exec, pn.start, r.start) != cudaSuccess ||
+        cudaGraphExecEventRecordNodeSetEvent(c->exec, pn.stop, r.stop) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, PID_ERR_CUDA, "re-arming the timing nodes of the batch graph");
+    }
+    h->prof_pending.push_back(r);
+  }
+  return PID_OK;
+}
+
+// The event-record nodes that the captured ProfScopes left in `graph`.
+static pid_status collect_graph_profiling(pid_handle h, cudaGraph_t graph, BatchCache* c) {
+  c->prof.clear();
+  size_t n = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &n) != cudaSuccess) return fail(h, PID_ERR_CUDA, "graph nodes");
+  std::vector<cudaGraphNode_t> nodes(n);
+  if (n && cudaGraphGetNodes(graph, nodes.data(), &n) != cudaSuccess)
+    return fail(h, PID_ERR_CUDA, "graph nodes");
+  std::map<cudaEvent_t, cudaGraphNode_t> by_event;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    cudaEvent_t e = nullptr;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeEventRecord &&
+        cudaGraphEventRecordNodeGetEvent(nd, &e) == cudaSuccess)
+      by_event[e] = nd;
+  }
+  for (const ProfRecord& r : h->prof_captured) {
+    auto a = by_event.find(r.start), b = by_event.find(r.stop);
+    if (a == by_event.end() || b == by_event.end())
+      return fail(h, PID_ERR_CUDA, "a timing node of the batch graph is missing");
+    c->prof.push_back({a->second, b->second, r.kind, r.bytes, r.flops});
+    h->event_pool.push_back(r.start);   // the graph's nodes get fresh events at every replay
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof_captured.clear();
+  return PID_OK;
+}
 
 void batch_use_graphs(pid_handle h, bool on) {
   if (!h->batch) h->batch = new BatchCache();
@@ -80,8 +126,11 @@ struct Launch {
   double bytes = 0, flops = 0;
   GramPlan gp;             // GRAM launches
   int iso_mode = 0;
-  struct Scale { EnsInput in; float* out; };
-  std::vector<Scale> scales;  // E4M3 member scales to compute before the Gram launch
+  // E4M3 member scales to compute before the Gram launch: by a pass of their own, or from
+  // the keys that a first streaming pass over the same soft masks reduced (from_keys)
+  struct Scale { EnsInput in; float* out; bool from_keys; };
+  std::vector<Scale> scales;
+  bool maxu = false;       // STREAM: some descriptor reduces E4M3 maxima (umax)
   // TILED launches (one ensemble or time step): operand staging + tiled Gram
   EnsInput in;
   TiledPlan tp;
@@ -89,12 +138,14 @@ struct Launch {
   bool stage = true;       // stage the operands (else the streaming pass wrote them)
   float* gpart = nullptr;
   float* scale = nullptr;
+  bool scale_from_keys = false;   // E4M3: the streaming pass reduced the maxima
 };
 
 struct BatchPlan {
   std::vector<EnsDesc> sdesc;   // streaming descriptors (pass 1 then pass 2), grouped by class
   std::vector<FinDesc> fdesc;   // finalisation descriptors (phase 1 then phase 2)
   std::vector<Launch> launches;
+  std::vector<std::pair<unsigned int*, int64_t>> key_resets;   // E4M3 keys zeroed first
   size_t desc_bytes = 0;
   size_t work_bytes = 0;
 };
@@ -162,6 +213,27 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
         return fail(h, PID_ERR_INVALID_ARG, "the time steps of a space-time ensemble differ");
     }
   }
+  // A fused-Gram ensemble of soft masks takes its exact PID-mean partials (m, A) from a
+  // first streaming pass over the same data where the batch has one (a PID-mean or exact
+  // full-PID item of the same masks: same pointer, shape, stride and cell measures), and its
+  // converters then skip that arithmetic. An E4M3 ensemble without such a sibling runs a
+  // streaming pass of its own, as a single call does, which also reduces its member scales.
+  std::vector<int> sib(count, -1), own_pass(count, 0);
+  if (!st4) {
+    for (int e = 0; e < count; ++e) {
+      if (!is_gram[e] || tiled[e] || in[e].is_field) continue;
+      for (int f = 0; f < count && sib[e] < 0; ++f) {
+        if (f != e && !(is_gram[f] && !tiled[f]) && !in[f].is_field && in[f].data == in[e].data &&
+            in[f].N == in[e].N && in[f].M == in[e].M && in[f].ld == in[e].ld && in[f].w == in[e].w)
+          sib[e] = f;
+      }
+      if (sib[e] < 0 && in[e].precision == PID_FP8) {
+        sib[e] = e;
+        own_pass[e] = 1;
+      }
+      gp[e].exact = sib[e] < 0;
+    }
+  }
   // Workspace: descriptors first (64-byte aligned tensor maps), then per-ensemble buffers.
   std::map<ClassKey, std::vector<int>> pass1, pass2;
   // ((((precision x 2 + TMA) x 2 + wide) x 32 + group size) x 32 + members per warp,
@@ -169,10 +241,13 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   std::map<std::pair<int, int>, std::vector<int>> gram_cls;
   for (int e = 0; e < count; ++e) {
     if (is_gram[e] && !tiled[e]) {
-      gram_cls[{(((gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 2 + (gp[e].wide ? 1 : 0)) * 32 +
-                 gp[e].G) * 32 + gp[e].mpw,
+      gram_cls[{((((gp[e].prec * 2 + (gp[e].tma ? 1 : 0)) * 2 + (gp[e].wide ? 1 : 0)) * 32 +
+                  gp[e].G) * 32 + gp[e].mpw) * 2 + (gp[e].exact ? 1 : 0),
                 iso_kind(gp[e].desc.iso_mode)}]
           .push_back(e);
+      if (own_pass[e])
+        pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, iso_kind(pl[e].desc.iso_mode), pl[e].use_tma ? 1 : 0,
+               pl[e].cfg.mpw}].push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
       pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, pl[e].use_tma ? 1 : 0, pl[e].cfg.mpw}].push_back(e);
@@ -264,6 +339,22 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   }
   bp->work_bytes = off;
   if (n_logical > kMaxTickets) return fail(h, PID_ERR_UNSUPPORTED, "too many ensembles in one batch");
+  // E4M3 scales of soft masks from a first streaming pass over the same data, where the
+  // batch has one: a tiled Gram's own exact-sums pass, or a PID-mean / exact full PID item of
+  // the same masks (same pointer, shape, stride and cell measures); otherwise a pass of
+  // their own before the Gram.
+  std::vector<int> keys_src(count, -1);
+  auto claim = [&](int e, int f) {
+    pl[f].desc.umax = scale_keys(scale[e]);
+    keys_src[e] = f;
+    bp->key_resets.push_back({pl[f].desc.umax, in[e].N});
+  };
+  for (int e = 0; e < count; ++e)
+    if (tiled[e] && in[e].precision == PID_FP8 && !in[e].is_field) claim(e, e);
+  for (int e = 0; e < count; ++e)   // a second E4M3 item on the same masks runs its own max pass
+    if (is_gram[e] && !tiled[e] && in[e].precision == PID_FP8 && sib[e] >= 0 &&
+        pl[sib[e]].desc.umax == nullptr)
+      claim(e, sib[e]);
 
   auto add_stream_class = [&](const std::vector<int>& members, bool coef_pass) {
     Launch L;
@@ -277,7 +368,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     for (int e : members) {
       const EnsPlan& p = (coef_pass && stored[e]) ? pl2[e] : pl[e];
       EnsDesc d = p.desc;
-      if (coef_pass) { d.u_out = nullptr; d.op_out = nullptr; }
+      if (coef_pass) { d.u_out = nullptr; d.op_out = nullptr; d.umax = nullptr; }
+      L.maxu = L.maxu || d.umax != nullptr;
       d.unit_begin = units;
       d.work_begin = L.cells;
       d.coef = coef_pass ? coef[e] : nullptr;
@@ -312,13 +404,19 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       f.n_gchunks = steps * gram_chunks(e);
       f.P = o.P;
       f.err_est = o.err_est;
+      if (sib[e] >= 0) {   // (m, A) from the first streaming pass over the same masks
+        f.part = part[sib[e]];
+        f.n_chunks = pl[sib[e]].desc.n_chunks;
+      }
     }
     const int nb = (2 * f.N + 31) / 32 + (kind == FIN_GRAM ? fin_gram_items(f.N) : 0);
     f.slices = std::max(1, std::min(nb, 2 * h->sms));
     return f;
   };
 
-  // Phase 1: Gram launches and first streaming passes.
+  // Phase 1: first streaming passes (which may also reduce E4M3 maxima), then the Gram
+  // launches.
+  for (auto& kv : pass1) add_stream_class(kv.second, false);
   for (auto& kv : gram_cls) {
     Launch L;
     L.kind = Launch::GRAM;
@@ -336,7 +434,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       d.op_scale = nullptr;
       if (gp[e].prec == PID_FP8) {
         d.op_scale = scale[e];
-        L.scales.push_back({in[e], scale[e]});
+        L.scales.push_back({in[e], scale[e], keys_src[e] >= 0});
       }
       units += gp[e].n_gchunks;
       L.bytes += gp[e].bytes;
@@ -350,7 +448,6 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.total_units = units;
     bp->launches.push_back(L);
   }
-  for (auto& kv : pass1) add_stream_class(kv.second, false);
   for (int e = 0; e < count; ++e) {
     if (!tiled[e]) continue;
     Launch L;
@@ -363,6 +460,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
     L.stage = !fused[e];
     L.gpart = gpart[e];
     L.scale = scale[e];
+    L.scale_from_keys = keys_src[e] >= 0;
     bp->launches.push_back(L);
   }
   {
@@ -399,6 +497,10 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
                           cudaStream_t s) {
   cudaError_t e = cudaMemcpyAsync(base, host_image, bp.desc_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch descriptor upload");
+  for (const auto& kr : bp.key_resets) {
+    e = cudaMemsetAsync(kr.first, 0, static_cast<size_t>(kr.second) * sizeof(unsigned int), s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "scale key reset");
+  }
   const EnsDesc* sdev = reinterpret_cast<const EnsDesc*>(base);
   const size_t sdesc_bytes = align_up(static_cast<int64_t>(bp.sdesc.size()) * sizeof(EnsDesc), 256);
   const FinDesc* fdev = reinterpret_cast<const FinDesc*>(base + sdesc_bytes);
@@ -416,20 +518,26 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       sp.use_tma = L.tma ? 1 : 0;
       sp.err = h->err_word;
       sp.stage_floats = L.stage_floats;
+      sp.maxu = L.maxu ? 1 : 0;
       const int n_groups = kStreamWarps / L.cfg.G;
       const int grid = std::max(1, std::min<int>(h->sms, (L.total_units + n_groups - 1) / n_groups));
       pid_status st = stream_launch(h, sp, L.cfg, L.coef, grid, L.max_n, L.cells, L.bytes, s);
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::GRAM) {
       for (const auto& sc : L.scales) {
-        const pid_status st = launch_member_scales_one(h, sc.in, sc.out, s);
+        const pid_status st = sc.from_keys ? launch_scales_from_keys(h, sc.in.N, sc.out, s)
+                                           : launch_member_scales_one(h, sc.in, sc.out, s);
         if (st != PID_OK) return st;
       }
       pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units,
                                         L.cells, L.iso_mode, L.bytes, L.flops, s);
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::TILED) {
-      pid_status st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, L.stage, s);
+      pid_status st = PID_OK;
+      if (L.scale_from_keys && (st = launch_scales_from_keys(h, L.in.N, L.scale, s)) != PID_OK)
+        return st;
+      st = launch_gram_tiled_one(h, L.in, L.tp, L.op, L.gpart, L.scale, L.stage, s,
+                                 L.scale_from_keys);
       if (st != PID_OK) return st;
     } else {
       FinParams fp;
@@ -464,11 +572,17 @@ pid_status run_batch(pid_handle h, const pid_ensemble* ens, int32_t count, int s
   const bool profiled = h->profiling;
   // Replay the cached graph when the batch is the one it was recorded for (same ensemble
   // records, same workspace): no planning, no tensor-map encoding, one graph launch.
-  std::vector<unsigned char> key(sizeof(pid_ensemble) * count + sizeof(void*) + sizeof(int));
+  // key: the records, the workspace address, the steps and whether the graph is profiled
+  std::vector<unsigned char> key(sizeof(pid_ensemble) * count + sizeof(void*) + sizeof(int) + 1);
   std::memcpy(key.data(), ens, sizeof(pid_ensemble) * count);
   std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
   std::memcpy(key.data() + sizeof(pid_ensemble) * count + sizeof(void*), &steps, sizeof(int));
-  if (c->use_graphs && !capturing && !profiled && c->exec && key == c->key) {
+  key.back() = profiled ? 1 : 0;
+  if (c->use_graphs && !capturing && c->exec && key == c->key) {
+    if (profiled) {
+      const pid_status ps = arm_graph_profiling(h, c);
+      if (ps != PID_OK) return ps;
+    }
     cudaError_t e = cudaGraphLaunch(c->exec, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "batch graph replay");
     ++c->replays;
@@ -520,7 +634,7 @@ pid_status run_batch(pid_handle h, const pid_ensemble* ens, int32_t count, int s
   std::memcpy(static_cast<char*>(c->host_desc) + sdesc_bytes, bp.fdesc.data(),
               bp.fdesc.size() * sizeof(FinDesc));
 
-  if (!c->use_graphs || capturing || profiled) {
+  if (!c->use_graphs || capturing) {
     return enqueue(h, bp, base, c->host_desc, s);
   }
   if (h->autotune) {
@@ -536,10 +650,20 @@ pid_status run_batch(pid_handle h, const pid_ensemble* ens, int32_t count, int s
   if (e != cudaSuccess) return cuda_fail(h, e, "capture stream");
   e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) { cudaStreamDestroy(cap); return cuda_fail(h, e, "begin capture"); }
+  h->prof_graph = profiled;
+  h->prof_captured.clear();
   st = enqueue(h, bp, base, c->host_desc, cap);
+  h->prof_graph = false;
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(cap, &graph);
   cudaStreamDestroy(cap);
+  c->prof.clear();
+  if (st == PID_OK && e == cudaSuccess && profiled) st = collect_graph_profiling(h, graph, c);
+  for (const ProfRecord& r : h->prof_captured) {   // left over after a failed capture
+    h->event_pool.push_back(r.start);
+    h->event_pool.push_back(r.stop);
+  }
+  h->prof_captured.clear();
   if (st != PID_OK) { if (graph) cudaGraphDestroy(graph); return st; }
   if (e != cudaSuccess) return cuda_fail(h, e, "end capture");
   cudaGraphExec_t exec = nullptr;
@@ -548,6 +672,7 @@ pid_status run_batch(pid_handle h, const pid_ensemble* ens, int32_t count, int s
   c->graph = graph;
   c->exec = exec;
   c->key = key;
+  if (profiled && (st = arm_graph_profiling(h, c)) != PID_OK) return st;
   e = cudaGraphLaunch(exec, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "batch graph launch");
   return PID_OK;

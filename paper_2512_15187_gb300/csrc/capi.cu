@@ -50,7 +50,7 @@ DeviceGuard::~DeviceGuard() {
 // Kernel timing
 // ---------------------------------------------------------------------------------------
 
-static cudaEvent_t pool_event(pid_handle h) {
+cudaEvent_t prof_event(pid_handle h) {
   if (!h->event_pool.empty()) {
     cudaEvent_t e = h->event_pool.back();
     h->event_pool.pop_back();
@@ -64,8 +64,9 @@ static cudaEvent_t pool_event(pid_handle h) {
 // NVTX range names of the kernel kinds (pid_kernel_kind order): every launch the library
 // makes is bracketed by a host range, so external profilers attribute kernels to the calls.
 static const char* const kNvtxNames[PID_KERNEL_KINDS] = {
-    "pid: streaming pass", "pid: tensor-core Gram", "pid: finalisation", "pid: isovalue map",
-    "pid: contour bands"};
+    "pid: streaming pass", "pid: tensor-core Gram (BF16)", "pid: finalisation",
+    "pid: isovalue map", "pid: contour bands", "pid: tensor-core Gram (split BF16)",
+    "pid: tensor-core Gram (E4M3)", "pid: Gram operand staging", "pid: E4M3 member scales"};
 
 ProfScope::ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStream_t s)
     : h_(h), s_(s) {
@@ -73,15 +74,32 @@ ProfScope::ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStr
   if (!h_ || !h_->profiling) return;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(s_, &cs);
-  if (cs != cudaStreamCaptureStatusNone) return;  // captured launches are not timed here
-  ProfRecord r{kind, pool_event(h_), pool_event(h_), bytes, flops};
+  ProfRecord r{kind, nullptr, nullptr, bytes, flops};
+  if (cs != cudaStreamCaptureStatusNone) {
+    // only the library's own profiled batch graphs are timed (a caller's capture is not)
+    if (!h_->prof_graph) return;
+    r.start = prof_event(h_);
+    r.stop = prof_event(h_);
+    cudaEventRecordWithFlags(r.start, s_, cudaEventRecordExternal);
+    h_->prof_captured.push_back(r);
+    idx_ = static_cast<int>(h_->prof_captured.size()) - 1;
+    captured_ = true;
+    return;
+  }
+  r.start = prof_event(h_);
+  r.stop = prof_event(h_);
   cudaEventRecord(r.start, s_);
   h_->prof_pending.push_back(r);
   idx_ = static_cast<int>(h_->prof_pending.size()) - 1;
 }
 
 ProfScope::~ProfScope() {
-  if (idx_ >= 0) cudaEventRecord(h_->prof_pending[idx_].stop, s_);
+  if (idx_ >= 0) {
+    if (captured_)
+      cudaEventRecordWithFlags(h_->prof_captured[idx_].stop, s_, cudaEventRecordExternal);
+    else
+      cudaEventRecord(h_->prof_pending[idx_].stop, s_);
+  }
   nvtxRangePop();
 }
 
@@ -478,6 +496,8 @@ static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef
   sp.use_tma = pl.use_tma ? 1 : 0;
   sp.err = h->err_word;
   sp.stage_floats = pl.stage_floats;
+  if (coef) sp.one.umax = nullptr;
+  sp.maxu = sp.one.umax != nullptr ? 1 : 0;
   const int n_groups = kStreamWarps / pl.cfg.G;
   int grid = std::min<int>(h->sms, (sp.total_units + n_groups - 1) / n_groups);
   grid = std::max(grid, 1);
@@ -536,9 +556,17 @@ static pid_status run_gram_tiled(pid_handle h, const EnsInput& in, EnsPlan& pl,
     pl.desc.op_out = reinterpret_cast<uint16_t*>(ws + off_op);
     pl.desc.op_ld = tp.ldo;
   }
+  // E4M3 of soft masks: the streaming pass also reduces the per-member maxima of the scales
+  float* scale = reinterpret_cast<float*>(ws + off_scale);
+  const bool keys_from_stream = tp.prec == PID_FP8 && !in.is_field;
+  if (keys_from_stream) {
+    pl.desc.umax = scale_keys(scale);
+    const cudaError_t e = cudaMemsetAsync(pl.desc.umax, 0, static_cast<size_t>(in.N) * 4, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "scale key reset");
+  }
   if ((st = launch_stream_one(h, pl, nullptr, s)) != PID_OK) return st;
-  st = launch_gram_tiled_one(h, in, tp, ws + off_op, gpart, reinterpret_cast<float*>(ws + off_scale),
-                             !fused, s);
+  if (keys_from_stream && (st = launch_scales_from_keys(h, in.N, scale, s)) != PID_OK) return st;
+  st = launch_gram_tiled_one(h, in, tp, ws + off_op, gpart, scale, !fused, s, keys_from_stream);
   if (st != PID_OK) return st;
   FinDesc fd;
   std::memset(&fd, 0, sizeof(fd));
@@ -605,10 +633,22 @@ pid_status run_single(pid_handle h, const EnsInput& in, const EnsOutputs& out, c
   if (gram) {
     float* gpart = reinterpret_cast<float*>(gbase + kScaleBytes);
     float* scale = reinterpret_cast<float*>(gbase);
-    st = launch_gram_one(h, in, gp, part, gpart, scale, s);
+    // E4M3 of soft masks needs a pass over the data for its member scales anyway: that pass
+    // is the streaming kernel, which also forms the exact (m, A) partials, and the Gram pass
+    // then skips them
+    const bool own_pass = gp.prec == PID_FP8 && !in.is_field;
+    if (own_pass) {
+      pl.desc.umax = scale_keys(scale);
+      const cudaError_t e = cudaMemsetAsync(pl.desc.umax, 0, static_cast<size_t>(in.N) * 4, s);
+      if (e != cudaSuccess) return cuda_fail(h, e, "scale key reset");
+      if ((st = launch_stream_one(h, pl, nullptr, s)) != PID_OK) return st;
+      if ((st = launch_scales_from_keys(h, in.N, scale, s)) != PID_OK) return st;
+      gp.exact = false;
+    }
+    st = launch_gram_one(h, in, gp, part, gpart, scale, s, own_pass);
     if (st != PID_OK) return st;
     fd.kind = FIN_GRAM;
-    fd.n_chunks = gp.n_gchunks;
+    fd.n_chunks = own_pass ? pl.desc.n_chunks : gp.n_gchunks;
     fd.gpart = gpart;
     fd.n_gchunks = gp.n_gchunks;
     fd.P = out.P;

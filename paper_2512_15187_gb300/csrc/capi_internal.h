@@ -29,6 +29,8 @@ struct ProfRecord {
 };
 
 // Brackets one kernel launch with events when profiling is on (RAII on the host side).
+// While the library records a batch into a CUDA graph with profiling on, the events become
+// event-record nodes of the graph (re-armed with fresh events at every replay).
 class ProfScope {
  public:
   ProfScope(pid_handle h, int kind, double bytes, double flops, cudaStream_t s);
@@ -36,8 +38,10 @@ class ProfScope {
  private:
   pid_handle h_;
   int idx_ = -1;
+  bool captured_ = false;
   cudaStream_t s_;
 };
+cudaEvent_t prof_event(pid_handle h);   // a timing event from the handle's pool
 
 }  // namespace pidh
 
@@ -62,6 +66,8 @@ struct pid_handle_s {
   std::vector<pidh::ProfRecord> prof_pending;
   std::vector<cudaEvent_t> event_pool;
   pid_kernel_stats prof_total[PID_KERNEL_KINDS] = {};
+  bool prof_graph = false;     // recording a profiled batch graph: time captured launches
+  std::vector<pidh::ProfRecord> prof_captured;   // their events, turned into graph nodes
   bool autotune = false;
   std::map<std::string, std::pair<int, int>> tuned;  // key -> (exchange scheme, ring depth)
   std::string tune_file;
@@ -122,6 +128,7 @@ struct GramPlan {
   int32_t stage_floats = 0;
   int dF = 2, dO = 2;
   size_t smem = 0;
+  bool exact = true;       // false: soft masks whose (m, A) come from a streaming pass
   size_t gpart_bytes = 0;  // [n_gchunks][N][N] float32
   size_t part_bytes = 0;   // [n_gchunks][2N] float64 (exact PID-mean partials)
   double bytes = 0, flops = 0;
@@ -196,11 +203,16 @@ inline int gram_operand_precision(int prec, int64_t cells, bool want_matrix) {
 // Per-member E4M3 operand scales of one ensemble into `region` (pidk::kScaleBytes of
 // workspace: [2N] scales and inverses, then [N] reduction keys).
 pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* region, cudaStream_t s);
+// The reduction keys inside a scale region, and the scales from keys a streaming pass filled.
+inline unsigned int* scale_keys(float* region) {
+  return reinterpret_cast<unsigned int*>(region + 2 * pidk::kGramTiledMaxN);
+}
+pid_status launch_scales_from_keys(pid_handle h, int64_t N, float* region, cudaStream_t s);
 pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp);
 void gram_geometry(pid_handle h, int G, int mpw, bool wide, int prec, int32_t stage_floats,
                    int* dF, int* dO, size_t* smem);
 pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
-                           float* gpart, float* scale, cudaStream_t s);
+                           float* gpart, float* scale, cudaStream_t s, bool scales_ready = false);
 // Gram launch over `count` device descriptors (part / gpart / op_scale already set).
 pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const pidk::EnsDesc* descs,
                              int count, int total_units, int64_t total_work, int iso_mode,
@@ -211,8 +223,10 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp);
 // Operand staging (unless the streaming pass already wrote the BF16 operands) and the
 // tiled Gram launch; `op` holds tp.op_bytes, `gpart` tp.gpart_bytes, `scale`
 // pidk::kScaleBytes (E4M3 member scales).
+// scales_ready: the E4M3 scales in `scale` were already computed (from streaming-pass keys).
 pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
-                                 float* gpart, float* scale, bool stage_operands, cudaStream_t s);
+                                 float* gpart, float* scale, bool stage_operands, cudaStream_t s,
+                                 bool scales_ready = false);
 
 // batch.cu
 void destroy_batch_cache(pid_handle h);

@@ -196,6 +196,16 @@ __device__ __forceinline__ unsigned long long order_key(double d) {
                 : ~static_cast<unsigned long long>(b);
 }
 
+// Order-preserving unsigned key of a float (keys compare as the floats do; 0 is below the
+// key of every float, so a zeroed key array is the identity of a maximum taken with atomicMax).
+__device__ __forceinline__ unsigned int fkey(float v) {
+  const unsigned int b = __float_as_uint(v);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float fkey_inv(unsigned int k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));

@@ -97,9 +97,21 @@ pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* reg
   sp.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
               (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
   sp.scale = region;
-  sp.maxkey = reinterpret_cast<unsigned int*>(region + 2 * kGramTiledMaxN);
+  sp.maxkey = scale_keys(region);
   ProfScope ps(h, PID_KERNEL_SCALE, 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0), 0.0, s);
   const cudaError_t e = launch_member_scales(sp, h->sms, s);
+  if (e != cudaSuccess) return cuda_fail(h, e, "E4M3 member scale launch");
+  return PID_OK;
+}
+
+pid_status launch_scales_from_keys(pid_handle h, int64_t N, float* region, cudaStream_t s) {
+  ScaleParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.N = static_cast<int32_t>(N);
+  sp.scale = region;
+  sp.maxkey = scale_keys(region);
+  ProfScope ps(h, PID_KERNEL_SCALE, 4.0 * N, 0.0, s);
+  const cudaError_t e = launch_member_scales_from_keys(sp, s);
   if (e != cudaSuccess) return cuda_fail(h, e, "E4M3 member scale launch");
   return PID_OK;
 }
@@ -118,7 +130,7 @@ static pid_status gram_launch(pid_handle h, const GramParams& gpar, int G, int m
 }
 
 pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, double* part,
-                           float* gpart, float* scale, cudaStream_t s) {
+                           float* gpart, float* scale, cudaStream_t s, bool scales_ready) {
   GramParams gpar;
   std::memset(&gpar, 0, sizeof(gpar));
   gpar.one = gp.desc;
@@ -126,8 +138,10 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   gpar.one.gpart = gpart;
   gpar.one.op_scale = nullptr;
   if (gp.prec == PID_FP8) {
-    const pid_status st = launch_member_scales_one(h, in, scale, s);
-    if (st != PID_OK) return st;
+    if (!scales_ready) {
+      const pid_status st = launch_member_scales_one(h, in, scale, s);
+      if (st != PID_OK) return st;
+    }
     gpar.one.op_scale = scale;
   }
   gpar.n_ens = 1;
@@ -141,6 +155,7 @@ pid_status launch_gram_one(pid_handle h, const EnsInput& in, GramPlan& gp, doubl
   gpar.xchg = gp.G >= 16 ? 1 : 0;   // one group barrier per stage for 8-warp groups
   gpar.use_tma = gp.tma ? 1 : 0;
   gpar.err = h->err_word;
+  gpar.exact = gp.exact ? 1 : 0;
   const int ng = kGramConvWarps / gp.G;
   const int grid = std::max(1, std::min(h->sms, (gp.n_gchunks + ng - 1) / ng));
   return gram_launch(h, gpar, gp.G, gp.mpw, gp.wide, gp.prec, gp.desc.iso_mode, grid, gp.smem,
@@ -163,6 +178,7 @@ pid_status launch_gram_batch(pid_handle h, const GramPlan& gp, const EnsDesc* de
   gpar.xchg = gp.G >= 16 ? 1 : 0;
   gpar.use_tma = gp.tma ? 1 : 0;
   gpar.err = h->err_word;
+  gpar.exact = gp.exact ? 1 : 0;
   const int ng = kGramConvWarps / gp.G;
   const int grid = std::max(1, std::min(h->sms, (total_units + ng - 1) / ng));
   return gram_launch(h, gpar, gp.G, gp.mpw, gp.wide, gp.prec, iso_mode, grid, gp.smem, bytes,
@@ -216,11 +232,14 @@ pid_status plan_gram_tiled(pid_handle h, const EnsInput& in, TiledPlan* tp) {
 }
 
 pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPlan& tp, void* op,
-                                 float* gpart, float* scale, bool stage_operands, cudaStream_t s) {
+                                 float* gpart, float* scale, bool stage_operands, cudaStream_t s,
+                                 bool scales_ready) {
   const float* op_scale = nullptr;
   if (tp.prec == PID_FP8) {
-    const pid_status st = launch_member_scales_one(h, in, scale, s);
-    if (st != PID_OK) return st;
+    if (!scales_ready) {
+      const pid_status st = launch_member_scales_one(h, in, scale, s);
+      if (st != PID_OK) return st;
+    }
     op_scale = scale;
   }
   const int64_t plane = rup(static_cast<int64_t>(in.N) * tp.ldo * tp.elem_bytes, 1024);

@@ -64,22 +64,13 @@ cudaError_t gram_kernels_init(int max_smem) {
 // values are all small keeps E4M3's full relative precision instead of falling into its
 // subnormal range.
 //
-// One pass finds the per-member maxima. Soft masks, and weighted fields (mapped element by
-// element), reduce the operand u sqrt(w) itself. For unweighted fields it is enough to find
+// One pass finds the per-member maxima (or, in a batch that also streams the same soft
+// masks for PID-mean, that streaming pass does, see stream_kernel's MAXU). Soft masks, and
+// weighted fields (mapped element by element), reduce the operand u sqrt(w) itself. For unweighted fields it is enough to find
 // the field value that the map sends highest, since every isovalue map is monotone in a
 // simple function of F (its "proxy"), and to map that one value.
 
 namespace {
-
-// Order-preserving unsigned key of a float (keys compare as the floats do; 0 is below the
-// key of every float, so a zeroed key array is the identity of the maximum).
-__device__ __forceinline__ unsigned int fkey(float v) {
-  const unsigned int b = __float_as_uint(v);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float fkey_inv(unsigned int k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
-}
 
 // Proxy of a field value: the soft mask of each isovalue mode is a non-decreasing function
 // of it (Normal: u = erfc(xs)/2 decreases in xs = (F - mu) inv, whose sign carries the
@@ -187,6 +178,11 @@ __global__ void member_scale_kernel(const __grid_constant__ ScaleParams p, bool 
 }
 
 }  // namespace
+
+cudaError_t launch_member_scales_from_keys(const ScaleParams& p, cudaStream_t s) {
+  member_scale_kernel<<<(p.N + 255) / 256, 256, 0, s>>>(p, false);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_member_scales(const ScaleParams& p, int sms, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(p.maxkey, 0, static_cast<size_t>(p.N) * sizeof(unsigned int), s);

@@ -99,8 +99,15 @@ __device__ __forceinline__ uint32_t sw128_offset(int i, int b) {
 // it to the stage's "operand free" mbarrier and, at a chunk's end, to the accumulator's
 // "ready" mbarrier; warps 0-3 drain the previous chunk's accumulator halfway through the
 // next chunk.
-template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = (WIDE ? 16 : 8)>
+//
+// EXACT = false (soft masks whose exact PID-mean sums m_i, A_i come from a streaming pass over
+// the same data, e.g. the PID-mean item of the same ensemble in a batch): the converters
+// skip the mean-contour arithmetic and its column-sum exchange; one group barrier per stage
+// remains, after the stage's FP32 tile has been read, and the kernel writes no (m, A)
+// partials.
+template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = (WIDE ? 16 : 8), bool EXACT = true>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams p) {
+  static_assert(EXACT || ISO == ISOK_NONE, "fields map in the Gram pass, with the exact sums");
   using S = GramShape<WIDE, NMPW>;
   constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, SPO = S::SPO, MB = S::MB, NBUF = S::NBUF;
   static_assert(!WIDE || G == 16, "the wide tile uses all 16 warps as one group");
@@ -406,9 +413,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     const int c = u - e_begin;
     const int cell0 = c * e_chunk;
     const int n_st = SPO * ((min(e_chunk, M - cell0) + 127) / 128);   // FP32 stages
-    float accM[MPW], accA[MPW];
+    float accM[EXACT ? MPW : 1], accA[EXACT ? MPW : 1];
 #pragma unroll
-    for (int m = 0; m < MPW; ++m) { accM[m] = 0.f; accA[m] = 0.f; }
+    for (int m = 0; m < (EXACT ? MPW : 1); ++m) { accM[m] = 0.f; accA[m] = 0.f; }
 
     for (int st = 0; st < n_st; ++st, ++k, ++kt) {
       // Ring positions, kept incrementally (no 64-bit division per stage):
@@ -484,54 +491,64 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
           }
         }
       }
-      // ---- exact PID-mean arithmetic, as in the streaming kernel ----
-      float s[VEC];
-      {
-        float2 s2[VEC / 2];
+      if constexpr (EXACT) {
+        // ---- exact PID-mean arithmetic, as in the streaming kernel ----
+        float s[VEC];
+        {
+          float2 s2[VEC / 2];
 #pragma unroll
-        for (int v = 0; v < VEC / 2; ++v) s2[v] = f2(0.f);
+          for (int v = 0; v < VEC / 2; ++v) s2[v] = f2(0.f);
 #pragma unroll
-        for (int m = 0; m < MPW; ++m)
+          for (int m = 0; m < MPW; ++m)
 #pragma unroll
-          for (int v = 0; v < VEC / 2; ++v)
-            s2[v] = f2_add(s2[v], make_float2(x[m][2 * v], x[m][2 * v + 1]));
+            for (int v = 0; v < VEC / 2; ++v)
+              s2[v] = f2_add(s2[v], make_float2(x[m][2 * v], x[m][2 * v + 1]));
 #pragma unroll
-        for (int v = 0; v < VEC / 2; ++v) { s[2 * v] = s2[v].x; s[2 * v + 1] = s2[v].y; }
-      }
-      float* rb = red + static_cast<int>(kt & 1) * RB;  // this group's exchange buffer
-      sts_vec<VEC>(rb + q * T + lane * VEC, s);
-      named_barrier(1 + grp, G * 32);
-      if (cflag[kt & 1]) { aborted = true; break; }
-      if (leader) {
-        if (!issue_pending()) cflag[(kt + 1) & 1] = 1;   // stage k-1 to the tensor cores
-        if (TMA) issue_next();                          // every warp has read this FP32 stage
-      }
-      if (p.xchg == 1) {
-        constexpr int cpw = T / G;
-        if (lane < cpw) {
-          const int cc = q * cpw + lane;
-          float acc = 0.f;
-#pragma unroll
-          for (int r = 0; r < G; ++r) acc += rb[r * T + cc];
-          rb[G * T + cc] = acc;
+          for (int v = 0; v < VEC / 2; ++v) { s[2 * v] = s2[v].x; s[2 * v + 1] = s2[v].y; }
         }
+        float* rb = red + static_cast<int>(kt & 1) * RB;  // this group's exchange buffer
+        sts_vec<VEC>(rb + q * T + lane * VEC, s);
         named_barrier(1 + grp, G * 32);
-        lds_vec<VEC>(s, rb + G * T + lane * VEC);
+        if (cflag[kt & 1]) { aborted = true; break; }
+        if (leader) {
+          if (!issue_pending()) cflag[(kt + 1) & 1] = 1;   // stage k-1 to the tensor cores
+          if (TMA) issue_next();                          // every warp has read this FP32 stage
+        }
+        if (p.xchg == 1) {
+          constexpr int cpw = T / G;
+          if (lane < cpw) {
+            const int cc = q * cpw + lane;
+            float acc = 0.f;
+#pragma unroll
+            for (int r = 0; r < G; ++r) acc += rb[r * T + cc];
+            rb[G * T + cc] = acc;
+          }
+          named_barrier(1 + grp, G * 32);
+          lds_vec<VEC>(s, rb + G * T + lane * VEC);
+        } else {
+          sum_partials<VEC, G>(s, rb + lane * VEC, T);
+        }
+#pragma unroll
+        for (int m = 0; m < MPW; ++m) {
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const float t = has_w ? wv[v] * x[m][v] : x[m][v];
+            accM[m] += t;
+            accA[m] = fmaf(t, s[v], accA[m]);
+          }
+        }
       } else {
-        sum_partials<VEC, G>(s, rb + lane * VEC, T);
+        // every warp has read this FP32 stage, and written its operands of the previous one
+        named_barrier(1 + grp, G * 32);
+        if (cflag[kt & 1]) { aborted = true; break; }
+        if (leader) {
+          if (!issue_pending()) cflag[(kt + 1) & 1] = 1;   // stage k-1 to the tensor cores
+          if (TMA) issue_next();
+        }
       }
       float sw[VEC];
 #pragma unroll
       for (int v = 0; v < VEC; ++v) sw[v] = 1.f;
-#pragma unroll
-      for (int m = 0; m < MPW; ++m) {
-#pragma unroll
-        for (int v = 0; v < VEC; ++v) {
-          const float t = has_w ? wv[v] * x[m][v] : x[m][v];
-          accM[m] += t;
-          accA[m] = fmaf(t, s[v], accA[m]);
-        }
-      }
       if (has_w) {
 #pragma unroll
         for (int v = 0; v < VEC; ++v) sw[v] = sqrtf(wv[v]);
@@ -598,14 +615,16 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     prev_N = N;
     prev_osc = osc;
     prev_kc = kc;
+    if constexpr (EXACT) {
 #pragma unroll
-    for (int m = 0; m < MPW; ++m) {
-      const float ms = warp_sum(accM[m]);
-      const float as = warp_sum(accA[m]);
-      const int i = q + m * G;
-      if (lane == 0 && i < N) {
-        d.part[static_cast<size_t>(c) * 2 * N + i] = static_cast<double>(ms);
-        d.part[static_cast<size_t>(c) * 2 * N + N + i] = static_cast<double>(as);
+      for (int m = 0; m < MPW; ++m) {
+        const float ms = warp_sum(accM[m]);
+        const float as = warp_sum(accA[m]);
+        const int i = q + m * G;
+        if (lane == 0 && i < N) {
+          d.part[static_cast<size_t>(c) * 2 * N + i] = static_cast<double>(ms);
+          d.part[static_cast<size_t>(c) * 2 * N + N + i] = static_cast<double>(as);
+        }
       }
     }
   }
@@ -645,6 +664,15 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 // with 12.
 template <int G, int ISO, int PREC, int NMPW, bool WIDE>
 cudaError_t gram_tile_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
+  if constexpr (ISO == ISOK_NONE) {
+    if (!p.exact) {   // soft masks with the exact sums from a streaming pass
+      if (p.use_tma)
+        gram_kernel<G, ISO, PREC, true, WIDE, NMPW, false><<<grid, kGramThreads, smem, s>>>(p);
+      else
+        gram_kernel<G, ISO, PREC, false, WIDE, NMPW, false><<<grid, kGramThreads, smem, s>>>(p);
+      return cudaGetLastError();
+    }
+  }
   if (p.use_tma)
     gram_kernel<G, ISO, PREC, true, WIDE, NMPW><<<grid, kGramThreads, smem, s>>>(p);
   else
@@ -682,6 +710,15 @@ cudaError_t gram_tile_init(int max_smem) {
   PIDK_GRAM_INIT(ISOK_NORMAL, 1) PIDK_GRAM_INIT(ISOK_NORMAL, 2) PIDK_GRAM_INIT(ISOK_NORMAL, 3)
   PIDK_GRAM_INIT(ISOK_STEP, 1) PIDK_GRAM_INIT(ISOK_STEP, 2) PIDK_GRAM_INIT(ISOK_STEP, 3)
 #undef PIDK_GRAM_INIT
+#define PIDK_GRAM_INIT_LEAN(PREC)                                                                \
+  if (e == cudaSuccess)                                                                          \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISOK_NONE, PREC, true, WIDE, NMPW, false>,           \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);             \
+  if (e == cudaSuccess)                                                                          \
+    e = cudaFuncSetAttribute(gram_kernel<G, ISOK_NONE, PREC, false, WIDE, NMPW, false>,          \
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+  PIDK_GRAM_INIT_LEAN(1) PIDK_GRAM_INIT_LEAN(2) PIDK_GRAM_INIT_LEAN(3)
+#undef PIDK_GRAM_INIT_LEAN
   return e;
 }
 

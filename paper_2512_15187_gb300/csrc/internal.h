@@ -61,6 +61,9 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   uint16_t* op_out;     // first streaming pass: also store u sqrt(w) as BF16 tensor-core
                         // operands of the row-block-tiled Gram, [N][op_ld] (nullptr = no)
   int64_t op_ld;        // a multiple of 64
+  unsigned int* umax;   // first streaming pass of soft masks: per-member maxima of u sqrt(w)
+                        // as order-preserving keys (atomicMax; zeroed before), the E4M3
+                        // scales of a Gram over the same data (nullptr = no)
 };
 
 struct StreamParams {
@@ -76,6 +79,8 @@ struct StreamParams {
   int32_t sub;             // register tiles of T cells per TMA stage
   int32_t xchg;            // column-sum exchange: 0 direct, 1 reduce-scatter (G > 2)
   uint32_t* err;           // device error word
+  int32_t maxu;            // some descriptor has umax: the instantiation that tracks maxima
+  int32_t pad;
 };
 
 // Tensor-core Gram pass: 16 warps convert tiles (the streaming arithmetic plus operand
@@ -101,6 +106,9 @@ struct GramParams {
   int32_t xchg;
   int32_t use_tma;       // 0: converters read FP32 directly (rows not 16-byte aligned)
   uint32_t* err;
+  int32_t exact;         // 1: the converters also form the exact PID-mean sums (m, A);
+                         // 0: soft masks whose sums come from a streaming pass
+  int32_t pad;
 };
 
 // Row-block-tiled Gram (256 < N <= 512): operand rows staged in HBM, then one CTA per
@@ -226,6 +234,8 @@ struct ScaleParams {
 };
 // Zero the keys, reduce the per-member maxima and write the scales (three launches).
 cudaError_t launch_member_scales(const ScaleParams& p, int sms, cudaStream_t s);
+// The scales from keys that a streaming pass has already reduced (p.maxkey, p.N, p.scale).
+cudaError_t launch_member_scales_from_keys(const ScaleParams& p, cudaStream_t s);
 // Workspace of one ensemble's scales: [2N] floats and [N] keys, for N <= 512.
 constexpr size_t kScaleBytes = 8192;
 // Row-block-tiled Gram (gram_tiled.cu).

@@ -216,9 +216,12 @@ __device__ __forceinline__ void iso_map_tile(float (&x)[MPW][VEC], float mu, flo
 //   bars  [n_groups][depth]                 "stage full" mbarriers
 //   flags [n_groups][2]                     abort flags (bounded wait ran out), one per
 //                                           exchange-buffer parity (see below)
-template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
+// MAXU (soft masks, first pass only): also reduce each member's largest u sqrt(w) into
+// the descriptor's umax keys (the per-member E4M3 scales of a Gram over the same masks).
+template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA, bool MAXU = false>
 __global__ void __launch_bounds__(kStreamThreads, 1)
 stream_kernel(const __grid_constant__ StreamParams p) {
+  static_assert(!MAXU || (ISO == ISOK_NONE && !COEF), "maxima of soft masks, first pass");
   static_assert(MPW <= 32, "member coefficients are broadcast from one lane each");
   static_assert(VEC % 2 == 0 || MPW % 2 == 0, "values are processed in packed pairs");
   constexpr int T = 32 * VEC;
@@ -371,9 +374,11 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     const int cell0 = c * e_chunk;
     const int cells = min(e_chunk, M - cell0);
     const int n_st = (cells + TS - 1) / TS;
-    float accM[MPW], accA[MPW];
+    float accM[MPW], accA[MPW], accX[MAXU ? MPW : 1];
 #pragma unroll
     for (int k = 0; k < MPW; ++k) { accM[k] = 0.f; accA[k] = 0.f; }
+#pragma unroll
+    for (int k = 0; k < (MAXU ? MPW : 1); ++k) accX[k] = 0.f;
 
     for (int st = 0; st < n_st && !aborted; ++st, ++k_cons) {
       const int slot = c_slot;          // k_cons % depth
@@ -583,6 +588,17 @@ stream_kernel(const __grid_constant__ StreamParams p) {
             accA[k] = fmaf(t, s[v], accA[k]);
           }
         }
+        if constexpr (MAXU) {
+          // the operand u sqrt(w), rounded as the Gram kernels round it
+          float sw[VEC];
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) sw[v] = has_w ? sqrtf(wv[v]) : 1.f;
+#pragma unroll
+          for (int k = 0; k < MPW; ++k)
+#pragma unroll
+            for (int v = 0; v < VEC; ++v)
+              accX[k] = fmaxf(accX[k], has_w ? x[k][v] * sw[v] : x[k][v]);
+        }
       }
       if (aborted) break;
     }
@@ -597,6 +613,19 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       if (lane == 0 && i < N) {
         d.part[static_cast<size_t>(c) * 2 * N + i] = static_cast<double>(m);
         d.part[static_cast<size_t>(c) * 2 * N + N + i] = static_cast<double>(a);
+      }
+    }
+    if constexpr (MAXU) {
+      unsigned int* const um = dp->umax;
+      if (um != nullptr) {
+#pragma unroll
+        for (int k = 0; k < MPW; ++k) {
+          float mx = accX[k];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          const int i = q + k * G;
+          if (lane == 0 && i < N) atomicMax(um + i, fkey(mx));
+        }
       }
     }
   }
@@ -614,15 +643,15 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   }
 }
 
-template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
+template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA, bool MAXU = false>
 cudaError_t launch_stream_inst(const StreamParams& p, int grid, size_t smem, cudaStream_t s) {
-  stream_kernel<VEC, MPW, G, ISO, COEF, TMA><<<grid, kStreamThreads, smem, s>>>(p);
+  stream_kernel<VEC, MPW, G, ISO, COEF, TMA, MAXU><<<grid, kStreamThreads, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA>
+template <int VEC, int MPW, int G, int ISO, bool COEF, bool TMA, bool MAXU = false>
 cudaError_t init_stream_inst(int smem) {
-  return cudaFuncSetAttribute(stream_kernel<VEC, MPW, G, ISO, COEF, TMA>,
+  return cudaFuncSetAttribute(stream_kernel<VEC, MPW, G, ISO, COEF, TMA, MAXU>,
                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
@@ -632,6 +661,9 @@ struct StreamClass {
   static cudaError_t launch(const StreamParams& p, int iso, bool coef, int grid, size_t smem,
                             cudaStream_t s) {
     const bool tma = p.use_tma != 0;
+    if (p.maxu && iso == ISOK_NONE && !coef)   // the first pass also reduces the maxima
+      return tma ? launch_stream_inst<VEC, MPW, G, ISOK_NONE, false, true, true>(p, grid, smem, s)
+                 : launch_stream_inst<VEC, MPW, G, ISOK_NONE, false, false, true>(p, grid, smem, s);
 #define PIDK_STREAM_CASE(ISO)                                                           \
   if (iso == ISO) {                                                                     \
     if (tma) return coef ? launch_stream_inst<VEC, MPW, G, ISO, true, true>(p, grid, smem, s)  \
@@ -656,6 +688,8 @@ struct StreamClass {
     PIDK_STREAM_INIT(ISOK_NORMAL)
     PIDK_STREAM_INIT(ISOK_STEP)
 #undef PIDK_STREAM_INIT
+    if (e == cudaSuccess) e = init_stream_inst<VEC, MPW, G, ISOK_NONE, false, true, true>(smem);
+    if (e == cudaSuccess) e = init_stream_inst<VEC, MPW, G, ISOK_NONE, false, false, true>(smem);
     return e;
   }
 };

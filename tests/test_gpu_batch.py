@@ -130,3 +130,35 @@ def test_empty_batch_and_bad_entries(H):
     with pytest.raises(B.PidError) as e:
         H.batch([dict(data=U, mode="mean"), dict(data=U[:, :0], mode="mean")])
     assert e.value.status == B.PID_ERR_INVALID_ARG
+
+
+def test_profiled_graph_replays_time_every_launch(H):
+    """With profiling on, the batch is recorded with timing nodes around every kernel and
+    replayed as a graph: every replay's launches are counted and timed, and the results
+    are bitwise those of the unprofiled graph."""
+    import torch
+    from paper_2512_15187_gb300 import binding
+    h = binding.Handle(0)
+    U = [torch.rand((64, 40000 + 4 * k), device="cuda") for k in range(3)]
+    items = [dict(data=X, mode="mean") for X in U]       # one streaming class: 1 launch
+    items += [dict(data=U[0], mode="full", precision="fp8")]   # scale pass + E4M3 Gram
+    ref = h.batch(items)
+    h.sync()
+    h.profile(True)
+    outs = h.batch(items)                                  # records the profiled graph
+    for _ in range(3):
+        h.batch(items, outs=outs)                          # replays
+    h.sync()
+    prof = h.profile_read()
+    h.profile(False)
+    assert prof["stream"]["launches"] == 4, prof["stream"]
+    assert prof["gram_fp8"]["launches"] == 4, prof["gram_fp8"]
+    assert prof["scale"]["launches"] == 4, prof["scale"]
+    assert prof["finalize"]["launches"] == 4, prof["finalize"]
+    for k in ("stream", "gram_fp8", "scale", "finalize"):
+        assert prof[k]["total_ms"] > 0.0, (k, prof[k])
+    assert prof["stream"]["bytes"] == 4 * 4.0 * sum(X.numel() for X in U)
+    for a, b in zip(ref, outs):
+        for k in ("depth", "in_in", "in_out", "rank"):
+            assert torch.equal(a[k], b[k]), k
+    h.close()

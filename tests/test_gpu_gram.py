@@ -222,3 +222,52 @@ def test_gram_unaligned_rows_read_directly(H, prec, N):
         H.sync()
         _check(o, U, None, GRAM_TOL, f"{prec} ld=M+3 P={want_P}",
                raw_err_bound(_operands(prec, M, want_P), M))
+
+
+@pytest.mark.parametrize("N", [96, 200, 300])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_e4m3_scales_from_the_streaming_pass_in_a_batch(H, N, weighted):
+    """In a batch that also runs PID-mean of the same soft masks, the E4M3 Gram takes its
+    per-member scales from that streaming pass (no pass of its own); the maxima are those
+    of the same operands, so the results are bitwise those of a single E4M3 call."""
+    import torch
+    M = 50021
+    U = _dev(synth.random_soft(N, M, seed=N + 77, binary_frac=0.1))
+    U[5] *= 1e-4
+    w = _dev(np.random.default_rng(2).uniform(0.3, 3, M).astype(np.float32)) if weighted else None
+    H.profile(True)
+    outs = H.batch([dict(data=U, w=w, mode="mean"), dict(data=U, w=w, mode="full", precision="fp8")])
+    H.sync()
+    prof = H.profile_read()
+    H.profile(False)
+    # only the scale finalisation ran (N keys read), no read of the ensemble for its maxima
+    assert prof["scale"]["launches"] == 1 and prof["scale"]["bytes"] == 4.0 * N, prof["scale"]
+    single = H.full(U, w, mode="full", precision="fp8")
+    H.sync()
+    for k in ("depth", "in_in", "in_out", "rank"):
+        assert torch.equal(outs[1][k], single[k]), k
+    Un = to_np(U)
+    _check(outs[1], Un, None if w is None else to_np(w), GRAM_TOL, f"batch e4m3 N={N}")
+
+
+@pytest.mark.parametrize("N", [40, 130, 256])
+def test_gram_takes_exact_sums_from_a_sibling_pass(H, N):
+    """Gram items of a batch that also runs PID-mean of the same soft masks take the exact
+    (m, A) partials from that streaming pass and skip them in the Gram pass: the results stay
+    within the bar, and IN_in equals the sibling PID-mean's IN_in (recall identity, Eq. 17)."""
+    M = 30011
+    Un = synth.random_soft(N, M, seed=N + 3, binary_frac=0.2)
+    U = _dev(Un)
+    items = [dict(data=U, mode="mean")]
+    items += [dict(data=U, mode="full", precision=p) for p in PRECS]
+    outs = H.batch(items)
+    H.sync()
+    ref_mean = O.pid_mean(Un)
+    assert_close(to_np(outs[0]["depth"]), ref_mean[2], FP32_TOL, "sibling PID-mean")
+    for o, p in zip(outs[1:], PRECS):
+        _check(o, Un, None, GRAM_TOL, f"lean {p} N={N}")
+        assert_close(to_np(o["in_in"]), to_np(outs[0]["in_in"]), 1e-12, f"lean {p} IN_in")
+        single = H.full(U, mode="full", precision=p)
+        H.sync()
+        assert_close(to_np(o["depth"]), to_np(single["depth"]), 2e-6 if p == "split_bf16" else 2e-4,
+                     f"lean {p} vs single call")
