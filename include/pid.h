@@ -331,7 +331,14 @@ typedef struct pid_ensemble {
 /*
  * pid_batch — many ensembles of uneven N and M in one persistent launch per kernel class,
  * the class launches recorded in order as one CUDA graph and replayed while the batch
- * layout is unchanged. Results are bitwise identical to the single-ensemble calls.
+ * layout is unchanged. Results are bitwise identical to the single-ensemble calls, with one
+ * exception: a BF16 or split-BF16 Gram item (PID_MODE_FULL, up to 256 members) whose soft
+ * masks are also those of a PID-mean or exact-full-PID item of the same batch (the same
+ * data pointer, N, M, ld and cell measures) takes that item's exact PID-mean sums (m_i,
+ * A_i of Eq. 16) instead of forming them in its own pass, so its IN_in is bitwise the
+ * sibling's and its outputs differ from a single call only by the FP32 rounding of those
+ * sums (below 1e-6). E4M3 items always take such sums from a streaming pass (their own
+ * or an identical sibling's), which also yields their member scales.
  * Gram-mode ensembles of 257 to 512 members run the row-block-tiled Gram after their
  * class's streaming launch, one operand-staging and one tile launch each; they share one
  * operand buffer in the workspace, sized for the largest of them.
@@ -345,7 +352,8 @@ pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void*
  * `max_inflight` slots (each with its own stream and workspace) as soon as a slot is free,
  * so requests that arrive while others are on the GPU join the next step and steps overlap
  * on the device (continuous batching). A request's results do not depend on the requests
- * it is batched with (pid_batch results are bitwise identical to single calls).
+ * it is batched with: they are bitwise identical to a single call (the server's batches
+ * never let a Gram request take a step-mate's sums).
  * Admission: ensembles are registered against an HBM budget; submissions beyond
  * max_queue are refused with PID_ERR_BUSY.
  */

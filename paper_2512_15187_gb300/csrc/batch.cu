@@ -32,12 +32,36 @@ struct BatchCache {
   void* host_desc = nullptr;          // pinned descriptor image read by the graph's memcpy
   size_t host_bytes = 0;
   bool use_graphs = true;
+  bool share_sums = true;             // BF16 / split Gram items may take a sibling's (m, A)
   int64_t replays = 0;
   // A graph recorded with profiling on brackets every kernel with two event-record nodes;
   // each replay sets fresh events on them, so every replay's launches are timed.
   struct ProfNodes { cudaGraphNode_t start, stop; int kind; double bytes, flops; };
   std::vector<ProfNodes> prof;
+  // Side streams on which the independent launches of one phase (the streaming classes of a
+  // pass, the Gram classes) run side by side, forked from and joined back to the caller's
+  // stream by events (in a recorded graph: parallel branches).
+  static constexpr int kSide = 4;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork_ev = nullptr;
+  cudaEvent_t join_ev[kSide] = {};
 };
+
+static pid_status ensure_side_streams(pid_handle h, BatchCache* c) {
+  if (c->fork_ev) return PID_OK;
+  for (int k = 0; k < BatchCache::kSide; ++k) {
+    if (cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join_ev[k], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(h, PID_ERR_CUDA, "batch side streams");
+    }
+  }
+  if (cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, PID_ERR_CUDA, "batch side streams");
+  }
+  return PID_OK;
+}
 
 // Fresh events on the graph's timing nodes, queued for the profiler, before a replay.
 static pid_status arm_graph_profiling(pid_handle h, BatchCache* c) {
@@ -86,12 +110,22 @@ void batch_use_graphs(pid_handle h, bool on) {
   h->batch->use_graphs = on;
 }
 
+void batch_share_sums(pid_handle h, bool on) {
+  if (!h->batch) h->batch = new BatchCache();
+  h->batch->share_sums = on;
+}
+
 void destroy_batch_cache(pid_handle h) {
   if (!h->batch) return;
   BatchCache* c = h->batch;
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->graph) cudaGraphDestroy(c->graph);
   if (c->host_desc) cudaFreeHost(c->host_desc);
+  for (int k = 0; k < BatchCache::kSide; ++k) {
+    if (c->side[k]) cudaStreamDestroy(c->side[k]);
+    if (c->join_ev[k]) cudaEventDestroy(c->join_ev[k]);
+  }
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   delete c;
   h->batch = nullptr;
 }
@@ -218,10 +252,15 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   // full-PID item of the same masks: same pointer, shape, stride and cell measures), and its
   // converters then skip that arithmetic. An E4M3 ensemble without such a sibling runs a
   // streaming pass of its own, as a single call does, which also reduces its member scales.
+  // E4M3 items always take a first pass (their own, or an identical sibling's: the same
+  // plan, hence bitwise the same partials); BF16 and split-BF16 items take a sibling's
+  // partials unless the handle keeps every item bitwise equal to its single call (serving).
+  const bool share = !h->batch || h->batch->share_sums;
   std::vector<int> sib(count, -1), own_pass(count, 0);
   if (!st4) {
     for (int e = 0; e < count; ++e) {
       if (!is_gram[e] || tiled[e] || in[e].is_field) continue;
+      if (!share && in[e].precision != PID_FP8) continue;
       for (int f = 0; f < count && sib[e] < 0; ++f) {
         if (f != e && !(is_gram[f] && !tiled[f]) && !in[f].is_field && in[f].data == in[e].data &&
             in[f].N == in[e].N && in[f].M == in[e].M && in[f].ld == in[e].ld && in[f].w == in[e].w)
@@ -504,7 +543,8 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
   const EnsDesc* sdev = reinterpret_cast<const EnsDesc*>(base);
   const size_t sdesc_bytes = align_up(static_cast<int64_t>(bp.sdesc.size()) * sizeof(EnsDesc), 256);
   const FinDesc* fdev = reinterpret_cast<const FinDesc*>(base + sdesc_bytes);
-  for (const Launch& L : bp.launches) {
+  auto launch_one = [&](const Launch& L, cudaStream_t s) -> pid_status {
+    cudaError_t e = cudaSuccess;
     if (L.kind == Launch::STREAM) {
       StreamParams sp;
       std::memset(&sp, 0, sizeof(sp));
@@ -549,6 +589,41 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       e = launch_finalize(fp, L.grid_x, L.count, s);
       if (e != cudaSuccess) return cuda_fail(h, e, "batch finalize launch");
     }
+    return PID_OK;
+  };
+  // Consecutive streaming launches (one pass's classes) are independent: they run on the
+  // side streams, forked from `s` and joined back before the next phase, so that classes
+  // whose grids leave SMs idle (a few small ensembles) fill them. Gram launches fill the
+  // GPU on their own and run in order on `s`.
+  BatchCache* c = h->batch;
+  const size_t n = bp.launches.size();
+  for (size_t i = 0; i < n;) {
+    const Launch::Kind kind = bp.launches[i].kind;
+    size_t j = i + 1;
+    if (kind == Launch::STREAM)
+      while (j < n && bp.launches[j].kind == kind) ++j;
+    if (j - i == 1 || !c || !c->fork_ev) {
+      for (size_t k = i; k < j; ++k) {
+        const pid_status st = launch_one(bp.launches[k], s);
+        if (st != PID_OK) return st;
+      }
+    } else {
+      if ((e = cudaEventRecord(c->fork_ev, s)) != cudaSuccess) return cuda_fail(h, e, "fork");
+      const int used = static_cast<int>(std::min<size_t>(j - i, BatchCache::kSide));
+      for (int k = 0; k < used; ++k)
+        if ((e = cudaStreamWaitEvent(c->side[k], c->fork_ev, 0)) != cudaSuccess)
+          return cuda_fail(h, e, "fork");
+      for (size_t k = i; k < j; ++k) {
+        const pid_status st = launch_one(bp.launches[k], c->side[(k - i) % BatchCache::kSide]);
+        if (st != PID_OK) return st;
+      }
+      for (int k = 0; k < used; ++k) {
+        if ((e = cudaEventRecord(c->join_ev[k], c->side[k])) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(s, c->join_ev[k], 0)) != cudaSuccess)
+          return cuda_fail(h, e, "join");
+      }
+    }
+    i = j;
   }
   return PID_OK;
 }
@@ -610,6 +685,7 @@ pid_status run_batch(pid_handle h, const pid_ensemble* ens, int32_t count, int s
     }
   }
   if ((st = ensure_workspace(h, sizing.work_bytes, s)) != PID_OK) return st;
+  if ((st = ensure_side_streams(h, c)) != PID_OK) return st;
   std::memcpy(key.data() + sizeof(pid_ensemble) * count, &h->ws, sizeof(void*));
   BatchPlan bp;
   char* base = static_cast<char*>(h->ws);

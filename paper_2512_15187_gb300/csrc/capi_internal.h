@@ -232,5 +232,9 @@ pid_status launch_gram_tiled_one(pid_handle h, const EnsInput& in, const TiledPl
 void destroy_batch_cache(pid_handle h);
 // Record batches into CUDA graphs and replay them while the layout repeats (default on).
 void batch_use_graphs(pid_handle h, bool on);
+// Let BF16 / split-BF16 Gram items take the exact (m, A) partials of a first-pass sibling
+// over the same soft masks (default on); off keeps every item bitwise equal to its single
+// call whatever it is batched with.
+void batch_share_sums(pid_handle h, bool on);
 
 }  // namespace pidh

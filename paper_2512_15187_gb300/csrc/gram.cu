@@ -25,7 +25,7 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   gp->wide = in.N > kGramNarrowMaxN;   // two M = 128 row blocks, 64-cell FP32 stages
   // 6 members per warp when they hold the ensemble (48 or 96 rows): the converters then
   // skip the rows a tile of 8 per warp would leave empty
-  gp->mpw = gp->wide ? (in.N <= 192 ? 12 : 16)
+  gp->mpw = gp->wide ? (in.N <= 192 ? 12 : (in.N <= 208 ? 13 : 16))
                      : ((in.N <= 48 || (in.N > 64 && in.N <= 96)) ? 6 : 8);
   gp->TS = gp->wide ? 64 : 128;
   // Chunks (one FP32 partial Gram each) of 32 to 256 operand stages: every chunk costs a

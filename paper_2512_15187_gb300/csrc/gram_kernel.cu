@@ -13,6 +13,9 @@ cudaError_t gram_wide_init(int max_smem);
 cudaError_t launch_gram_wide12(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
                                cudaStream_t s);
 cudaError_t gram_wide12_init(int max_smem);
+cudaError_t launch_gram_wide13(const GramParams& p, int prec, int iso_kind, int grid, size_t smem,
+                               cudaStream_t s);
+cudaError_t gram_wide13_init(int max_smem);
 cudaError_t launch_gram_narrow6(const GramParams& p, int G, int prec, int iso_kind, int grid,
                                 size_t smem, cudaStream_t s);
 cudaError_t gram_narrow6_init(int max_smem);
@@ -22,7 +25,9 @@ size_t gram_smem_bytes(int G, int mpw, bool wide, int prec, int dF, int dO, int 
   const size_t NG = kGramConvWarps / G;
   const size_t T = wide ? GramShape<true>::T : GramShape<false>::T;
   const size_t plane = static_cast<size_t>(mpw) * G * 128;
-  const size_t op_stage = (prec == 2 ? 2 : 1) * (prec == 3 ? 1 : 2) * plane;
+  // K-blocks per operand stage: one for E4M3 (128 cells) and for the wide tile's 16-bit
+  // operands (64 cells, its FP32 stage), two for the narrow tile's 16-bit operands
+  const size_t op_stage = (prec == 2 ? 2 : 1) * ((prec == 3 || wide) ? 1 : 2) * plane;
   const size_t rb = static_cast<size_t>(G) * T + T;
   return 1024 + NG * (dO * op_stage + static_cast<size_t>(dF) * stage_floats * 4 + 2 * rb * 4 +
                       (static_cast<size_t>(dF) + dO + 5) * 8 + 8) + 16 +
@@ -35,6 +40,7 @@ cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec
     if (G != 16) return cudaErrorInvalidValue;
     if (mpw == 16) return launch_gram_wide(p, prec, iso_kind, grid, smem, s);
     if (mpw == 12) return launch_gram_wide12(p, prec, iso_kind, grid, smem, s);
+    if (mpw == 13) return launch_gram_wide13(p, prec, iso_kind, grid, smem, s);
     return cudaErrorInvalidValue;
   }
   if (mpw == 6) return launch_gram_narrow6(p, G, prec, iso_kind, grid, smem, s);
@@ -49,6 +55,7 @@ cudaError_t gram_kernels_init(int max_smem) {
   if (e == cudaSuccess) e = gram_tile_init<16, 8>(max_smem);
   if (e == cudaSuccess) e = gram_narrow6_init(max_smem);
   if (e == cudaSuccess) e = gram_wide12_init(max_smem);
+  if (e == cudaSuccess) e = gram_wide13_init(max_smem);
   if (e == cudaSuccess) e = gram_tiled_init(max_smem);
   return e == cudaSuccess ? gram_wide_init(max_smem) : e;
 }

@@ -60,7 +60,7 @@ struct GramShape {
   static constexpr int VEC = WIDE ? 2 : 4;             // cells per lane per register tile
   static constexpr int T = 32 * VEC;                   // cells per FP32 stage
   static constexpr int MPW = NMPW;                     // members per warp
-  static constexpr int SPO = WIDE ? 2 : 1;             // FP32 stages per operand stage
+  static constexpr int FPS = WIDE ? 2 : 1;             // FP32 stages per 128 cells
   static constexpr int MB = WIDE ? 2 : 1;              // M = 128 row blocks
   static constexpr int NBUF = WIDE ? 1 : 2;            // accumulator buffers
   static constexpr uint32_t TMEM_COLS = WIDE ? 512 : 256;
@@ -109,7 +109,11 @@ template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = (WIDE ? 16 :
 __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams p) {
   static_assert(EXACT || ISO == ISOK_NONE, "fields map in the Gram pass, with the exact sums");
   using S = GramShape<WIDE, NMPW>;
-  constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, SPO = S::SPO, MB = S::MB, NBUF = S::NBUF;
+  constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, FPS = S::FPS, MB = S::MB, NBUF = S::NBUF;
+  // FP32 stages per operand stage: an E4M3 K-block is 128 cells (two wide FP32 stages); a
+  // 16-bit K-block is 64 cells, so the wide tile's operand stage is one K-block (64 cells)
+  // and the narrow tile's two (its 128-cell FP32 stage)
+  constexpr int SPO = (WIDE && PREC == 3) ? 2 : 1;
   static_assert(!WIDE || G == 16, "the wide tile uses all 16 warps as one group");
   static_assert(SPO == 1 || SPO == 2, "FP32 stages per operand stage");
   static_assert(MPW <= kGramMaxMpw, "member scale slots per warp");
@@ -117,7 +121,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   constexpr int ROWS = MPW * G;                      // operand rows a group writes (>= N)
   constexpr uint32_t PLANE = ROWS * 128;             // one K-block: [ROWS][128 bytes]
   constexpr int PLANES = PREC == 2 ? 2 : 1;          // hi (+ lo)
-  constexpr int KBLK = PREC == 3 ? 1 : 2;            // K-blocks per 128-cell operand stage
+  constexpr int KBLK = (PREC == 3 || WIDE) ? 1 : 2;  // K-blocks per operand stage
   constexpr uint32_t OP_STAGE = PLANES * KBLK * PLANE;
   constexpr uint32_t FMT = PREC == 3 ? 0u : 1u;      // E4M3 : BF16
   constexpr int RB = G * T + T;                      // exchange buffer floats
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       L.has_w = pd->w != nullptr;
     }
     L.icell0 = (u - L.e_begin) * L.chunk;
-    L.in_st = SPO * ((min(L.chunk, L.M - L.icell0) + 127) / 128);
+    L.in_st = FPS * ((min(L.chunk, L.M - L.icell0) + 127) / 128);
   };
   auto issue_next = [&]() {
     if (L.iu >= L.u_end) return;
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     const EnsDesc& d = *dp;
     const int c = u - e_begin;
     const int cell0 = c * e_chunk;
-    const int n_st = SPO * ((min(e_chunk, M - cell0) + 127) / 128);   // FP32 stages
+    const int n_st = FPS * ((min(e_chunk, M - cell0) + 127) / 128);   // FP32 stages
     float accM[EXACT ? MPW : 1], accA[EXACT ? MPW : 1];
 #pragma unroll
     for (int m = 0; m < (EXACT ? MPW : 1); ++m) { accM[m] = 0.f; accA[m] = 0.f; }

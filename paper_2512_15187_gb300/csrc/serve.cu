@@ -301,6 +301,7 @@ pid_status pid_serve_start(pid_server* out, const pid_serve_cfg* cfg) {
     pid_status st = pid_create(&sl.h, cfg->device, 0);
     if (st != PID_OK) return st;
     batch_use_graphs(sl.h, false);  // a new batch layout every step: launch directly
+    batch_share_sums(sl.h, false);  // a request's results do not depend on its step-mates
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();

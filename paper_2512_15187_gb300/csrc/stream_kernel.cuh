@@ -252,8 +252,11 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   uint64_t* my_bars = bars + grp * depth;
   const bool leader = (q == 0) && (lane == 0);
 
-  if (TMA && leader) {
-    for (int s = 0; s < depth; ++s) mbar_init(&my_bars[s], 1);
+  // The ring's stages are filled by the leader's TMA copies (rows 16-byte aligned), or else
+  // by every thread's 4-byte cp.async copies (see cpa_issue), each thread arriving once per
+  // stage when its copies have landed.
+  if (leader) {
+    for (int s = 0; s < depth; ++s) mbar_init(&my_bars[s], TMA ? 1u : static_cast<uint32_t>(G * 32));
     fence_mbar_init();
   }
   // A warp that gives up on a wait sets the flag of the register tile whose group barrier
@@ -380,14 +383,50 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 #pragma unroll
     for (int k = 0; k < (MAXU ? MPW : 1); ++k) accX[k] = 0.f;
 
+    // Rows that are not 16-byte aligned: warp q copies the cells of its members' rows (warp
+    // 0 also the cell measures) with 4-byte cp.async into the ring, `depth` stages of this
+    // chunk ahead, each instruction 32 consecutive cells of one row (128 coalesced bytes);
+    // cells past M are zero-filled without a read. Every thread arrives on the stage's
+    // barrier once its copies have landed, so the stage is whole when the barrier completes.
+    auto cpa_issue = [&](int st_i, int slot_i) {
+      float* dst = my_ring + static_cast<size_t>(slot_i) * SF + lane;
+      const int xs = cell0 + st_i * TS + lane;
+#pragma unroll
+      for (int k = 0; k < MPW; ++k) {
+        const int i = q + k * G;
+        if (i < N) {
+          const float* src = d.data + static_cast<int64_t>(i) * d.ld;
+#pragma unroll
+          for (int v = 0; v < VEC; ++v) {
+            const bool in = xs + 32 * v < M;
+            cp_async4(dst + static_cast<size_t>(i) * TS + 32 * v, src + (in ? xs + 32 * v : 0),
+                      in ? 4u : 0u);
+          }
+        }
+      }
+      if (q == 0 && has_w) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const bool in = xs + 32 * v < M;
+          cp_async4(dst + SF - TS + 32 * v, d.w + (in ? xs + 32 * v : 0), in ? 4u : 0u);
+        }
+      }
+      cp_async_arrive(&my_bars[slot_i]);
+    };
+    if constexpr (!TMA) {
+      int sl = c_slot;
+      for (int st_i = 0; st_i < depth && st_i < n_st; ++st_i) {
+        cpa_issue(st_i, sl);
+        if (++sl == depth) sl = 0;
+      }
+    }
+
     for (int st = 0; st < n_st && !aborted; ++st, ++k_cons) {
       const int slot = c_slot;          // k_cons % depth
       const uint32_t par = c_par;       // (k_cons / depth) & 1
       if (++c_slot == depth) { c_slot = 0; c_par ^= 1u; }
       const float* sb = my_ring + static_cast<size_t>(slot) * SF;
-      if constexpr (TMA) {
-        if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[2 * grp + (k_sub & 1)] = 1;
-      }
+      if (!mbar_wait_bounded(&my_bars[slot], par, kWaitTimeoutNs)) flags[2 * grp + (k_sub & 1)] = 1;
       for (int j = 0; j < SUB; ++j, ++k_sub) {
         const int x0 = cell0 + st * TS + j * T;     // first cell of this register tile
         const int xl = x0 + lane * VEC;             // first cell of this lane
@@ -395,34 +434,18 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         float x[MPW][VEC];
         float wv[VEC];
 
-        if constexpr (TMA) {
+        // the stage in shared memory, filled by TMA or by the threads' cp.async copies
 #pragma unroll
-          for (int k = 0; k < MPW; ++k) {
-            const int i = q + k * G;
-            if (i < N) {
-              lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
-            } else {
+        for (int k = 0; k < MPW; ++k) {
+          const int i = q + k * G;
+          if (i < N) {
+            lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
+          } else {
 #pragma unroll
-              for (int v = 0; v < VEC; ++v) x[k][v] = pad;
-            }
-          }
-          if (has_w) lds_vec<VEC>(wv, sb + SF - TS + j * T + lane * VEC);
-        } else {
-#pragma unroll
-          for (int k = 0; k < MPW; ++k) {
-            const int i = q + k * G;
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) {
-              const int xc = xl + v;
-              x[k][v] = (i < N && xc < M) ? __ldg(d.data + static_cast<int64_t>(i) * d.ld + xc)
-                                          : (i < N ? 0.f : pad);
-            }
-          }
-          if (has_w) {
-#pragma unroll
-            for (int v = 0; v < VEC; ++v) wv[v] = (xl + v < M) ? __ldg(d.w + xl + v) : 0.f;
+            for (int v = 0; v < VEC; ++v) x[k][v] = pad;
           }
         }
+        if (has_w) lds_vec<VEC>(wv, sb + SF - TS + j * T + lane * VEC);
 
         if (validate) {
 #pragma unroll
@@ -559,6 +582,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         if (flags[2 * grp + (k_sub & 1)]) { aborted = true; break; }
         if constexpr (TMA) {
           if (leader && j == SUB - 1) issue_next();  // every warp has read this slot: refill it
+        } else {
+          if (j == SUB - 1 && st + depth < n_st) cpa_issue(st + depth, slot);
         }
         if constexpr (G > 2) {
           if (p.xchg == 1) {
@@ -633,6 +658,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   if (bad) atomicOr(p.err, bad);
   if (aborted && lane == 0 && q == 0) atomicOr(p.err, ERR_TIMEOUT);
   // On an early exit, let this group's copies in flight land before the CTA retires.
+  if constexpr (!TMA) cp_async_wait_all();   // this thread's copies, before the CTA retires
   if (TMA && leader) {
     while (k_cons < P.n_issued) {
       const int slot = static_cast<int>(k_cons % depth);
