@@ -71,6 +71,8 @@ def parse_args():
                     help="seconds of Poisson arrivals per serving scenario (0 = skip serving)")
     ap.add_argument("--no-workloads", action="store_true",
                     help="skip the other benchmark workloads (ellipses, non-Cartesian, tiled, scalability)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="stop after the timed headline steps (for a profiler's launch list)")
     ap.add_argument("--source-hash", action="store_true",
                     help="print the kernel-source stamp that ncu summaries carry, and exit")
     return ap.parse_args()
@@ -318,15 +320,57 @@ def roofline_record(kind, st, peaks, sustained, traffic):
 # per request)
 # ---------------------------------------------------------------------------------------
 
-SERVE_GRIDS = [(256, 256), (512, 512), (1024, 1024), (64 * 8, 64 * 8 * 8 // 8),
-               (128 * 16, 128 * 128 // 16), (192 * 24, 192 * 192 // 24)]   # 2D grids, 3D grids flattened
+def serve_pool(dev, budget_bytes, seed=5):
+    """Resident ensembles of the serving mix, drawn from the workloads' generators until
+    their footprint reaches the HBM budget: 2D ellipse soft masks, 2D RBF fields (isovalue
+    Normal(0.5, 0.05)), non-Cartesian weighted radial masks, and 3D plume soft masks and
+    ellipsoid masks; N ~ U{16..256}, 2D grids 256^2 / 512^2 / 1024^2, 3D grids 64^3 / 128^3
+    / 192^3. Returns [(tensor, weights or None, is_field, generator name)]."""
+    import numpy as np
+    import torch
+
+    from paper_2512_15187_gb300 import synth
+    rng = np.random.default_rng(seed)
+    pool, total, k = [], 0, 0
+    while True:
+        N = int(rng.integers(16, 257))
+        kind = ["ellipses_2d", "rbf_fields_2d", "radial_disk", "plume_3d", "ellipsoids_3d"][k % 5]
+        w = None
+        field = False
+        if kind in ("ellipses_2d", "rbf_fields_2d", "radial_disk"):
+            side = [256, 512, 1024][int(rng.integers(0, 3))]
+            M = side * side
+        else:
+            side = [64, 128, 192][int(rng.integers(0, 3))]
+            M = side ** 3
+        size = 4 * N * M + (4 * M if kind == "radial_disk" else 0)
+        if total + size > budget_bytes:
+            break
+        sd = synth.DEFAULT_SEED + 77 + k
+        if kind == "ellipses_2d":
+            t = synth.ellipses_2d_torch(N, side, side, seed=sd, device=dev)
+        elif kind == "rbf_fields_2d":
+            t = synth.rbf_fields_2d_torch(N, side, side, 32, seed=sd, device=dev)
+            field = True
+        elif kind == "radial_disk":
+            t, w = synth.radial_disk_torch(N, M, seed=sd, device=dev)
+        elif kind == "plume_3d":
+            t = synth.plume_3d(N, side, t=int(rng.integers(0, 16)), seed=sd, device=dev)
+        else:
+            t = synth.ellipsoids_3d(N, side, seed=sd, device=dev)
+        pool.append((t, w, field, kind))
+        total += size
+        k += 1
+    return pool
 
 
-def run_serving(device, seconds, rate_hz, budget_bytes=150 << 30, n_ens=24, seed=5):
-    """Resident ensembles drawn from the 2D / non-Cartesian / 3D shape mix: N ~ U{16..256},
-    grids 256^2..1024^2 or 64^3..192^3 (flattened), fields (isovalue Normal(0.5, 0.05)) or
-    soft masks. Requests arrive as a Poisson process and ask for PID-mean, exact full PID
-    or the BF16 tensor-core full PID. Returns per-scenario latency and throughput."""
+def run_serving(device, seconds, rate_hz, budget_bytes=150 * 10 ** 9, seed=5):
+    """The serving loop of the fifth workload: resident ensembles of the mix (serve_pool)
+    registered under a 150 GB HBM budget; requests arrive as a Poisson process and ask for
+    PID-mean, exact full PID or the BF16 tensor-core full PID. Continuous batching (2 slots,
+    up to 32 requests per step) against one launch per request, at the configured rate and
+    at 15 times it. Returns per-scenario latency and throughput, the mix and the admission
+    record (what the budget refused)."""
     import math
     import threading
     import time
@@ -336,24 +380,34 @@ def run_serving(device, seconds, rate_hz, budget_bytes=150 << 30, n_ens=24, seed
 
     from paper_2512_15187_gb300 import binding, synth
 
-    rng = np.random.default_rng(seed)
     dev = torch.device("cuda", device)
-    pool = []
-    for k in range(n_ens):
-        N = int(rng.integers(16, 257))
-        H, W = SERVE_GRIDS[int(rng.integers(0, len(SERVE_GRIDS)))]
-        t = synth.rbf_fields_2d_torch(N, H, W, 32, seed=synth.DEFAULT_SEED + 77 + k, device=dev)
-        field = bool(k % 2)
-        if not field:
-            t = torch.sigmoid((t - 0.5) / 0.05)
-        pool.append((t, field))
+    # generate to 140 GB, then let admission decide at 150 GB with 4 GB of slot workspace
+    pool = serve_pool(dev, 140 * 10 ** 9, seed)
+    mix = {}
+    for t, w, f, kind in pool:
+        m = mix.setdefault(kind, {"ensembles": 0, "gb": 0.0})
+        m["ensembles"] += 1
+        m["gb"] += (4.0 * t.numel() + (4.0 * w.numel() if w is not None else 0.0)) / 1e9
+    # admission under load: one more 192^3 ensemble of 256 members beyond the budget
+    extra = synth.ellipsoids_3d(256, 192, seed=synth.DEFAULT_SEED + 999, device=dev)
+    admission = {}
     out = {}
     for name, inflight, batch in (("continuous_batching", 2, 32), ("one_launch_per_request", 1, 1)):
         for load_name, hz in (("poisson_%d_per_s" % int(rate_hz), rate_hz),
                               ("poisson_%d_per_s" % int(rate_hz * 15), rate_hz * 15)):
             srv = binding.Server(device=device, max_inflight=inflight, max_batch=batch,
-                                 max_queue=1 << 16, hbm_budget_bytes=budget_bytes)
-            ids = [(srv.register(t, iso=(0.5, 0.05, 0) if f else None), t.shape[0]) for t, f in pool]
+                                 max_queue=1 << 16, hbm_budget_bytes=budget_bytes,
+                                 workspace_reserve_bytes=2 << 30)
+            ids = [(srv.register(t, w=w, iso=(0.5, 0.05, 0) if f else None), t.shape[0])
+                   for t, w, f, _ in pool]
+            if not admission:
+                try:
+                    srv.register(extra)
+                    admission["extra_7.5gb_ensemble"] = "admitted"
+                except binding.PidError as ex:
+                    admission["extra_7.5gb_ensemble"] = f"refused (status {ex.status})"
+                admission["resident_gb"] = srv.stats()["resident_bytes"] / 1e9
+                admission["budget_gb"] = budget_bytes / 1e9
             # warm-up: every ensemble once in every mode
             for i, n in ids:
                 for mode, prec in (("mean", "fp32"), ("linear", "fp32")):
@@ -391,6 +445,10 @@ def run_serving(device, seconds, rate_hz, budget_bytes=150 << 30, n_ens=24, seed
                 "member_cells_per_s": st["member_cells_per_s"], "mean_batch": st["mean_batch"],
                 "resident_gb": st["resident_bytes"] / 1e9}
             srv.stop()
+    out["mix"] = mix
+    out["admission"] = admission
+    del pool, extra
+    torch.cuda.empty_cache()
     return out
 
 
@@ -807,10 +865,14 @@ def main():
     member_cells = sum(it["data"].shape[0] * it["data"].shape[1] for it in items)
     resident_gb = (sum(4.0 * U.numel() for U in steps) + sum(4.0 * X.numel() for X in extras)) / 1e9
 
-    h.autotune(True)                                 # the first call times the candidates
+    # tile shapes per ensemble shape (streaming class, Gram chunk), then the launch
+    # parameters that leave results unchanged (exchange scheme, ring depth) on the first call
+    h.autotune_shapes(items, stream=stream)
+    h.autotune(True)
     outs = h.batch(items, stream=stream)
     h.sync()
     h.autotune(False)
+    tuned = h.autotune_describe()
     # The timed steps replay the batch's CUDA graph with the library's timing nodes armed
     # (two event records around every kernel), so each kernel's device time is measured in
     # the timed region itself; profiling is switched on before the warm-up, so that the
@@ -860,6 +922,17 @@ def main():
     prefix = {"gram_split": "gram_kernel_split_bf16_plume", "gram_fp8": "gram_kernel_e4m3_plume",
               "stream": "stream_kernel_plume"}.get(dom, dom)
     roof = roofline_record(dom, prof[dom], peaks, True, ncu_traffic(prefix))
+
+    if args.headline_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "ms_per_step": ms / args.steps,
+                              "gpu_launches": gpu_launches, "roofline": roof, "kernels": kt,
+                              "config": {"workload": WORKLOAD, "time_steps": n_steps}}), flush=True)
+        h.close()
+        if dist:
+            dist.destroy_process_group()
+        return
 
     # ---- the same batch as one call per item ----
     loop_ms = None
@@ -936,6 +1009,11 @@ def main():
                             "copies overlap the previous step's compute"},
             "gpu_launches": gpu_launches,
             "clocks": clocks,
+            "autotune": {"entries": tuned.strip().splitlines(),
+                         "note": "shape entries: 'stream' = streaming tile class index (default: "
+                                 "the first whose member rows hold N), 'gram' = chunk choice "
+                                 "(0 as planned, 1 doubled, -1 halved); the others: exchange "
+                                 "scheme and ring depth"},
         }
         if loop_ms is not None:
             line["one_call_per_item"] = {"ms_per_step": loop_ms,

@@ -178,6 +178,7 @@ pid_status pid_profile_read(pid_handle h, int kind, pid_kernel_stats* out);
  */
 pid_status pid_autotune_enable(pid_handle h, int enable, int32_t* n_entries);
 
+
 /*
  * pid_soft_masks — the isovalue map alone (Sec. 3.5): U_out[i*ld_out + x] = u_i(x) for
  * x < M. F: [N][ld] float32 scalar fields; U_out: [N][ld_out] float32, ld_out >= M.
@@ -344,6 +345,27 @@ typedef struct pid_ensemble {
  * operand buffer in the workspace, sized for the largest of them.
  */
 pid_status pid_batch(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
+
+/*
+ * Tile shapes. pid_autotune_shapes times, on the ensembles given (their data, shapes and
+ * options, as for pid_batch), the tile choices that depend on the problem's shape, and keeps
+ * the fastest per shape key (member count, cell-count octave, isovalue kind, cell measures;
+ * for the Gram also the operand precision):
+ *   - the streaming tile class: the default class (the first whose member rows hold N) and
+ *     the next two larger ones (more member slots per warp, other cell widths);
+ *   - the fused tensor-core Gram's cell chunk (one partial Gram per chunk): as planned,
+ *     halved or doubled.
+ * Each candidate runs once untimed and three times timed (CUDA events on `stream`; the call
+ * synchronises it; not while the stream is being captured). Keys already tuned are kept.
+ * Later single calls and batches on this handle plan with the chosen shapes, so a batch
+ * stays bitwise equal to its single calls; a chosen shape changes the order of the FP32
+ * sums (results move by FP32 rounding, within the stated bars). With PID_AUTOTUNE_CACHE set
+ * the choices are appended to that file and loaded by later handles.
+ */
+pid_status pid_autotune_shapes(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream);
+/* Text of the handle's tuned entries (one per line) into buf (cap bytes, NUL-terminated);
+ * returns the full length, or -1 for a NULL handle. */
+int32_t pid_autotune_describe(pid_handle h, char* buf, int32_t cap);
 
 /*
  * Serving. A server keeps ensembles resident on one GPU and answers depth requests that

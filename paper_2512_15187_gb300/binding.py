@@ -35,6 +35,7 @@ EXPORTS = [
     "pid_serve_stats_get", "pid_serve_stats_reset", "pid_contour_bands", "pid_mean_weighted",
     "pid_spacetime", "pid_depth_from_matrix", "pid_soft_masks_bf16",
     "pid_selftest_wait_timeout", "pid_gram_operands", "pid_serve_cancel",
+    "pid_autotune_shapes", "pid_autotune_describe",
 ]
 PID_KERNEL_STREAM, PID_KERNEL_GRAM, PID_KERNEL_FINALIZE, PID_KERNEL_ISO, PID_KERNEL_BANDS = 0, 1, 2, 3, 4
 PID_KERNEL_GRAM_SPLIT, PID_KERNEL_GRAM_FP8, PID_KERNEL_OPERANDS, PID_KERNEL_SCALE = 5, 6, 7, 8
@@ -137,6 +138,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "pid_profile_enable": ([P, c_int], c_int),
         "pid_profile_read": ([P, c_int, POINTER(pid_kernel_stats)], c_int),
         "pid_autotune_enable": ([P, c_int, POINTER(c_int32)], c_int),
+        "pid_autotune_shapes": ([P, POINTER(pid_ensemble), c_int32, P], c_int),
+        "pid_autotune_describe": ([P, ctypes.c_char_p, c_int32], c_int32),
         "pid_mean_noalloc": ([P, c_int64, c_int64, c_int64, P, P, P, P, P, P, P], c_int),
         "pid_serve_start": ([POINTER(c_void_p), POINTER(pid_serve_cfg)], c_int),
         "pid_serve_stop": ([P], c_int),
@@ -486,11 +489,20 @@ class Handle:
                         _stream(stream))
         return o
 
-    def batch(self, items, stream=None, outs=None):
-        """items: list of dicts with keys data (tensor), w, iso=(mu, sigma, superlevel) or None,
-        mode, precision, want_P. Returns a list of output dicts (with mass and mean_depth).
-        `outs`: the list a previous call returned for the same items, written again in place
-        (the same records then replay the batch's recorded graph)."""
+    def autotune_shapes(self, items, stream=None):
+        """Time the shape-dependent tile choices (streaming tile class, Gram cell chunk) on
+        the ensembles of `items` (as for batch) and keep the fastest per shape."""
+        ens, _ = self._records(items, None)
+        arr = (pid_ensemble * len(ens))(*ens)
+        _check(self.h, load().pid_autotune_shapes(self.h, arr, len(ens), _stream(stream)))
+
+    def autotune_describe(self) -> str:
+        n = load().pid_autotune_describe(self.h, None, 0)
+        buf = ctypes.create_string_buffer(max(1, n + 1))
+        load().pid_autotune_describe(self.h, buf, n + 1)
+        return buf.value.decode()
+
+    def _records(self, items, outs):
         reuse = outs is not None
         if reuse and len(outs) != len(items):
             raise ValueError("outs must come from a call with the same items")
@@ -515,6 +527,14 @@ class Handle:
                 setattr(e, k, _ptr(o.get(k)))
             ens.append(e)
             new_outs.append(o)
+        return ens, new_outs
+
+    def batch(self, items, stream=None, outs=None):
+        """items: list of dicts with keys data (tensor), w, iso=(mu, sigma, superlevel) or None,
+        mode, precision, want_P. Returns a list of output dicts (with mass and mean_depth).
+        `outs`: the list a previous call returned for the same items, written again in place
+        (the same records then replay the batch's recorded graph)."""
+        ens, new_outs = self._records(items, outs)
         pid_batch(self.h, ens, _stream(stream))
         return new_outs
 

@@ -193,23 +193,55 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
 // Each warp holds MPW = ceil(N / G) members x VEC cells in registers (MPW x VEC <= 32);
 // a TMA stage moves sub x T cells of every member (sub = 1 keeps three stages in flight
 // for N up to 512).
-StreamCfg stream_cfg(int64_t N) {
-  // Every member slot of a class costs arithmetic whether or not a member fills it, so the
-  // classes above 16 members come in steps that keep the empty slots to about a fifth.
-  if (N <= 8) return {4, 1, 128, 1, 8};
-  if (N <= 16) return {4, 2, 128, 1, 8};
-  if (N <= 24) return {4, 4, 128, 1, 6};
-  if (N <= 32) return {4, 4, 128, 1, 8};
-  if (N <= 48) return {4, 8, 128, 1, 6};
-  if (N <= 64) return {4, 8, 128, 1, 8};
-  if (N <= 96) return {4, 16, 128, 1, 6};
-  if (N <= 128) return {4, 16, 128, 1, 8};
-  if (N <= 192) return {2, 16, 64, 1, 12};
-  if (N <= 256) return {2, 16, 64, 1, 16};
-  if (N <= 320) return {1, 16, 32, 1, 20};
-  if (N <= 384) return {1, 16, 32, 1, 24};
-  if (N <= 448) return {1, 16, 32, 1, 28};
-  return {1, 16, 32, 1, 32};
+// The streaming tile classes {VEC, G, T, sub, members per warp}, in order of the member rows
+// they hold (G x members per warp). Every member slot of a class costs arithmetic whether
+// or not a member fills it, so the classes above 16 members come in steps that keep the
+// empty slots to about a fifth; an ensemble's default class is the first that holds it.
+static const StreamCfg kStreamClasses[] = {
+    {4, 1, 128, 1, 8},  {4, 2, 128, 1, 8},   {4, 4, 128, 1, 6},  {4, 4, 128, 1, 8},
+    {4, 8, 128, 1, 6},  {4, 8, 128, 1, 8},   {4, 16, 128, 1, 6}, {4, 16, 128, 1, 8},
+    {2, 16, 64, 1, 12}, {2, 16, 64, 1, 16},  {1, 16, 32, 1, 20}, {1, 16, 32, 1, 24},
+    {1, 16, 32, 1, 28}, {1, 16, 32, 1, 32}};
+constexpr int kNumStreamClasses = sizeof(kStreamClasses) / sizeof(kStreamClasses[0]);
+
+static int default_stream_class(int64_t N) {
+  for (int c = 0; c < kNumStreamClasses; ++c)
+    if (static_cast<int64_t>(kStreamClasses[c].G) * kStreamClasses[c].mpw >= N) return c;
+  return kNumStreamClasses - 1;
+}
+
+StreamCfg stream_cfg(int64_t N) { return kStreamClasses[default_stream_class(N)]; }
+
+static int log2_floor(int64_t v) {
+  int lg = 0;
+  while ((int64_t(1) << (lg + 1)) <= v) ++lg;
+  return lg;
+}
+
+// Shape keys of the tile choices: member count, cell-count octave, isovalue kind, weights.
+static std::string stream_shape_key(const EnsInput& in) {
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "stream n%lld m%d iso%d w%d", static_cast<long long>(in.N),
+                log2_floor(in.M), in.is_field ? (in.iso.sigma > 0 ? 1 : 2) : 0, in.w != nullptr);
+  return buf;
+}
+
+std::string gram_shape_key(const EnsInput& in) {
+  char buf[96];
+  std::snprintf(buf, sizeof(buf), "gram n%lld m%d p%d iso%d w%d", static_cast<long long>(in.N),
+                log2_floor(in.M), in.precision, in.is_field ? (in.iso.sigma > 0 ? 1 : 2) : 0,
+                in.w != nullptr);
+  return buf;
+}
+
+StreamCfg stream_cfg_for(pid_handle h, const EnsInput& in) {
+  const int def = default_stream_class(in.N);
+  if (h && !h->shapes.empty()) {
+    auto it = h->shapes.find(stream_shape_key(in));
+    if (it != h->shapes.end() && it->second >= def && it->second < kNumStreamClasses)
+      return kStreamClasses[it->second];
+  }
+  return kStreamClasses[def];
 }
 
 static int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
@@ -302,7 +334,7 @@ pid_status check_opt(pid_handle h, const pid_options* o) {
 // Plan one ensemble for the streaming kernel. Pointers into the workspace are filled later.
 pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
   std::memset(pl, 0, sizeof(*pl));
-  const StreamCfg cfg = stream_cfg(in.N);
+  const StreamCfg cfg = stream_cfg_for(h, in);
   pl->cfg = cfg;
   EnsDesc& d = pl->desc;
   d.data = in.data;
@@ -361,8 +393,7 @@ void stream_launch_geometry(const StreamCfg& cfg, int32_t stage_floats, int* dep
 
 static std::string stream_tune_key(const StreamCfg& cfg, bool coef, const pidk::StreamParams& sp,
                                    int32_t max_n, int64_t cells) {
-  int lg = 0;
-  while ((int64_t(1) << (lg + 1)) <= cells) ++lg;
+  const int lg = log2_floor(cells);
   const pidk::EnsDesc& d = sp.one;   // iso and weight flags: those of the class's first ensemble
   char buf[160];
   std::snprintf(buf, sizeof(buf), "stream v%d k%d g%d s%d c%d iso%d w%d tma%d n%d m%d", cfg.vec,
@@ -384,6 +415,10 @@ void load_tune_cache(pid_handle h) {
     const size_t bar = l.find('|');
     if (bar == std::string::npos) continue;
     int x = 0, d = 0;
+    if (l.compare(0, 6, "shape ") == 0) {   // "shape <key>|<choice>"
+      if (std::sscanf(l.c_str() + bar + 1, "%d", &x) == 1) h->shapes[l.substr(6, bar - 6)] = x;
+      continue;
+    }
     if (std::sscanf(l.c_str() + bar + 1, "%d %d", &x, &d) == 2) h->tuned[l.substr(0, bar)] = {x, d};
   }
   std::fclose(fp);
@@ -688,6 +723,38 @@ using namespace pidh;
 // Exported C ABI
 // =======================================================================================
 
+namespace {
+
+// Time `reps` runs of `fn` on `s` with CUDA events, after one untimed run.
+template <typename Fn>
+static float time_runs(cudaStream_t s, int reps, Fn&& fn, pid_status* st) {
+  *st = fn();
+  if (*st != PID_OK) return 0.f;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  for (int r = 0; r < reps && *st == PID_OK; ++r) *st = fn();
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ms;
+}
+
+static void record_shape(pid_handle h, const std::string& key, int choice) {
+  h->shapes[key] = choice;
+  if (h->tune_file.empty()) return;
+  if (FILE* fp = std::fopen(h->tune_file.c_str(), "a")) {
+    std::fprintf(fp, "shape %s|%d\n", key.c_str(), choice);
+    std::fclose(fp);
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 pid_status pid_gram_operands(int32_t precision, int64_t cells, int32_t want_matrix,
@@ -810,6 +877,93 @@ pid_status pid_autotune_enable(pid_handle h, int enable, int32_t* n_entries) {
   h->autotune = enable != 0;
   if (n_entries) *n_entries = static_cast<int32_t>(h->tuned.size());
   return PID_OK;
+}
+
+pid_status pid_autotune_shapes(pid_handle h, const pid_ensemble* ens, int32_t count, void* stream) {
+  if (!h) return PID_ERR_INVALID_ARG;
+  if (count < 0 || (count > 0 && !ens)) return fail(h, PID_ERR_INVALID_ARG, "bad ensemble array");
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs != cudaStreamCaptureStatusNone)
+    return fail(h, PID_ERR_INVALID_ARG, "tile shapes are tuned outside stream capture");
+  for (int32_t k = 0; k < count; ++k) {
+    const pid_ensemble& e = ens[k];
+    pid_status st = check_shape(h, e.data, e.N, e.M, e.ld);
+    if (st != PID_OK) return st;
+    if (e.is_field && (st = check_iso(h, &e.iso)) != PID_OK) return st;
+    if ((st = check_opt(h, &e.opt)) != PID_OK) return st;
+    EnsInput in;
+    in.data = e.data; in.N = e.N; in.M = e.M; in.ld = e.ld; in.w = e.w;
+    in.is_field = e.is_field;
+    if (e.is_field) in.iso = e.iso;
+    in.mode = e.opt.mode;
+    in.precision = e.opt.mode == PID_MODE_FULL ? gram_operand_precision(e.opt.precision, e.M, e.P != nullptr)
+                                               : PID_FP32;
+    // Streaming tile: the default class and the next two larger ones (more member slots per
+    // warp, other cell widths), each timed over 3 runs of the PID-mean pass on this data.
+    const std::string skey = stream_shape_key(in);
+    if (!h->shapes.count(skey)) {
+      const int def = default_stream_class(in.N);
+      float best = 1e30f;
+      int pick = def;
+      for (int c = def; c < std::min(def + 3, kNumStreamClasses); ++c) {
+        h->shapes[skey] = c;
+        EnsPlan pl;
+        if ((st = plan_stream(h, in, &pl)) != PID_OK) break;
+        if ((st = ensure_workspace(h, pl.part_bytes, s)) != PID_OK) break;
+        pl.desc.part = static_cast<double*>(h->ws);
+        const float ms = time_runs(s, 3, [&] { return launch_stream_one(h, pl, nullptr, s); }, &st);
+        if (st != PID_OK) break;
+        if (ms < best) { best = ms; pick = c; }
+      }
+      if (st != PID_OK) { h->shapes.erase(skey); return st; }
+      record_shape(h, skey, pick);
+    }
+    // Tensor-core Gram (fused tile, up to 256 members): the chunk of cells per partial Gram,
+    // as planned, halved or doubled.
+    if (in.mode == PID_MODE_FULL && in.precision != PID_FP32 && in.N <= kGramMaxN) {
+      const std::string gkey = gram_shape_key(in);
+      if (!h->shapes.count(gkey)) {
+        float best = 1e30f;
+        int pick = 0;
+        for (int c : {0, 1, -1}) {
+          h->shapes[gkey] = c;
+          GramPlan gp;
+          if ((st = plan_gram(h, in, &gp)) != PID_OK) break;
+          const size_t need = gp.part_bytes + kScaleBytes + gp.gpart_bytes;
+          if ((st = ensure_workspace(h, need, s)) != PID_OK) break;
+          char* ws = static_cast<char*>(h->ws);
+          double* part = reinterpret_cast<double*>(ws);
+          float* scale = reinterpret_cast<float*>(ws + gp.part_bytes);
+          float* gpart = reinterpret_cast<float*>(ws + gp.part_bytes + kScaleBytes);
+          const float ms =
+              time_runs(s, 3, [&] { return launch_gram_one(h, in, gp, part, gpart, scale, s); }, &st);
+          if (st != PID_OK) break;
+          if (ms < best) { best = ms; pick = c; }
+        }
+        if (st != PID_OK) { h->shapes.erase(gkey); return st; }
+        record_shape(h, gkey, pick);
+      }
+    }
+  }
+  return pid_sync(h, stream);
+}
+
+int32_t pid_autotune_describe(pid_handle h, char* buf, int32_t cap) {
+  if (!h) return -1;
+  std::string out;
+  for (const auto& kv : h->shapes) out += "shape " + kv.first + " -> " + std::to_string(kv.second) + "\n";
+  for (const auto& kv : h->tuned)
+    out += kv.first + " -> xchg " + std::to_string(kv.second.first) + " depth " +
+           std::to_string(kv.second.second) + "\n";
+  if (buf && cap > 0) {
+    const size_t n = std::min<size_t>(out.size(), static_cast<size_t>(cap) - 1);
+    std::memcpy(buf, out.data(), n);
+    buf[n] = 0;
+  }
+  return static_cast<int32_t>(out.size());
 }
 
 pid_status pid_profile_read(pid_handle h, int kind, pid_kernel_stats* out) {

@@ -70,6 +70,7 @@ struct pid_handle_s {
   std::vector<pidh::ProfRecord> prof_captured;   // their events, turned into graph nodes
   bool autotune = false;
   std::map<std::string, std::pair<int, int>> tuned;  // key -> (exchange scheme, ring depth)
+  std::map<std::string, int> shapes;   // shape key -> tile choice (pid_autotune_shapes)
   std::string tune_file;
 };
 
@@ -165,6 +166,9 @@ class DeviceGuard {
 pid_status fail(pid_handle h, pid_status s, const std::string& msg);
 pid_status cuda_fail(pid_handle h, cudaError_t e, const char* where);
 StreamCfg stream_cfg(int64_t N);
+// The streaming tile class of an ensemble: the tuned choice of its shape, else the default.
+StreamCfg stream_cfg_for(pid_handle h, const EnsInput& in);
+std::string gram_shape_key(const EnsInput& in);
 void iso_fill(const pid_iso* iso, int32_t* mode, float* mu, float* inv, float* t);
 pid_status check_iso(pid_handle h, const pid_iso* iso);
 pid_status check_shape(pid_handle h, const void* data, int64_t N, int64_t M, int64_t ld,

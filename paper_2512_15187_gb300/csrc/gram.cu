@@ -32,10 +32,22 @@ pid_status plan_gram(pid_handle h, const EnsInput& in, GramPlan* gp) {
   // TMEM drain, an N x N partial written and read back, and the MMA pipeline's ramp, so a
   // few large chunks per ensemble beat one per group (batches supply the parallelism); the
   // upper bound keeps the exact FP32 PID-mean sums of a chunk short enough for 1e-6.
+  // Small ensembles (up to 2^16 cells) take chunks from 4 stages (512 cells) on: their few
+  // long chunks would otherwise run as a latency-bound chain on a handful of SMs.
   const int64_t groups = static_cast<int64_t>(h->sms) * (kGramConvWarps / gp->G);
+  const int64_t min_chunk = in.M <= 65536 ? 4 * 128 : 32 * 128;
   int64_t chunk = rup((in.M + groups - 1) / groups, 128);
-  chunk = std::max<int64_t>(chunk, std::min<int64_t>(rup(in.M, 128), 32 * 128));
+  chunk = std::max<int64_t>(chunk, std::min<int64_t>(rup(in.M, 128), min_chunk));
   chunk = std::min<int64_t>(chunk, 256 * 128);
+  // A tuned shape may halve or double the chunk (pid_autotune_shapes), within the same bounds.
+  if (!h->shapes.empty()) {
+    auto it = h->shapes.find(gram_shape_key(in));
+    if (it != h->shapes.end() && it->second != 0) {
+      chunk = it->second > 0 ? 2 * chunk : rup(chunk / 2, 128);
+      chunk = std::min<int64_t>(std::max<int64_t>(chunk, std::min<int64_t>(rup(in.M, 128), min_chunk)),
+                                256 * 128);
+    }
+  }
   gp->chunk_cells = chunk;
   gp->n_gchunks = static_cast<int>((in.M + chunk - 1) / chunk);
 

@@ -59,10 +59,12 @@ cudaError_t launch_stream(const StreamParams& p, int vec, int mpw, int G, int is
   return cudaErrorInvalidValue;
 }
 
+cudaError_t finalize_kernel_init();
+
 // Opt every streaming instantiation in to the largest dynamic shared memory once per
 // device (before any launch, so that launches can be captured into graphs).
 cudaError_t stream_kernels_init(int max_smem) {
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = finalize_kernel_init();
   if (e == cudaSuccess) e = init_stream_c4_8_1(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_2(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_6_4(max_smem);
@@ -129,10 +131,12 @@ __device__ __forceinline__ void kahan_add(float& acc, float& comp, float v) {
   acc = t;
 }
 
-// Row r of an [N][N] FP32 matrix written by this kernel's grid (read through L2), dotted
-// with the shared vector v (v == nullptr: summed), by one warp: lane l takes the columns
-// l, l + 32, ... in order, then a fixed xor tree. A lane loads 8 columns (a 256-column
-// block) before it adds them, so a block costs one L2 round trip instead of one per column.
+// Row r of an [N][N] FP32 matrix, dotted with the shared vector v (v == nullptr: summed),
+// by one warp: lane l takes the columns l, l + 32, ... in order, then a fixed xor tree. A
+// lane loads 8 columns (a 256-column block) before it adds them, so a block costs one
+// memory round trip instead of one per column. SHARED: the row is in this CTA's shared
+// memory; else it was written by this kernel's grid and is read through L2.
+template <bool SHARED = false>
 __device__ __forceinline__ float row_dot_warp(const float* row, const float* v, int N, int ln) {
   float acc = 0.f;
   for (int b = 0; b < N; b += 256) {
@@ -140,7 +144,7 @@ __device__ __forceinline__ float row_dot_warp(const float* row, const float* v, 
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int j = b + ln + 32 * k;
-      x[k] = j < N ? __ldcg(row + j) : 0.f;
+      x[k] = j < N ? (SHARED ? row[j] : __ldcg(row + j)) : 0.f;
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -151,7 +155,13 @@ __device__ __forceinline__ float row_dot_warp(const float* row, const float* v, 
   return warp_sum(acc);
 }
 
+// The calibrated Gram C0 of an ensemble of up to 128 members stays in the finishing CTA's
+// shared memory: the Sinkhorn sweeps then read it at shared-memory latency instead of one
+// L2 round trip per sweep (the cost that dominated small ensembles).
+constexpr int kFinC0Floats = 128 * 128;
+
 __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_constant__ FinParams p) {
+  extern __shared__ float fin_c0[];
   const FinDesc& d = fin_desc(p, blockIdx.y);
   if (static_cast<int>(blockIdx.x) >= d.slices) return;
   __shared__ double scratch[32][33];
@@ -292,7 +302,8 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     // runs in FP32 (the scales converge to FP32 precision, ~1e-7, far inside the Gram
     // bound); only the per-member scalars stay in FP64.
     const float* Cg = reinterpret_cast<const float*>(d.sums + 4 * N);   // G' (phase 1)
-    float* C0 = reinterpret_cast<float*>(d.sums + 4 * N) + N * N;       // (G' + G'^T) / 2
+    const bool c0s = N * N <= kFinC0Floats;                             // C0 in shared memory
+    float* C0 = c0s ? fin_c0 : reinterpret_cast<float*>(d.sums + 4 * N) + N * N;   // (G' + G'^T) / 2
     const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
     // Every row loop below runs one warp per row with the lanes on contiguous columns.
     // Raw sums: row r of the stored array is G'_{., r}, which equals row r of G' up to
@@ -331,7 +342,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     // more than 2^-22 relative (at most 24 sweeps).
     for (int it = 0; it < 24; ++it) {
       for (int r = wi; r < N; r += kFinThreads / 32) {
-        const float acc = row_dot_warp(C0 + r * N, sd, N, ln);
+        const float acc = c0s ? row_dot_warp<true>(C0 + r * N, sd, N, ln) : row_dot_warp(C0 + r * N, sd, N, ln);
         if (ln == 0) sdn[r] = (sd[r] > 0.f && acc > 0.f) ? sqrtf(sd[r] * sdm[r] / acc) : 0.f;
       }
       __syncthreads();
@@ -346,7 +357,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     if (i < N) sdm[i] = m > 0.0 ? static_cast<float>(sd[i] / m) : 0.f;
     __syncthreads();
     for (int r = wi; r < N; r += kFinThreads / 32) {
-      const float acc = row_dot_warp(C0 + r * N, sdm, N, ln);
+      const float acc = c0s ? row_dot_warp<true>(C0 + r * N, sdm, N, ln) : row_dot_warp(C0 + r * N, sdm, N, ln);
       if (ln == 0) sdn[r] = sd[r] * acc;
     }
     __syncthreads();
@@ -379,7 +390,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
     }
     if (i == 0 && d.err_est) d.err_est[0] = sred[0];
     if (d.P) {
-      const float* C0 = reinterpret_cast<const float*>(S + 4 * N) + N * N;   // symmetrised above
+      const float* C0 = N * N <= kFinC0Floats ? fin_c0 : reinterpret_cast<const float*>(S + 4 * N) + N * N;
       // P[r][cc] = C_{r,cc} / m_r: one warp per row, one FP64 division per row
       const int wi = threadIdx.x >> 5, ln = threadIdx.x & 31;
       for (int r = wi; r < N; r += kFinThreads / 32) {
@@ -390,7 +401,7 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int cc = c0 + ln + 32 * k;
-            x[k] = cc < N ? __ldcg(C0 + r * N + cc) : 0.f;
+            x[k] = cc < N ? C0[r * N + cc] : 0.f;   // written by this CTA (shared or global)
           }
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
@@ -405,8 +416,13 @@ __global__ void __launch_bounds__(kFinThreads, 1) finalize_kernel(const __grid_c
   if (threadIdx.x == 0) *d.ticket = 0u;
 }
 
+cudaError_t finalize_kernel_init() {
+  return cudaFuncSetAttribute(finalize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              static_cast<int>(kFinC0Floats * sizeof(float)));
+}
+
 cudaError_t launch_finalize(const FinParams& p, int grid_x, int grid_y, cudaStream_t s) {
-  finalize_kernel<<<dim3(grid_x, grid_y), kFinThreads, 0, s>>>(p);
+  finalize_kernel<<<dim3(grid_x, grid_y), kFinThreads, kFinC0Floats * sizeof(float), s>>>(p);
   return cudaGetLastError();
 }
 

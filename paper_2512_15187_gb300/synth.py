@@ -247,6 +247,58 @@ def plume_3d_slab(N: int, R: int, z0: int, nz: int, t: int = 0, T: int = 16,
     return out
 
 
+def ellipses_2d_torch(N: int, H: int, W: int, seed: int = DEFAULT_SEED + 1, device: str = "cuda"):
+    """The recipe of ellipses_2d on the device (torch's generator: other draws, the same
+    distribution): float32 [N, H*W] soft ellipses of semi-axes U[25, 45] px around the grid
+    centre +- 10 px, rotation U[0, pi), edge width U[1, 4] px."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    p = torch.rand((N, 6), generator=g, device=device, dtype=torch.float64)
+    cy = H / 2 + (p[:, 0] * 20 - 10)
+    cx = W / 2 + (p[:, 1] * 20 - 10)
+    a = 25 + 20 * p[:, 2]
+    b = 25 + 20 * p[:, 3]
+    th = math.pi * p[:, 4]
+    wd = 1 + 3 * p[:, 5]
+    yy = torch.arange(H, device=device, dtype=torch.float64).view(1, H, 1)
+    xx = torch.arange(W, device=device, dtype=torch.float64).view(1, 1, W)
+    out = torch.empty((N, H * W), dtype=torch.float32, device=device)
+    for i0 in range(0, N, 16):
+        sl = slice(i0, min(N, i0 + 16))
+        v = lambda t: t[sl].view(-1, 1, 1)
+        dx, dy = xx - v(cx), yy - v(cy)
+        xr = torch.cos(v(th)) * dx + torch.sin(v(th)) * dy
+        yr = -torch.sin(v(th)) * dx + torch.cos(v(th)) * dy
+        sdist = torch.sqrt((xr / v(a)) ** 2 + (yr / v(b)) ** 2)
+        out[sl] = torch.sigmoid((1.0 - sdist) * torch.sqrt(v(a) * v(b)) / v(wd)).reshape(-1, H * W).float()
+    return out
+
+
+def radial_disk_torch(N: int, M: int, seed: int = DEFAULT_SEED + 3, device: str = "cuda"):
+    """The recipe of radial_disk on the device (torch's generator: other draws, the same
+    distribution): points uniform in the unit disk with cell measures 10^U[0, 2] scaled to sum
+    to pi, masks (1 + tanh((0.5 + 0.1 xi_i(theta) - r) / 0.02)) / 2 with xi_i an 8-term Fourier
+    series (a_k, b_k ~ N(0, 1/k^2)) normalised to max |xi_i| = 1. Returns (U [N, M], w [M])."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    r = torch.sqrt(torch.rand(M, generator=g, device=device, dtype=torch.float64))
+    th = 2 * math.pi * torch.rand(M, generator=g, device=device, dtype=torch.float64)
+    w = 10.0 ** (2 * torch.rand(M, generator=g, device=device, dtype=torch.float64))
+    w = (w * (math.pi / w.sum())).float()
+    K = 8
+    ks = torch.arange(1, K + 1, device=device, dtype=torch.float64)
+    basis = torch.cat([torch.cos(th[:, None] * ks), torch.sin(th[:, None] * ks)], dim=1)  # [M, 2K]
+    coef = torch.randn((N, 2 * K), generator=g, device=device, dtype=torch.float64) / torch.cat([ks, ks])
+    U = torch.empty((N, M), dtype=torch.float32, device=device)
+    for i0 in range(0, N, 32):
+        xi = coef[i0:i0 + 32] @ basis.T
+        xi = xi / xi.abs().amax(dim=1, keepdim=True).clamp_min(1e-12)
+        U[i0:i0 + 32] = (0.5 * (1.0 + torch.tanh((0.5 + 0.1 * xi - r) / 0.02))).float()
+    return U, w
+
+
 def rbf_fields_2d_torch(N: int = 64, H: int = 512, W: int = 512, n_rbf: int = 32,
                         seed: int = DEFAULT_SEED + 2, device: str = "cuda", out=None,
                         chunk: int = 256):
