@@ -50,7 +50,7 @@ struct GramLeader {
   int iu, u_end, ist, in_st, icell0, slot;
   int e_begin, e_end, chunk, M, boxes, rows, has_w;
   int pend, pend_first, pend_last, pend_slot, pend_buf;
-  uint32_t pend_idesc;
+  uint32_t pend_idesc, pend_idesc1;
 };
 
 // NMPW: members per warp: 8 (narrow) or 16 (wide), or 6 / 12 for ensembles that fill at
@@ -260,6 +260,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     const int buf = L.pend_buf, slot = L.pend_slot;
     const long pkc = L.pend_kc;
     const uint32_t idsc = L.pend_idesc;
+    const uint32_t idsc1 = L.pend_idesc1;   // wide: the second row block's narrower N
     // The unit's first MMA overwrites its accumulator buffer: the unit that used that
     // buffer before must have been drained (two units back, or one with a single buffer).
     if (first && pkc >= NBUF &&
@@ -276,19 +277,24 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       for (int ks = 0; ks < 4; ++ks) {   // 4 x 32 bytes along K in the 128-byte row
         const uint64_t hi = d0 + static_cast<uint64_t>((kb * PLANE + ks * 32) >> 4);
         const uint32_t acc = (first && kb == 0 && ks == 0) ? 0u : 1u;
+        // Wide tile: row block 1 (members 128..) multiplies only the columns from 128 on;
+        // its block left of the diagonal is the transpose of row block 0's right part, which
+        // the drain mirrors.
 #pragma unroll
         for (int mb = 0; mb < MB; ++mb) {
           const uint32_t dmb = dt + static_cast<uint32_t>(mb * 256);
           const uint64_t ha = hi + static_cast<uint64_t>((mb * 128 * 128) >> 4);
+          const uint64_t hb = mb == 1 ? ha : hi;
+          const uint32_t id = mb == 1 ? idsc1 : idsc;
           if constexpr (PREC == 3) {
-            umma_f8(dmb, ha, hi, idsc, acc);
+            umma_f8(dmb, ha, hb, id, acc);
           } else {
-            umma_f16(dmb, ha, hi, idsc, acc);
+            umma_f16(dmb, ha, hb, id, acc);
             if constexpr (PREC == 2) {
-              const uint64_t lo = hi + static_cast<uint64_t>((KBLK * PLANE) >> 4);
+              const uint64_t lb = hb + static_cast<uint64_t>((KBLK * PLANE) >> 4);
               const uint64_t la = ha + static_cast<uint64_t>((KBLK * PLANE) >> 4);
-              umma_f16(dmb, ha, lo, idsc, 1u);
-              umma_f16(dmb, la, hi, idsc, 1u);
+              umma_f16(dmb, ha, lb, id, 1u);
+              umma_f16(dmb, la, hb, id, 1u);
             }
           }
         }
@@ -304,7 +310,6 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   // E4M3 operands carry the per-member scales osc[0..N) (nullptr: 256 for every member),
   // undone here exactly: G_ij = G'_ij / (s_i s_j), the inverses osc[N + i] being powers of two.
   auto drain = [&](float* gp, int N, const float* osc, long kc) -> bool {
-    const int nmma = (N + 15) & ~15;
     const int b = static_cast<int>(kc % NBUF);
     if (!mbar_wait_bounded(&accF[b], static_cast<uint32_t>((kc / NBUF) & 1), kWaitTimeoutNs))
       return false;
@@ -313,26 +318,24 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     for (int mb = 0; mb < MB; ++mb) {
       const int row = 128 * mb + 32 * q + lane;
       if (128 * mb >= N) break;
-      for (int j0 = 0; j0 < nmma; j0 += 32) {
+      // columns of this row block's accumulator: all N for block 0, those from 128 on for
+      // block 1 (wide tile); block 0's columns past 127 also fill the mirrored entries
+      const int jbase = 128 * mb;
+      const int ncol = (N - jbase + 15) & ~15;
+      const float ir = PREC == 3 ? (osc != nullptr ? osc[N + min(row, N - 1)] : 1.0f / 65536.0f) : 1.0f;
+      for (int j0 = 0; j0 < ncol; j0 += 32) {
         float v[32];
         tmem_ld32(tmem_base + (static_cast<uint32_t>(32 * q) << 16) + b * BUFC + mb * 256 + j0, v);
         if (row < N) {
-          if constexpr (PREC == 3) {
-            if (osc != nullptr) {
-              const float ir = osc[N + row];
 #pragma unroll
-              for (int jj = 0; jj < 32; ++jj)
-                if (j0 + jj < N)
-                  gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj] * (ir * osc[N + j0 + jj]);
-            } else {
-#pragma unroll
-              for (int jj = 0; jj < 32; ++jj)
-                if (j0 + jj < N) gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj] * (1.0f / 65536.0f);
+          for (int jj = 0; jj < 32; ++jj) {
+            const int j = jbase + j0 + jj;
+            if (j < N) {
+              // E4M3: G_ij = G'_ij / (s_i s_j) with the inverse scales osc[N + .]
+              const float g = PREC == 3 ? v[jj] * (osc != nullptr ? ir * osc[N + j] : ir) : v[jj];
+              gp[static_cast<size_t>(j) * N + row] = g;
+              if (WIDE && mb == 0 && j >= 128) gp[static_cast<size_t>(row) * N + j] = g;
             }
-          } else {
-#pragma unroll
-            for (int jj = 0; jj < 32; ++jj)
-              if (j0 + jj < N) gp[static_cast<size_t>(j0 + jj) * N + row] = v[jj];
           }
         }
       }
@@ -375,7 +378,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   const float* data = nullptr;
   const float* wptr = nullptr;
   int64_t ld = 0;
-  uint32_t idesc = 0;
+  uint32_t idesc = 0, idesc1 = 0;
   float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f;
   const float* osc = nullptr;   // E4M3 member scales of the current ensemble
   int iso_md = 0;
@@ -393,6 +396,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       ld = dp->ld;
       has_w = wptr != nullptr;
       idesc = umma_idesc(FMT, 128, static_cast<uint32_t>((N + 15) & ~15));
+      idesc1 = WIDE ? umma_idesc(FMT, 128, static_cast<uint32_t>(max(16, (N - 128 + 15) & ~15))) : idesc;
       iso_mu = dp->iso_mu;
       iso_inv = dp->iso_inv;
       iso_t = dp->iso_t;
@@ -605,6 +609,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         L.pend_buf = static_cast<int>(kc % NBUF);
         L.pend_kc = kc;
         L.pend_idesc = idesc;
+        L.pend_idesc1 = idesc1;
       }
       // Double-buffered accumulators are drained halfway through the next chunk, when the
       // last products have long landed; a single buffer must be drained before the next
