@@ -30,7 +30,7 @@ size_t gram_smem_bytes(int G, int mpw, bool wide, int prec, int dF, int dO, int 
   const size_t op_stage = (prec == 2 ? 2 : 1) * ((prec == 3 || wide) ? 1 : 2) * plane;
   const size_t rb = static_cast<size_t>(G) * T + T;
   return 1024 + NG * (dO * op_stage + static_cast<size_t>(dF) * stage_floats * 4 + 2 * rb * 4 +
-                      (static_cast<size_t>(dF) + dO + 5) * 8 + 8) + 16 +
+                      (static_cast<size_t>(dF) + 2 * dO + 5) * 8 + 8) + 16 +
          16 + NG * sizeof(GramLeader) + kGramConvWarps * kGramMaxMpw * sizeof(float);
 }
 

@@ -105,9 +105,20 @@ __device__ __forceinline__ uint32_t sw128_offset(int i, int b) {
 // skip the mean-contour arithmetic and its column-sum exchange; one group barrier per stage
 // remains, after the stage's FP32 tile has been read, and the kernel writes no (m, A)
 // partials.
+//
+// With one group of 16 converter warps and no exact sums (EXACT = false, G = 16), a 17th
+// warp issues the tensor-core work: the converters mark each finished operand stage on an
+// mbarrier and go on, so no converter waits at the group barrier while MMAs are being issued
+// (the issue of a stage's 8 to 24 MMAs blocks while the tensor pipe's queue is full).
+template <int G, bool EXACT>
+constexpr bool gram_has_issuer() { return !EXACT && G == kGramConvWarps; }
+template <int G, bool EXACT>
+constexpr int gram_threads() { return kGramThreads + (gram_has_issuer<G, EXACT>() ? 32 : 0); }
+
 template <int G, int ISO, int PREC, bool TMA, bool WIDE, int NMPW = (WIDE ? 16 : 8), bool EXACT = true>
-__global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_constant__ GramParams p) {
+__global__ void __launch_bounds__(gram_threads<G, EXACT>(), 1) gram_kernel(const __grid_constant__ GramParams p) {
   static_assert(EXACT || ISO == ISOK_NONE, "fields map in the Gram pass, with the exact sums");
+  constexpr bool ISSUER = gram_has_issuer<G, EXACT>();
   using S = GramShape<WIDE, NMPW>;
   constexpr int VEC = S::VEC, T = S::T, MPW = S::MPW, FPS = S::FPS, MB = S::MB, NBUF = S::NBUF;
   // FP32 stages per operand stage: an E4M3 K-block is 128 cells (two wide FP32 stages); a
@@ -133,7 +144,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int grp = warp / G;
+  const bool issuer_warp = ISSUER && warp == kGramConvWarps;
+  const int grp = issuer_warp ? 0 : warp / G;
   const int q = warp - grp * G;
   const bool leader = (q == 0) && (lane == 0);
   const int dF = p.dF, dO = p.dO, SF = p.stage_floats;
@@ -147,7 +159,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   float* f_all = reinterpret_cast<float*>(smem + static_cast<size_t>(NG) * dO * OP_STAGE);
   float* red_all = f_all + static_cast<size_t>(NG) * dF * SF;
   uint64_t* bars_all = reinterpret_cast<uint64_t*>(red_all + NG * 2 * RB);
-  int* flags_all = reinterpret_cast<int*>(bars_all + NG * (dF + dO + 5));
+  int* flags_all = reinterpret_cast<int*>(bars_all + NG * (dF + 2 * dO + 5));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(flags_all + 2 * NG);
   GramLeader* lead_all = reinterpret_cast<GramLeader*>(
       (reinterpret_cast<uintptr_t>(tmem_slot + 1) + 15) & ~static_cast<uintptr_t>(15));
@@ -158,12 +170,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   unsigned char* op_ring = smem + static_cast<size_t>(grp) * dO * OP_STAGE;
   float* f_ring = f_all + static_cast<size_t>(grp) * dF * SF;
   float* red = red_all + grp * 2 * RB;
-  uint64_t* bars = bars_all + grp * (dF + dO + 5);
+  uint64_t* bars = bars_all + grp * (dF + 2 * dO + 5);
   uint64_t* fF = bars;              // FP32 stage landed (TMA)
   uint64_t* opE = fF + dF;          // operand stage consumed (tcgen05.commit)
   uint64_t* accF = opE + dO;        // accumulator ready (tcgen05.commit)
   uint64_t* accE = accF + 2;        // accumulator drained (the group's warps 0-3)
   uint64_t* finB = accE + 2;        // all of the group's tensor-core work done
+  uint64_t* opF = finB + 1;         // ISSUER: operand stage written (one arrival per warp)
   // Abort flags, one per exchange-buffer parity: a warp that gives up on a wait sets the
   // flag of the group barrier it reaches next, and every warp of the group reads that flag
   // after that barrier, so all of them leave together.
@@ -174,12 +187,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     for (int s = 0; s < dO; ++s) mbar_init(&opE[s], 1);
     for (int b = 0; b < 2; ++b) { mbar_init(&accF[b], 1); mbar_init(&accE[b], kGramEpiWarps); }
     mbar_init(finB, 1);
+    if constexpr (ISSUER)
+      for (int s = 0; s < dO; ++s) mbar_init(&opF[s], static_cast<uint32_t>(G));
     cflag[0] = 0;
     cflag[1] = 0;
     fence_mbar_init();
   }
   // Operand rows past N must be finite on first use: clear every operand ring.
-  for (uint32_t o = threadIdx.x * 16; o < static_cast<uint32_t>(NG) * dO * OP_STAGE; o += kGramThreads * 16)
+  for (uint32_t o = threadIdx.x * 16; o < static_cast<uint32_t>(NG) * dO * OP_STAGE; o += blockDim.x * 16)
     *reinterpret_cast<uint4*>(smem + o) = make_uint4(0, 0, 0, 0);
   fence_proxy_async_smem();
   if (warp == 0) {
@@ -252,15 +267,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     }
   }
 
-  // ---- tensor-core issue (leader): the stage written last, issued after the next barrier ----
-  auto issue_pending = [&]() -> bool {
-    if (!L.pend) return true;
-    L.pend = 0;
-    const bool first = L.pend_first != 0;
-    const int buf = L.pend_buf, slot = L.pend_slot;
-    const long pkc = L.pend_kc;
-    const uint32_t idsc = L.pend_idesc;
-    const uint32_t idsc1 = L.pend_idesc1;   // wide: the second row block's narrower N
+  // ---- tensor-core issue of one operand stage (into accumulator buffer `buf`) ----
+  auto issue_stage = [&](int slot, int buf, bool first, long pkc, uint32_t idsc, uint32_t idsc1,
+                         bool last) -> bool {
     // The unit's first MMA overwrites its accumulator buffer: the unit that used that
     // buffer before must have been drained (two units back, or one with a single buffer).
     if (first && pkc >= NBUF &&
@@ -301,8 +310,15 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
       }
     }
     tc_commit(&opE[slot]);
-    if (L.pend_last) tc_commit(&accF[buf]);
+    if (last) tc_commit(&accF[buf]);
     return true;
+  };
+  // The leader's form: the stage written last, issued after the next group barrier.
+  auto issue_pending = [&]() -> bool {
+    if (!L.pend) return true;
+    L.pend = 0;
+    return issue_stage(L.pend_slot, L.pend_buf, L.pend_first != 0, L.pend_kc, L.pend_idesc,
+                       L.pend_idesc1, L.pend_last != 0);
   };
 
   // ---- accumulator drain of the group's kc-th unit (warps 0-3, one TMEM lane quarter each)
@@ -382,7 +398,44 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f;
   const float* osc = nullptr;   // E4M3 member scales of the current ensemble
   int iso_md = 0;
-  for (int u = u_begin; u < u_end && !aborted; ++u, ++kc) {
+  // ---- the issuer warp (lane 0): each finished operand stage to the tensor cores ----
+  if (issuer_warp) {
+    if (lane == 0) {
+      bool ok = true;
+      int os = 0, ie_begin = 0, ie_end = 0, ichunk = 0, iM = 0;
+      long orr = 0, ikc = 0;
+      uint32_t id0 = 0, id1 = 0;
+      for (int u = u_begin; u < u_end && ok; ++u, ++ikc) {
+        if (u >= ie_end) {
+          const EnsDesc& de = gdesc(p, gram_find_ens(p, u));
+          ie_begin = de.unit_begin;
+          ie_end = ie_begin + de.n_chunks;
+          ichunk = de.chunk_cells;
+          iM = de.M;
+          id0 = umma_idesc(FMT, 128, static_cast<uint32_t>((de.N + 15) & ~15));
+          id1 = WIDE ? umma_idesc(FMT, 128, static_cast<uint32_t>(max(16, (de.N - 128 + 15) & ~15))) : id0;
+        }
+        const int cell0 = (u - ie_begin) * ichunk;
+        const int n_ops = FPS * ((min(ichunk, iM - cell0) + 127) / 128) / SPO;
+        for (int j = 0; j < n_ops; ++j) {
+          // A converter that gives up stops arriving: this wait then ends the issue, and the
+          // converters' own bounded waits on the operand slots end theirs.
+          if (!mbar_wait_bounded(&opF[os], static_cast<uint32_t>(orr & 1), kWaitTimeoutNs) ||
+              !issue_stage(os, static_cast<int>(ikc % NBUF), j == 0, ikc, id0, id1, j == n_ops - 1)) {
+            ok = false;
+            break;
+          }
+          if (++os == dO) { os = 0; ++orr; }
+        }
+      }
+      if (!ok) atomicOr(p.err, ERR_TIMEOUT);
+      tc_commit(finB);
+      mbar_wait_bounded(finB, 0, kWaitTimeoutNs);
+    }
+    __syncwarp();
+  }
+  const int u_conv_end = issuer_warp ? u_begin : u_end;
+  for (int u = u_begin; u < u_conv_end && !aborted; ++u, ++kc) {
     if (u >= e_end) {
       dp = &gdesc(p, gram_find_ens(p, u));
       N = dp->N;
@@ -550,7 +603,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         named_barrier(1 + grp, G * 32);
         if (cflag[kt & 1]) { aborted = true; break; }
         if (leader) {
-          if (!issue_pending()) cflag[(kt + 1) & 1] = 1;   // stage k-1 to the tensor cores
+          if (!ISSUER && !issue_pending()) cflag[(kt + 1) & 1] = 1;   // stage k-1 to the tensor cores
           if (TMA) issue_next();
         }
       }
@@ -601,7 +654,12 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
         }
       }
       fence_proxy_async_smem();
-      if (leader && jh == SPO - 1) {   // a full operand stage: to the tensor cores after the next barrier
+      if constexpr (ISSUER) {   // a full operand stage: every warp marks its rows written
+        if (jh == SPO - 1) {
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&opF[oslot]);
+        }
+      } else if (leader && jh == SPO - 1) {   // a full operand stage: to the tensor cores after the next barrier
         L.pend = 1;
         L.pend_slot = oslot;
         L.pend_first = st < SPO;
@@ -638,11 +696,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
     }
   }
   if (!aborted) {
-    // The last stage goes to the tensor cores after one more group barrier; then the last
-    // chunk's accumulator is drained.
-    named_barrier(1 + grp, G * 32);
-    if (cflag[kt & 1]) aborted = true;
-    if (!aborted && leader && !issue_pending()) aborted = true;
+    // The last stage goes to the tensor cores after one more group barrier (the issuer warp
+    // takes it without); then the last chunk's accumulator is drained.
+    if constexpr (!ISSUER) {
+      named_barrier(1 + grp, G * 32);
+      if (cflag[kt & 1]) aborted = true;
+      if (!aborted && leader && !issue_pending()) aborted = true;
+    }
     if (!aborted && q < kGramEpiWarps && prev_gp != nullptr &&
         !drain(prev_gp, prev_N, prev_osc, prev_kc))
       aborted = true;
@@ -650,10 +710,13 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_kernel(const __grid_cons
   if (bad) atomicOr(p.err, bad);
   if (aborted && lane == 0) atomicOr(p.err, ERR_TIMEOUT);
   if (leader) {
-    // All tensor-core work issued so far must finish before the tensor memory is released,
-    // and all TMA copies in flight must land before the CTA retires.
-    tc_commit(finB);
-    mbar_wait_bounded(finB, 0, kWaitTimeoutNs);
+    // All tensor-core work issued so far must finish before the tensor memory is released
+    // (the issuer warp waits for its own), and all TMA copies in flight must land before
+    // the CTA retires.
+    if constexpr (!ISSUER) {
+      tc_commit(finB);
+      mbar_wait_bounded(finB, 0, kWaitTimeoutNs);
+    }
     if (TMA) {
       while (k < L.n_issued) {
         if (!mbar_wait_bounded(&fF[k % dF], static_cast<uint32_t>((k / dF) & 1), kWaitTimeoutNs)) break;
@@ -675,10 +738,11 @@ template <int G, int ISO, int PREC, int NMPW, bool WIDE>
 cudaError_t gram_tile_launch_t(const GramParams& p, int grid, size_t smem, cudaStream_t s) {
   if constexpr (ISO == ISOK_NONE) {
     if (!p.exact) {   // soft masks with the exact sums from a streaming pass
+      constexpr int threads = gram_threads<G, false>();
       if (p.use_tma)
-        gram_kernel<G, ISO, PREC, true, WIDE, NMPW, false><<<grid, kGramThreads, smem, s>>>(p);
+        gram_kernel<G, ISO, PREC, true, WIDE, NMPW, false><<<grid, threads, smem, s>>>(p);
       else
-        gram_kernel<G, ISO, PREC, false, WIDE, NMPW, false><<<grid, kGramThreads, smem, s>>>(p);
+        gram_kernel<G, ISO, PREC, false, WIDE, NMPW, false><<<grid, threads, smem, s>>>(p);
       return cudaGetLastError();
     }
   }
