@@ -564,9 +564,11 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       pid_status st = stream_launch(h, sp, L.cfg, L.coef, grid, L.max_n, L.cells, L.bytes, s);
       if (st != PID_OK) return st;
     } else if (L.kind == Launch::GRAM) {
-      for (const auto& sc : L.scales) {
-        const pid_status st = sc.from_keys ? launch_scales_from_keys(h, sc.in.N, sc.out, s)
-                                           : launch_member_scales_one(h, sc.in, sc.out, s);
+      if (!L.scales.empty()) {
+        std::vector<ScaleJob> jobs;
+        jobs.reserve(L.scales.size());
+        for (const auto& sc : L.scales) jobs.push_back(ScaleJob{sc.in, sc.out, sc.from_keys});
+        const pid_status st = launch_member_scales_many(h, jobs, s);
         if (st != PID_OK) return st;
       }
       pid_status st = launch_gram_batch(h, L.gp, sdev + L.first, L.count, L.total_units,

@@ -205,8 +205,16 @@ inline int gram_operand_precision(int prec, int64_t cells, bool want_matrix) {
 
 // gram.cu
 // Per-member E4M3 operand scales of one ensemble into `region` (pidk::kScaleBytes of
-// workspace: [2N] scales and inverses, then [N] reduction keys).
+// workspace: [2N] scales and inverses, then reduction keys or CTA maxima).
 pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* region, cudaStream_t s);
+// The scales of several ensembles, up to pidk::kScaleBatch per pair of launches; from_keys:
+// a streaming pass already reduced the maxima into the region's keys.
+struct ScaleJob {
+  EnsInput in;
+  float* region;
+  bool from_keys;
+};
+pid_status launch_member_scales_many(pid_handle h, const std::vector<ScaleJob>& jobs, cudaStream_t s);
 // The reduction keys inside a scale region, and the scales from keys a streaming pass filled.
 inline unsigned int* scale_keys(float* region) {
   return reinterpret_cast<unsigned int*>(region + 2 * pidk::kGramTiledMaxN);

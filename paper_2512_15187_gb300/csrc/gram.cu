@@ -97,35 +97,57 @@ void gram_geometry(pid_handle h, int G, int mpw, bool wide, int prec, int32_t st
   *smem = gram_smem_bytes(G, mpw, wide, prec, f, o, stage_floats);
 }
 
-pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* region, cudaStream_t s) {
-  ScaleParams sp;
-  std::memset(&sp, 0, sizeof(sp));
-  sp.data = in.data;
-  sp.w = in.w;
-  sp.ld = in.ld;
-  sp.N = static_cast<int32_t>(in.N);
-  sp.M = static_cast<int32_t>(in.M);
-  iso_fill(in.is_field ? &in.iso : nullptr, &sp.iso_mode, &sp.iso_mu, &sp.iso_inv, &sp.iso_t);
-  sp.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
-              (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
-  sp.scale = region;
-  sp.maxkey = scale_keys(region);
-  ProfScope ps(h, PID_KERNEL_SCALE, 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0), 0.0, s);
-  const cudaError_t e = launch_member_scales(sp, h->sms, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "E4M3 member scale launch");
+pid_status launch_member_scales_many(pid_handle h, const std::vector<ScaleJob>& jobs, cudaStream_t s) {
+  for (size_t j0 = 0; j0 < jobs.size(); j0 += kScaleBatch) {
+    ScaleBatchParams sb;
+    std::memset(&sb, 0, sizeof(sb));
+    double bytes = 0.0;
+    const size_t j1 = std::min(jobs.size(), j0 + kScaleBatch);
+    for (size_t j = j0; j < j1; ++j) {
+      const EnsInput& in = jobs[j].in;
+      ScaleDesc& d = sb.d[sb.n++];
+      d.data = in.data;
+      d.w = in.w;
+      d.ld = in.ld;
+      d.N = static_cast<int32_t>(in.N);
+      d.M = static_cast<int32_t>(in.M);
+      iso_fill(in.is_field ? &in.iso : nullptr, &d.iso_mode, &d.iso_mu, &d.iso_inv, &d.iso_t);
+      d.vec_ok = in.ld % 4 == 0 && reinterpret_cast<uintptr_t>(in.data) % 16 == 0 &&
+                 (!in.w || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
+      d.proxy = in.is_field && in.w == nullptr;
+      d.scale = jobs[j].region;
+      d.from_keys = jobs[j].from_keys ? 1 : 0;
+      if (d.from_keys) {
+        bytes += 4.0 * in.N;
+        continue;
+      }
+      // about four CTAs per SM over the members, segments of at least 4096 cells, and the
+      // CTA maxima within the region
+      const int64_t want = std::max<int64_t>(1, (4LL * h->sms + in.N - 1) / in.N);
+      int64_t segs = std::max<int64_t>(
+          1, std::min({want, (in.M + 4095) / 4096, static_cast<int64_t>(kScaleMaxSlots) / in.N}));
+      d.seg_cells = static_cast<int32_t>(((in.M + segs - 1) / segs + 1023) / 1024 * 1024);
+      segs = (in.M + d.seg_cells - 1) / d.seg_cells;
+      d.segs = static_cast<int32_t>(segs);
+      d.block_begin = sb.total_blocks;
+      sb.total_blocks += static_cast<int32_t>(segs * in.N);
+      bytes += 4.0 * in.N * in.M + (in.w ? 4.0 * in.M : 0.0);
+    }
+    ProfScope ps(h, PID_KERNEL_SCALE, bytes, 0.0, s);
+    const cudaError_t e = launch_member_scales(sb, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "E4M3 member scale launch");
+  }
   return PID_OK;
 }
 
+pid_status launch_member_scales_one(pid_handle h, const EnsInput& in, float* region, cudaStream_t s) {
+  return launch_member_scales_many(h, {ScaleJob{in, region, false}}, s);
+}
+
 pid_status launch_scales_from_keys(pid_handle h, int64_t N, float* region, cudaStream_t s) {
-  ScaleParams sp;
-  std::memset(&sp, 0, sizeof(sp));
-  sp.N = static_cast<int32_t>(N);
-  sp.scale = region;
-  sp.maxkey = scale_keys(region);
-  ProfScope ps(h, PID_KERNEL_SCALE, 4.0 * N, 0.0, s);
-  const cudaError_t e = launch_member_scales_from_keys(sp, s);
-  if (e != cudaSuccess) return cuda_fail(h, e, "E4M3 member scale launch");
-  return PID_OK;
+  EnsInput in;
+  in.N = N;
+  return launch_member_scales_many(h, {ScaleJob{in, region, true}}, s);
 }
 
 static int gram_kind(int prec) {

@@ -111,101 +111,125 @@ __device__ __forceinline__ float iso_from_proxy(float p, int32_t mode, float mu,
 
 constexpr int kScaleThreads = 256;
 
-// PROXY: unweighted fields (reduce the proxy of F); otherwise reduce u sqrt(w), mapping
-// fields element by element. One CTA per (member, segment of seg_cells cells).
+// The value whose maximum a member's scale needs: the proxy of F for unweighted fields
+// (PROXY), otherwise u sqrt(w), mapping fields element by element.
 template <bool PROXY>
-__global__ void __launch_bounds__(kScaleThreads) member_max_kernel(const __grid_constant__ ScaleParams p) {
-  const int i = blockIdx.y;
-  const int64_t c0 = static_cast<int64_t>(blockIdx.x) * p.seg_cells;
-  const int64_t c1 = min(static_cast<int64_t>(p.M), c0 + p.seg_cells);
-  const float* row = p.data + static_cast<int64_t>(i) * p.ld;
-  const bool field = p.iso_mode != ISO_NONE;
-  float best = PROXY ? -__int_as_float(0x7f800000) : 0.0f;
-  for (int64_t x = c0 + 4 * static_cast<int64_t>(threadIdx.x); x < c1; x += 4 * kScaleThreads) {
-    float f[4], w[4] = {1.f, 1.f, 1.f, 1.f};
-    int n = 4;
-    if (p.vec_ok && x + 4 <= c1) {
-      const float4 a = __ldcs(reinterpret_cast<const float4*>(row + x));
-      f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
-      if (!PROXY && p.w) {
-        const float4 b = __ldg(reinterpret_cast<const float4*>(p.w + x));
-        w[0] = b.x; w[1] = b.y; w[2] = b.z; w[3] = b.w;
-      }
-    } else {
-      n = static_cast<int>(c1 - x < 4 ? c1 - x : 4);
-      for (int v = 0; v < n; ++v) {
-        f[v] = __ldcs(row + x + v);
-        if (!PROXY && p.w) w[v] = __ldg(p.w + x + v);
-      }
-    }
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      if (v >= n) break;
-      float val;
-      if constexpr (PROXY) {
-        val = iso_proxy(f[v], p.iso_mode, p.iso_mu, p.iso_inv);
-      } else {
-        const float u = field ? iso_value(f[v], p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t) : f[v];
-        val = p.w ? u * sqrtf(w[v]) : u;
-      }
-      best = fmaxf(best, val);
-    }
+__device__ __forceinline__ float scale_value(const ScaleDesc& d, float f, float w) {
+  if constexpr (PROXY) {
+    return iso_proxy(f, d.iso_mode, d.iso_mu, d.iso_inv);
+  } else {
+    const float u = d.iso_mode != ISO_NONE ? iso_value(f, d.iso_mode, d.iso_mu, d.iso_inv, d.iso_t) : f;
+    return d.w ? u * sqrtf(w) : u;
   }
-  // block maximum, then one atomic per CTA
+}
+
+// The maximum over one CTA's segment [c0, c1) of member i. Aligned rows are read as float4
+// with four loads in flight per thread; the rest cell by cell.
+template <bool PROXY>
+__device__ __forceinline__ float member_segment_max(const ScaleDesc& d, int i, int64_t c0, int64_t c1) {
+  constexpr int U = 4;
+  const float* row = d.data + static_cast<int64_t>(i) * d.ld;
+  const bool use_w = !PROXY && d.w != nullptr;
+  float best = PROXY ? -__int_as_float(0x7f800000) : 0.0f;
+  int64_t tail = c0;
+  if (d.vec_ok) {
+    const int64_t n4 = (c1 - c0) >> 2;   // c0 is a multiple of 1024: float4-aligned
+    const float4* r4 = reinterpret_cast<const float4*>(row + c0);
+    const float4* w4 = use_w ? reinterpret_cast<const float4*>(d.w + c0) : nullptr;
+    for (int64_t j0 = threadIdx.x; j0 < n4; j0 += static_cast<int64_t>(U) * kScaleThreads) {
+      float4 a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t j = j0 + static_cast<int64_t>(u) * kScaleThreads;
+        if (j < n4) {
+          a[u] = __ldcs(r4 + j);
+          b[u] = use_w ? __ldg(w4 + j) : make_float4(1.f, 1.f, 1.f, 1.f);
+        } else {
+          a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+          b[u] = make_float4(1.f, 1.f, 1.f, 1.f);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (j0 + static_cast<int64_t>(u) * kScaleThreads >= n4) break;
+        best = fmaxf(best, scale_value<PROXY>(d, a[u].x, b[u].x));
+        best = fmaxf(best, scale_value<PROXY>(d, a[u].y, b[u].y));
+        best = fmaxf(best, scale_value<PROXY>(d, a[u].z, b[u].z));
+        best = fmaxf(best, scale_value<PROXY>(d, a[u].w, b[u].w));
+      }
+    }
+    tail = c0 + 4 * n4;
+  }
+  for (int64_t x = tail + threadIdx.x; x < c1; x += kScaleThreads)
+    best = fmaxf(best, scale_value<PROXY>(d, __ldcs(row + x), use_w ? __ldg(d.w + x) : 1.f));
+  return best;
+}
+
+// One CTA per (ensemble, member, segment): the CTA's maximum goes to its own slot of the
+// ensemble's scale region, so the pass needs no atomics and no cleared keys.
+__global__ void __launch_bounds__(kScaleThreads) member_max_kernel(const __grid_constant__ ScaleBatchParams p) {
+  const int b = blockIdx.x;
+  int e = -1;   // the last descriptor with a max pass that starts at or before this CTA
+  for (int k = 0; k < p.n; ++k)
+    if (!p.d[k].from_keys && p.d[k].block_begin <= b) e = k;
+  if (e < 0) return;
+  const ScaleDesc& d = p.d[e];
+  const int local = b - d.block_begin;
+  const int i = local / d.segs;
+  const int sg = local - i * d.segs;
+  const int64_t c0 = static_cast<int64_t>(sg) * d.seg_cells;
+  const int64_t c1 = min(static_cast<int64_t>(d.M), c0 + d.seg_cells);
+  float best = d.proxy ? member_segment_max<true>(d, i, c0, c1) : member_segment_max<false>(d, i, c0, c1);
   __shared__ float red[kScaleThreads / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
   __syncthreads();
   if (threadIdx.x == 0) {
-    float b = red[0];
-    for (int k = 1; k < kScaleThreads / 32; ++k) b = fmaxf(b, red[k]);
-    atomicMax(p.maxkey + i, fkey(b));
+    float m = red[0];
+    for (int k = 1; k < kScaleThreads / 32; ++k) m = fmaxf(m, red[k]);
+    d.scale[2 * kGramTiledMaxN + local] = m;
   }
 }
 
 // s_i from the maximum: the largest k with v 2^k <= 448 = 1.75 * 2^8, i.e. k = 8 - e when
 // the significand of v (in [1, 2)) is at most 1.75, else 7 - e; k is kept within [-63, 63]
 // so that every product of two inverse scales is a normal FP32 power of two. A member with
-// no positive value (all zeros) takes s_i = 1.
-__global__ void member_scale_kernel(const __grid_constant__ ScaleParams p, bool proxy) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= p.N) return;
-  float v = fkey_inv(p.maxkey[i]);
-  if (proxy) v = iso_from_proxy(v, p.iso_mode, p.iso_mu, p.iso_inv, p.iso_t);
-  int k = 0;
-  if (v > 0.f && v < __int_as_float(0x7f800000)) {
-    const unsigned int b = __float_as_uint(v);
-    const int e = static_cast<int>((b >> 23) & 0xffu) - 127;   // -127: subnormal v
-    k = ((b & 0x7fffffu) <= 0x600000u ? 8 : 7) - e;
-    k = max(-63, min(63, k));
+// no positive value (all zeros) takes s_i = 1. One CTA per ensemble.
+__global__ void __launch_bounds__(kScaleThreads) member_scale_kernel(const __grid_constant__ ScaleBatchParams p) {
+  const ScaleDesc& d = p.d[blockIdx.x];
+  const float* slots = d.scale + 2 * kGramTiledMaxN;
+  for (int i = threadIdx.x; i < d.N; i += kScaleThreads) {
+    float v;
+    if (d.from_keys) {
+      v = fkey_inv(reinterpret_cast<const unsigned int*>(slots)[i]);
+    } else {
+      v = slots[i * d.segs];
+      for (int sg = 1; sg < d.segs; ++sg) v = fmaxf(v, slots[i * d.segs + sg]);
+      if (d.proxy) v = iso_from_proxy(v, d.iso_mode, d.iso_mu, d.iso_inv, d.iso_t);
+    }
+    int k = 0;
+    if (v > 0.f && v < __int_as_float(0x7f800000)) {
+      const unsigned int b = __float_as_uint(v);
+      const int e = static_cast<int>((b >> 23) & 0xffu) - 127;   // -127: subnormal v
+      k = ((b & 0x7fffffu) <= 0x600000u ? 8 : 7) - e;
+      k = max(-63, min(63, k));
+    }
+    d.scale[i] = __uint_as_float(static_cast<unsigned int>(127 + k) << 23);
+    d.scale[d.N + i] = __uint_as_float(static_cast<unsigned int>(127 - k) << 23);
   }
-  p.scale[i] = __uint_as_float(static_cast<unsigned int>(127 + k) << 23);
-  p.scale[p.N + i] = __uint_as_float(static_cast<unsigned int>(127 - k) << 23);
 }
 
 }  // namespace
 
-cudaError_t launch_member_scales_from_keys(const ScaleParams& p, cudaStream_t s) {
-  member_scale_kernel<<<(p.N + 255) / 256, 256, 0, s>>>(p, false);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_member_scales(const ScaleParams& p, int sms, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(p.maxkey, 0, static_cast<size_t>(p.N) * sizeof(unsigned int), s);
-  if (e != cudaSuccess) return e;
-  ScaleParams q = p;
-  // about four CTAs per SM over all members, segments of at least 4096 cells
-  const int64_t want = std::max<int64_t>(1, (4LL * sms + p.N - 1) / p.N);
-  const int64_t segs = std::max<int64_t>(1, std::min<int64_t>(want, (p.M + 4095) / 4096));
-  q.seg_cells = static_cast<int32_t>(((p.M + segs - 1) / segs + 1023) / 1024 * 1024);
-  const dim3 grid(static_cast<unsigned>((p.M + q.seg_cells - 1) / q.seg_cells), static_cast<unsigned>(p.N));
-  const bool proxy = p.iso_mode != ISO_NONE && p.w == nullptr;
-  if (proxy) member_max_kernel<true><<<grid, kScaleThreads, 0, s>>>(q);
-  else member_max_kernel<false><<<grid, kScaleThreads, 0, s>>>(q);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  member_scale_kernel<<<(p.N + 255) / 256, 256, 0, s>>>(q, proxy);
+cudaError_t launch_member_scales(const ScaleBatchParams& p, cudaStream_t s) {
+  if (p.n <= 0 || p.n > kScaleBatch) return cudaErrorInvalidValue;
+  if (p.total_blocks > 0) {
+    member_max_kernel<<<p.total_blocks, kScaleThreads, 0, s>>>(p);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  member_scale_kernel<<<p.n, kScaleThreads, 0, s>>>(p);
   return cudaGetLastError();
 }
 

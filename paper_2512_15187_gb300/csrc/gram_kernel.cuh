@@ -589,13 +589,29 @@ __global__ void __launch_bounds__(gram_threads<G, EXACT>(), 1) gram_kernel(const
         } else {
           sum_partials<VEC, G>(s, rb + lane * VEC, T);
         }
+        // uniform branches on the weights and on padding rows, as in the streaming kernel
+        if (has_w) {
 #pragma unroll
-        for (int m = 0; m < MPW; ++m) {
+          for (int m = 0; m < MPW; ++m) {
+            if (q + m * G < N) {
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            const float t = has_w ? wv[v] * x[m][v] : x[m][v];
-            accM[m] += t;
-            accA[m] = fmaf(t, s[v], accA[m]);
+              for (int v = 0; v < VEC; ++v) {
+                const float t = wv[v] * x[m][v];
+                accM[m] += t;
+                accA[m] = fmaf(t, s[v], accA[m]);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < MPW; ++m) {
+            if (q + m * G < N) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) {
+                accM[m] += x[m][v];
+                accA[m] = fmaf(x[m][v], s[v], accA[m]);
+              }
+            }
           }
         }
       } else {

@@ -220,7 +220,7 @@ cudaError_t launch_gram(const GramParams& p, int G, int mpw, bool wide, int prec
 cudaError_t gram_kernels_init(int max_smem);
 // Per-member E4M3 operand scales (gram_kernel.cu): s_i is the largest power of two with
 // max_x u_i(x) sqrt(w_x) s_i <= 448, the largest finite E4M3 value.
-struct ScaleParams {
+struct ScaleDesc {
   const float* data;       // [N][ld] soft masks, or fields mapped by iso_mode
   const float* w;          // [M] cell measures or nullptr
   int64_t ld;
@@ -228,16 +228,27 @@ struct ScaleParams {
   int32_t iso_mode;
   float iso_mu, iso_inv, iso_t;
   int32_t vec_ok;          // rows and weights 16-byte aligned: 4-cell vector loads
+  int32_t proxy;           // unweighted fields: reduce the proxy of F (see iso_proxy)
+  int32_t from_keys;       // the maxima are already reduced into the region's keys
+  int32_t segs;            // CTAs per member of the max pass (segs * N <= kScaleMaxSlots)
   int32_t seg_cells;       // cells per CTA (a multiple of 1024)
-  unsigned int* maxkey;    // [N] order-preserving keys of the per-member maxima (workspace)
-  float* scale;            // [2N] out: s_i, then 1/s_i
+  int32_t block_begin;     // the ensemble's first CTA in the max pass
+  float* scale;            // scale region: [2N] out (s_i, then 1/s_i), then keys or CTA maxima
 };
-// Zero the keys, reduce the per-member maxima and write the scales (three launches).
-cudaError_t launch_member_scales(const ScaleParams& p, int sms, cudaStream_t s);
-// The scales from keys that a streaming pass has already reduced (p.maxkey, p.N, p.scale).
-cudaError_t launch_member_scales_from_keys(const ScaleParams& p, cudaStream_t s);
-// Workspace of one ensemble's scales: [2N] floats and [N] keys, for N <= 512.
+// Ensembles per scale launch (the descriptors travel as kernel parameters).
+constexpr int kScaleBatch = 32;
+struct ScaleBatchParams {
+  int32_t n;               // descriptors
+  int32_t total_blocks;    // CTAs of the max pass (descriptors with from_keys = 0)
+  ScaleDesc d[kScaleBatch];
+};
+// The per-member maxima of every descriptor that has no keys yet (one launch, each CTA
+// writing the maximum of its segment), then every descriptor's scales (one launch).
+cudaError_t launch_member_scales(const ScaleBatchParams& p, cudaStream_t s);
+// Workspace of one ensemble's scales: [2N] floats, then from float 2 * 512 on either [N]
+// reduction keys (maxima reduced by a streaming pass) or [N][segs] CTA maxima.
 constexpr size_t kScaleBytes = 8192;
+constexpr int kScaleMaxSlots = static_cast<int>(kScaleBytes / 4) - 2 * kGramTiledMaxN;
 // Row-block-tiled Gram (gram_tiled.cu).
 cudaError_t launch_gram_operands(const OperandParams& p, int prec, cudaStream_t s);
 cudaError_t launch_gram_tiled(const TiledParams& p, int prec, int grid, size_t smem, cudaStream_t s);

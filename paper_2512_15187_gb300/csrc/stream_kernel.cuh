@@ -603,26 +603,65 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         } else if constexpr (G == 2) {
           sum_partials<VEC, G>(s, rb + lane * VEC, T);
         }
-        // Per-member accumulation: m_i += w u_i, A_i += w u_i s.
+        // Per-member accumulation: m_i += w u_i, A_i += w u_i s. The branches on the
+        // weights and on padding rows (i >= N: zeros, nothing to add) are uniform across
+        // the warp; the arithmetic of each member is the same on every path. (The
+        // one-cell-per-lane classes keep a single loop: the duplicated code costs them
+        // registers.)
+        if constexpr (VEC == 1) {
 #pragma unroll
-        for (int k = 0; k < MPW; ++k) {
-#pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            const float t = has_w ? wv[v] * x[k][v] : x[k][v];
+          for (int k = 0; k < MPW; ++k) {
+            const float t = has_w ? wv[0] * x[k][0] : x[k][0];
             accM[k] += t;
-            accA[k] = fmaf(t, s[v], accA[k]);
+            accA[k] = fmaf(t, s[0], accA[k]);
+          }
+        } else if (has_w) {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k) {
+            if (q + k * G < N) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) {
+                const float t = wv[v] * x[k][v];
+                accM[k] += t;
+                accA[k] = fmaf(t, s[v], accA[k]);
+              }
+            }
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < MPW; ++k) {
+            if (q + k * G < N) {
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) {
+                accM[k] += x[k][v];
+                accA[k] = fmaf(x[k][v], s[v], accA[k]);
+              }
+            }
           }
         }
-        if constexpr (MAXU) {
+        if constexpr (MAXU && VEC == 1) {
           // the operand u sqrt(w), rounded as the Gram kernels round it
-          float sw[VEC];
+          const float sw = has_w ? sqrtf(wv[0]) : 1.f;
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) sw[v] = has_w ? sqrtf(wv[v]) : 1.f;
+          for (int k = 0; k < MPW; ++k) accX[k] = fmaxf(accX[k], has_w ? x[k][0] * sw : x[k][0]);
+        } else if constexpr (MAXU) {
+          // the operand u sqrt(w), rounded as the Gram kernels round it
+          if (has_w) {
+            float sw[VEC];
 #pragma unroll
-          for (int k = 0; k < MPW; ++k)
+            for (int v = 0; v < VEC; ++v) sw[v] = sqrtf(wv[v]);
 #pragma unroll
-            for (int v = 0; v < VEC; ++v)
-              accX[k] = fmaxf(accX[k], has_w ? x[k][v] * sw[v] : x[k][v]);
+            for (int k = 0; k < MPW; ++k)
+              if (q + k * G < N)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) accX[k] = fmaxf(accX[k], x[k][v] * sw[v]);
+          } else {
+#pragma unroll
+            for (int k = 0; k < MPW; ++k)
+              if (q + k * G < N)
+#pragma unroll
+                for (int v = 0; v < VEC; ++v) accX[k] = fmaxf(accX[k], x[k][v]);
+          }
         }
       }
       if (aborted) break;
