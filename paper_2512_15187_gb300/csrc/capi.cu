@@ -364,7 +364,9 @@ pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
     if (ok && in.w) ok = encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), static_cast<uint32_t>(TS));
     pl->use_tma = ok;
   }
-  pl->stage_floats = static_cast<int32_t>(round_up(int64_t(d.n_boxes) * d.box_rows * TS + TS, 32));
+  // rows of TS cells (TMA), or of TS + 4: the 16-byte-aligned spans the cp.async path copies
+  const int64_t row_floats = pl->use_tma ? TS : TS + 4;
+  pl->stage_floats = static_cast<int32_t>(round_up(int64_t(d.n_boxes) * d.box_rows * row_floats + TS, 32));
   pl->part_bytes = round_up(static_cast<int64_t>(d.n_chunks) * 2 * in.N * 8, 256);
   pl->sums_bytes = round_up((4 * in.N + in.N * in.N) * 8, 256);
   pl->coef_bytes = round_up(in.N * 4, 256);

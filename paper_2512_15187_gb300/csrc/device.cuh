@@ -88,6 +88,13 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, uint32_t b
                "r"(bytes)
                : "memory");
 }
+// 16-byte copy of which the first `bytes` (0..16) are read and the rest zero-filled; both
+// addresses 16-byte aligned. Cached in L2 only.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(bytes)
+               : "memory");
+}
 // Arrive on `bar` once this thread's earlier cp.async copies have landed (the arrival counts
 // toward the barrier's expected count).
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {

@@ -239,6 +239,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   // width is a compile-time constant, so row offsets fold into the shared-memory loads.
   constexpr int SUB = 1;
   constexpr int TS = SUB * T;
+  // Row stride of a stage: TMA stores rows back to back; the cp.async path stores each
+  // row's enclosing 16-byte-aligned span (4 floats more), the row's first cell `roff` floats in.
+  constexpr int RS = TMA ? TS : TS + 4;
 
   float* ring = reinterpret_cast<float*>(smem);
   float* red = ring + static_cast<size_t>(NG) * depth * SF;
@@ -383,32 +386,46 @@ stream_kernel(const __grid_constant__ StreamParams p) {
 #pragma unroll
     for (int k = 0; k < (MAXU ? MPW : 1); ++k) accX[k] = 0.f;
 
-    // Rows that are not 16-byte aligned: warp q copies the cells of its members' rows (warp
-    // 0 also the cell measures) with 4-byte cp.async into the ring, `depth` stages of this
-    // chunk ahead, each instruction 32 consecutive cells of one row (128 coalesced bytes);
-    // cells past M are zero-filled without a read. Every thread arrives on the stage's
-    // barrier once its copies have landed, so the stage is whole when the barrier completes.
+    // Rows that are not 16-byte aligned (no TMA): each stage holds, per member row, the
+    // 16-byte-aligned span that encloses the stage's cells, its first cell `ro` floats
+    // before the stage's first cell, copied in 16-byte pieces by the warp that owns the row
+    // (its lanes take the rows' pieces in turn). A piece reads only the row's cells below M
+    // (zero-filling the rest) and pieces wholly past M are skipped: cells past M are masked
+    // to zero after they are read. A span starts at most 3 cells before the row's first
+    // cell, inside the previous row; only row 0's first piece can start before the data,
+    // and it is copied cell by cell from cell 0 on (the cells before are never read).
+    // Warp 0 also copies the cell measures with 4-byte copies. Every thread arrives on the
+    // stage's barrier once its copies have landed.
+    const int boff = static_cast<int>((reinterpret_cast<uintptr_t>(d.data) >> 2) & 3u);
+    const int ld3 = static_cast<int>(d.ld & 3);
     auto cpa_issue = [&](int st_i, int slot_i) {
-      float* dst = my_ring + static_cast<size_t>(slot_i) * SF + lane;
-      const int xs = cell0 + st_i * TS + lane;
-#pragma unroll
-      for (int k = 0; k < MPW; ++k) {
+      float* stage = my_ring + static_cast<size_t>(slot_i) * SF;
+      const int xs0 = cell0 + st_i * TS;   // the stage's first cell (a multiple of 32)
+      constexpr int NC = TS / 4 + 1;       // 16-byte pieces per row span
+      for (int t = lane; t < MPW * NC; t += 32) {
+        const int k = t / NC, c = t - k * NC;
         const int i = q + k * G;
-        if (i < N) {
-          const float* src = d.data + static_cast<int64_t>(i) * d.ld;
+        const int ro = (boff + i * ld3) & 3;
+        const int first = xs0 - ro + 4 * c;   // the piece's first cell (row-relative)
+        const int left = M - first;
+        if (i < N && left > 0) {
+          float* dst = stage + static_cast<size_t>(i) * RS + 4 * c;
+          const float* row = d.data + static_cast<int64_t>(i) * d.ld;
+          if (first >= 0 || i > 0) {
+            cp_async16(dst, row + first, left >= 4 ? 16u : static_cast<uint32_t>(4 * left));
+          } else {
 #pragma unroll
-          for (int v = 0; v < VEC; ++v) {
-            const bool in = xs + 32 * v < M;
-            cp_async4(dst + static_cast<size_t>(i) * TS + 32 * v, src + (in ? xs + 32 * v : 0),
-                      in ? 4u : 0u);
+            for (int e = 0; e < 4; ++e)
+              if (first + e >= 0 && first + e < M) cp_async4(dst + e, row + first + e, 4u);
           }
         }
       }
       if (q == 0 && has_w) {
+        const int xs = xs0 + lane;
 #pragma unroll
         for (int v = 0; v < VEC; ++v) {
           const bool in = xs + 32 * v < M;
-          cp_async4(dst + SF - TS + 32 * v, d.w + (in ? xs + 32 * v : 0), in ? 4u : 0u);
+          cp_async4(stage + SF - TS + lane + 32 * v, d.w + (in ? xs + 32 * v : 0), in ? 4u : 0u);
         }
       }
       cp_async_arrive(&my_bars[slot_i]);
@@ -439,7 +456,15 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         for (int k = 0; k < MPW; ++k) {
           const int i = q + k * G;
           if (i < N) {
-            lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
+            if constexpr (TMA) {
+              lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
+            } else {
+              // the row's cells start `ro` floats into its span: scalar loads
+              const int ro = (boff + i * ld3) & 3;
+              const float* src = sb + static_cast<size_t>(i) * RS + ro + j * T + lane * VEC;
+#pragma unroll
+              for (int v = 0; v < VEC; ++v) x[k][v] = src[v];
+            }
           } else {
 #pragma unroll
             for (int v = 0; v < VEC; ++v) x[k][v] = pad;
