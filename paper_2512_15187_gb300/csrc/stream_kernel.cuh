@@ -79,6 +79,33 @@ __device__ __forceinline__ void lds_vec(float (&dst)[VEC], const float* src) {
   }
 }
 
+// VEC floats starting `ro` (0..3) floats after `base` (VEC-aligned, in a row with at least
+// 4 floats after the VEC read): aligned vector loads, shifted by the warp-uniform ro.
+template <int VEC>
+__device__ __forceinline__ void lds_shifted(float (&dst)[VEC], const float* base, int ro) {
+  if constexpr (VEC == 1) {
+    dst[0] = base[ro];
+  } else if constexpr (VEC == 2) {
+    if ((ro & 1) == 0) {
+      lds_vec<2>(dst, base + ro);
+    } else {
+      const float2 a = *reinterpret_cast<const float2*>(base + ro - 1);
+      const float2 b = *reinterpret_cast<const float2*>(base + ro + 1);
+      dst[0] = a.y; dst[1] = b.x;
+    }
+  } else {
+    const float4 a = *reinterpret_cast<const float4*>(base);
+    if (ro == 0) {
+      dst[0] = a.x; dst[1] = a.y; dst[2] = a.z; dst[3] = a.w;
+    } else {
+      const float4 b = *reinterpret_cast<const float4*>(base + 4);
+      if (ro == 1) { dst[0] = a.y; dst[1] = a.z; dst[2] = a.w; dst[3] = b.x; }
+      else if (ro == 2) { dst[0] = a.z; dst[1] = a.w; dst[2] = b.x; dst[3] = b.y; }
+      else { dst[0] = a.w; dst[1] = b.x; dst[2] = b.y; dst[3] = b.z; }
+    }
+  }
+}
+
 // Streaming (evict-first) global store of VEC consecutive floats.
 template <int VEC>
 __device__ __forceinline__ void stg_cs_vec(float* dst, const float (&src)[VEC]) {
@@ -398,27 +425,44 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     // stage's barrier once its copies have landed.
     const int boff = static_cast<int>((reinterpret_cast<uintptr_t>(d.data) >> 2) & 3u);
     const int ld3 = static_cast<int>(d.ld & 3);
+    // Lane l copies piece l % PR (of the PR = TS / 4 main pieces of a span) of rows
+    // r RPI + l / PR for every r; lane k also copies the span's last piece of row k (the
+    // classes of 28 and 32 members per warp walk the pieces in one strided loop instead).
+    constexpr int PR = TS / 4;          // main 16-byte pieces of a span (the last is extra)
+    constexpr int RPI = 32 / PR;        // rows per copy instruction
+    static_assert(TMA || MPW % RPI == 0, "a warp's rows fill whole copy instructions");
+    auto cpa_piece = [&](float* stage, int xs0, int i, int pc) {
+      const int ro = (boff + i * ld3) & 3;
+      const int first = xs0 - ro + 4 * pc;   // the piece's first cell (row-relative)
+      const int left = M - first;
+      if (left <= 0) return;
+      float* dst = stage + static_cast<size_t>(i) * RS + 4 * pc;
+      const float* row = d.data + static_cast<int64_t>(i) * d.ld;
+      if (first >= 0 || i > 0) {
+        cp_async16(dst, row + first, left >= 4 ? 16u : static_cast<uint32_t>(4 * left));
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (first + e >= 0 && first + e < M) cp_async4(dst + e, row + first + e, 4u);
+      }
+    };
     auto cpa_issue = [&](int st_i, int slot_i) {
       float* stage = my_ring + static_cast<size_t>(slot_i) * SF;
       const int xs0 = cell0 + st_i * TS;   // the stage's first cell (a multiple of 32)
-      constexpr int NC = TS / 4 + 1;       // 16-byte pieces per row span
-      for (int t = lane; t < MPW * NC; t += 32) {
-        const int k = t / NC, c = t - k * NC;
-        const int i = q + k * G;
-        const int ro = (boff + i * ld3) & 3;
-        const int first = xs0 - ro + 4 * c;   // the piece's first cell (row-relative)
-        const int left = M - first;
-        if (i < N && left > 0) {
-          float* dst = stage + static_cast<size_t>(i) * RS + 4 * c;
-          const float* row = d.data + static_cast<int64_t>(i) * d.ld;
-          if (first >= 0 || i > 0) {
-            cp_async16(dst, row + first, left >= 4 ? 16u : static_cast<uint32_t>(4 * left));
-          } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-              if (first + e >= 0 && first + e < M) cp_async4(dst + e, row + first + e, 4u);
-          }
+      if constexpr (VEC == 1 && MPW > 24) {
+        // the widest classes: the warp's pieces in one strided loop (fewer registers)
+        for (int t = lane; t < MPW * (PR + 1); t += 32) {
+          const int k = t / (PR + 1), c = t - k * (PR + 1);
+          if (q + k * G < N) cpa_piece(stage, xs0, q + k * G, c);
         }
+      } else {
+        const int sr = lane / PR, pc = lane - sr * PR;
+#pragma unroll
+        for (int r = 0; r < MPW / RPI; ++r) {
+          const int i = q + (r * RPI + sr) * G;
+          if (i < N) cpa_piece(stage, xs0, i, pc);
+        }
+        if (lane < MPW && q + lane * G < N) cpa_piece(stage, xs0, q + lane * G, PR);
       }
       if (q == 0 && has_w) {
         const int xs = xs0 + lane;
@@ -459,11 +503,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
             if constexpr (TMA) {
               lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
             } else {
-              // the row's cells start `ro` floats into its span: scalar loads
-              const int ro = (boff + i * ld3) & 3;
-              const float* src = sb + static_cast<size_t>(i) * RS + ro + j * T + lane * VEC;
-#pragma unroll
-              for (int v = 0; v < VEC; ++v) x[k][v] = src[v];
+              // the row's cells start `ro` floats into its span (the same for the warp)
+              lds_shifted<VEC>(x[k], sb + static_cast<size_t>(i) * RS + j * T + lane * VEC,
+                               (boff + i * ld3) & 3);
             }
           } else {
 #pragma unroll
