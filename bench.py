@@ -755,7 +755,8 @@ def fields_2d_record(h, dev, stream, args, rank, peaks):
         t_ms = b0.elapsed_time(b1) / args.other_steps
         kt = kernel_table(prof, peaks, sustained=False)
         dom = max(kt, key=lambda k: kt[k]["share"])
-        traffic = ncu_traffic("stream_kernel_fields_exact_64x512x512") if mode == "linear" else None
+        traffic = ncu_traffic("stream_kernel_fields_pidmean_64x512x512") if mode == "mean" else (
+            ncu_traffic("gram_kernel_bf16_fields_64x512x512") if prec == "bf16" else None)
         rec["paths"][name] = {"value": E * N * M / (t_ms * 1e-3), "unit": UNIT, "ms_per_step": t_ms,
                               "roofline": roofline_record(dom, {**prof[dom]}, peaks, False, traffic),
                               "kernels": kt}

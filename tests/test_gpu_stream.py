@@ -86,6 +86,26 @@ def test_unaligned_stride_uses_generic_loads(H):
     H.sync()
 
 
+@pytest.mark.parametrize("N", [37, 200, 300, 500])      # one, two and one cell per lane classes
+@pytest.mark.parametrize("boff,pad", [(1, 1), (2, 2), (3, 5)])
+def test_unaligned_spans_every_class(H, N, boff, pad):
+    """Rows staged as 16-byte-aligned spans: a base `boff` floats past an aligned address
+    (row 0's first span would start before the data), row strides of M + pad floats (every
+    row at another offset in its span), a ragged last stage, cell measures, PID-mean and
+    the exact full PID (which also streams the rows a second time)."""
+    import torch
+    M = 1003
+    U = synth.random_soft(N, M, seed=N + 17 * boff, binary_frac=0.2)
+    w = np.random.default_rng(N + boff).uniform(0.1, 10, M).astype(np.float32)
+    ld = M + pad
+    buf = torch.zeros(boff + N * ld, dtype=torch.float32, device="cuda")
+    view = buf[boff:].view(N, ld)[:, :M]
+    view.copy_(_dev(U))
+    _check(H.mean(view, _dev(w)), O.pid_mean(U, w), what=f"mean N={N} boff={boff} ld=M+{pad}")
+    _check(H.full(view, mode="linear"), O.pid(U), what=f"linear N={N} boff={boff} ld=M+{pad}")
+    H.sync()
+
+
 def test_zero_mass_and_binary_members(H):
     N, M = 6, 900
     U = synth.random_soft(N, M, seed=2)
