@@ -103,6 +103,12 @@ pid_status launch_member_scales_many(pid_handle h, const std::vector<ScaleJob>& 
     std::memset(&sb, 0, sizeof(sb));
     double bytes = 0.0;
     const size_t j1 = std::min(jobs.size(), j0 + kScaleBatch);
+    // member rows of this launch that need a max pass: about four CTAs per SM over all of
+    // them (the maxima are exact whatever the segments, so the scales do not depend on it)
+    int64_t rows = 0;
+    for (size_t j = j0; j < j1; ++j)
+      if (!jobs[j].from_keys) rows += jobs[j].in.N;
+    const int64_t want = std::max<int64_t>(1, (4LL * h->sms + rows - 1) / std::max<int64_t>(1, rows));
     for (size_t j = j0; j < j1; ++j) {
       const EnsInput& in = jobs[j].in;
       ScaleDesc& d = sb.d[sb.n++];
@@ -121,9 +127,7 @@ pid_status launch_member_scales_many(pid_handle h, const std::vector<ScaleJob>& 
         bytes += 4.0 * in.N;
         continue;
       }
-      // about four CTAs per SM over the members, segments of at least 4096 cells, and the
-      // CTA maxima within the region
-      const int64_t want = std::max<int64_t>(1, (4LL * h->sms + in.N - 1) / in.N);
+      // segments of at least 4096 cells, the CTA maxima within the region
       int64_t segs = std::max<int64_t>(
           1, std::min({want, (in.M + 4095) / 4096, static_cast<int64_t>(kScaleMaxSlots) / in.N}));
       d.seg_cells = static_cast<int32_t>(((in.M + segs - 1) / segs + 1023) / 1024 * 1024);
