@@ -200,8 +200,8 @@ bool encode_1d(CUtensorMap* m, const void* base, uint64_t n, uint32_t box) {
 static const StreamCfg kStreamClasses[] = {
     {4, 1, 128, 1, 8},  {4, 2, 128, 1, 8},   {4, 4, 128, 1, 6},  {4, 4, 128, 1, 8},
     {4, 8, 128, 1, 6},  {4, 8, 128, 1, 8},   {4, 16, 128, 1, 6}, {4, 16, 128, 1, 8},
-    {2, 16, 64, 1, 12}, {2, 16, 64, 1, 16},  {1, 16, 32, 1, 20}, {1, 16, 32, 1, 24},
-    {1, 16, 32, 1, 28}, {1, 16, 32, 1, 32}};
+    {2, 16, 64, 1, 12}, {2, 16, 64, 1, 13},  {2, 16, 64, 1, 16}, {1, 16, 32, 1, 20},
+    {1, 16, 32, 1, 24}, {1, 16, 32, 1, 28},  {1, 16, 32, 1, 32}};
 constexpr int kNumStreamClasses = sizeof(kStreamClasses) / sizeof(kStreamClasses[0]);
 
 static int default_stream_class(int64_t N) {

@@ -29,6 +29,7 @@ PIDK_CLASS(4, 8, 8)
 PIDK_CLASS(4, 6, 16)
 PIDK_CLASS(4, 8, 16)
 PIDK_CLASS(2, 12, 16)
+PIDK_CLASS(2, 13, 16)
 PIDK_CLASS(2, 16, 16)
 PIDK_CLASS(1, 20, 16)
 PIDK_CLASS(1, 24, 16)
@@ -50,6 +51,7 @@ cudaError_t launch_stream(const StreamParams& p, int vec, int mpw, int G, int is
   PIDK_CASE(4, 6, 16)
   PIDK_CASE(4, 8, 16)
   PIDK_CASE(2, 12, 16)
+  PIDK_CASE(2, 13, 16)
   PIDK_CASE(2, 16, 16)
   PIDK_CASE(1, 20, 16)
   PIDK_CASE(1, 24, 16)
@@ -74,6 +76,7 @@ cudaError_t stream_kernels_init(int max_smem) {
   if (e == cudaSuccess) e = init_stream_c4_6_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c4_8_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c2_12_16(max_smem);
+  if (e == cudaSuccess) e = init_stream_c2_13_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c2_16_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c1_20_16(max_smem);
   if (e == cudaSuccess) e = init_stream_c1_24_16(max_smem);

@@ -427,10 +427,11 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     const int ld3 = static_cast<int>(d.ld & 3);
     // Lane l copies piece l % PR (of the PR = TS / 4 main pieces of a span) of rows
     // r RPI + l / PR for every r; lane k also copies the span's last piece of row k (the
-    // classes of 28 and 32 members per warp walk the pieces in one strided loop instead).
+    // classes of 28 and 32 members per warp, and odd member counts, walk the pieces in one
+    // strided loop instead).
     constexpr int PR = TS / 4;          // main 16-byte pieces of a span (the last is extra)
     constexpr int RPI = 32 / PR;        // rows per copy instruction
-    static_assert(TMA || MPW % RPI == 0, "a warp's rows fill whole copy instructions");
+
     auto cpa_piece = [&](float* stage, int xs0, int i, int pc) {
       const int ro = (boff + i * ld3) & 3;
       const int first = xs0 - ro + 4 * pc;   // the piece's first cell (row-relative)
@@ -449,8 +450,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     auto cpa_issue = [&](int st_i, int slot_i) {
       float* stage = my_ring + static_cast<size_t>(slot_i) * SF;
       const int xs0 = cell0 + st_i * TS;   // the stage's first cell (a multiple of 32)
-      if constexpr (VEC == 1 && MPW > 24) {
-        // the widest classes: the warp's pieces in one strided loop (fewer registers)
+      if constexpr ((VEC == 1 && MPW > 24) || MPW % RPI != 0) {
+        // the widest classes (fewer registers), and member counts that do not fill whole
+        // copy instructions: the warp's pieces in one strided loop
         for (int t = lane; t < MPW * (PR + 1); t += 32) {
           const int k = t / (PR + 1), c = t - k * (PR + 1);
           if (q + k * G < N) cpa_piece(stage, xs0, q + k * G, c);

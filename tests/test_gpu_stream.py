@@ -38,11 +38,12 @@ def _check(o, ref, tol=FP32_TOL, what=""):
     assert_rank_agrees_outside_ties(to_np(o["rank"]), d, tol)
 
 
-# every tile class (members <= 8, 16, 24, 32, 48, 64, 96, 128, 192, 256, 320, 384, 448,
+# every tile class (members <= 8, 16, 24, 32, 48, 64, 96, 128, 192, 208, 256, 320, 384, 448,
 # 512), filled and partly filled, with ragged cell counts
 SHAPES = [(1, 1), (1, 300), (2, 7), (3, 129), (7, 1000), (8, 4099), (9, 513), (16, 2000),
           (17, 3001), (24, 2500), (31, 777), (33, 5000), (48, 3000), (64, 4097), (65, 2049),
-          (96, 1000), (128, 1025), (129, 999), (192, 800), (200, 1500), (256, 640), (257, 333),
+          (96, 1000), (128, 1025), (129, 999), (192, 800), (193, 777), (200, 1500), (208, 1001),
+          (256, 640), (257, 333),
           (350, 300), (384, 257), (420, 260), (448, 130), (500, 450), (512, 257)]
 
 
