@@ -8,6 +8,8 @@
 // tensor cores runs one Gram launch per class instead of the first streaming pass; above 256
 // members the Gram is row-block-tiled (operands staged in HBM, one launch pair per ensemble)
 // and the ensemble's exact PID-mean sums come from the first streaming pass of its class.
+// Items over the same data share first passes: a Gram item of soft masks takes the (m, A)
+// of a PID-mean or exact item's pass, and a PID-mean item those of an exact item's pass.
 //
 // The whole sequence (descriptor upload + launches) is recorded once into a CUDA graph and
 // replayed while the caller submits the same batch layout (same pointers and shapes).
@@ -256,13 +258,43 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
   // plan, hence bitwise the same partials); BF16 and split-BF16 items take a sibling's
   // partials unless the handle keeps every item bitwise equal to its single call (serving).
   const bool share = !h->batch || h->batch->share_sums;
+  // A PID-mean item whose masks (or fields) the batch also streams for an exact full PID
+  // takes that item's first-pass partials instead of a pass of its own: both passes sum
+  // m_i and N A_i (Eq. 6, 16; the exact full PID's IN_in is the same A_i / m_i, Eq. 17), and
+  // with the same data, cell measures, isovalue map and tile plan they sum them in the same
+  // order, so the shared partials are bitwise those the item's own pass would give.
+  std::vector<int> mshare(count, -1);
+  if (!st4 && share) {
+    auto same_iso = [&](const EnsInput& a, const EnsInput& b) {
+      return !a.is_field || (a.iso.kind == b.iso.kind && a.iso.superlevel == b.iso.superlevel &&
+                             a.iso.mu == b.iso.mu && a.iso.sigma == b.iso.sigma);
+    };
+    for (int e = 0; e < count; ++e) {
+      if (is_gram[e] || is_lin[e]) continue;
+      for (int f = 0; f < count && mshare[e] < 0; ++f) {
+        if (!is_lin[f] || in[f].data != in[e].data || in[f].N != in[e].N || in[f].M != in[e].M ||
+            in[f].ld != in[e].ld || in[f].w != in[e].w || in[f].is_field != in[e].is_field ||
+            !same_iso(in[f], in[e]) || in[f].validate < in[e].validate)
+          continue;
+        const EnsPlan &a = pl[e], &b = pl[f];
+        if (a.cfg.vec == b.cfg.vec && a.cfg.G == b.cfg.G && a.cfg.mpw == b.cfg.mpw &&
+            a.cfg.sub == b.cfg.sub && a.use_tma == b.use_tma &&
+            a.desc.n_chunks == b.desc.n_chunks && a.desc.chunk_cells == b.desc.chunk_cells &&
+            a.desc.iso_mode == b.desc.iso_mode && a.desc.iso_mu == b.desc.iso_mu &&
+            a.desc.iso_inv == b.desc.iso_inv && a.desc.iso_t == b.desc.iso_t)
+          mshare[e] = f;
+      }
+    }
+  }
   std::vector<int> sib(count, -1), own_pass(count, 0);
   if (!st4) {
     for (int e = 0; e < count; ++e) {
       if (!is_gram[e] || tiled[e] || in[e].is_field) continue;
       if (!share && in[e].precision != PID_FP8) continue;
       for (int f = 0; f < count && sib[e] < 0; ++f) {
-        if (f != e && !(is_gram[f] && !tiled[f]) && !in[f].is_field && in[f].data == in[e].data &&
+        // (a PID-mean item that shares an exact item's pass runs none of its own)
+        if (f != e && !(is_gram[f] && !tiled[f]) && !in[f].is_field && mshare[f] < 0 &&
+            in[f].data == in[e].data &&
             in[f].N == in[e].N && in[f].M == in[e].M && in[f].ld == in[e].ld && in[f].w == in[e].w)
           sib[e] = f;
       }
@@ -289,7 +321,8 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
                pl[e].cfg.mpw}].push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
-      pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, pl[e].use_tma ? 1 : 0, pl[e].cfg.mpw}].push_back(e);
+      if (mshare[e] < 0)
+        pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, pl[e].use_tma ? 1 : 0, pl[e].cfg.mpw}].push_back(e);
       if (is_lin[e]) {
         // stored soft masks are 16-byte aligned rows, read through TMA in pass 2
         const int tma2 = stored[e] ? 1 : (pl[e].use_tma ? 1 : 0);
@@ -438,6 +471,10 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       f.depth = o.depth; f.in_in = o.in_in; f.in_out = o.in_out; f.rank = o.rank;
     }
     if (kind != FIN_LIN2) { f.mass = o.mass; f.mean_depth = o.mean_depth; }
+    if (kind == FIN_MEAN && mshare[e] >= 0) {   // (m, A) from the exact item's first pass
+      f.part = part[mshare[e]];
+      f.n_chunks = pl[mshare[e]].desc.n_chunks;
+    }
     if (kind == FIN_GRAM) {
       f.gpart = gpart[e];
       f.n_gchunks = steps * gram_chunks(e);

@@ -162,3 +162,43 @@ def test_profiled_graph_replays_time_every_launch(H):
         for k in ("depth", "in_in", "in_out", "rank"):
             assert torch.equal(a[k], b[k]), k
     h.close()
+
+
+def test_pid_mean_shares_the_exact_items_first_pass():
+    """A PID-mean item and an exact full-PID item over the same data run one first pass
+    between them (both sum m_i and A_i, Eq. 6, 16, 17): every result stays bitwise that of
+    its single call, and the streaming kernels read such an ensemble twice (pass 1 and
+    pass 2), not three times. A PID-mean item under another isovalue map runs its own pass."""
+    import torch
+    from paper_2512_15187_gb300 import binding
+    h = binding.Handle(0)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    items, expect = [], 0.0
+    # 16-byte aligned rows, rows that are not (odd M), weighted cells
+    for N, M, weighted in [(64, 40000, False), (37, 9001, True), (200, 30003, False)]:
+        U = torch.rand((N, M), generator=g, device="cuda")
+        w = torch.rand(M, generator=g, device="cuda") + 0.5 if weighted else None
+        items += [dict(data=U, w=w, mode="mean"), dict(data=U, w=w, mode="linear")]
+        expect += 2 * (4.0 * N * M + (4.0 * M if weighted else 0.0))
+    F = torch.randn((20, 5000), generator=g, device="cuda")
+    items += [dict(data=F, iso=(0.1, 0.5, 0), mode="mean"),
+              dict(data=F, iso=(0.1, 0.5, 0), mode="linear"),
+              dict(data=F, iso=(0.2, 0.5, 0), mode="mean")]
+    expect += 3 * 4.0 * F.numel()
+    h.profile(True)
+    outs = h.batch(items)
+    h.sync()
+    prof = h.profile_read()
+    h.profile(False)
+    assert prof["stream"]["bytes"] == expect, (prof["stream"]["bytes"], expect)
+    for it, o in zip(items, outs):
+        if it.get("iso") is None:
+            single = h.mean(it["data"], it["w"]) if it["mode"] == "mean" else \
+                h.full(it["data"], it["w"], mode="linear")
+        else:
+            mu, sg, sup = it["iso"]
+            single = h.from_fields(it["data"], mu, sg, superlevel=bool(sup), mode=it["mode"])
+        h.sync()
+        for k in ("in_in", "in_out", "depth", "rank"):
+            assert torch.equal(o[k], single[k]), (it["mode"], tuple(it["data"].shape), k)
+    h.close()
