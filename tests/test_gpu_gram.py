@@ -155,6 +155,20 @@ def test_split_bf16_is_much_tighter(H):
     assert errs["bf16"] <= GRAM_TOL and errs["fp8"] <= GRAM_TOL, errs
 
 
+@pytest.mark.parametrize("N,weighted", [(150, False), (200, True), (208, False), (256, True)])
+def test_split_bf16_wide_tile_is_much_tighter(H, N, weighted):
+    """The wide tile (128 < N <= 256: two row blocks, the second against the columns from
+    128 on, mirrored by the drain) keeps split BF16's accuracy: depths, IN_out, P and the
+    raw Gram within 2e-5, with and without cell measures, on TMA and cp.async rows."""
+    M = 30011 if weighted else 30016   # rows staged by cp.async, and by TMA
+    U = synth.random_soft(N, M, seed=N + 17, binary_frac=0.1)
+    w = np.random.default_rng(N).uniform(0.2, 5, M).astype(np.float32) if weighted else None
+    o = H.full(_dev(U), None if w is None else _dev(w), mode="full", precision="split_bf16",
+               want_P=True, want_err=True)
+    H.sync()
+    _check(o, U, w, 2e-5, f"split wide N={N} w={weighted}", raw_bound=2e-5)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_gram_binary_masks_are_exact(H, prec):
     # {0,1} operands are exact in BF16 and E4M3 and the Gram sums are integer counts; what
