@@ -134,8 +134,13 @@ void destroy_batch_cache(pid_handle h) {
 
 static int64_t align_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
 
-// One persistent launch per key. TMA-fed and directly loaded ensembles (rows not 16-byte
-// aligned) launch apart, so that one unaligned ensemble does not slow down its whole class.
+// How a streaming plan stages its rows: 1 = TMA boxes of aligned rows, 2 = TMA boxes through
+// residue-class maps (rows not 16-byte aligned), 0 = cp.async spans. Each mode launches
+// apart.
+static int stage_mode(const EnsPlan& p) { return p.use_tma ? 1 : (p.cls ? 2 : 0); }
+
+// One persistent launch per key. Ensembles staged in different ways (stage_mode) launch
+// apart, so that one unaligned ensemble does not slow down its whole class.
 struct ClassKey {
   int vec, G, coef, iso, tma, mpw;
   bool operator<(const ClassKey& o) const {
@@ -154,6 +159,7 @@ struct Launch {
   StreamCfg cfg;
   bool coef = false;
   bool tma = true;
+  bool cls = true;         // STREAM: every row staged through residue-class maps
   int32_t stage_floats = 0;
   int32_t total_units = 0;
   int32_t max_n = 0;
@@ -278,7 +284,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
           continue;
         const EnsPlan &a = pl[e], &b = pl[f];
         if (a.cfg.vec == b.cfg.vec && a.cfg.G == b.cfg.G && a.cfg.mpw == b.cfg.mpw &&
-            a.cfg.sub == b.cfg.sub && a.use_tma == b.use_tma &&
+            a.cfg.sub == b.cfg.sub && a.use_tma == b.use_tma && a.cls == b.cls &&
             a.desc.n_chunks == b.desc.n_chunks && a.desc.chunk_cells == b.desc.chunk_cells &&
             a.desc.iso_mode == b.desc.iso_mode && a.desc.iso_mu == b.desc.iso_mu &&
             a.desc.iso_inv == b.desc.iso_inv && a.desc.iso_t == b.desc.iso_t)
@@ -317,15 +323,15 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
                 iso_kind(gp[e].desc.iso_mode)}]
           .push_back(e);
       if (own_pass[e])
-        pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, iso_kind(pl[e].desc.iso_mode), pl[e].use_tma ? 1 : 0,
+        pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, iso_kind(pl[e].desc.iso_mode), stage_mode(pl[e]),
                pl[e].cfg.mpw}].push_back(e);
     } else {
       const int ik = iso_kind(pl[e].desc.iso_mode);
       if (mshare[e] < 0)
-        pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, pl[e].use_tma ? 1 : 0, pl[e].cfg.mpw}].push_back(e);
+        pass1[{pl[e].cfg.vec, pl[e].cfg.G, 0, ik, stage_mode(pl[e]), pl[e].cfg.mpw}].push_back(e);
       if (is_lin[e]) {
         // stored soft masks are 16-byte aligned rows, read through TMA in pass 2
-        const int tma2 = stored[e] ? 1 : (pl[e].use_tma ? 1 : 0);
+        const int tma2 = stored[e] ? 1 : stage_mode(pl[e]);
         pass2[{pl[e].cfg.vec, pl[e].cfg.G, 1, stored[e] ? 0 : ik, tma2, pl[e].cfg.mpw}].push_back(e);
       }
     }
@@ -448,6 +454,7 @@ static pid_status plan_batch(pid_handle h, const pid_ensemble* ens, int count, c
       units += d.n_chunks;
       L.stage_floats = std::max(L.stage_floats, p.stage_floats);
       L.tma = L.tma && p.use_tma;
+      L.cls = L.cls && p.cls;
       L.bytes += 4.0 * d.N * d.M + (d.w ? 4.0 * d.M : 0.0);
       L.max_n = std::max(L.max_n, d.N);
       L.cells += static_cast<int64_t>(d.N) * d.M;
@@ -592,7 +599,7 @@ static pid_status enqueue(pid_handle h, const BatchPlan& bp, char* base, const v
       sp.total_work = L.cells;
       sp.G = L.cfg.G;
       sp.sub = L.cfg.sub;
-      sp.use_tma = L.tma ? 1 : 0;
+      sp.use_tma = L.tma ? 1 : (L.cls ? 2 : 0);
       sp.err = h->err_word;
       sp.stage_floats = L.stage_floats;
       sp.maxu = L.maxu ? 1 : 0;

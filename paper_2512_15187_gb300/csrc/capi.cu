@@ -357,6 +357,7 @@ pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
   const bool tma_ok = (in.ld % 4 == 0) && (a % 16 == 0) &&
                       (in.w == nullptr || reinterpret_cast<uintptr_t>(in.w) % 16 == 0);
   pl->use_tma = false;
+  pl->cls = false;
   if (tma_ok && get_encode_fn()) {
     bool ok = encode_2d(&d.tmap, in.data, static_cast<uint64_t>(in.M), static_cast<uint64_t>(in.N),
                         static_cast<uint64_t>(in.ld) * 4, static_cast<uint32_t>(TS),
@@ -364,9 +365,46 @@ pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
     if (ok && in.w) ok = encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), static_cast<uint32_t>(TS));
     pl->use_tma = ok;
   }
-  // rows of TS cells (TMA), or of TS + 4: the 16-byte-aligned spans the cp.async path copies
+  if (!pl->use_tma && get_encode_fn()) {
+    // Rows that are not 16-byte aligned: members of one residue class (i mod n_cls) share
+    // their offset from the 16-byte boundary and lie n_cls ld floats apart, so each class is
+    // a 2D tensor of its own (base rounded down, cells shifted by the offset) and TMA boxes
+    // of TS + 4 cells stage each row's aligned span. A warp's members must share a class
+    // (G a multiple of n_cls) and the cell measures be aligned for their 1D map; otherwise
+    // the rows are staged by cp.async.
+    const int ncls = in.ld % 2 != 0 ? 4 : (in.ld % 4 != 0 ? 2 : 1);
+    const bool w_ok = in.w == nullptr || reinterpret_cast<uintptr_t>(in.w) % 16 == 0;
+    if (w_ok && cfg.G % ncls == 0 && in.N >= ncls) {
+      const int64_t crows = (in.N + ncls - 1) / ncls;   // rows of the largest class
+      const int32_t nb = static_cast<int32_t>((crows + 255) / 256);
+      // boxes of a multiple of 8 rows: every box lands on a 128-byte boundary of the stage
+      const int32_t br = static_cast<int32_t>(round_up((crows + nb - 1) / nb, 8));
+      bool ok = br <= 256;
+      for (int c = 0; c < ncls && ok; ++c) {
+        const uintptr_t row_c = a + static_cast<uintptr_t>(c) * static_cast<uintptr_t>(in.ld) * 4;
+        const uintptr_t base_c = row_c & ~static_cast<uintptr_t>(15);
+        const uint64_t r_c = (row_c - base_c) / 4;
+        const uint64_t rows_c = static_cast<uint64_t>((in.N - c + ncls - 1) / ncls);
+        CUtensorMap* m = c == 0 ? &d.tmap : &d.tmap_cls[c - 1];
+        ok = encode_2d(m, reinterpret_cast<const void*>(base_c), static_cast<uint64_t>(in.M) + r_c,
+                       rows_c, static_cast<uint64_t>(ncls) * in.ld * 4,
+                       static_cast<uint32_t>(TS + 4), static_cast<uint32_t>(br));
+      }
+      if (ok && in.w) ok = encode_1d(&d.tmap_w, in.w, static_cast<uint64_t>(in.M), static_cast<uint32_t>(TS));
+      if (ok) {
+        pl->cls = true;
+        d.n_cls = ncls;
+        d.n_boxes = nb;
+        d.box_rows = br;
+      }
+    }
+  }
+  // rows of TS cells (TMA), or of TS + 4: the 16-byte-aligned spans of unaligned rows; with
+  // class maps, ncls class slots of n_boxes x box_rows rows each
   const int64_t row_floats = pl->use_tma ? TS : TS + 4;
-  pl->stage_floats = static_cast<int32_t>(round_up(int64_t(d.n_boxes) * d.box_rows * row_floats + TS, 32));
+  const int64_t stage_rows = pl->cls ? int64_t(d.n_cls) * d.n_boxes * d.box_rows
+                                     : int64_t(d.n_boxes) * d.box_rows;
+  pl->stage_floats = static_cast<int32_t>(round_up(stage_rows * row_floats + TS, 32));
   pl->part_bytes = round_up(static_cast<int64_t>(d.n_chunks) * 2 * in.N * 8, 256);
   pl->sums_bytes = round_up((4 * in.N + in.N * in.N) * 8, 256);
   pl->coef_bytes = round_up(in.N * 4, 256);
@@ -530,7 +568,7 @@ static pid_status launch_stream_one(pid_handle h, EnsPlan& pl, const float* coef
   sp.total_work = static_cast<int64_t>(pl.desc.N) * pl.desc.M;
   sp.G = pl.cfg.G;
   sp.sub = pl.cfg.sub;
-  sp.use_tma = pl.use_tma ? 1 : 0;
+  sp.use_tma = pl.use_tma ? 1 : (pl.cls ? 2 : 0);
   sp.err = h->err_word;
   sp.stage_floats = pl.stage_floats;
   if (coef) sp.one.umax = nullptr;

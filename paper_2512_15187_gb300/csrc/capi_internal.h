@@ -110,7 +110,8 @@ struct EnsOutputs {
 struct EnsPlan {
   pidk::EnsDesc desc;
   StreamCfg cfg;
-  bool use_tma;
+  bool use_tma;            // rows 16-byte aligned: TMA boxes of the rows
+  bool cls;                // rows not aligned, staged by TMA through residue-class maps
   int32_t stage_floats;
   size_t part_bytes, sums_bytes, coef_bytes;
 };

@@ -37,7 +37,16 @@ constexpr int kStreamProducerBytes = 96;   // shared-memory TMA cursor per group
 // One ensemble as seen by the streaming kernel.
 struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   CUtensorMap tmap;     // data [N][ld] float32; box {T cells, box_rows members}
+                        // (n_cls > 0: residue class 0, see tmap_cls)
   CUtensorMap tmap_w;   // weights [M] float32; box {T}
+  // Rows that are not 16-byte aligned, staged by TMA (n_cls > 0): members c, c + n_cls,
+  // c + 2 n_cls, ... start at the same offset r_c = (data + c ld) mod 16 bytes and lie
+  // n_cls ld floats apart (a multiple of 16 bytes; n_cls = 4 for odd ld, 2 for ld = 2 mod 4,
+  // 1 for a base alone off the boundary). Class c's map has its base rounded down to
+  // 16 bytes, cells x' = x + r_c / 4 (extent M + r_c / 4) and its members as rows; a box of
+  // T + 4 cells at x' = x0 holds the aligned span around cells [x0, x0 + T) of each row.
+  // tmap is class 0's map, tmap_cls[c - 1] class c's.
+  CUtensorMap tmap_cls[3];
   const float* data;    // [N][ld]
   const float* w;       // [M] or nullptr (unit cell measure)
   const float* coef;    // [N] column-sum coefficients c_j; nullptr = 1/N for every member
@@ -52,7 +61,8 @@ struct EnsDesc {  // 64-byte aligned through its CUtensorMap members
   int32_t iso_mode;     // IsoMode
   float iso_mu, iso_inv, iso_t;
   int32_t validate;
-  int32_t pad0;
+  int32_t n_cls;        // 0: TMA rows (tmap) or cp.async spans; 1, 2, 4: class maps (above),
+                        // each class taking n_boxes boxes of box_rows rows in a stage
   float* gpart;         // Gram launches: [n_chunks][N][N] float32 partial Gram (G_ij at j*N + i)
   const float* op_scale;  // Gram E4M3: [2N] per-member scales s_i, then 1/s_i (nullptr = 256)
   int64_t work_begin;   // member-cells of the launch's earlier ensembles (0 for the first)

@@ -107,7 +107,7 @@ extern "C" pid_status pid_mean_noalloc(const float* U, int64_t N, int64_t M, int
   sp.total_work = static_cast<int64_t>(pl.desc.N) * pl.desc.M;
   sp.G = pl.cfg.G;
   sp.sub = pl.cfg.sub;
-  sp.use_tma = pl.use_tma ? 1 : 0;
+  sp.use_tma = pl.use_tma ? 1 : (pl.cls ? 2 : 0);
   sp.err = err_word;
   sp.stage_floats = pl.stage_floats;
   int ring_depth;

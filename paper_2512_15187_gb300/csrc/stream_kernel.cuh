@@ -188,6 +188,7 @@ struct StreamProducer {
   int ist, in_st;      // stage within the unit, stages of the unit
   int icell0, slot;    // first cell of the unit, ring slot of the next stage
   int e_begin, e_end, chunk, M, boxes, rows, has_w;
+  int ncls;            // residue classes of unaligned rows staged by TMA (0: none)
 };
 static_assert(sizeof(StreamProducer) <= kStreamProducerBytes, "producer cursor size");
 
@@ -269,6 +270,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   // Row stride of a stage: TMA stores rows back to back; the cp.async path stores each
   // row's enclosing 16-byte-aligned span (4 floats more), the row's first cell `roff` floats in.
   constexpr int RS = TMA ? TS : TS + 4;
+  // Unaligned rows staged by TMA through the residue-class maps (see EnsDesc::tmap_cls)
+  // instead of the threads' cp.async copies; the whole launch takes one of the two.
+  const bool CLS = !TMA && p.use_tma == 2;
 
   float* ring = reinterpret_cast<float*>(smem);
   float* red = ring + static_cast<size_t>(NG) * depth * SF;
@@ -286,7 +290,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   // by every thread's 4-byte cp.async copies (see cpa_issue), each thread arriving once per
   // stage when its copies have landed.
   if (leader) {
-    for (int s = 0; s < depth; ++s) mbar_init(&my_bars[s], TMA ? 1u : static_cast<uint32_t>(G * 32));
+    for (int s = 0; s < depth; ++s)
+      mbar_init(&my_bars[s], (TMA || CLS) ? 1u : static_cast<uint32_t>(G * 32));
     fence_mbar_init();
   }
   // A warp that gives up on a wait sets the flag of the register tile whose group barrier
@@ -317,6 +322,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       P.boxes = pd->n_boxes;
       P.rows = pd->box_rows;
       P.has_w = pd->w != nullptr;
+      P.ncls = pd->n_cls;
     }
     P.icell0 = (u - P.e_begin) * P.chunk;
     P.in_st = (min(P.chunk, P.M - P.icell0) + TS - 1) / TS;
@@ -341,6 +347,33 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       if (++P.iu < P.u_end) set_unit(P.iu);
     }
   };
+  // Unaligned rows through the class maps: class c's boxes fill the stage rows from
+  // c n_boxes box_rows on, each row the 16-byte-aligned span of TS + 4 cells around the
+  // stage's cells (its first cell (data + i ld) mod 16 bytes in); cells past M read as 0.
+  auto issue_next_cls = [&]() {
+    if (P.iu >= P.u_end) return;
+    const int slot = P.slot;
+    P.slot = slot + 1 == depth ? 0 : slot + 1;
+    float* dst = my_ring + static_cast<size_t>(slot) * SF;
+    const int boxes = P.boxes, rows = P.rows, nc = P.ncls;
+    const bool has_w_p = P.has_w != 0;
+    const EnsDesc* pd = P.pd;
+    const uint32_t bytes = static_cast<uint32_t>(nc * boxes * rows * RS + (has_w_p ? TS : 0)) * 4u;
+    mbar_arrive_expect_tx(&my_bars[slot], bytes);
+    const int x0 = P.icell0 + P.ist * TS;
+    for (int c = 0; c < nc; ++c) {
+      const CUtensorMap* m = c == 0 ? &pd->tmap : &pd->tmap_cls[c - 1];
+      for (int b = 0; b < boxes; ++b)
+        tma_load_2d(dst + static_cast<size_t>(c * boxes + b) * rows * RS, m, &my_bars[slot], x0,
+                    b * rows);
+    }
+    if (has_w_p) tma_load_1d(dst + SF - TS, &pd->tmap_w, &my_bars[slot], x0);
+    ++P.n_issued;
+    if (++P.ist == P.in_st) {
+      P.ist = 0;
+      if (++P.iu < P.u_end) set_unit(P.iu);
+    }
+  };
   if (leader) {
     P.pd = nullptr;
     P.n_issued = 0;
@@ -355,6 +388,9 @@ stream_kernel(const __grid_constant__ StreamParams p) {
     if (TMA) {
       if (P.iu < P.u_end) set_unit(P.iu);
       for (int s = 0; s < depth; ++s) issue_next();
+    } else if (CLS) {
+      if (P.iu < P.u_end) set_unit(P.iu);
+      for (int s = 0; s < depth; ++s) issue_next_cls();
     }
   }
 
@@ -374,9 +410,20 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   float* u_out = nullptr;   // pass 1 of a field: soft masks stored for pass 2
   float iso_mu = 0.f, iso_inv = 0.f, iso_t = 0.f, dir = 1.f, pad = 0.f, my_cf = 0.f;
   int iso_md = 0;
+  // Stage row of this warp's k-th member (unaligned rows): srow0 + k sstep. The cp.async
+  // spans keep member order (row q + k G); with class maps the member q + k G sits in the
+  // slot of class q mod n_cls, at row (q + k G) / n_cls (G is a multiple of n_cls).
+  int srow0 = q, sstep = G;
   for (int u = u_begin; u < u_end && !aborted; ++u) {
     if (u >= e_end) {
       dp = &stream_desc(p, stream_find_ens(p, u));
+      if constexpr (!TMA) {
+        if (CLS) {
+          const int nc = dp->n_cls;
+          srow0 = (q & (nc - 1)) * dp->n_boxes * dp->box_rows + q / nc;
+          sstep = G / nc;
+        }
+      }
       N = dp->N;
       M = dp->M;
       e_begin = dp->unit_begin;
@@ -477,10 +524,12 @@ stream_kernel(const __grid_constant__ StreamParams p) {
       cp_async_arrive(&my_bars[slot_i]);
     };
     if constexpr (!TMA) {
-      int sl = c_slot;
-      for (int st_i = 0; st_i < depth && st_i < n_st; ++st_i) {
-        cpa_issue(st_i, sl);
-        if (++sl == depth) sl = 0;
+      if (!CLS) {
+        int sl = c_slot;
+        for (int st_i = 0; st_i < depth && st_i < n_st; ++st_i) {
+          cpa_issue(st_i, sl);
+          if (++sl == depth) sl = 0;
+        }
       }
     }
 
@@ -506,7 +555,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
               lds_vec<VEC>(x[k], sb + static_cast<size_t>(i) * TS + j * T + lane * VEC);
             } else {
               // the row's cells start `ro` floats into its span (the same for the warp)
-              lds_shifted<VEC>(x[k], sb + static_cast<size_t>(i) * RS + j * T + lane * VEC,
+              lds_shifted<VEC>(x[k], sb + static_cast<size_t>(srow0 + k * sstep) * RS + j * T + lane * VEC,
                                (boff + i * ld3) & 3);
             }
           } else {
@@ -651,6 +700,8 @@ stream_kernel(const __grid_constant__ StreamParams p) {
         if (flags[2 * grp + (k_sub & 1)]) { aborted = true; break; }
         if constexpr (TMA) {
           if (leader && j == SUB - 1) issue_next();  // every warp has read this slot: refill it
+        } else if (CLS) {
+          if (leader && j == SUB - 1) issue_next_cls();  // every warp has read this slot
         } else {
           if (j == SUB - 1 && st + depth < n_st) cpa_issue(st + depth, slot);
         }
@@ -767,7 +818,7 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   if (aborted && lane == 0 && q == 0) atomicOr(p.err, ERR_TIMEOUT);
   // On an early exit, let this group's copies in flight land before the CTA retires.
   if constexpr (!TMA) cp_async_wait_all();   // this thread's copies, before the CTA retires
-  if (TMA && leader) {
+  if ((TMA || CLS) && leader) {
     while (k_cons < P.n_issued) {
       const int slot = static_cast<int>(k_cons % depth);
       const uint32_t par = static_cast<uint32_t>((k_cons / depth) & 1);
@@ -794,7 +845,7 @@ template <int VEC, int MPW, int G>
 struct StreamClass {
   static cudaError_t launch(const StreamParams& p, int iso, bool coef, int grid, size_t smem,
                             cudaStream_t s) {
-    const bool tma = p.use_tma != 0;
+    const bool tma = p.use_tma == 1;   // 2: unaligned rows through class maps (TMA = false)
     if (p.maxu && iso == ISOK_NONE && !coef)   // the first pass also reduces the maxima
       return tma ? launch_stream_inst<VEC, MPW, G, ISOK_NONE, false, true, true>(p, grid, smem, s)
                  : launch_stream_inst<VEC, MPW, G, ISOK_NONE, false, false, true>(p, grid, smem, s);

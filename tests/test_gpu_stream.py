@@ -107,6 +107,43 @@ def test_unaligned_spans_every_class(H, N, boff, pad):
     H.sync()
 
 
+@pytest.mark.parametrize("N", [3, 4, 13, 37, 200, 300, 500])
+@pytest.mark.parametrize("boff,pad", [(0, 0), (0, 1), (1, 3), (2, 2), (3, 1)])
+def test_unaligned_rows_match_aligned_rows_bitwise(H, N, boff, pad):
+    """Rows that are not 16-byte aligned are staged by TMA through residue-class tensor maps
+    (odd ld: four classes of members i mod 4; ld = 2 mod 4: two; a base alone off the
+    16-byte boundary: one), or by cp.async spans where a class map does not apply (fewer
+    members than classes, a warp whose members straddle classes, cell measures off the
+    boundary). Either way each row's cells reach the same arithmetic: PID-mean and the
+    exact full PID equal, bit for bit, those of an aligned copy of the ensemble."""
+    import torch
+    M = 1001
+    ld = M + pad                       # 1001, 1002, 1004, 1003, 1002
+    U = synth.random_soft(N, M, seed=N * 7 + pad, binary_frac=0.2)
+    w = np.random.default_rng(N + pad).uniform(0.1, 10, M).astype(np.float32)
+    buf = torch.zeros(boff + N * ld, dtype=torch.float32, device="cuda")
+    view = buf[boff:].view(N, ld)[:, :M]
+    view.copy_(_dev(U))
+    ref_buf = torch.zeros((N, (M + 3) // 4 * 4), dtype=torch.float32, device="cuda")
+    ref_view = ref_buf[:, :M]
+    ref_view.copy_(_dev(U))
+    wd = _dev(w)
+    wbuf = torch.zeros(M + 1, dtype=torch.float32, device="cuda")
+    w_off = wbuf[1:]                   # cell measures 4 bytes past the boundary
+    w_off.copy_(wd)
+    for got_w, what in ((wd, "measures aligned"), (w_off, "measures unaligned"), (None, "unit measures")):
+        ref_w = None if got_w is None else wd
+        a = H.mean(view, got_w)
+        b = H.mean(ref_view, ref_w)
+        c = H.full(view, got_w, mode="linear")
+        d = H.full(ref_view, ref_w, mode="linear")
+        H.sync()
+        for x, y, mode in ((a, b, "mean"), (c, d, "linear")):
+            for k in ("in_in", "in_out", "depth", "rank"):
+                assert torch.equal(x[k], y[k]), (N, boff, pad, what, mode, k)
+    _check(a, O.pid_mean(U), what=f"mean N={N} boff={boff} ld={ld}")
+
+
 def test_zero_mass_and_binary_members(H):
     N, M = 6, 900
     U = synth.random_soft(N, M, seed=2)
