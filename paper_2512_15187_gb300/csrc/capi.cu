@@ -371,10 +371,12 @@ pid_status plan_stream(pid_handle h, const EnsInput& in, EnsPlan* pl) {
     // a 2D tensor of its own (base rounded down, cells shifted by the offset) and TMA boxes
     // of TS + 4 cells stage each row's aligned span. A warp's members must share a class
     // (G a multiple of n_cls) and the cell measures be aligned for their 1D map; otherwise
-    // the rows are staged by cp.async.
+    // the rows are staged by cp.async, as they are in the one-cell-per-lane classes (N > 256),
+    // where a span of TS + 4 = 36 cells per row and stage costs more L2 traffic than the
+    // copies it saves.
     const int ncls = in.ld % 2 != 0 ? 4 : (in.ld % 4 != 0 ? 2 : 1);
     const bool w_ok = in.w == nullptr || reinterpret_cast<uintptr_t>(in.w) % 16 == 0;
-    if (w_ok && cfg.G % ncls == 0 && in.N >= ncls) {
+    if (cfg.vec > 1 && w_ok && cfg.G % ncls == 0 && in.N >= ncls) {
       const int64_t crows = (in.N + ncls - 1) / ncls;   // rows of the largest class
       const int32_t nb = static_cast<int32_t>((crows + 255) / 256);
       // boxes of a multiple of 8 rows: every box lands on a 128-byte boundary of the stage

@@ -271,8 +271,10 @@ stream_kernel(const __grid_constant__ StreamParams p) {
   // row's enclosing 16-byte-aligned span (4 floats more), the row's first cell `roff` floats in.
   constexpr int RS = TMA ? TS : TS + 4;
   // Unaligned rows staged by TMA through the residue-class maps (see EnsDesc::tmap_cls)
-  // instead of the threads' cp.async copies; the whole launch takes one of the two.
-  const bool CLS = !TMA && p.use_tma == 2;
+  // instead of the threads' cp.async copies; the whole launch takes one of the two. The
+  // one-cell-per-lane classes keep the cp.async spans (their spans of TS + 4 = 36 cells
+  // cost more L2 traffic than the copies save), and compile without the class code.
+  const bool CLS = !TMA && VEC > 1 && p.use_tma == 2;
 
   float* ring = reinterpret_cast<float*>(smem);
   float* red = ring + static_cast<size_t>(NG) * depth * SF;
