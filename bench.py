@@ -287,6 +287,18 @@ def kernel_table(prof, peaks, sustained):
     return rows
 
 
+def step_hbm_record(prof, steps, ms, peaks):
+    """The whole step against the HBM roofline: the algorithmic bytes that all of the step's
+    kernels stream (each launch's own count: a pass over an ensemble reads it once, a
+    PID-mean item that shares an exact item's first pass adds none) over the step's time."""
+    gb = sum(v["bytes"] for v in prof.values() if v["launches"]) / steps / 1e9
+    achieved = gb / (ms / steps * 1e-3)
+    return {"algorithmic_gb_per_step": gb, "achieved_gbs": achieved, "peak_gbs": peaks["hbm_gbs"],
+            "frac": achieved / peaks["hbm_gbs"],
+            "note": "bytes every kernel of the step streams, summed, over the CUDA-event step "
+                    "time: the step's average HBM rate (its kernels overlap or run in turn)"}
+
+
 def roofline_record(kind, st, peaks, sustained, traffic):
     """The contract's roofline object for one kernel kind: the roofline that binds is the one
     with the longer ideal time (bytes / HBM peak against useful flops / tensor peak)."""
@@ -1009,6 +1021,7 @@ def main():
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
             "kernels": kt,
+            "step_hbm": step_hbm_record(prof, args.steps, ms, peaks),
             "e2e": {"value": world * e2e_mc / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_ms,

@@ -89,3 +89,13 @@ def test_committed_summaries_describe_the_committed_sources():
             stamps[name] = line[0].split(":")[1].strip() if line else None
     assert stamps, "no ncu summaries"
     assert all(v == sha for v in stamps.values()), stamps
+
+
+def test_step_hbm_rate_sums_every_launch_over_the_step_time():
+    prof = {"stream": {"launches": 10, "bytes": 20e9, "total_ms": 5.0, "flops": 0.0},
+            "gram": {"launches": 0, "bytes": 0.0, "total_ms": 0.0, "flops": 0.0},
+            "gram_split": {"launches": 2, "bytes": 400e9, "total_ms": 80.0, "flops": 1e12}}
+    r = bench.step_hbm_record(prof, 2, 200.0, PEAKS)      # 2 steps in 200 ms
+    assert r["algorithmic_gb_per_step"] == pytest.approx(210.0)
+    assert r["achieved_gbs"] == pytest.approx(2100.0)
+    assert r["frac"] == pytest.approx(2100.0 / 6000.0)
