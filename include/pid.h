@@ -339,7 +339,10 @@ typedef struct pid_ensemble {
  * A_i of Eq. 16) instead of forming them in its own pass, so its IN_in is bitwise the
  * sibling's and its outputs differ from a single call only by the FP32 rounding of those
  * sums (below 1e-6). E4M3 items always take such sums from a streaming pass (their own
- * or an identical sibling's), which also yields their member scales.
+ * or an identical sibling's), which also yields their member scales. A PID-mean item over
+ * the same data, cell measures and isovalue map as an exact-full-PID item of the batch
+ * reads that item's first-pass partials instead of streaming the data again; those are
+ * bitwise the partials its own pass would write, so this adds no exception.
  * Gram-mode ensembles of 257 to 512 members run the row-block-tiled Gram after their
  * class's streaming launch, one operand-staging and one tile launch each; they share one
  * operand buffer in the workspace, sized for the largest of them.
