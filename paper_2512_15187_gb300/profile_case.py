@@ -7,6 +7,8 @@
     python -m paper_2512_15187_gb300.profile_case gram --precision bf16 --ensembles 4
     python -m paper_2512_15187_gb300.profile_case plume --side 128   # one 3D plume step:
         # PID-mean, E4M3 Gram and split-BF16 Gram of 200 members on side^3 cells, one batch
+    python -m paper_2512_15187_gb300.profile_case bands --members 64 --cells 4194304
+        # contour boxplot bands of 64 fields on 2048^2 cells
 
 Each case builds its inputs on the device (seeded), makes one call (planning, tuning and
 graph capture), then `--repeat` timed calls, and prints the best call time (CUDA events,
@@ -21,7 +23,8 @@ import argparse
 
 def main(argv=None) -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["fields", "fields-full", "mean", "linear", "gram", "plume"])
+    ap.add_argument("case", choices=["fields", "fields-full", "mean", "linear", "gram", "plume",
+                                     "bands"])
     ap.add_argument("--side", type=int, default=128, help="plume: cells per axis")
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--cells", type=int, default=1 << 20)
@@ -53,6 +56,9 @@ def main(argv=None) -> None:
                  dict(data=U, mode="full", precision="split_bf16")]
         _run(h, items, a, f"plume N={N} M={M} (mean, fp8, split_bf16)")
         return
+    if a.case == "bands":
+        _run_bands(h, N, M, a)
+        return
     X = torch.empty((E, N, M), device="cuda")
     side = int(round(M ** 0.5))
     for e in range(E):
@@ -68,6 +74,38 @@ def main(argv=None) -> None:
     items = [dict(data=X[e], iso=(0.5, 0.05, 0) if is_field else None, mode=mode, precision=prec)
              for e in range(E)]
     _run(h, items, a, f"{a.case} {mode} {prec} N={N} M={M} E={E}")
+
+
+def _run_bands(h, N, M, a) -> None:
+    """Contour boxplot bands of one ensemble of N fields on M = side^2 cells (Sec. 6), from
+    the ranks of its exact full PID: one bands launch per call."""
+    import torch
+    from . import synth
+    side = int(round(M ** 0.5))
+    F = torch.empty((N, side * side), device="cuda")
+    synth.rbf_fields_2d_torch(N, side, side, 32, seed=7, device="cuda", out=F)
+    iso = (0.5, 0.05, 0)
+    rank = h.from_fields(F, *iso[:2], mode="linear")["rank"]
+    out = h.contour_bands(F, rank, 0.5, 0.5, iso=iso)
+    h.sync()
+    h.profile(True)
+    ms = []
+    for _ in range(a.repeat):
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        h.contour_bands(F, rank, 0.5, 0.5, iso=iso, out=out)
+        t1.record()
+        t1.synchronize()
+        ms.append(t0.elapsed_time(t1))
+    h.sync()
+    st = h.profile_read()["bands"]
+    h.profile(False)
+    per = st["total_ms"] / st["launches"]
+    print("ok bands", f"N={N} M={side * side}", int(out.sum()), f"call best {min(ms):.3f} ms")
+    print(f"  bands     {st['launches']:4d} launches  {per:8.3f} ms/launch  "
+          f"{st['bytes'] / st['launches'] / per / 1e6:8.1f} GB/s algorithmic")
+    h.close()
 
 
 def _run(h, items, a, label) -> None:
