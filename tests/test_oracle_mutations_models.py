@@ -2,9 +2,10 @@
 
 Each mutant is a deliberately broken version of one oracle routine (a non-strict
 threshold, a floor for a ceiling, a reversed order, swapped flags, a dropped sqrt 2, a
-wrong normalisation, groups or time steps ignored). The oracle module's routine is
-replaced by the mutant and the routine's pin tests run against it; at least one of them
-must fail, so a mistake of that kind in the real oracle could not pass. CPU only.
+wrong normalisation, groups or time steps ignored, blocks of the accumulated forms lost).
+The oracle module's routine is replaced by the mutant and the routine's pin tests run
+against it; at least one of them must fail, so a mistake of that kind in the real oracle
+could not pass. CPU only.
 """
 import math
 
@@ -16,7 +17,8 @@ from tests import test_oracle_pins as P
 
 REAL = {name: getattr(O, name) for name in (
     "contour_bands", "iso_soft_mask", "iso_soft_mask_uniform", "level_soft_mask",
-    "rank_by_depth", "pid_grouped", "spacetime_cells", "pid_mean_weighted")}
+    "rank_by_depth", "pid_grouped", "spacetime_cells", "pid_mean_weighted", "pid_chunked",
+    "pid_mean_chunked")}
 
 
 # --- mutants ------------------------------------------------------------------------------
@@ -99,7 +101,52 @@ def _wmean_by_n(U, member_weights, w=None):
     return a, b, np.minimum(a, b)
 
 
+def _chunked_last_block_only(chunks):
+    last = list(chunks)[-1:]
+    return REAL["pid_chunked"](iter(last))
+
+
+def _chunked_mass_of_first_block(chunks):
+    chunks = list(chunks)
+    a, b, d = REAL["pid_chunked"](iter(chunks))
+    # the pairs' ratios formed with the first block's masses instead of the totals
+    U0, w0 = chunks[0]
+    m0 = np.atleast_2d(U0) @ O.cell_measure(np.atleast_2d(U0).shape[1], w0)
+    m = sum(np.atleast_2d(Ub) @ O.cell_measure(np.atleast_2d(Ub).shape[1], wb) for Ub, wb in chunks)
+    f = np.where(m0 > 0, m / np.where(m0 > 0, m0, 1.0), 0.0)
+    return a * f, b, np.minimum(a * f, b)
+
+
+def _mean_chunked_without_measures(chunks):
+    # every sum over cells taken without the cell measures
+    chunks = list(chunks)
+    a, b, d = REAL["pid_mean_chunked"](iter([(Ub, None) for Ub, _ in chunks]))
+    return a, b, d
+
+
+def _mean_chunked_sum_not_mean(chunks):
+    num, m, mbar = None, None, 0.0
+    for Ub, wb in chunks:
+        Ub = np.atleast_2d(np.asarray(Ub, np.float64))
+        wb = O.cell_measure(Ub.shape[1], wb)
+        ubar = Ub.sum(axis=0)                    # without the 1/N of Eq. 15
+        num = (0 if num is None else num) + Ub @ (wb * ubar)
+        m = (0 if m is None else m) + Ub @ wb
+        mbar += float(wb @ ubar)
+    a = np.where(m > 0, num / np.where(m > 0, m, 1.0), 0.0)
+    b = num / mbar
+    return a, b, np.minimum(a, b)
+
+
 MUTANTS = {
+    "pid_chunked": {
+        "last_block_only": _chunked_last_block_only,
+        "masses_of_the_first_block": _chunked_mass_of_first_block,
+    },
+    "pid_mean_chunked": {
+        "cell_measures_dropped": _mean_chunked_without_measures,
+        "sum_not_mean": _mean_chunked_sum_not_mean,
+    },
     "contour_bands": {
         "non_strict_threshold": lambda U, rank, tau, f=0.5:
             REAL["contour_bands"](U, rank, np.nextafter(tau, -np.inf), f),
@@ -149,6 +196,12 @@ MUTANTS = {
 
 # the pins that hold each routine
 PINS = {
+    "pid_chunked": [(P.test_chunked_forms_match_closed_forms_and_set_counts, ()),
+                    (P.test_chunked_forms_do_not_depend_on_the_blocks, (0,)),
+                    (P.test_chunked_forms_do_not_depend_on_the_blocks, (1,))],
+    "pid_mean_chunked": [(P.test_chunked_forms_match_closed_forms_and_set_counts, ()),
+                         (P.test_chunked_forms_do_not_depend_on_the_blocks, (0,)),
+                         (P.test_chunked_forms_do_not_depend_on_the_blocks, (1,))],
     "contour_bands": [(P.test_bands_hand_example, ()), (P.test_bands_nesting_invariants, (0,)),
                       (P.test_bands_nesting_invariants, (1,)), (P.test_bands_nesting_invariants, (2,)),
                       (P.test_bands_of_nested_disks_are_the_extreme_disks, ())],
